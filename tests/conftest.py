@@ -1,0 +1,13 @@
+"""Shared pytest configuration: the ``gpu`` marker and the repository root on
+``sys.path`` (the package, the oracle and the input generator are imported
+from the source tree, never installed)."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
