@@ -1,0 +1,214 @@
+/*
+ * hd.h -- C ABI of the GB300 HyperOMS hot path: hyperdimensional encoding of
+ * preprocessed MS/MS spectra and the open-modification Hamming search.
+ *
+ * Method: Kang, Xu, Bittremieux, Rosing, "Massively Parallel Open
+ * Modification Spectral Library Searching with Hyperdimensional Computing".
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Hypervector (HV): D bits stored as D/64 little-endian uint64 words, bit d
+ *    in word d/64 at position d%64.  Bit b is the bipolar component 1-2b
+ *    (0 -> +1, 1 -> -1); the element-wise product of bipolar HVs is the XOR
+ *    of their bits.  Rows of an HV array are contiguous (stride D/8 bytes);
+ *    D is a multiple of 128, so every row starts on a 16-byte boundary when
+ *    the array does.
+ *  - Pointers named d_* are DEVICE pointers on the current CUDA device; h_*
+ *    are host pointers (page-locked memory gives asynchronous copies).  The
+ *    caller owns every buffer it passes; the library owns hd_ctx and
+ *    hd_library objects and the scratch it allocates (stream-ordered, freed
+ *    on the same stream).
+ *  - Calls taking a stream are asynchronous on it unless stated otherwise;
+ *    results are valid once the stream has been synchronised.  A NULL stream
+ *    is the legacy default stream.
+ *  - Argument errors are detected on the host before anything is launched
+ *    and return HD_ERR_INVALID_ARG.  Errors found by a kernel (a malformed
+ *    CSR row, a bounded device wait that expired) are recorded in the
+ *    status word of the hd_ctx or hd_library used; hd_ctx_status() /
+ *    hd_library_status() return and clear it after the caller synchronised.
+ *  - hd_last_error_message() gives a text for the last failure on the
+ *    calling thread.
+ *  - Thread safety: distinct objects are independent.  One hd_ctx or
+ *    hd_library may serve concurrent read-only calls (hd_encode,
+ *    hd_search_open*) from several host threads and streams.
+ */
+#ifndef HD_H
+#define HD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HD_API __attribute__((visibility("default")))
+#else
+#define HD_API
+#endif
+
+struct CUstream_st;                       /* == cudaStream_t */
+typedef struct CUstream_st *hd_stream;
+
+typedef enum {
+    HD_OK = 0,
+    HD_ERR_INVALID_ARG = 1,   /* bad argument, or malformed input found on the device */
+    HD_ERR_OOM = 2,           /* device allocation failed; nothing launched */
+    HD_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has details) */
+    HD_ERR_TIMEOUT = 4,       /* a bounded device wait expired; results are invalid */
+    HD_ERR_UNSUPPORTED = 5    /* valid request this build or GPU does not serve */
+} hd_status;
+
+typedef enum { HD_TOL_DA = 0, HD_TOL_PPM = 1 } hd_tol_unit;
+
+/* Item-memory parameters (Section 3.3).
+ *  dim      D, multiple of 128, 128..32768 (paper: 8192, Section 4.2)
+ *  n_levels Q intensity levels 0..Q-1, 2..256 (paper: 16)
+ *  n_bins   f spectrum-vector dimensionality (m/z bins), >= 1
+ *  alpha    total position flips from the first to the last bin, <= D
+ *           (paper: D/2, Section 4.2)
+ *  seed     Philox4x32-10 key of the random base vectors and permutations */
+typedef struct {
+    uint32_t dim;
+    uint32_t n_levels;
+    uint32_t n_bins;
+    uint32_t alpha;
+    uint64_t seed;
+} hd_params;
+
+/* Preprocessing parameters (Section 3.2, Table 1). */
+typedef struct {
+    double mz_min, mz_max;     /* fragment m/z range kept, inclusive (Table 1: 101 / 1500) */
+    double bin_width;          /* > 0 (Table 1: 0.05 or 0.04) */
+    double min_rel_intensity;  /* peaks below this fraction of the top peak are dropped (0.01) */
+    uint32_t n_bins;           /* bins 0..n_bins-1; m/z beyond are clamped */
+    uint32_t max_peaks;        /* most intense peaks kept, 1..1023 (Table 1: 50) */
+    uint32_t n_levels;         /* Q, 2..256 */
+} hd_preprocess_params;
+
+typedef struct hd_ctx hd_ctx;
+typedef struct hd_library hd_library;
+
+typedef enum {
+    HD_FORM_AUTO = 0,   /* fastest exact form for the request */
+    HD_FORM_POPC = 1    /* XOR + population count on the integer pipes */
+} hd_search_form;
+
+HD_API const char *hd_status_string(hd_status s);
+HD_API const char *hd_last_error_message(void);
+/* Library version as major*10000 + minor*100 + patch. */
+HD_API uint32_t hd_version(void);
+
+/* Item memory (Section 3.3.1 position HVs, Section 3.3.2 level HVs).
+ * Builds F_0..F_{f-1} and L_0..L_{Q-1} on the current device.  Position HVs
+ * share one random base F_0; F_i differs from it in the m_i lowest-ranked
+ * positions of one random permutation, m_i = floor(i*alpha/(f-1)), so the
+ * distance between bins grows linearly and the last bin is alpha flips away.
+ * Level HVs do the same from L_0 with n_j = floor(j*(D/2)/(Q-1)) (level j is
+ * j/(Q-1) of the way, Section 3.3.2), so L_{Q-1} is orthogonal to L_0.
+ * Random words: Philox4x32-10 of `seed`, counter (i/4, stream, 0, 0), word
+ * i%4; stream 0 = F_0 bits, 1 = F permutation keys, 2 = L_0 bits, 3 = L
+ * permutation keys; a position's rank is its place in ascending (key, pos).
+ * Synchronous.  Allocates f*D/8 + Q*D/8 bytes of device memory. */
+HD_API hd_status hd_ctx_create(const hd_params *params, hd_ctx **out);
+HD_API void hd_ctx_destroy(hd_ctx *ctx);
+/* Copies the item memory out: d_F [n_bins][D/64], d_L [n_levels][D/64],
+ * d_rank_F / d_rank_L [D] (each may be NULL).  Asynchronous on `stream`. */
+HD_API hd_status hd_ctx_item_memory(const hd_ctx *ctx, uint64_t *d_F, uint64_t *d_L,
+                             uint32_t *d_rank_F, uint32_t *d_rank_L, hd_stream stream);
+/* Returns and clears the device status recorded by kernels of this ctx. */
+HD_API hd_status hd_ctx_status(hd_ctx *ctx);
+
+/* Preprocessing (Section 3.2, Table 1): raw peaks -> CSR spectrum vectors.
+ * Per spectrum: drop peaks with non-finite values or intensity <= 0; drop
+ * m/z outside [mz_min, mz_max]; drop intensity < min_rel * top intensity;
+ * keep the max_peaks most intense (ties: lower m/z, then input position);
+ * bin = clamp(floor((mz - mz_min)/bin_width), 0, n_bins-1); sum intensities
+ * sharing a bin in ascending m/z order; level = min(Q-1, floor(Q*v/v_max)).
+ * All arithmetic in IEEE double.  Rows come out in ascending bin order.
+ *  d_raw_off  [n+1] uint32 offsets into d_raw_mz / d_raw_int (non-decreasing)
+ *  d_out_off  [n+1]; d_out_bins / d_out_levels need n*max_peaks entries.
+ * A spectrum with more than 8192 raw peaks is emptied and flagged
+ * (HD_ERR_INVALID_ARG from hd_ctx_status).  Asynchronous. */
+HD_API hd_status hd_preprocess(hd_ctx *ctx, const hd_preprocess_params *pp, const uint32_t *d_raw_off,
+                        const double *d_raw_mz, const double *d_raw_int, uint32_t n_spectra,
+                        uint32_t *d_out_off, uint32_t *d_out_bins, uint8_t *d_out_levels,
+                        hd_stream stream);
+
+/* Encoding (Section 3.3, Eq. 1): for each CSR row with n peaks (bin i,
+ * level j), out = sign(sum F_i (.) L_j), positive -> +1 (bit 0), zero or
+ * negative -> -1 (bit 1).  Equivalently with c_d the number of bound bits
+ * equal to 1 at d: out_d = [2*c_d >= n]; an empty row gives all ones.
+ *  d_offsets [n+1] non-decreasing; rows hold <= 1023 peaks; d_bins < n_bins,
+ *  d_levels < n_levels (violations flag HD_ERR_INVALID_ARG and the bad peak
+ *  or row is skipped).  d_out_hv [n][D/64], 16-byte aligned.  Asynchronous. */
+HD_API hd_status hd_encode(hd_ctx *ctx, const uint32_t *d_offsets, const uint32_t *d_bins,
+                    const uint8_t *d_levels, uint32_t n_spectra, uint64_t *d_out_hv,
+                    hd_stream stream);
+
+/* Reference library (Section 3.3 reuse of reference HVs; Section 3.4
+ * candidate filter by charge and precursor m/z).  Copies the n_refs HVs,
+ * precursor m/z and charges into library-owned memory sorted by (charge,
+ * m/z, input index), so every query window is one contiguous row range.
+ * m/z must be finite (else HD_ERR_INVALID_ARG).  Synchronous; the caller
+ * may free its buffers afterwards. */
+HD_API hd_status hd_build_library(hd_ctx *ctx, const uint64_t *d_hv, const double *d_prec_mz,
+                           const uint8_t *d_charge, uint32_t n_refs, hd_library **out);
+HD_API void hd_library_free(hd_library *lib);
+HD_API hd_status hd_library_info(const hd_library *lib, uint32_t *n_refs, uint32_t *dim);
+/* Copies the sorted rows out (any pointer may be NULL): d_hv [n][D/64],
+ * d_mz [n], d_charge [n], d_orig [n] (input index of each row). */
+HD_API hd_status hd_library_export(const hd_library *lib, uint64_t *d_hv, double *d_mz,
+                            uint8_t *d_charge, uint32_t *d_orig, hd_stream stream);
+HD_API hd_status hd_library_status(hd_library *lib);
+
+/* Candidate windows (Section 3.4, Table 1): for each query, rows [lo, hi) of
+ * the sorted library whose charge equals the query's and whose precursor
+ * m/z satisfies fabs(mz_r - mz_q) <= tol_q in IEEE double, tol_q = tol
+ * (HD_TOL_DA, an m/z difference) or mz_q * (tol * 1e-6) (HD_TOL_PPM).  A
+ * query with no candidate gets lo == hi.  tol >= 0 and finite. */
+HD_API hd_status hd_query_windows(const hd_library *lib, const double *d_q_mz, const uint8_t *d_q_charge,
+                           uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *d_lo,
+                           uint32_t *d_hi, hd_stream stream);
+
+/* Open-modification search (Section 3.4): for each query, the k candidates
+ * with the smallest Hamming distance popcount(q XOR r), ascending, ties to
+ * the lowest input reference index.  d_out_idx [n_q][k] input indices of
+ * the references, d_out_dist [n_q][k]; fewer than k candidates leave
+ * idx 0xFFFFFFFF, dist 0xFFFF in the remaining slots.  1 <= k <= 16.
+ * Query rows d_q_hv [n_q][D/64], 16-byte aligned.  Scratch is allocated and
+ * freed stream-ordered on `stream`.  Asynchronous. */
+HD_API hd_status hd_search_open(const hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                         const uint8_t *d_q_charge, uint32_t n_q, double tol, hd_tol_unit unit,
+                         uint32_t k, uint32_t *d_out_idx, uint16_t *d_out_dist, hd_stream stream);
+/* Same, with the scoring form chosen by the caller. */
+HD_API hd_status hd_search_open_ex(const hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                            const uint8_t *d_q_charge, uint32_t n_q, double tol, hd_tol_unit unit,
+                            uint32_t k, hd_search_form form, uint32_t *d_out_idx,
+                            uint16_t *d_out_dist, hd_stream stream);
+
+/* End to end from host memory: copies a CSR query batch (h_offsets [n_q+1],
+ * h_bins / h_levels [h_offsets[n_q]]), its precursor m/z and charges to the
+ * device, encodes it with `ctx`, searches `lib`, copies the results to
+ * h_out_idx / h_out_dist [n_q][k] and synchronises `stream`.  Synchronous. */
+HD_API hd_status hd_search_host(hd_ctx *ctx, const hd_library *lib, const uint32_t *h_offsets,
+                         const uint32_t *h_bins, const uint8_t *h_levels, const double *h_q_mz,
+                         const uint8_t *h_q_charge, uint32_t n_q, double tol, hd_tol_unit unit,
+                         uint32_t k, uint32_t *h_out_idx, uint16_t *h_out_dist, hd_stream stream);
+
+/* Measurement hooks (no counterpart in the paper).  While enabled, libhd
+ * records a CUDA event pair around every launch of the given kernel kind, on
+ * the stream the kernel runs on.  hd_profile_collect() waits for the
+ * recorded events, returns their summed milliseconds and the launch count,
+ * and forgets them.  hd_launch_count() is the number of kernels libhd has
+ * launched in this process. */
+typedef enum { HD_KERNEL_ENCODE = 0, HD_KERNEL_SEARCH = 1, HD_KERNEL_KINDS = 2 } hd_kernel_kind;
+HD_API hd_status hd_profile_enable(int on);
+HD_API hd_status hd_profile_collect(hd_kernel_kind kind, double *total_ms, uint32_t *launches);
+HD_API uint64_t hd_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HD_H */

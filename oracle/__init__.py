@@ -47,7 +47,7 @@ def _load():
             lib.orc_item_memory.argtypes = [u32, u32, u32, u32, u64, P, P, P, P]
             lib.orc_preprocess.argtypes = [u32, P, P, P, dbl, dbl, dbl, u32, u32, dbl, u32, P, P, P]
             lib.orc_preprocess.restype = C.c_longlong
-            lib.orc_encode.argtypes = [u32, P, u32, P, u32, u32, P, P, P, P]
+            lib.orc_encode.argtypes = [u32, P, u32, P, u32, u32, P, P, P, P, u32]
             lib.orc_window_count.argtypes = [u32, P, P, u32, P, P, dbl, i32, P]
             lib.orc_library_order.argtypes = [u32, P, P, P]
             lib.orc_search.argtypes = [u32, u32, P, P, P, u32, P, P, P, dbl, i32, u32, P, u32, P, P, u32]
@@ -101,14 +101,17 @@ def preprocess(offsets, mz, intensity, *, mz_min, mz_max, bin_width, n_bins, max
     return o_off, o_bin[:nnz].copy(), o_lvl[:nnz].copy()
 
 
-def encode(dim, F, L, offsets, bins, levels):
+def encode(dim, F, L, offsets, bins, levels, n_threads=None):
     """Binary HVs [n, D/64] u64 of CSR spectrum vectors (Eq. 1 + sign)."""
     off = _c(offsets, np.uint32)
     n = off.size - 1
     out = np.zeros((n, dim // 64), np.uint64)
     F, L = _c(F, np.uint64), _c(L, np.uint64)
     b, lv = _c(bins, np.uint32), _c(levels, np.uint8)
-    rc = _load().orc_encode(dim, _p(F), F.shape[0], _p(L), L.shape[0], n, _p(off), _p(b), _p(lv), _p(out))
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    rc = _load().orc_encode(dim, _p(F), F.shape[0], _p(L), L.shape[0], n, _p(off), _p(b), _p(lv), _p(out),
+                            n_threads)
     if rc:
         raise ValueError(f"orc_encode rc={rc}")
     return out

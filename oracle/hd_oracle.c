@@ -237,30 +237,66 @@ long long orc_preprocess(uint32_t n_spec, const uint32_t *raw_off, const double 
  * arithmetic I = sum over peaks (i, j) of F_i (.) L_j, then component d of
  * the output is +1 when I_d > 0 and -1 otherwise.
  * ------------------------------------------------------------------------- */
-int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L, uint32_t n_levels,
-               uint32_t n_spec, const uint32_t *off, const uint32_t *bin, const uint8_t *level,
-               uint64_t *out)
+typedef struct {
+    uint32_t D, n_bins, n_levels, s0, s1;
+    const uint64_t *F, *L;
+    const uint32_t *off, *bin;
+    const uint8_t *level;
+    uint64_t *out;
+    int rc;
+} encode_job;
+
+static void *encode_worker(void *arg)
 {
-    if (D == 0 || D % 64u) return -1;
-    const uint32_t W = D / 64u;
+    encode_job *j = (encode_job *)arg;
+    const uint32_t D = j->D, W = D / 64u;
     int32_t *I = (int32_t *)malloc(sizeof(int32_t) * D);
-    if (!I) return -2;
-    for (uint32_t s = 0; s < n_spec; ++s) {
-        if (off[s + 1] < off[s]) { free(I); return -1; }
+    if (!I) { j->rc = -2; return NULL; }
+    for (uint32_t s = j->s0; s < j->s1; ++s) {
         memset(I, 0, sizeof(int32_t) * D);
-        for (uint32_t p = off[s]; p < off[s + 1]; ++p) {
-            if (bin[p] >= n_bins || level[p] >= n_levels) { free(I); return -1; }
-            const uint64_t *Fi = F + (size_t)bin[p] * W, *Lj = L + (size_t)level[p] * W;
+        for (uint32_t p = j->off[s]; p < j->off[s + 1]; ++p) {
+            if (j->bin[p] >= j->n_bins || j->level[p] >= j->n_levels) { j->rc = -1; free(I); return NULL; }
+            const uint64_t *Fi = j->F + (size_t)j->bin[p] * W, *Lj = j->L + (size_t)j->level[p] * W;
             for (uint32_t d = 0; d < D; ++d) {
                 int f = 1 - 2 * get_bit(Fi, d), l = 1 - 2 * get_bit(Lj, d);
                 I[d] += f * l;
             }
         }
-        uint64_t *o = out + (size_t)s * W;
+        uint64_t *o = j->out + (size_t)s * W;
         for (uint32_t d = 0; d < D; ++d) set_bit(o, d, I[d] > 0 ? 0 : 1);
     }
     free(I);
-    return 0;
+    return NULL;
+}
+
+/* Spectra are split into `n_threads` contiguous ranges, one per thread. */
+int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L, uint32_t n_levels,
+               uint32_t n_spec, const uint32_t *off, const uint32_t *bin, const uint8_t *level,
+               uint64_t *out, uint32_t n_threads)
+{
+    if (D == 0 || D % 64u) return -1;
+    for (uint32_t s = 0; s < n_spec; ++s) if (off[s + 1] < off[s]) return -1;
+    if (n_threads == 0) n_threads = 1;
+    if (n_threads > n_spec) n_threads = n_spec ? n_spec : 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * n_threads);
+    encode_job *jobs = (encode_job *)malloc(sizeof(encode_job) * n_threads);
+    char *started = (char *)calloc(n_threads, 1);
+    if (!th || !jobs || !started) { free(th); free(jobs); free(started); return -2; }
+    for (uint32_t t = 0; t < n_threads; ++t) {
+        encode_job j = { D, n_bins, n_levels, (uint32_t)((uint64_t)n_spec * t / n_threads),
+                         (uint32_t)((uint64_t)n_spec * (t + 1) / n_threads), F, L, off, bin, level, out, 0 };
+        jobs[t] = j;
+    }
+    for (uint32_t t = 1; t < n_threads; ++t) started[t] = pthread_create(&th[t], NULL, encode_worker, &jobs[t]) == 0;
+    for (uint32_t t = 1; t < n_threads; ++t) if (!started[t]) encode_worker(&jobs[t]);
+    encode_worker(&jobs[0]);
+    int rc = 0;
+    for (uint32_t t = 0; t < n_threads; ++t) {
+        if (t > 0 && started[t]) pthread_join(th[t], NULL);
+        if (jobs[t].rc) rc = jobs[t].rc;
+    }
+    free(th); free(jobs); free(started);
+    return rc;
 }
 
 /* ---------------------------------------------------------------------------

@@ -1,0 +1,104 @@
+// encode.cu -- spectrum vectors -> binary hypervectors (Section 3.3, Eq. 1).
+//
+// out_d = [2 c_d >= n], with c_d the number of peaks whose bound bit
+// F_bin XOR L_level is 1 at d (Eq. 1's bipolar sum is n - 2 c_d and the
+// binarisation maps a sum <= 0 to -1, bit 1).
+//
+// One warp per spectrum; each lane owns WPL 64-bit words of a 32*WPL-word
+// slice of the HV and keeps, per word, a bit-sliced counter: plane i holds
+// bit i of the 64 per-bit counts.  Adding a bound word is a ripple-carry add
+// across the planes that can be non-zero so far.  The majority test compares
+// the planes with ceil(n/2) from the top bit down.
+#include "hd_internal.cuh"
+
+namespace {
+
+constexpr int ENC_PLANES = 10;          // counts up to 1023 peaks
+constexpr uint32_t ENC_MAX_PEAKS = (1u << ENC_PLANES) - 1u;
+constexpr int ENC_WARPS = 8;
+
+template <int WPL>
+__global__ void __launch_bounds__(ENC_WARPS * 32)
+k_encode(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__restrict__ L,
+         uint32_t n_levels, uint32_t W, const uint32_t *__restrict__ off,
+         const uint32_t *__restrict__ bins, const uint8_t *__restrict__ levels, uint32_t n_spec,
+         uint64_t *__restrict__ out, uint32_t *status)
+{
+    const uint32_t sp = blockIdx.x * ENC_WARPS + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31;
+    if (sp >= n_spec) return;
+    uint32_t beg = off[sp], end = off[sp + 1];
+    if (end < beg || end - beg > ENC_MAX_PEAKS) {
+        if (lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
+        end = beg;   // encode as an empty row
+    }
+    for (uint32_t w0 = 0; w0 < W; w0 += 32u * WPL) {
+        uint64_t c[WPL][ENC_PLANES];
+#pragma unroll
+        for (int j = 0; j < WPL; ++j)
+#pragma unroll
+            for (int i = 0; i < ENC_PLANES; ++i) c[j][i] = 0;
+        bool any_bad = false;
+        uint32_t added = 0;
+        for (uint32_t p = beg; p < end; ++p) {
+            const uint32_t b = __ldg(bins + p), l = __ldg(levels + p);
+            if (b >= n_bins || l >= n_levels) {
+                any_bad = true;
+                continue;
+            }
+            const uint64_t *fr = F + (size_t)b * W, *lr = L + (size_t)l * W;
+            uint64_t x[WPL];
+#pragma unroll
+            for (int j = 0; j < WPL; ++j) {
+                const uint32_t w = w0 + lane + 32u * j;
+                x[j] = w < W ? (__ldg(fr + w) ^ __ldg(lr + w)) : 0ull;
+            }
+            ++added;
+            const int lim = 32 - __clz(added);   // planes that can be non-zero
+#pragma unroll
+            for (int i = 0; i < ENC_PLANES; ++i) {
+                if (i < lim) {
+#pragma unroll
+                    for (int j = 0; j < WPL; ++j) {
+                        const uint64_t t = c[j][i] & x[j];
+                        c[j][i] ^= x[j];
+                        x[j] = t;
+                    }
+                }
+            }
+        }
+        if (any_bad && lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
+        const uint32_t thresh = (added + 1) >> 1;   // c >= ceil(n/2)  <=>  2c >= n
+#pragma unroll
+        for (int j = 0; j < WPL; ++j) {
+            const uint32_t w = w0 + lane + 32u * j;
+            uint64_t gt = 0, eq = ~0ull;
+#pragma unroll
+            for (int i = ENC_PLANES - 1; i >= 0; --i) {
+                if ((thresh >> i) & 1u) eq &= c[j][i];
+                else gt |= eq & c[j][i];
+            }
+            if (w < W) out[(size_t)sp * W + w] = gt | eq;
+        }
+    }
+}
+
+}  // namespace
+
+void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins,
+                      const uint8_t *levels, uint32_t n, uint64_t *out, cudaStream_t s)
+{
+    const uint32_t W = ctx->W;
+    const unsigned grid = hd_ceil_div(n, ENC_WARPS);
+    const uint32_t *st = ctx->status.dev;
+    hd_prof_scope timed(HD_KERNEL_ENCODE, s);
+    if (W >= 128)
+        hd_count_launches(1), k_encode<4><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
+                                                    W, off, bins, levels, n, out, (uint32_t *)st);
+    else if (W >= 64)
+        hd_count_launches(1), k_encode<2><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
+                                                    W, off, bins, levels, n, out, (uint32_t *)st);
+    else
+        hd_count_launches(1), k_encode<1><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
+                                                    W, off, bins, levels, n, out, (uint32_t *)st);
+}

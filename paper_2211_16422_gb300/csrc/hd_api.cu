@@ -1,0 +1,459 @@
+// hd_api.cu -- the extern "C" boundary of libhd: argument checks, object
+// life cycle and the order of launches.  Every computation runs in the
+// kernels of the other translation units.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "hd_internal.cuh"
+
+static thread_local std::string g_msg;
+
+hd_status hd_fail(hd_status s, const std::string &msg)
+{
+    g_msg = msg;
+    return s;
+}
+
+hd_status hd_cuda_fail(cudaError_t e, const char *what)
+{
+    g_msg = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return HD_ERR_OOM;
+    return HD_ERR_CUDA;
+}
+
+#define HD_CHECK(cond, msg)                                                 \
+    do {                                                                    \
+        if (!(cond)) return hd_fail(HD_ERR_INVALID_ARG, msg);               \
+    } while (0)
+
+namespace {
+
+hd_status status_alloc(hd_status_word &w)
+{
+    HD_CUDA_TRY(cudaHostAlloc((void **)&w.host, sizeof(uint32_t), cudaHostAllocMapped));
+    *w.host = 0;
+    HD_CUDA_TRY(cudaHostGetDevicePointer((void **)&w.dev, w.host, 0));
+    return HD_OK;
+}
+
+void status_free(hd_status_word &w)
+{
+    if (w.host) cudaFreeHost(w.host);
+    w.host = w.dev = nullptr;
+}
+
+hd_status status_take(hd_status_word &w, const char *who)
+{
+    if (!w.host) return HD_OK;
+    const uint32_t v = __atomic_exchange_n(w.host, 0u, __ATOMIC_SEQ_CST);
+    if (v & HD_DEV_TIMEOUT)
+        return hd_fail(HD_ERR_TIMEOUT, std::string(who) + ": a bounded device wait expired");
+    if (v & HD_DEV_BAD_INPUT)
+        return hd_fail(HD_ERR_INVALID_ARG, std::string(who) + ": malformed input found on the device");
+    return HD_OK;
+}
+
+hd_status check_device(int want)
+{
+    int dev = -1;
+    HD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != want) return hd_fail(HD_ERR_INVALID_ARG, "object belongs to another CUDA device");
+    return HD_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool tol_ok(double tol) { return std::isfinite(tol) && tol >= 0.0; }
+
+// --------------------------------------------------------------- library
+__global__ void k_gather_rows(const uint64_t *__restrict__ hv, const double *__restrict__ mz,
+                              const uint8_t *__restrict__ z, const uint32_t *__restrict__ perm,
+                              uint32_t n, uint32_t W, uint64_t *__restrict__ o_hv,
+                              double *__restrict__ o_mz, uint8_t *__restrict__ o_z,
+                              uint32_t *__restrict__ o_orig, uint32_t *status)
+{
+    const uint32_t r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const uint32_t lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const uint32_t src = perm[r];
+    const uint2 *s2 = reinterpret_cast<const uint2 *>(hv + (size_t)src * W);
+    uint2 *d2 = reinterpret_cast<uint2 *>(o_hv + (size_t)r * W);
+    for (uint32_t w = lane; w < W; w += 32) d2[w] = s2[w];
+    if (lane == 0) {
+        const double m = mz[src];
+        if (!isfinite(m)) hd_flag(status, HD_DEV_BAD_INPUT);
+        o_mz[r] = m;
+        o_z[r] = z[src];
+        o_orig[r] = src;
+    }
+}
+
+// cstart[c] = first row whose charge is >= c, c = 0..256.
+__global__ void k_charge_start(const uint8_t *__restrict__ z, uint32_t n, uint32_t *__restrict__ cstart)
+{
+    const uint32_t c = threadIdx.x;
+    if (c > 256) return;
+    uint32_t a = 0, b = n;
+    while (a < b) {
+        const uint32_t m = a + ((b - a) >> 1);
+        if ((uint32_t)z[m] >= c) b = m; else a = m + 1;
+    }
+    cstart[c] = a;
+}
+
+void lib_release(hd_library *lib)
+{
+    if (!lib) return;
+    cudaFree(lib->hv);
+    cudaFree(lib->mz);
+    cudaFree(lib->charge);
+    cudaFree(lib->orig);
+    cudaFree(lib->charge_start);
+    status_free(lib->status);
+    delete lib;
+}
+
+void ctx_release(hd_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaFree(ctx->F);
+    cudaFree(ctx->L);
+    cudaFree(ctx->rank_F);
+    cudaFree(ctx->rank_L);
+    status_free(ctx->status);
+    delete ctx;
+}
+
+struct scoped_stream {
+    cudaStream_t s = nullptr;
+    ~scoped_stream()
+    {
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *hd_status_string(hd_status s)
+{
+    switch (s) {
+    case HD_OK: return "HD_OK";
+    case HD_ERR_INVALID_ARG: return "HD_ERR_INVALID_ARG";
+    case HD_ERR_OOM: return "HD_ERR_OOM";
+    case HD_ERR_CUDA: return "HD_ERR_CUDA";
+    case HD_ERR_TIMEOUT: return "HD_ERR_TIMEOUT";
+    case HD_ERR_UNSUPPORTED: return "HD_ERR_UNSUPPORTED";
+    }
+    return "HD_ERR_UNKNOWN";
+}
+
+const char *hd_last_error_message(void) { return g_msg.c_str(); }
+
+uint32_t hd_version(void) { return 100u; }
+
+hd_status hd_ctx_create(const hd_params *p, hd_ctx **out)
+{
+    HD_CHECK(p && out, "hd_ctx_create: null argument");
+    *out = nullptr;
+    HD_CHECK(p->dim >= 128 && p->dim <= 32768 && p->dim % 128 == 0,
+             "hd_ctx_create: dim must be a multiple of 128 in [128, 32768]");
+    HD_CHECK(p->n_levels >= 2 && p->n_levels <= 256, "hd_ctx_create: n_levels must be in [2, 256]");
+    HD_CHECK(p->n_bins >= 1, "hd_ctx_create: n_bins must be >= 1");
+    HD_CHECK(p->alpha <= p->dim, "hd_ctx_create: alpha must be <= dim");
+    hd_ctx *c = new hd_ctx;
+    c->p = *p;
+    c->W = p->dim / 64;
+    auto fail = [&](hd_status s) {
+        ctx_release(c);
+        return s;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return fail(hd_fail(HD_ERR_CUDA, "hd_ctx_create: no usable CUDA device"));
+    const size_t nF = (size_t)p->n_bins * c->W, nL = (size_t)p->n_levels * c->W;
+    if (cudaMalloc(&c->F, nF * 8) != cudaSuccess || cudaMalloc(&c->L, nL * 8) != cudaSuccess ||
+        cudaMalloc(&c->rank_F, (size_t)p->dim * 4) != cudaSuccess ||
+        cudaMalloc(&c->rank_L, (size_t)p->dim * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(hd_fail(HD_ERR_OOM, "hd_ctx_create: item memory allocation failed"));
+    }
+    hd_status st = status_alloc(c->status);
+    if (st != HD_OK) return fail(st);
+    scoped_stream ss;
+    if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(hd_fail(HD_ERR_CUDA, "hd_ctx_create: stream creation failed"));
+    st = hd_item_memory_build(c, ss.s);
+    if (st != HD_OK) return fail(st);
+    cudaError_t e = cudaStreamSynchronize(ss.s);
+    if (e != cudaSuccess) return fail(hd_cuda_fail(e, "hd_ctx_create"));
+    *out = c;
+    return HD_OK;
+}
+
+void hd_ctx_destroy(hd_ctx *ctx) { ctx_release(ctx); }
+
+hd_status hd_ctx_item_memory(const hd_ctx *ctx, uint64_t *d_F, uint64_t *d_L, uint32_t *d_rank_F,
+                             uint32_t *d_rank_L, hd_stream stream)
+{
+    HD_CHECK(ctx, "hd_ctx_item_memory: null ctx");
+    hd_status st = check_device(ctx->device);
+    if (st != HD_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto D2D = cudaMemcpyDeviceToDevice;
+    if (d_F) HD_CUDA_TRY(cudaMemcpyAsync(d_F, ctx->F, (size_t)ctx->p.n_bins * ctx->W * 8, D2D, s));
+    if (d_L) HD_CUDA_TRY(cudaMemcpyAsync(d_L, ctx->L, (size_t)ctx->p.n_levels * ctx->W * 8, D2D, s));
+    if (d_rank_F) HD_CUDA_TRY(cudaMemcpyAsync(d_rank_F, ctx->rank_F, (size_t)ctx->p.dim * 4, D2D, s));
+    if (d_rank_L) HD_CUDA_TRY(cudaMemcpyAsync(d_rank_L, ctx->rank_L, (size_t)ctx->p.dim * 4, D2D, s));
+    return HD_OK;
+}
+
+hd_status hd_ctx_status(hd_ctx *ctx)
+{
+    HD_CHECK(ctx, "hd_ctx_status: null ctx");
+    return status_take(ctx->status, "hd_ctx");
+}
+
+hd_status hd_preprocess(hd_ctx *ctx, const hd_preprocess_params *pp, const uint32_t *d_raw_off,
+                        const double *d_raw_mz, const double *d_raw_int, uint32_t n_spectra,
+                        uint32_t *d_out_off, uint32_t *d_out_bins, uint8_t *d_out_levels,
+                        hd_stream stream)
+{
+    HD_CHECK(ctx && pp, "hd_preprocess: null argument");
+    HD_CHECK(std::isfinite(pp->mz_min) && std::isfinite(pp->mz_max) && pp->mz_min <= pp->mz_max,
+             "hd_preprocess: mz_min/mz_max must be finite, mz_min <= mz_max");
+    HD_CHECK(std::isfinite(pp->bin_width) && pp->bin_width > 0.0, "hd_preprocess: bin_width must be > 0");
+    HD_CHECK(std::isfinite(pp->min_rel_intensity) && pp->min_rel_intensity >= 0.0,
+             "hd_preprocess: min_rel_intensity must be finite and >= 0");
+    HD_CHECK(pp->n_bins >= 1, "hd_preprocess: n_bins must be >= 1");
+    HD_CHECK(pp->max_peaks >= 1 && pp->max_peaks <= 1023, "hd_preprocess: max_peaks must be in [1, 1023]");
+    HD_CHECK(pp->n_levels >= 2 && pp->n_levels <= 256, "hd_preprocess: n_levels must be in [2, 256]");
+    HD_CHECK(d_out_off, "hd_preprocess: null output offsets");
+    HD_CHECK(n_spectra == 0 || (d_raw_off && d_raw_mz && d_raw_int && d_out_bins && d_out_levels),
+             "hd_preprocess: null buffer");
+    hd_status st = check_device(ctx->device);
+    if (st != HD_OK) return st;
+    return hd_preprocess_launch(*pp, d_raw_off, d_raw_mz, d_raw_int, n_spectra, d_out_off, d_out_bins,
+                                d_out_levels, ctx->status.dev, (cudaStream_t)stream);
+}
+
+hd_status hd_encode(hd_ctx *ctx, const uint32_t *d_offsets, const uint32_t *d_bins,
+                    const uint8_t *d_levels, uint32_t n_spectra, uint64_t *d_out_hv, hd_stream stream)
+{
+    HD_CHECK(ctx, "hd_encode: null ctx");
+    if (n_spectra == 0) return HD_OK;
+    HD_CHECK(d_offsets && d_bins && d_levels && d_out_hv, "hd_encode: null buffer");
+    HD_CHECK(aligned16(d_out_hv), "hd_encode: d_out_hv must be 16-byte aligned");
+    hd_status st = check_device(ctx->device);
+    if (st != HD_OK) return st;
+    hd_encode_launch(ctx, d_offsets, d_bins, d_levels, n_spectra, d_out_hv, (cudaStream_t)stream);
+    HD_CUDA_TRY(cudaGetLastError());
+    return HD_OK;
+}
+
+hd_status hd_build_library(hd_ctx *ctx, const uint64_t *d_hv, const double *d_prec_mz,
+                           const uint8_t *d_charge, uint32_t n_refs, hd_library **out)
+{
+    HD_CHECK(ctx && out, "hd_build_library: null argument");
+    *out = nullptr;
+    HD_CHECK(n_refs == 0 || (d_hv && d_prec_mz && d_charge), "hd_build_library: null buffer");
+    hd_status st = check_device(ctx->device);
+    if (st != HD_OK) return st;
+    hd_library *lib = new hd_library;
+    lib->n = n_refs;
+    lib->dim = ctx->p.dim;
+    lib->W = ctx->W;
+    lib->device = ctx->device;
+    lib->num_sms = ctx->num_sms;
+    auto fail = [&](hd_status s) {
+        lib_release(lib);
+        return s;
+    };
+    const size_t n1 = n_refs ? n_refs : 1;
+    if (cudaMalloc(&lib->hv, n1 * lib->W * 8) != cudaSuccess || cudaMalloc(&lib->mz, n1 * 8) != cudaSuccess ||
+        cudaMalloc(&lib->charge, n1) != cudaSuccess || cudaMalloc(&lib->orig, n1 * 4) != cudaSuccess ||
+        cudaMalloc(&lib->charge_start, 257 * 4) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(hd_fail(HD_ERR_OOM, "hd_build_library: allocation failed"));
+    }
+    st = status_alloc(lib->status);
+    if (st != HD_OK) return fail(st);
+    scoped_stream ss;
+    if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(hd_fail(HD_ERR_CUDA, "hd_build_library: stream creation failed"));
+    if (n_refs > 0) {
+        hd_arena plan;
+        uint32_t *perm = plan.take<uint32_t>(n_refs);
+        hd_sort_charge_mz(d_prec_mz, d_charge, n_refs, nullptr, plan, ss.s);
+        hd_arena ar;
+        if (cudaMallocAsync((void **)&ar.base, plan.used, ss.s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(hd_fail(HD_ERR_OOM, "hd_build_library: scratch allocation failed"));
+        }
+        perm = ar.take<uint32_t>(n_refs);
+        hd_sort_charge_mz(d_prec_mz, d_charge, n_refs, perm, ar, ss.s);
+        hd_count_launches(1), k_gather_rows<<<hd_ceil_div(n_refs, 8), 256, 0, ss.s>>>(d_hv, d_prec_mz, d_charge, perm, n_refs,
+                                                                lib->W, lib->hv, lib->mz, lib->charge,
+                                                                lib->orig, lib->status.dev);
+        cudaFreeAsync(ar.base, ss.s);
+    }
+    hd_count_launches(1), k_charge_start<<<1, 288, 0, ss.s>>>(lib->charge, n_refs, lib->charge_start);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lib->charge_start_h, lib->charge_start, 257 * 4,
+                                              cudaMemcpyDeviceToHost, ss.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ss.s);
+    if (e != cudaSuccess) return fail(hd_cuda_fail(e, "hd_build_library"));
+    st = status_take(lib->status, "hd_build_library");
+    if (st != HD_OK) return fail(hd_fail(st, "hd_build_library: precursor m/z must be finite"));
+    *out = lib;
+    return HD_OK;
+}
+
+void hd_library_free(hd_library *lib) { lib_release(lib); }
+
+hd_status hd_library_info(const hd_library *lib, uint32_t *n_refs, uint32_t *dim)
+{
+    HD_CHECK(lib, "hd_library_info: null library");
+    if (n_refs) *n_refs = lib->n;
+    if (dim) *dim = lib->dim;
+    return HD_OK;
+}
+
+hd_status hd_library_export(const hd_library *lib, uint64_t *d_hv, double *d_mz, uint8_t *d_charge,
+                            uint32_t *d_orig, hd_stream stream)
+{
+    HD_CHECK(lib, "hd_library_export: null library");
+    hd_status st = check_device(lib->device);
+    if (st != HD_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto D2D = cudaMemcpyDeviceToDevice;
+    if (lib->n == 0) return HD_OK;
+    if (d_hv) HD_CUDA_TRY(cudaMemcpyAsync(d_hv, lib->hv, (size_t)lib->n * lib->W * 8, D2D, s));
+    if (d_mz) HD_CUDA_TRY(cudaMemcpyAsync(d_mz, lib->mz, (size_t)lib->n * 8, D2D, s));
+    if (d_charge) HD_CUDA_TRY(cudaMemcpyAsync(d_charge, lib->charge, lib->n, D2D, s));
+    if (d_orig) HD_CUDA_TRY(cudaMemcpyAsync(d_orig, lib->orig, (size_t)lib->n * 4, D2D, s));
+    return HD_OK;
+}
+
+hd_status hd_library_status(hd_library *lib)
+{
+    HD_CHECK(lib, "hd_library_status: null library");
+    return status_take(lib->status, "hd_library");
+}
+
+hd_status hd_query_windows(const hd_library *lib, const double *d_q_mz, const uint8_t *d_q_charge,
+                           uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *d_lo, uint32_t *d_hi,
+                           hd_stream stream)
+{
+    HD_CHECK(lib, "hd_query_windows: null library");
+    HD_CHECK(tol_ok(tol), "hd_query_windows: tol must be finite and >= 0");
+    HD_CHECK(unit == HD_TOL_DA || unit == HD_TOL_PPM, "hd_query_windows: bad unit");
+    if (n_q == 0) return HD_OK;
+    HD_CHECK(d_q_mz && d_q_charge && d_lo && d_hi, "hd_query_windows: null buffer");
+    hd_status st = check_device(lib->device);
+    if (st != HD_OK) return st;
+    hd_windows_launch(lib, d_q_mz, d_q_charge, nullptr, n_q, tol, unit == HD_TOL_PPM, d_lo, d_hi,
+                      (cudaStream_t)stream);
+    HD_CUDA_TRY(cudaGetLastError());
+    return HD_OK;
+}
+
+hd_status hd_search_open_ex(const hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                            const uint8_t *d_q_charge, uint32_t n_q, double tol, hd_tol_unit unit,
+                            uint32_t k, hd_search_form form, uint32_t *d_out_idx, uint16_t *d_out_dist,
+                            hd_stream stream)
+{
+    HD_CHECK(lib, "hd_search_open: null library");
+    HD_CHECK(k >= 1 && k <= 16, "hd_search_open: k must be in [1, 16]");
+    HD_CHECK(tol_ok(tol), "hd_search_open: tol must be finite and >= 0");
+    HD_CHECK(unit == HD_TOL_DA || unit == HD_TOL_PPM, "hd_search_open: bad unit");
+    HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_POPC, "hd_search_open: unknown form");
+    if (n_q == 0) return HD_OK;
+    HD_CHECK(d_q_hv && d_q_mz && d_q_charge && d_out_idx && d_out_dist, "hd_search_open: null buffer");
+    HD_CHECK(aligned16(d_q_hv), "hd_search_open: d_q_hv must be 16-byte aligned");
+    hd_status st = check_device(lib->device);
+    if (st != HD_OK) return st;
+    return hd_search_popc_run(lib, d_q_hv, d_q_mz, d_q_charge, n_q, tol, unit == HD_TOL_PPM, k, d_out_idx,
+                              d_out_dist, (cudaStream_t)stream);
+}
+
+hd_status hd_search_open(const hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                         const uint8_t *d_q_charge, uint32_t n_q, double tol, hd_tol_unit unit, uint32_t k,
+                         uint32_t *d_out_idx, uint16_t *d_out_dist, hd_stream stream)
+{
+    return hd_search_open_ex(lib, d_q_hv, d_q_mz, d_q_charge, n_q, tol, unit, k, HD_FORM_AUTO, d_out_idx,
+                             d_out_dist, stream);
+}
+
+hd_status hd_search_host(hd_ctx *ctx, const hd_library *lib, const uint32_t *h_offsets, const uint32_t *h_bins,
+                         const uint8_t *h_levels, const double *h_q_mz, const uint8_t *h_q_charge,
+                         uint32_t n_q, double tol, hd_tol_unit unit, uint32_t k, uint32_t *h_out_idx,
+                         uint16_t *h_out_dist, hd_stream stream)
+{
+    HD_CHECK(ctx && lib, "hd_search_host: null ctx or library");
+    HD_CHECK(ctx->p.dim == lib->dim, "hd_search_host: ctx and library dims differ");
+    HD_CHECK(k >= 1 && k <= 16, "hd_search_host: k must be in [1, 16]");
+    HD_CHECK(tol_ok(tol), "hd_search_host: tol must be finite and >= 0");
+    if (n_q == 0) return HD_OK;
+    HD_CHECK(h_offsets && h_q_mz && h_q_charge && h_out_idx && h_out_dist, "hd_search_host: null buffer");
+    const uint32_t nnz = h_offsets[n_q];
+    HD_CHECK(nnz == 0 || (h_bins && h_levels), "hd_search_host: null CSR buffer");
+    hd_status st = check_device(ctx->device);
+    if (st != HD_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    hd_arena plan;
+    auto carve = [&](hd_arena &ar, uint32_t **off, uint32_t **bins, uint8_t **lv, double **mz,
+                     uint8_t **z, uint64_t **hv, uint32_t **oi, uint16_t **od) {
+        *off = ar.take<uint32_t>(n_q + 1);
+        *bins = ar.take<uint32_t>(nnz ? nnz : 1);
+        *lv = ar.take<uint8_t>(nnz ? nnz : 1);
+        *mz = ar.take<double>(n_q);
+        *z = ar.take<uint8_t>(n_q);
+        *hv = ar.take<uint64_t>((size_t)n_q * ctx->W);
+        *oi = ar.take<uint32_t>((size_t)n_q * k);
+        *od = ar.take<uint16_t>((size_t)n_q * k);
+    };
+    uint32_t *off, *bins, *oi;
+    uint8_t *lv, *z;
+    double *mz;
+    uint64_t *hv;
+    uint16_t *od;
+    carve(plan, &off, &bins, &lv, &mz, &z, &hv, &oi, &od);
+    hd_arena ar;
+    if (cudaMallocAsync((void **)&ar.base, plan.used, s) != cudaSuccess) {
+        cudaGetLastError();
+        return hd_fail(HD_ERR_OOM, "hd_search_host: device buffer allocation failed");
+    }
+    carve(ar, &off, &bins, &lv, &mz, &z, &hv, &oi, &od);
+    const auto H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(off, h_offsets, (size_t)(n_q + 1) * 4, H2D, s);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(bins, h_bins, (size_t)nnz * 4, H2D, s);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(lv, h_levels, nnz, H2D, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mz, h_q_mz, (size_t)n_q * 8, H2D, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(z, h_q_charge, n_q, H2D, s);
+    if (e == cudaSuccess) {
+        hd_encode_launch(ctx, off, bins, lv, n_q, hv, s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        st = hd_search_popc_run(lib, hv, mz, z, n_q, tol, unit == HD_TOL_PPM, k, oi, od, s);
+        if (st != HD_OK) {
+            cudaFreeAsync(ar.base, s);
+            cudaStreamSynchronize(s);
+            return st;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out_idx, oi, (size_t)n_q * k * 4, D2H, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out_dist, od, (size_t)n_q * k * 2, D2H, s);
+    cudaFreeAsync(ar.base, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return hd_cuda_fail(e, "hd_search_host");
+    if (e2 != cudaSuccess) return hd_cuda_fail(e2, "hd_search_host");
+    st = status_take(ctx->status, "hd_search_host (encode)");
+    if (st != HD_OK) return st;
+    return status_take(const_cast<hd_library *>(lib)->status, "hd_search_host (search)");
+}
+
+}  // extern "C"

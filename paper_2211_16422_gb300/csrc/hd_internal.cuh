@@ -1,0 +1,131 @@
+// hd_internal.cuh -- definitions shared by the CUDA translation units of
+// libhd: object layouts, device status flags, launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "hd.h"
+
+// ---------------------------------------------------------------------------
+// Device status word.  Kernels OR these bits into a word in mapped page-locked
+// host memory; the host reads it without a device synchronisation.
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+    HD_DEV_BAD_INPUT = 1u,   // malformed CSR row, bin or level out of range, ...
+    HD_DEV_TIMEOUT = 2u      // a bounded wait (mbarrier, work queue) expired
+};
+
+__device__ __forceinline__ void hd_flag(uint32_t *status, uint32_t bits)
+{
+    if (status) atomicOr_system(status, bits);
+}
+
+// Every device-side wait gives up after this much wall time, flags
+// HD_DEV_TIMEOUT and lets its kernel return.
+constexpr uint64_t HD_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint64_t hd_globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct hd_status_word {
+    uint32_t *host = nullptr;   // mapped, page-locked
+    uint32_t *dev = nullptr;    // device alias of `host`
+};
+
+struct hd_ctx {
+    hd_params p{};
+    int device = 0;
+    int num_sms = 0;
+    uint32_t W = 0;               // D / 64
+    uint64_t *F = nullptr;        // [n_bins][W]
+    uint64_t *L = nullptr;        // [n_levels][W]
+    uint32_t *rank_F = nullptr;   // [D]
+    uint32_t *rank_L = nullptr;   // [D]
+    hd_status_word status;
+};
+
+struct hd_library {
+    uint32_t n = 0, dim = 0, W = 0;
+    int device = 0;
+    int num_sms = 0;
+    uint64_t *hv = nullptr;        // [n][W] sorted rows
+    double *mz = nullptr;          // [n]
+    uint8_t *charge = nullptr;     // [n]
+    uint32_t *orig = nullptr;      // [n] input index of each row
+    uint32_t *charge_start = nullptr;   // [257] first row with charge >= c (device)
+    uint32_t charge_start_h[257] = {};
+    hd_status_word status;
+};
+
+// ---------------------------------------------------------------------------
+// Host-side error reporting.
+// ---------------------------------------------------------------------------
+hd_status hd_fail(hd_status s, const std::string &msg);
+hd_status hd_cuda_fail(cudaError_t e, const char *what);
+
+#define HD_CUDA_TRY(call)                                                   \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return hd_cuda_fail(e_, #call);              \
+    } while (0)
+
+// Launch accounting and the optional event timing of the hot kernels.
+void hd_count_launches(uint32_t n);
+struct hd_prof_scope {
+    hd_prof_scope(hd_kernel_kind kind, cudaStream_t s);
+    ~hd_prof_scope();
+    hd_kernel_kind kind;
+    cudaStream_t s;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+};
+
+static inline unsigned hd_ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Stream-ordered scratch arena: one cudaMallocAsync, carved in 256-byte
+// aligned pieces, released with cudaFreeAsync on the same stream.
+// ---------------------------------------------------------------------------
+struct hd_arena {
+    size_t used = 0;
+    char *base = nullptr;
+    template <class T> T *take(size_t count)
+    {
+        size_t off = (used + 255) & ~size_t(255);
+        used = off + count * sizeof(T);
+        return base ? reinterpret_cast<T *>(base + off) : nullptr;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Launchers implemented in the other translation units.
+// ---------------------------------------------------------------------------
+hd_status hd_item_memory_build(hd_ctx *ctx, cudaStream_t s);
+
+hd_status hd_preprocess_launch(const hd_preprocess_params &pp, const uint32_t *raw_off,
+                               const double *raw_mz, const double *raw_int, uint32_t n,
+                               uint32_t *out_off, uint32_t *out_bins, uint8_t *out_levels,
+                               uint32_t *status, cudaStream_t s);
+
+void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins,
+                      const uint8_t *levels, uint32_t n, uint64_t *out, cudaStream_t s);
+
+// Stable sort of n items by (charge, m/z): writes the permutation `perm`
+// (perm[rank] = input index).  Scratch from `arena` (sized by a first call
+// with arena.base == nullptr).
+void hd_sort_charge_mz(const double *mz, const uint8_t *charge, uint32_t n, uint32_t *perm,
+                       hd_arena &arena, cudaStream_t s);
+
+void hd_windows_launch(const hd_library *lib, const double *q_mz, const uint8_t *q_charge,
+                       const uint32_t *perm, uint32_t n_q, double tol, int ppm, uint32_t *lo,
+                       uint32_t *hi, cudaStream_t s);
+
+hd_status hd_search_popc_run(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
+                             const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
+                             uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);

@@ -1,0 +1,316 @@
+"""Python binding of libhd (ctypes): the same entry points as include/hd.h.
+
+Argument marshalling only -- every step runs in libhd's CUDA kernels.  Device
+buffers are torch CUDA tensors (PyTorch serves as the allocator and stream
+provider); hypervectors are int64 tensors of shape [n, D/64] holding the
+uint64 words bit for bit.  Loading fails loudly when libhd.so is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+HD_OK, HD_ERR_INVALID_ARG, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_TIMEOUT, HD_ERR_UNSUPPORTED = range(6)
+HD_TOL_DA, HD_TOL_PPM = 0, 1
+HD_FORM_AUTO, HD_FORM_POPC = 0, 1
+FORMS = {"auto": HD_FORM_AUTO, "popc": HD_FORM_POPC}
+NO_IDX, NO_DIST = 0xFFFFFFFF, 0xFFFF
+
+
+class HDError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class _Params(C.Structure):
+    _fields_ = [("dim", C.c_uint32), ("n_levels", C.c_uint32), ("n_bins", C.c_uint32),
+                ("alpha", C.c_uint32), ("seed", C.c_uint64)]
+
+
+class _PPParams(C.Structure):
+    _fields_ = [("mz_min", C.c_double), ("mz_max", C.c_double), ("bin_width", C.c_double),
+                ("min_rel_intensity", C.c_double), ("n_bins", C.c_uint32),
+                ("max_peaks", C.c_uint32), ("n_levels", C.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+P, u32, u64, dbl, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double, C.c_int
+
+_SIGS = {
+    "hd_status_string": ([i32], C.c_char_p),
+    "hd_last_error_message": ([], C.c_char_p),
+    "hd_version": ([], u32),
+    "hd_ctx_create": ([P, P], i32),
+    "hd_ctx_destroy": ([P], None),
+    "hd_ctx_item_memory": ([P, P, P, P, P, P], i32),
+    "hd_ctx_status": ([P], i32),
+    "hd_preprocess": ([P, P, P, P, P, u32, P, P, P, P], i32),
+    "hd_encode": ([P, P, P, P, u32, P, P], i32),
+    "hd_build_library": ([P, P, P, P, u32, P], i32),
+    "hd_library_free": ([P], None),
+    "hd_library_info": ([P, P, P], i32),
+    "hd_library_export": ([P, P, P, P, P, P], i32),
+    "hd_library_status": ([P], i32),
+    "hd_query_windows": ([P, P, P, u32, dbl, i32, P, P, P], i32),
+    "hd_search_open": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
+    "hd_search_open_ex": ([P, P, P, P, u32, dbl, i32, u32, i32, P, P, P], i32),
+    "hd_search_host": ([P, P, P, P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
+    "hd_profile_enable": ([i32], i32),
+    "hd_profile_collect": ([i32, P, P], i32),
+    "hd_launch_count": ([], u64),
+}
+HD_KERNEL_ENCODE, HD_KERNEL_SEARCH = 0, 1
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """The loaded libhd (raises if it was never built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libhd.so not built ({path}); run __graft_entry__.build()")
+            lib = C.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != HD_OK:
+        lib = load()
+        raise HDError(status, lib.hd_last_error_message().decode(errors="replace"))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return C.c_void_p(t.data_ptr()) if t.numel() else C.c_void_p(0)
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    raise TypeError(type(t))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+def _unit(unit) -> int:
+    return HD_TOL_PPM if unit in ("ppm", HD_TOL_PPM) else HD_TOL_DA
+
+
+class Ctx:
+    """Item memory (hd_ctx) on the current CUDA device."""
+
+    def __init__(self, dim, n_levels, n_bins, alpha=None, seed=0):
+        lib = load()
+        self.dim, self.n_levels, self.n_bins = int(dim), int(n_levels), int(n_bins)
+        self.alpha = self.dim // 2 if alpha is None else int(alpha)
+        p = _Params(self.dim, self.n_levels, self.n_bins, self.alpha, int(seed))
+        h = C.c_void_p()
+        _check(lib.hd_ctx_create(C.byref(p), C.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hd_ctx_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def status(self):
+        _check(load().hd_ctx_status(self._h))
+
+
+class Library:
+    """Sorted, device-resident reference library (hd_library)."""
+
+    def __init__(self, handle, n, dim):
+        self._h, self.n, self.dim = handle, n, dim
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hd_library_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def status(self):
+        _check(load().hd_library_status(self._h))
+
+
+def hd_ctx_create(dim, n_levels, n_bins, alpha=None, seed=0) -> Ctx:
+    return Ctx(dim, n_levels, n_bins, alpha, seed)
+
+
+def hd_ctx_item_memory(ctx: Ctx, stream=None):
+    """(F [f, D/64] i64, L [Q, D/64] i64, rank_F [D] i32, rank_L [D] i32) on the device."""
+    W = ctx.dim // 64
+    F = torch.empty((ctx.n_bins, W), dtype=torch.int64, device="cuda")
+    L = torch.empty((ctx.n_levels, W), dtype=torch.int64, device="cuda")
+    rF = torch.empty(ctx.dim, dtype=torch.int32, device="cuda")
+    rL = torch.empty(ctx.dim, dtype=torch.int32, device="cuda")
+    _check(load().hd_ctx_item_memory(ctx.handle, _ptr(F), _ptr(L), _ptr(rF), _ptr(rL), _stream(stream)))
+    return F, L, rF, rL
+
+
+def hd_preprocess(ctx: Ctx, raw_off, raw_mz, raw_int, *, mz_min, mz_max, bin_width, n_bins, max_peaks,
+                  n_levels, min_rel_intensity=0.01, stream=None):
+    """Raw peak CSR on the device -> (offsets i32 [n+1], bins i32 [cap], levels u8 [cap]); the
+    valid prefix of bins/levels is offsets[-1] long."""
+    raw_off = _dev(raw_off, torch.int32, "raw_off")
+    raw_mz = _dev(raw_mz, torch.float64, "raw_mz")
+    raw_int = _dev(raw_int, torch.float64, "raw_int")
+    n = raw_off.numel() - 1
+    off = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    cap = max(1, n * int(max_peaks))
+    bins = torch.empty(cap, dtype=torch.int32, device="cuda")
+    lv = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    pp = _PPParams(mz_min, mz_max, bin_width, min_rel_intensity, n_bins, max_peaks, n_levels)
+    _check(load().hd_preprocess(ctx.handle, C.byref(pp), _ptr(raw_off), _ptr(raw_mz), _ptr(raw_int), n,
+                                _ptr(off), _ptr(bins), _ptr(lv), _stream(stream)))
+    return off, bins, lv
+
+
+def hd_encode(ctx: Ctx, offsets, bins, levels, out=None, stream=None):
+    offsets = _dev(offsets, torch.int32, "offsets")
+    bins = _dev(bins, torch.int32, "bins")
+    levels = _dev(levels, torch.uint8, "levels")
+    n = offsets.numel() - 1
+    if out is None:
+        out = torch.empty((n, ctx.dim // 64), dtype=torch.int64, device="cuda")
+    _check(load().hd_encode(ctx.handle, _ptr(offsets), _ptr(bins), _ptr(levels), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def hd_build_library(ctx: Ctx, hv, prec_mz, charge) -> Library:
+    hv = _dev(hv, torch.int64, "hv")
+    prec_mz = _dev(prec_mz, torch.float64, "prec_mz")
+    charge = _dev(charge, torch.uint8, "charge")
+    n = prec_mz.numel()
+    torch.cuda.current_stream().synchronize()
+    h = C.c_void_p()
+    _check(load().hd_build_library(ctx.handle, _ptr(hv), _ptr(prec_mz), _ptr(charge), n, C.byref(h)))
+    return Library(h, n, ctx.dim)
+
+
+def hd_library_export(lib: Library, stream=None):
+    """Sorted rows: (hv [n, D/64] i64, mz f64, charge u8, orig i32)."""
+    n, W = lib.n, lib.dim // 64
+    hv = torch.empty((n, W), dtype=torch.int64, device="cuda")
+    mz = torch.empty(n, dtype=torch.float64, device="cuda")
+    z = torch.empty(n, dtype=torch.uint8, device="cuda")
+    orig = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(load().hd_library_export(lib.handle, _ptr(hv), _ptr(mz), _ptr(z), _ptr(orig), _stream(stream)))
+    return hv, mz, z, orig
+
+
+def hd_query_windows(lib: Library, q_mz, q_charge, tol, unit="da", stream=None):
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    n = q_mz.numel()
+    lo = torch.empty(n, dtype=torch.int32, device="cuda")
+    hi = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(load().hd_query_windows(lib.handle, _ptr(q_mz), _ptr(q_charge), n, float(tol), _unit(unit),
+                                   _ptr(lo), _ptr(hi), _stream(stream)))
+    return lo, hi
+
+
+def hd_search_open(lib: Library, q_hv, q_mz, q_charge, tol, unit="da", k=1, form="auto",
+                   out_idx=None, out_dist=None, stream=None):
+    """(idx i32 [n_q, k] input reference indices, dist i16 [n_q, k]); padding 0xFFFFFFFF /
+    0xFFFF (read them as unsigned)."""
+    q_hv = _dev(q_hv, torch.int64, "q_hv")
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    n = q_mz.numel()
+    if out_idx is None:
+        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    if out_dist is None:
+        out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
+    _check(load().hd_search_open_ex(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), n, float(tol),
+                                    _unit(unit), int(k), FORMS[form], _ptr(out_idx), _ptr(out_dist),
+                                    _stream(stream)))
+    return out_idx, out_dist
+
+
+def hd_search_host(ctx: Ctx, lib: Library, offsets, bins, levels, q_mz, q_charge, tol, unit="da", k=1,
+                   out_idx=None, out_dist=None, stream=None):
+    """End to end from host arrays (numpy, or pinned CPU tensors); returns host arrays."""
+    def host(a, dt):
+        if isinstance(a, torch.Tensor):
+            assert not a.is_cuda and a.is_contiguous()
+            return a
+        return np.ascontiguousarray(a, dtype=dt)
+    offsets, bins = host(offsets, np.uint32), host(bins, np.uint32)
+    levels, q_mz, q_charge = host(levels, np.uint8), host(q_mz, np.float64), host(q_charge, np.uint8)
+    n = (offsets.numel() if isinstance(offsets, torch.Tensor) else offsets.size) - 1
+    if out_idx is None:
+        out_idx = np.empty((n, k), np.uint32)
+    if out_dist is None:
+        out_dist = np.empty((n, k), np.uint16)
+    _check(load().hd_search_host(ctx.handle, lib.handle, _ptr(offsets), _ptr(bins), _ptr(levels), _ptr(q_mz),
+                                 _ptr(q_charge), n, float(tol), _unit(unit), int(k), _ptr(out_idx),
+                                 _ptr(out_dist), _stream(stream)))
+    return out_idx, out_dist
+
+
+def hd_profile_enable(on: bool = True):
+    _check(load().hd_profile_enable(1 if on else 0))
+
+
+def hd_profile_collect(kind: int):
+    """(total milliseconds, launches) of the recorded launches of `kind`."""
+    ms, n = C.c_double(), C.c_uint32()
+    _check(load().hd_profile_collect(kind, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def hd_launch_count() -> int:
+    return int(load().hd_launch_count())
+
+
+def as_u64(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+def as_u32(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)
+
+
+def as_u16(t: torch.Tensor) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint16)

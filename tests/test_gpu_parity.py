@@ -1,0 +1,326 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Integer and bit results must be identical: item memory, CSR spectrum
+vectors, hypervectors, library order, windows, distances and top-k indices.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_16422_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_16422_gb300 import build, hd as _hd
+    build.build()
+    return _hd
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    elif a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).cuda()
+
+
+def pp_args(n_levels, bin_width=synth.BIN_WIDTH, max_peaks=synth.MAX_PEAKS, n_bins=synth.N_BINS):
+    return dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=bin_width, n_bins=n_bins,
+                max_peaks=max_peaks, n_levels=n_levels)
+
+
+def gpu_csr(hd, ctx, sp, **pp):
+    off, b, lv = hd.hd_preprocess(ctx, dev(sp.offsets), dev(sp.mz), dev(sp.intensity), **pp)
+    torch.cuda.synchronize()
+    return off, b, lv
+
+
+def host_csr(hd, csr):
+    off, b, lv = csr
+    o = hd.as_u32(off)
+    n = int(o[-1])
+    return o, hd.as_u32(b[:n]) if n else np.zeros(0, np.uint32), lv[:n].cpu().numpy()
+
+
+# ------------------------------------------------------------ item memory
+@pytest.mark.parametrize("D,Q,f,alpha,seed", [(2048, 16, synth.N_BINS, 1024, 0), (8192, 32, synth.N_BINS, 4096, 7),
+                                              (384, 3, 5, 384, 123), (128, 2, 1, 0, 1)])
+def test_item_memory_bit_exact(hd, D, Q, f, alpha, seed):
+    ctx = hd.Ctx(D, Q, f, alpha, seed)
+    F, L, rF, rL = hd.hd_ctx_item_memory(ctx)
+    torch.cuda.synchronize()
+    oF, oL, orF, orL = oracle.item_memory(D, Q, f, alpha, seed)
+    assert np.array_equal(hd.as_u32(rF), orF)
+    assert np.array_equal(hd.as_u32(rL), orL)
+    assert np.array_equal(hd.as_u64(F), oF)
+    assert np.array_equal(hd.as_u64(L), oL)
+
+
+# ---------------------------------------------------------- preprocessing
+@pytest.mark.parametrize("n_levels,bin_width,max_peaks", [(16, 0.05, 50), (32, 0.04, 50), (256, 0.05, 3),
+                                                          (2, 0.05, 1023)])
+def test_preprocess_bit_exact(hd, n_levels, bin_width, max_peaks):
+    n_bins = int(np.floor((synth.MZ_MAX - synth.MZ_MIN) / bin_width)) + 1
+    rng = np.random.Generator(np.random.PCG64(11))
+    refs, qs, _ = synth.make_workload("tiny", scale=0.4)
+    soup = synth.raw_peak_soup(300, rng, max_len=1200)
+    ctx = hd.Ctx(128, n_levels, n_bins, 64, 0)
+    pp = pp_args(n_levels, bin_width, max_peaks, n_bins)
+    for sp in (refs, qs, soup):
+        got = host_csr(hd, gpu_csr(hd, ctx, sp, **pp))
+        want = oracle.preprocess(sp.offsets, sp.mz, sp.intensity, **pp)
+        for g, w in zip(got, want):
+            assert np.array_equal(g, w)
+    ctx.status()
+
+
+# ---------------------------------------------------------------- encode
+def _random_csr(rng, n, n_bins, n_levels, lens):
+    lens = np.asarray(lens)
+    off = np.zeros(n + 1, np.uint32)
+    off[1:] = np.cumsum(lens[:n])
+    nnz = int(off[-1])
+    return off, rng.integers(0, n_bins, nnz).astype(np.uint32), rng.integers(0, n_levels, nnz).astype(np.uint8)
+
+
+@pytest.mark.parametrize("D,f,Q", [(128, 50, 4), (2048, synth.N_BINS, 16), (8192, 3000, 32), (12288, 700, 16),
+                                   (32768, 300, 256)])
+def test_encode_bit_exact(hd, D, f, Q):
+    rng = np.random.default_rng(D)
+    special = [0, 1, 2, 3, 4, 5, 11, 12, 49, 50, 51, 150, 1023]
+    n = 200 if D <= 8192 else 40
+    lens = special + list(rng.integers(0, 160, n - len(special)))
+    off, b, lv = _random_csr(rng, n, f, Q, lens)
+    ctx = hd.Ctx(D, Q, f, D // 2, 5)
+    got = hd.hd_encode(ctx, dev(off), dev(b), dev(lv))
+    torch.cuda.synchronize()
+    ctx.status()
+    F, L, _, _ = oracle.item_memory(D, Q, f, D // 2, 5)
+    assert np.array_equal(hd.as_u64(got), oracle.encode(D, F, L, off, b, lv))
+
+
+# --------------------------------------------------------------- library
+def _refs_with_ties(rng, n):
+    mz = np.round(rng.uniform(400, 420, n), 1)
+    mz[:3] = [0.0, -0.0, 0.0]
+    z = rng.integers(0, 6, n).astype(np.uint8)
+    hv = rng.integers(-2**63, 2**63, (n, 4), dtype=np.int64).view(np.uint64)
+    return hv, mz, z
+
+
+def test_library_order_and_rows(hd):
+    rng = np.random.default_rng(3)
+    n = 20000
+    hv, mz, z = _refs_with_ties(rng, n)
+    ctx = hd.Ctx(256, 4, 10, 128, 0)
+    lib = hd.hd_build_library(ctx, dev(hv), dev(mz), dev(z))
+    s_hv, s_mz, s_z, s_orig = hd.hd_library_export(lib)
+    torch.cuda.synchronize()
+    order = oracle.library_order(mz, z)
+    assert np.array_equal(hd.as_u32(s_orig), order)
+    assert np.array_equal(hd.as_u64(s_hv), hv[order])
+    assert np.array_equal(s_z.cpu().numpy(), z[order])
+    assert np.array_equal(s_mz.cpu().numpy().view(np.uint64), mz[order].view(np.uint64))
+
+
+def test_library_rejects_nan_mz(hd):
+    ctx = hd.Ctx(128, 4, 10, 64, 0)
+    mz = np.array([500.0, np.nan, 600.0])
+    with pytest.raises(hd.HDError) as e:
+        hd.hd_build_library(ctx, dev(np.zeros((3, 2), np.uint64)), dev(mz), dev(np.full(3, 2, np.uint8)))
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+
+
+# --------------------------------------------------------------- windows
+@pytest.mark.parametrize("tol,unit", [(500.0, "da"), (150.0, "da"), (20.0, "ppm"), (0.0, "da"), (0.05, "da")])
+def test_windows_match_oracle(hd, tol, unit):
+    rng = np.random.default_rng(4)
+    n = 5000
+    mz = np.round(rng.uniform(400, 1500, n), 2)
+    z = rng.integers(1, 5, n).astype(np.uint8)
+    qmz = np.concatenate([rng.uniform(350, 1550, 400), mz[:50], mz[50:60] + tol, mz[60:70] - tol,
+                          [np.nan, np.inf, -np.inf]])
+    qz = np.concatenate([rng.integers(0, 6, 400), z[:70], [2, 2, 2]]).astype(np.uint8)
+    ctx = hd.Ctx(128, 4, 10, 64, 0)
+    lib = hd.hd_build_library(ctx, dev(np.zeros((n, 2), np.uint64)), dev(mz), dev(z))
+    lo, hi = hd.hd_query_windows(lib, dev(qmz), dev(qz), tol, unit)
+    _, s_mz, s_z, s_orig = hd.hd_library_export(lib)
+    torch.cuda.synchronize()
+    lo, hi = hd.as_u32(lo).astype(np.int64), hd.as_u32(hi).astype(np.int64)
+    want = oracle.window_count(mz, z, qmz, qz, tol, unit)
+    assert np.array_equal(hi - lo, want.astype(np.int64))
+    so = hd.as_u32(s_orig)
+    cnt = oracle.window_count(mz, z, qmz, qz, tol, unit)
+    for q in range(len(qmz)):
+        rows = so[lo[q]:hi[q]]
+        # every row of the range is a candidate and their number is the oracle's count
+        if len(rows):
+            sub = oracle.window_count(mz[rows], z[rows], qmz[q:q + 1], qz[q:q + 1], tol, unit)
+            assert sub[0] == len(rows)
+        assert len(rows) == cnt[q]
+
+
+# ---------------------------------------------------------------- search
+def _pipeline(hd, refs, qs, D, Q, k, tol, unit, seed=0, form="auto"):
+    pp = pp_args(Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, seed)
+    r_hv = hd.hd_encode(ctx, *gpu_csr(hd, ctx, refs, **pp))
+    q_hv = hd.hd_encode(ctx, *gpu_csr(hd, ctx, qs, **pp))
+    lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+    idx, dist = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), tol, unit, k, form=form)
+    torch.cuda.synchronize()
+    ctx.status()
+    lib.status()
+    return ctx, lib, r_hv, q_hv, hd.as_u32(idx), hd.as_u16(dist)
+
+
+def test_search_tiny_golden(hd):
+    g = json.load(open(os.path.join(GOLDEN, "tiny_search.json")))
+    refs, qs, spec = synth.make_workload("tiny")
+    _, _, r_hv, q_hv, idx, dist = _pipeline(hd, refs, qs, spec["dim"], spec["n_levels"], 1, spec["tol"],
+                                            spec["unit"])
+    import hashlib
+    assert hashlib.sha256(hd.as_u64(r_hv).tobytes()).hexdigest() == g["ref_hv_sha256"]
+    assert hashlib.sha256(hd.as_u64(q_hv).tobytes()).hexdigest() == g["query_hv_sha256"]
+    assert idx[:, 0].tolist() == g["top1_idx"]
+    assert dist[:, 0].tolist() == g["top1_dist"]
+
+
+def _medium(seed, n_refs=3000, n_q=500):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    refs = synth.make_references(n_refs, (1, 2, 3, 4), (0.1, 0.5, 0.3, 0.1), rng, decoy_fraction=0.5)
+    qs = synth.make_queries(refs, n_q, rng)
+    return refs, qs
+
+
+@pytest.mark.parametrize("D,k,tol,unit", [(2048, 1, 500.0, "da"), (8192, 5, 500.0, "da"), (8192, 16, 150.0, "da"),
+                                          (12288, 3, 500.0, "da"), (4096, 5, 20.0, "ppm"), (2048, 2, 0.0, "da"),
+                                          (128, 8, 1e6, "da")])
+def test_search_bit_exact(hd, D, k, tol, unit):
+    refs, qs = _medium(D + k)
+    Q = 32
+    _, lib, r_hv, q_hv, idx, dist = _pipeline(hd, refs, qs, D, Q, k, tol, unit)
+    oi, od = oracle.search(D, hd.as_u64(r_hv), refs.precursor_mz, refs.charge, hd.as_u64(q_hv), qs.precursor_mz,
+                           qs.charge, tol, unit, k)
+    assert np.array_equal(idx, oi)
+    assert np.array_equal(dist, od)
+
+
+def test_search_edge_cases(hd):
+    rng = np.random.default_rng(9)
+    D, W = 256, 4
+    n = 300
+    hv = rng.integers(-2**63, 2**63, (n, W), dtype=np.int64).view(np.uint64)
+    hv[100:110] = hv[0]                                   # ties broken by lowest index
+    mz = rng.uniform(400, 600, n)
+    z = np.where(np.arange(n) < 250, 2, 3).astype(np.uint8)
+    q = np.concatenate([hv[:5], hv[250:252], hv[:3]])
+    qmz = np.array([500, 500, 500, 500, 500, 450, 450, np.nan, 500, 500], float)
+    qz = np.array([2, 2, 2, 2, 2, 3, 3, 2, 9, 2], np.uint8)   # charge 9 has no reference
+    ctx = hd.Ctx(D, 4, 10, 128, 0)
+    lib = hd.hd_build_library(ctx, dev(hv), dev(mz), dev(z))
+    for k, tol in ((16, 1000.0), (1, 1000.0), (4, 0.5), (16, 0.0)):
+        i, d = hd.hd_search_open(lib, dev(q), dev(qmz), dev(qz), tol, "da", k)
+        torch.cuda.synchronize()
+        oi, od = oracle.search(D, hv, mz, z, q, qmz, qz, tol, "da", k)
+        assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
+    # empty query set is a no-op
+    hd.hd_search_open(lib, dev(q[:0]), dev(qmz[:0]), dev(qz[:0]), 10.0, "da", 3)
+    # a library of one row
+    lib1 = hd.hd_build_library(ctx, dev(hv[:1]), dev(mz[:1]), dev(z[:1]))
+    i, d = hd.hd_search_open(lib1, dev(q), dev(qmz), dev(qz), 1000.0, "da", 2)
+    torch.cuda.synchronize()
+    oi, od = oracle.search(D, hv[:1], mz[:1], z[:1], q, qmz, qz, 1000.0, "da", 2)
+    assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
+
+
+def test_search_host_matches_device(hd):
+    refs, qs = _medium(77, 2000, 300)
+    D, Q, k = 4096, 16, 5
+    ctx, lib, _, q_hv, idx, dist = _pipeline(hd, refs, qs, D, Q, k, 500.0, "da")
+    q_csr = oracle.preprocess(qs.offsets, qs.mz, qs.intensity, **pp_args(Q))
+    hi, hd_ = hd.hd_search_host(ctx, lib, *q_csr, qs.precursor_mz, qs.charge, 500.0, "da", k)
+    assert np.array_equal(hi, idx) and np.array_equal(hd_, dist)
+
+
+def test_invalid_arguments(hd):
+    with pytest.raises(hd.HDError) as e:
+        hd.Ctx(100, 16, 10)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    ctx = hd.Ctx(256, 4, 10, 128, 0)
+    rng = np.random.default_rng(1)
+    hv = rng.integers(-2**63, 2**63, (50, 4), dtype=np.int64)
+    lib = hd.hd_build_library(ctx, dev(hv), dev(rng.uniform(400, 500, 50)), dev(np.full(50, 2, np.uint8)))
+    q, qm, qz = dev(hv[:4]), dev(np.full(4, 450.0)), dev(np.full(4, 2, np.uint8))
+    for kw in (dict(k=0), dict(k=17), dict(tol=-1.0), dict(tol=float("nan")), dict(tol=float("inf"))):
+        args = dict(tol=10.0, k=1)
+        args.update(kw)
+        with pytest.raises(hd.HDError) as e:
+            hd.hd_search_open(lib, q, qm, qz, args["tol"], "da", args["k"])
+        assert e.value.status == hd.HD_ERR_INVALID_ARG
+    flat = dev(np.zeros(4 * 4 + 1, np.uint64))
+    with pytest.raises(hd.HDError) as e:      # rows not 16-byte aligned
+        hd.hd_search_open(lib, flat[1:].view(4, 4), qm, qz, 10.0, "da", 1)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    # a bin beyond n_bins is found on the device and reported by the ctx status
+    off, b, lv = dev(np.array([0, 2], np.uint32)), dev(np.array([3, 10], np.uint32)), dev(np.array([0, 1], np.uint8))
+    hd.hd_encode(ctx, off, b, lv)
+    torch.cuda.synchronize()
+    with pytest.raises(hd.HDError) as e:
+        ctx.status()
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    ctx.status()   # cleared
+
+
+# ----------------------------------------------- full-size workload, sampled
+def test_full_size_sampled(hd):
+    """The 1,000,000 x 50,000, D=8192, Q=32, +-500, top-5 workload in the
+    benchmark's launch configuration; the oracle answers a seeded sample of
+    queries and encodes a sample of spectra."""
+    refs, qs, spec = synth.make_workload("full")
+    D, Q, k = spec["dim"], spec["n_levels"], spec["k"]
+    pp = pp_args(Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, 0)
+    r_csr = gpu_csr(hd, ctx, refs, **pp)
+    q_csr = gpu_csr(hd, ctx, qs, **pp)
+    r_hv = hd.hd_encode(ctx, *r_csr)
+    q_hv = hd.hd_encode(ctx, *q_csr)
+    lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+    idx, dist = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), spec["tol"], spec["unit"], k)
+    torch.cuda.synchronize()
+    ctx.status()
+    lib.status()
+    rng = np.random.default_rng(2024)
+    # encode: a sample of spectra through the oracle's own preprocessing and encoder
+    F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, 0)
+    rs = np.sort(rng.choice(refs.n, 200, replace=False))
+    sub = refs.subset(rs)
+    o_csr = oracle.preprocess(sub.offsets, sub.mz, sub.intensity, **pp)
+    assert np.array_equal(hd.as_u64(r_hv[torch.from_numpy(rs).cuda()]), oracle.encode(D, F, L, *o_csr))
+    # search: a sample of queries by brute force over the whole library
+    which = np.sort(rng.choice(qs.n, 48, replace=False)).astype(np.uint32)
+    r_np, q_np = hd.as_u64(r_hv), hd.as_u64(q_hv)
+    oi, od = oracle.search(D, r_np, refs.precursor_mz, refs.charge, q_np, qs.precursor_mz, qs.charge,
+                           spec["tol"], spec["unit"], k, which=which)
+    gi, gd = hd.as_u32(idx), hd.as_u16(dist)
+    assert np.array_equal(gi[which], oi)
+    assert np.array_equal(gd[which], od)
+    # properties that hold for every query: ascending keys, candidates only
+    assert np.all((gd[:, 1:] > gd[:, :-1]) | ((gd[:, 1:] == gd[:, :-1]) & (gi[:, 1:] > gi[:, :-1])))
+    ok = gi != 0xFFFFFFFF
+    rows = gi[ok]
+    qq = np.nonzero(ok)[0]
+    assert np.all(refs.charge[rows] == qs.charge[qq])
+    assert np.all(np.abs(refs.precursor_mz[rows] - qs.precursor_mz[qq]) <= spec["tol"])
