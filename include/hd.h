@@ -197,6 +197,23 @@ HD_API hd_status hd_search_host(hd_ctx *ctx, const hd_library *lib, const uint32
                          const uint8_t *h_q_charge, uint32_t n_q, double tol, hd_tol_unit unit,
                          uint32_t k, uint32_t *h_out_idx, uint16_t *h_out_dist, hd_stream stream);
 
+/* hd_search_open with no device allocation (the paper has no counterpart:
+ * this serves callers that cannot allocate device memory while running, e.g.
+ * a server that reserved its memory up front or a host thread that must not
+ * block in the allocator).  Same arguments, results and padding as
+ * hd_search_open; the scratch comes from one fixed device buffer of 32 MiB
+ * held by every GPU that loads libhd until the process exits.  A request
+ * that needs more scratch than that (on a 152-SM GPU: above about 140,000
+ * queries at 9 <= k <= 16, more at smaller k) is rejected with
+ * HD_ERR_INVALID_ARG before any launch.  The first call on a device looks up the buffer's device address
+ * (make that first call before any stream capture).  All calls share the
+ * buffer: calls whose kernels overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other -- serialise them.  Asynchronous. */
+HD_API hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_t *d_q_hv,
+                                        const double *d_q_mz, const uint8_t *d_q_charge, uint32_t n_q,
+                                        double tol, hd_tol_unit unit, uint32_t k, uint32_t *d_out_idx,
+                                        uint16_t *d_out_dist, hd_stream stream);
+
 /* Measurement hooks (no counterpart in the paper).  While enabled, libhd
  * records a CUDA event pair around every launch of the given kernel kind, on
  * the stream the kernel runs on.  hd_profile_collect() waits for the

@@ -129,3 +129,11 @@ void hd_windows_launch(const hd_library *lib, const double *q_mz, const uint8_t 
 hd_status hd_search_popc_run(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
                              const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
                              uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);
+
+// hd_search_popc_run on caller-provided device scratch (nothing allocated);
+// fails with HD_ERR_INVALID_ARG when the request needs more than
+// `scratch_bytes`.
+hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
+                                     const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
+                                     uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s,
+                                     void *scratch, size_t scratch_bytes);

@@ -435,7 +435,8 @@ __global__ void k_merge(const uint64_t *__restrict__ partial, const uint32_t *__
 template <int K>
 hd_status run_k(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
                 const uint8_t *q_z, uint32_t n_q, double tol, int ppm, uint32_t k,
-                uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s)
+                uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s, char *ext = nullptr,
+                size_t ext_cap = 0)
 {
     const uint32_t n_blocks = (n_q + BQ - 1) / BQ;
     int occ = 0;
@@ -464,8 +465,16 @@ hd_status run_k(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
     carve(plan, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part);
     hd_sort_charge_mz(q_mz, q_z, n_q, nullptr, plan, s);
     hd_arena ar;
-    cudaError_t e = cudaMallocAsync((void **)&ar.base, plan.used, s);
-    if (e != cudaSuccess) return hd_fail(HD_ERR_OOM, "search scratch allocation failed");
+    if (ext) {   // caller-provided scratch: nothing is allocated
+        if (plan.used > ext_cap)
+            return hd_fail(HD_ERR_INVALID_ARG, "search needs " + std::to_string(plan.used) +
+                                                   " bytes of scratch, more than the fixed " +
+                                                   std::to_string(ext_cap));
+        ar.base = ext;
+    } else {
+        cudaError_t e = cudaMallocAsync((void **)&ar.base, plan.used, s);
+        if (e != cudaSuccess) return hd_fail(HD_ERR_OOM, "search scratch allocation failed");
+    }
     carve(ar, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part);
     hd_sort_charge_mz(q_mz, q_z, n_q, perm, ar, s);
     const double tq = ppm ? tol * 1e-6 : tol;
@@ -480,7 +489,7 @@ hd_status run_k(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
     }
     hd_count_launches(1), k_merge<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(part, ist, perm, n_q, k, out_idx, out_dist);
     HD_CUDA_TRY(cudaGetLastError());
-    HD_CUDA_TRY(cudaFreeAsync(ar.base, s));
+    if (!ext) HD_CUDA_TRY(cudaFreeAsync(ar.base, s));
     return HD_OK;
 }
 
@@ -504,4 +513,19 @@ hd_status hd_search_popc_run(const hd_library *lib, const uint64_t *q_hv, const 
     if (k <= 4) return run_k<4>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
     if (k <= 8) return run_k<8>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
     return run_k<16>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
+}
+
+hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
+                                     const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
+                                     uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s,
+                                     void *scratch, size_t scratch_bytes)
+{
+    char *x = static_cast<char *>(scratch);
+#define HD_RUN_K(KK) run_k<KK>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s, x, scratch_bytes)
+    if (k <= 1) return HD_RUN_K(1);
+    if (k <= 2) return HD_RUN_K(2);
+    if (k <= 4) return HD_RUN_K(4);
+    if (k <= 8) return HD_RUN_K(8);
+    return HD_RUN_K(16);
+#undef HD_RUN_K
 }

@@ -64,6 +64,7 @@ _SIGS = {
     "hd_search_open": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_search_open_ex": ([P, P, P, P, u32, dbl, i32, u32, i32, P, P, P], i32),
     "hd_search_host": ([P, P, P, P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
+    "hd_search_open_noalloc": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_profile_enable": ([i32], i32),
     "hd_profile_collect": ([i32, P, P], i32),
     "hd_launch_count": ([], u64),
@@ -265,6 +266,24 @@ def hd_search_open(lib: Library, q_hv, q_mz, q_charge, tol, unit="da", k=1, form
     _check(load().hd_search_open_ex(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), n, float(tol),
                                     _unit(unit), int(k), FORMS[form], _ptr(out_idx), _ptr(out_dist),
                                     _stream(stream)))
+    return out_idx, out_dist
+
+
+def hd_search_open_noalloc(lib: Library, q_hv, q_mz, q_charge, tol, unit="da", k=1, out_idx=None,
+                           out_dist=None, stream=None):
+    """hd_search_open without device allocation inside libhd (scratch from its fixed
+    device buffer).  The outputs are the caller's: pass preallocated tensors to keep the
+    whole call allocation-free."""
+    q_hv = _dev(q_hv, torch.int64, "q_hv")
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    n = q_mz.numel()
+    if out_idx is None:
+        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    if out_dist is None:
+        out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
+    _check(load().hd_search_open_noalloc(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), n, float(tol),
+                                         _unit(unit), int(k), _ptr(out_idx), _ptr(out_dist), _stream(stream)))
     return out_idx, out_dist
 
 
