@@ -90,9 +90,14 @@ typedef struct {
 typedef struct hd_ctx hd_ctx;
 typedef struct hd_library hd_library;
 
+/* Scoring forms; all give identical results.  The tensor-core forms score
+ * bipolar copies (bit 0 -> +1, bit 1 -> -1) of the HVs by matrix multiply,
+ * S = sum_d x_d y_d = D - 2*dist, accumulated exactly in fp32. */
 typedef enum {
-    HD_FORM_AUTO = 0,   /* fastest exact form for the request */
-    HD_FORM_POPC = 1    /* XOR + population count on the integer pipes */
+    HD_FORM_AUTO = 0,     /* fastest form the library was prepared for */
+    HD_FORM_POPC = 1,     /* XOR + population count on the integer pipes */
+    HD_FORM_TC_FP8 = 2,   /* tcgen05 kind::f8f6f4, +-1 as e4m3 (library: D bytes/row) */
+    HD_FORM_TC_BF16 = 3   /* tcgen05 kind::f16, +-1 as bf16 (library: 2D bytes/row) */
 } hd_search_form;
 
 HD_API const char *hd_status_string(hd_status s);
@@ -162,6 +167,10 @@ HD_API hd_status hd_library_info(const hd_library *lib, uint32_t *n_refs, uint32
 HD_API hd_status hd_library_export(const hd_library *lib, uint64_t *d_hv, double *d_mz,
                             uint8_t *d_charge, uint32_t *d_orig, hd_stream stream);
 HD_API hd_status hd_library_status(hd_library *lib);
+/* Builds the bipolar copy of the library a tensor-core form scores
+ * (HD_FORM_TC_FP8: n*D bytes; HD_FORM_TC_BF16: n*2D bytes of device memory,
+ * owned by the library).  HD_FORM_POPC needs nothing.  Synchronous; idempotent. */
+HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
 
 /* Candidate windows (Section 3.4, Table 1): for each query, rows [lo, hi) of
  * the sorted library whose charge equals the query's and whose precursor

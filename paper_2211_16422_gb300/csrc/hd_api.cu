@@ -110,6 +110,8 @@ void lib_release(hd_library *lib)
     cudaFree(lib->charge);
     cudaFree(lib->orig);
     cudaFree(lib->charge_start);
+    cudaFree(lib->x_fp8);
+    cudaFree(lib->x_bf16);
     status_free(lib->status);
     delete lib;
 }
@@ -343,6 +345,22 @@ hd_status hd_library_status(hd_library *lib)
     return status_take(lib->status, "hd_library");
 }
 
+hd_status hd_library_prepare(hd_library *lib, hd_search_form form)
+{
+    HD_CHECK(lib, "hd_library_prepare: null library");
+    HD_CHECK(form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
+             "hd_library_prepare: unknown form");
+    hd_status st = check_device(lib->device);
+    if (st != HD_OK || form == HD_FORM_POPC) return st;
+    scoped_stream ss;
+    if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess)
+        return hd_fail(HD_ERR_CUDA, "hd_library_prepare: stream creation failed");
+    st = hd_library_expand(lib, form == HD_FORM_TC_FP8, ss.s);
+    if (st != HD_OK) return st;
+    HD_CUDA_TRY(cudaStreamSynchronize(ss.s));
+    return HD_OK;
+}
+
 hd_status hd_query_windows(const hd_library *lib, const double *d_q_mz, const uint8_t *d_q_charge,
                            uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *d_lo, uint32_t *d_hi,
                            hd_stream stream)
@@ -369,12 +387,21 @@ hd_status hd_search_open_ex(const hd_library *lib, const uint64_t *d_q_hv, const
     HD_CHECK(k >= 1 && k <= 16, "hd_search_open: k must be in [1, 16]");
     HD_CHECK(tol_ok(tol), "hd_search_open: tol must be finite and >= 0");
     HD_CHECK(unit == HD_TOL_DA || unit == HD_TOL_PPM, "hd_search_open: bad unit");
-    HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_POPC, "hd_search_open: unknown form");
+    HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
+             "hd_search_open: unknown form");
     if (n_q == 0) return HD_OK;
     HD_CHECK(d_q_hv && d_q_mz && d_q_charge && d_out_idx && d_out_dist, "hd_search_open: null buffer");
     HD_CHECK(aligned16(d_q_hv), "hd_search_open: d_q_hv must be 16-byte aligned");
     hd_status st = check_device(lib->device);
     if (st != HD_OK) return st;
+    if (form == HD_FORM_AUTO) form = lib->x_fp8 ? HD_FORM_TC_FP8 : (lib->x_bf16 ? HD_FORM_TC_BF16 : HD_FORM_POPC);
+    if (form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16) {
+        const bool fp8 = form == HD_FORM_TC_FP8;
+        HD_CHECK(fp8 ? lib->x_fp8 != nullptr || lib->n == 0 : lib->x_bf16 != nullptr || lib->n == 0,
+                 "hd_search_open: call hd_library_prepare for this form first");
+        return hd_search_mma_run(lib, fp8, d_q_hv, d_q_mz, d_q_charge, n_q, tol, unit == HD_TOL_PPM, k, d_out_idx,
+                                 d_out_dist, (cudaStream_t)stream);
+    }
     return hd_search_popc_run(lib, d_q_hv, d_q_mz, d_q_charge, n_q, tol, unit == HD_TOL_PPM, k, d_out_idx,
                               d_out_dist, (cudaStream_t)stream);
 }

@@ -60,6 +60,8 @@ struct hd_library {
     uint8_t *charge = nullptr;     // [n]
     uint32_t *orig = nullptr;      // [n] input index of each row
     uint32_t *charge_start = nullptr;   // [257] first row with charge >= c (device)
+    uint8_t *x_fp8 = nullptr;      // [n][D] bipolar e4m3 rows (tensor-core form), optional
+    uint8_t *x_bf16 = nullptr;     // [n][2D] bipolar bf16 rows (tensor-core form), optional
     uint32_t charge_start_h[257] = {};
     hd_status_word status;
 };
@@ -137,3 +139,9 @@ hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv
                                      const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
                                      uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s,
                                      void *scratch, size_t scratch_bytes);
+
+// Tensor-core form: the bipolar copy of the library rows, and the search.
+hd_status hd_library_expand(hd_library *lib, bool fp8, cudaStream_t s);
+hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_hv, const double *q_mz,
+                            const uint8_t *q_charge, uint32_t n_q, double tol, int ppm, uint32_t k,
+                            uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);

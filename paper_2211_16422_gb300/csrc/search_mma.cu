@@ -1,0 +1,498 @@
+// search_mma.cu -- open-modification Hamming search (Section 3.4) on the
+// 5th-generation tensor cores (tcgen05), exact.
+//
+// Bits become bipolar values (bit 0 -> +1, bit 1 -> -1) stored as 8-bit e4m3
+// (+1 = 0x38, -1 = 0xB8) or bf16 (0x3F80 / 0xBF80).  For a query x and a
+// reference y the tensor core computes S = sum_d x_d y_d = D - 2 dist(x, y)
+// with fp32 accumulation in tensor memory.  Every product is +-1 and every
+// partial sum an integer of magnitude <= D <= 32768 < 2^24, so the sum is
+// exact and dist = (D - S) / 2 matches the popcount form bit for bit.
+//
+// Kernel layout (one persistent CTA per SM, 192 threads):
+//   warp 0      TMA producer: 2-D tensor loads of 128-byte K-slices of a
+//               query block (A: 128 rows) and a reference tile (B: 256 rows)
+//               into a 4-stage ring, 128B-swizzled for the MMA descriptors;
+//   warp 1      allocates 512 TMEM columns and issues tcgen05.mma
+//               (M=128, N=256, 32 bytes of K per instruction) into one of two
+//               accumulator buffers, committing stages and tiles to mbarriers;
+//   warps 2..5  epilogue: tcgen05.ld of the finished 128x256 accumulator,
+//               one query row per thread, window mask, top-k of (dist, input
+//               index) keys; the buffer is handed back while the next tile is
+//               being accumulated in the other one.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "hd_internal.cuh"
+#include "search_common.cuh"
+
+void hd_exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint32_t n, hd_arena &arena,
+                           cudaStream_t s);
+
+namespace {
+
+using namespace hd_search;
+
+constexpr int TM = 128;                 // queries per block (MMA M)
+constexpr int TN = 256;                 // reference rows per tile (MMA N)
+constexpr int KB = 128;                 // bytes of K per stage (one 128B swizzle atom)
+constexpr int STAGES = 4;
+constexpr int THREADS = 192;
+constexpr uint32_t A_BYTES = TM * KB;
+constexpr uint32_t B_BYTES = TN * KB;
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
+constexpr uint32_t TMEM_COLS = 2 * TN;
+
+// ------------------------------------------------------------ tcgen05 PTX
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <bool FP8>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    if (FP8)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+
+// Arrives on `bar` once every tcgen05.mma issued so far by this thread is done.
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// 32 lanes x 32 consecutive fp32 columns: thread i of the warp gets lane
+// (warp % 4) * 32 + i, columns [col, col + 32).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // version
+    d |= (uint64_t)2 << 61;               // 128B swizzle
+    return d;
+}
+
+// Instruction descriptor: fp32 accumulator, A/B e4m3 (kind::f8f6f4) or bf16
+// (kind::f16), both K-major, M = 128, N = 256.
+template <bool FP8>
+__host__ __device__ constexpr uint32_t instr_desc()
+{
+    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((uint32_t)(TN >> 3) << 17) |
+           ((uint32_t)(TM >> 4) << 24);
+}
+
+struct mma_args {
+    const uint32_t *lib_orig;
+    const uint32_t *lo, *hi;                    // windows, sorted query order
+    const uint32_t *blk_lo, *blk_hi, *blk_nt, *item_start;
+    const uint32_t *meta;                       // [0] tiles per item
+    uint64_t *partial;                          // [items][TM][K]
+    uint32_t *status;
+    uint32_t n_q, n_blocks, dim, row_bytes;
+};
+
+__device__ __forceinline__ uint32_t find_block(const uint32_t *item_start, uint32_t n_blocks, uint32_t item)
+{
+    uint32_t a = 0, b = n_blocks;
+    while (b - a > 1) {
+        const uint32_t m = (a + b) >> 1;
+        if (item_start[m] <= item) a = m; else b = m;
+    }
+    return a;
+}
+
+template <int K, bool FP8>
+__global__ void __launch_bounds__(THREADS, 1)
+k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *drain = acc_empty + 2;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 128);
+        }
+        mbar_init(drain, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(&s_tmem, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    const uint32_t total = a.item_start[a.n_blocks];
+    const uint32_t tpi = a.meta[0];
+    const uint32_t nchunks = a.row_bytes / KB;
+    volatile int *abort_flag = &s_abort;
+    auto give_up = [&]() {
+        *abort_flag = 1;
+        hd_flag(a.status, HD_DEV_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
+                const uint32_t b = find_block(a.item_start, a.n_blocks, item);
+                const uint32_t t0 = (item - a.item_start[b]) * tpi, t1 = min(a.blk_nt[b], t0 + tpi);
+                for (uint32_t t = t0; t < t1 && !*abort_flag; ++t) {
+                    const int32_t r0 = (int32_t)(a.blk_lo[b] + t * TN);
+                    for (uint32_t c = 0; c < nchunks; ++c, ++it) {
+                        const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
+                        if (!mbar_wait(&empty[s], ph ^ 1u)) { give_up(); break; }
+                        uint8_t *sa = smem + s * STAGE_BYTES, *sb = sa + A_BYTES;
+                        mbar_expect_tx(&full[s], STAGE_BYTES);
+                        tma_load_2d(sa, &qmap, (int32_t)(c * KB), (int32_t)(b * TM), &full[s]);
+                        tma_load_2d(sb, &lmap, (int32_t)(c * KB), r0, &full[s]);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ----------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc<FP8>();
+            uint32_t it = 0, acc_it = 0;
+            for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
+                const uint32_t b = find_block(a.item_start, a.n_blocks, item);
+                const uint32_t t0 = (item - a.item_start[b]) * tpi, t1 = min(a.blk_nt[b], t0 + tpi);
+                for (uint32_t t = t0; t < t1 && !*abort_flag; ++t, ++acc_it) {
+                    const uint32_t buf = acc_it & 1u, aph = (acc_it >> 1) & 1u;
+                    if (!mbar_wait(&acc_empty[buf], aph ^ 1u)) { give_up(); break; }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + buf * TN;
+                    bool ok = true;
+                    for (uint32_t c = 0; c < nchunks; ++c, ++it) {
+                        const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
+                        if (!mbar_wait(&full[s], ph)) { give_up(); ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sa = smem_addr(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
+                        const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
+#pragma unroll
+                        for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
+                            mma_issue<FP8>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
+                        mma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    mma_commit(&acc_full[buf]);
+                }
+            }
+            // every issued MMA has finished before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------- epilogue
+        const uint32_t quarter = warp & 3;              // TMEM lanes this warp may read
+        const uint32_t row = quarter * 32 + lane;       // query row within the block
+        const uint32_t lane_addr = (quarter * 32) << 16;
+        uint32_t acc_it = 0;
+        for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
+            const uint32_t b = find_block(a.item_start, a.n_blocks, item);
+            const uint32_t t0 = (item - a.item_start[b]) * tpi, t1 = min(a.blk_nt[b], t0 + tpi);
+            const uint32_t sq = b * TM + row;
+            const uint32_t lo = sq < a.n_q ? a.lo[sq] : 0u, hi = sq < a.n_q ? a.hi[sq] : 0u;
+            uint64_t best[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) best[i] = KEY_NONE;
+            bool ok = true;
+            for (uint32_t t = t0; t < t1; ++t, ++acc_it) {
+                const uint32_t buf = acc_it & 1u, aph = (acc_it >> 1) & 1u;
+                if (!mbar_wait(&acc_full[buf], aph)) { give_up(); ok = false; break; }
+                tc_fence_after();
+                const uint32_t r0 = a.blk_lo[b] + t * TN;
+                const uint32_t span = hi > lo ? hi - lo : 0u;
+#pragma unroll 1
+                for (uint32_t cg = 0; cg < TN / 32; ++cg) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
+                    tmem_ld_wait();
+                    const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const uint32_t r = r0 + cg * 32 + e;
+                        const int s = __float2int_rn(__uint_as_float(v[e]));
+                        const uint32_t d = (uint32_t)((int)a.dim - s) >> 1;
+                        if (r - lo < span && d <= thr) {
+                            const uint64_t key = ((uint64_t)d << 32) | __ldg(a.lib_orig + r);
+                            if (key < best[K - 1]) topk_insert<K>(best, key);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acc_empty[buf]);
+            }
+            if (!ok) break;
+            uint64_t *dst = a.partial + ((size_t)item * TM + row) * K;
+#pragma unroll
+            for (int i = 0; i < K; ++i) dst[i] = best[i];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// One row of packed bits per warp -> bipolar bytes (e4m3) or halves (bf16).
+template <bool FP8>
+__global__ void k_expand(const uint64_t *__restrict__ hv, const uint32_t *__restrict__ perm, uint32_t n,
+                         uint32_t W, uint8_t *__restrict__ out)
+{
+    const uint32_t r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const uint32_t lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const uint64_t *src = hv + (size_t)(perm ? perm[r] : r) * W;
+    constexpr uint32_t EB = FP8 ? 1 : 2;
+    uint8_t *dst = out + (size_t)r * W * 64 * EB;
+    for (uint32_t w = lane; w < W; w += 32) {
+        const uint64_t x = src[w];
+        uint4 *o = reinterpret_cast<uint4 *>(dst + (size_t)w * 64 * EB);
+#pragma unroll
+        for (int q = 0; q < 4 * (int)EB; ++q) {
+            uint32_t p[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                uint32_t word = 0;
+                if (FP8) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t bit = (uint32_t)(x >> (q * 16 + h * 4 + j)) & 1u;
+                        word |= (0x38u | (bit << 7)) << (8 * j);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t bit = (uint32_t)(x >> (q * 8 + h * 2 + j)) & 1u;
+                        word |= (0x3F80u | (bit << 15)) << (16 * j);
+                    }
+                }
+                p[h] = word;
+            }
+            o[q] = make_uint4(p[0], p[1], p[2], p[3]);
+        }
+    }
+}
+
+// ------------------------------------------------------------- host side
+using encode_fn = PFN_cuTensorMapEncodeTiled_v12000;
+
+encode_fn tensor_map_encoder()
+{
+    static std::once_flag once;
+    static encode_fn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<encode_fn>(p);
+    });
+    return fn;
+}
+
+// Rows of `row_bytes` bytes; boxes of 128 bytes x box_rows rows, 128B swizzle,
+// rows past `rows` read as zero.
+hd_status make_map(CUtensorMap *m, const void *base, uint64_t rows, uint32_t row_bytes, uint32_t box_rows)
+{
+    encode_fn enc = tensor_map_encoder();
+    if (!enc) return hd_fail(HD_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[2] = {row_bytes, rows};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)KB, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return hd_fail(HD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return HD_OK;
+}
+
+template <int K, bool FP8>
+hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
+                  uint32_t n_q, double tol, int ppm, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
+                  cudaStream_t s)
+{
+    const uint32_t n_blocks = (n_q + TM - 1) / TM;
+    const uint32_t row_bytes = lib->dim * (FP8 ? 1u : 2u);
+    const uint8_t *lib_x = FP8 ? lib->x_fp8 : lib->x_bf16;
+    if (!lib_x) return hd_fail(HD_ERR_INVALID_ARG, "library not prepared for this tensor-core form");
+    HD_CUDA_TRY(cudaFuncSetAttribute(k_search_mma<K, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_BYTES));
+    const uint32_t grid = (uint32_t)lib->num_sms;
+    const uint32_t target_items = 8 * grid;
+
+    auto carve = [&](hd_arena &ar, uint32_t **perm, uint32_t **lo, uint32_t **hi, uint32_t **blo,
+                     uint32_t **bhi, uint32_t **bnt, uint32_t **ist, uint32_t **meta, uint64_t **part,
+                     uint8_t **qx) {
+        *perm = ar.take<uint32_t>(n_q);
+        *lo = ar.take<uint32_t>(n_q);
+        *hi = ar.take<uint32_t>(n_q);
+        *blo = ar.take<uint32_t>(n_blocks);
+        *bhi = ar.take<uint32_t>(n_blocks);
+        *bnt = ar.take<uint32_t>(n_blocks);
+        *ist = ar.take<uint32_t>(n_blocks + 1);
+        *meta = ar.take<uint32_t>(4);
+        *part = ar.take<uint64_t>((size_t)(target_items + n_blocks) * TM * K);
+        *qx = ar.take<uint8_t>((size_t)n_q * row_bytes);
+    };
+    uint32_t *perm, *lo, *hi, *blo, *bhi, *bnt, *ist, *meta;
+    uint64_t *part;
+    uint8_t *qx;
+    hd_arena plan;
+    carve(plan, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part, &qx);
+    hd_sort_charge_mz(q_mz, q_z, n_q, nullptr, plan, s);
+    hd_arena ar;
+    if (cudaMallocAsync((void **)&ar.base, plan.used, s) != cudaSuccess) {
+        cudaGetLastError();
+        return hd_fail(HD_ERR_OOM, "tensor-core search scratch allocation failed");
+    }
+    carve(ar, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part, &qx);
+    CUtensorMap qmap, lmap;
+    hd_status st = make_map(&qmap, qx, n_q, row_bytes, TM);
+    if (st == HD_OK) st = make_map(&lmap, lib_x, lib->n, row_bytes, TN);
+    if (st != HD_OK) {
+        cudaFreeAsync(ar.base, s);
+        return st;
+    }
+    hd_sort_charge_mz(q_mz, q_z, n_q, perm, ar, s);
+    hd_count_launches(1), k_expand<FP8><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
+    const double tq = ppm ? tol * 1e-6 : tol;
+    hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z,
+                                                                          perm, n_q, tq, ppm, lo, hi);
+    hd_count_launches(1), k_worklist<<<1, 1024, 0, s>>>(lo, hi, n_q, TM, TN, n_blocks, target_items, blo, bhi,
+                                                        bnt, ist, meta);
+    mma_args ma{lib->orig, lo, hi, blo, bhi, bnt, ist, meta, part, lib->status.dev, n_q, n_blocks, lib->dim,
+                row_bytes};
+    {
+        hd_prof_scope timed(HD_KERNEL_SEARCH, s);
+        hd_count_launches(1), k_search_mma<K, FP8><<<grid, THREADS, SMEM_BYTES, s>>>(qmap, lmap, ma);
+    }
+    hd_count_launches(1), k_merge<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(part, ist, TM, perm, n_q, k, out_idx,
+                                                                          out_dist);
+    HD_CUDA_TRY(cudaGetLastError());
+    HD_CUDA_TRY(cudaFreeAsync(ar.base, s));
+    return HD_OK;
+}
+
+template <bool FP8>
+hd_status run_fmt(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
+                  uint32_t n_q, double tol, int ppm, uint32_t k, uint32_t *oi, uint16_t *od, cudaStream_t s)
+{
+    if (k <= 1) return run_mma<1, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
+    if (k <= 2) return run_mma<2, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
+    if (k <= 4) return run_mma<4, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
+    if (k <= 8) return run_mma<8, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
+    return run_mma<16, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
+}
+
+}  // namespace
+
+hd_status hd_library_expand(hd_library *lib, bool fp8, cudaStream_t s)
+{
+    uint8_t *&dst = fp8 ? lib->x_fp8 : lib->x_bf16;
+    if (dst || lib->n == 0) return HD_OK;
+    const size_t bytes = (size_t)lib->n * lib->dim * (fp8 ? 1 : 2);
+    if (cudaMalloc(&dst, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        dst = nullptr;
+        return hd_fail(HD_ERR_OOM, "expanded library allocation failed");
+    }
+    if (fp8)
+        hd_count_launches(1), k_expand<true><<<hd_ceil_div(lib->n, 8), 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
+    else
+        hd_count_launches(1), k_expand<false><<<hd_ceil_div(lib->n, 8), 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
+    HD_CUDA_TRY(cudaGetLastError());
+    return HD_OK;
+}
+
+hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_hv, const double *q_mz,
+                            const uint8_t *q_charge, uint32_t n_q, double tol, int ppm, uint32_t k,
+                            uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s)
+{
+    if (lib->n == 0) return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
+    if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
+    return run_fmt<false>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
+}

@@ -19,8 +19,8 @@ from . import build as _build
 
 HD_OK, HD_ERR_INVALID_ARG, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_TIMEOUT, HD_ERR_UNSUPPORTED = range(6)
 HD_TOL_DA, HD_TOL_PPM = 0, 1
-HD_FORM_AUTO, HD_FORM_POPC = 0, 1
-FORMS = {"auto": HD_FORM_AUTO, "popc": HD_FORM_POPC}
+HD_FORM_AUTO, HD_FORM_POPC, HD_FORM_TC_FP8, HD_FORM_TC_BF16 = 0, 1, 2, 3
+FORMS = {"auto": HD_FORM_AUTO, "popc": HD_FORM_POPC, "tc_fp8": HD_FORM_TC_FP8, "tc_bf16": HD_FORM_TC_BF16}
 NO_IDX, NO_DIST = 0xFFFFFFFF, 0xFFFF
 
 
@@ -60,6 +60,7 @@ _SIGS = {
     "hd_library_info": ([P, P, P], i32),
     "hd_library_export": ([P, P, P, P, P, P], i32),
     "hd_library_status": ([P], i32),
+    "hd_library_prepare": ([P, i32], i32),
     "hd_query_windows": ([P, P, P, u32, dbl, i32, P, P, P], i32),
     "hd_search_open": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_search_open_ex": ([P, P, P, P, u32, dbl, i32, u32, i32, P, P, P], i32),
@@ -227,6 +228,11 @@ def hd_build_library(ctx: Ctx, hv, prec_mz, charge) -> Library:
     h = C.c_void_p()
     _check(load().hd_build_library(ctx.handle, _ptr(hv), _ptr(prec_mz), _ptr(charge), n, C.byref(h)))
     return Library(h, n, ctx.dim)
+
+
+def hd_library_prepare(lib: Library, form: str):
+    """Build the library's copy for a tensor-core form ('tc_fp8' or 'tc_bf16')."""
+    _check(load().hd_library_prepare(lib.handle, FORMS[form]))
 
 
 def hd_library_export(lib: Library, stream=None):

@@ -1,0 +1,152 @@
+"""Tensor-core search forms (tcgen05, +-1 operands, fp32 accumulation) against
+the oracle and the popcount form: identical distances and indices.
+
+Exactness argument: products are +-1 and every partial sum is an integer of
+magnitude <= D < 2^24.  The adversarial cases below put the accumulator near
++-D (near-duplicates and complements) where a narrower internal accumulator
+would lose low bits."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_16422_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+FORMS = ("tc_fp8", "tc_bf16")
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_16422_gb300 import build, hd as _hd
+    build.build()
+    return _hd
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    elif a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).cuda()
+
+
+def _rand_hv(rng, n, W):
+    return rng.integers(-2**63, 2**63, (n, W), dtype=np.int64).view(np.uint64)
+
+
+def _search_all(hd, lib, q, qmz, qz, tol, unit, k):
+    out = {}
+    for form in ("popc",) + FORMS:
+        i, d = hd.hd_search_open(lib, dev(q), dev(qmz), dev(qz), tol, unit, k, form=form)
+        torch.cuda.synchronize()
+        lib.status()
+        out[form] = (hd.as_u32(i), hd.as_u16(d))
+    return out
+
+
+@pytest.mark.parametrize("D", [128, 2048, 8192])
+def test_tc_forms_small_exact(hd, D):
+    rng = np.random.default_rng(D)
+    W = D // 64
+    n = 700
+    refs = _rand_hv(rng, n, W)
+    mz = rng.uniform(400, 700, n)
+    z = rng.integers(1, 4, n).astype(np.uint8)
+    q = refs[rng.choice(n, 150)].copy()
+    # flip a few bits: near-duplicates put S close to D
+    for i in range(len(q)):
+        for b in rng.choice(D, int(rng.integers(0, 6)), replace=False):
+            q[i, b // 64] ^= np.uint64(1) << np.uint64(b % 64)
+    q[:10] = ~refs[:10]                      # complements: S = -D
+    qmz = rng.uniform(400, 700, len(q))
+    qz = rng.integers(1, 4, len(q)).astype(np.uint8)
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
+    for f in FORMS:
+        hd.hd_library_prepare(lib, f)
+    for k, tol, unit in ((5, 500.0, "da"), (1, 60.0, "da"), (16, 2e5, "ppm")):
+        res = _search_all(hd, lib, q, qmz, qz, tol, unit, k)
+        oi, od = oracle.search(D, refs, mz, z, q, qmz, qz, tol, unit, k)
+        for form, (i, d) in res.items():
+            assert np.array_equal(i, oi), form
+            assert np.array_equal(d, od), form
+
+
+def test_tc_forms_all_distances_exact(hd):
+    """k = n: every candidate distance of every query compared, including the
+    extremes dist = 0 and dist = D."""
+    rng = np.random.default_rng(5)
+    D, W, n = 8192, 128, 256
+    refs = _rand_hv(rng, n, W)
+    refs[1] = ~refs[0]
+    refs[2] = refs[0]
+    q = refs[:16].copy()
+    mz, z = np.full(n, 500.0), np.full(n, 2, np.uint8)
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
+    for f in FORMS:
+        hd.hd_library_prepare(lib, f)
+    # k is at most 16; sweep windows that each hold 16 references at a time
+    for start in range(0, n, 16):
+        sub_mz = mz.copy()
+        sub_mz[:] = 1000.0
+        sub_mz[start:start + 16] = 500.0
+        lib2 = hd.hd_build_library(ctx, dev(refs), dev(sub_mz), dev(z))
+        for f in FORMS:
+            hd.hd_library_prepare(lib2, f)
+        res = _search_all(hd, lib2, q, np.full(16, 500.0), np.full(16, 2, np.uint8), 0.5, "da", 16)
+        oi, od = oracle.search(D, refs, sub_mz, z, q, np.full(16, 500.0), np.full(16, 2, np.uint8), 0.5, "da", 16)
+        for form, (i, d) in res.items():
+            assert np.array_equal(i, oi) and np.array_equal(d, od), form
+    assert od.max() <= D
+
+
+@pytest.mark.parametrize("D,k", [(8192, 5), (4096, 2), (12288, 8)])
+def test_tc_forms_workload_exact(hd, D, k):
+    rng = np.random.Generator(np.random.PCG64(D + k))
+    refs = synth.make_references(6000, (1, 2, 3, 4), (0.1, 0.5, 0.3, 0.1), rng, decoy_fraction=0.5)
+    qs = synth.make_queries(refs, 900, rng)
+    Q = 32
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, 1)
+
+    def enc(sp):
+        return hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(sp.offsets), dev(sp.mz), dev(sp.intensity), **pp))
+
+    r_hv, q_hv = enc(refs), enc(qs)
+    lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+    for f in FORMS:
+        hd.hd_library_prepare(lib, f)
+    for tol, unit in ((500.0, "da"), (20.0, "ppm")):
+        res = {}
+        for form in ("popc",) + FORMS:
+            i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), tol, unit, k, form=form)
+            torch.cuda.synchronize()
+            res[form] = (hd.as_u32(i), hd.as_u16(d))
+        oi, od = oracle.search(D, hd.as_u64(r_hv), refs.precursor_mz, refs.charge, hd.as_u64(q_hv),
+                               qs.precursor_mz, qs.charge, tol, unit, k)
+        for form, (i, d) in res.items():
+            assert np.array_equal(i, oi), form
+            assert np.array_equal(d, od), form
+    lib.status()
+
+
+def test_auto_prefers_prepared_tc_form(hd):
+    rng = np.random.default_rng(2)
+    D, W = 1024, 16
+    refs = _rand_hv(rng, 100, W)
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library(ctx, dev(refs), dev(rng.uniform(400, 500, 100)), dev(np.full(100, 2, np.uint8)))
+    q, qm, qz = dev(refs[:5]), dev(np.full(5, 450.0)), dev(np.full(5, 2, np.uint8))
+    with pytest.raises(hd.HDError):
+        hd.hd_search_open(lib, q, qm, qz, 100.0, "da", 1, form="tc_fp8")   # not prepared
+    i0, d0 = hd.hd_search_open(lib, q, qm, qz, 100.0, "da", 3, form="auto")
+    hd.hd_library_prepare(lib, "tc_fp8")
+    i1, d1 = hd.hd_search_open(lib, q, qm, qz, 100.0, "da", 3, form="auto")
+    torch.cuda.synchronize()
+    assert torch.equal(i0, i1) and torch.equal(d0, d1)
