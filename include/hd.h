@@ -171,6 +171,14 @@ HD_API hd_status hd_library_status(hd_library *lib);
  * (HD_FORM_TC_FP8: n*D bytes; HD_FORM_TC_BF16: n*2D bytes of device memory,
  * owned by the library).  HD_FORM_POPC needs nothing.  Synchronous; idempotent. */
 HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
+/* Schedule of the tensor-core forms (no counterpart in the paper).  Reference
+ * rows form tiles of 256 on a grid fixed to row 0; one work item scores one
+ * block of 128 sorted queries against `tile_group` consecutive tiles, and
+ * items are ordered so that the CTAs running at once share `super_group`
+ * consecutive groups of tiles through L2.  0 keeps the default (8, 4).
+ * Results do not depend on the schedule.  Not to be changed while a search
+ * on this library is in flight. */
+HD_API hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group);
 
 /* Candidate windows (Section 3.4, Table 1): for each query, rows [lo, hi) of
  * the sorted library whose charge equals the query's and whose precursor

@@ -361,6 +361,15 @@ hd_status hd_library_prepare(hd_library *lib, hd_search_form form)
     return HD_OK;
 }
 
+hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group)
+{
+    HD_CHECK(lib, "hd_library_set_schedule: null library");
+    HD_CHECK(tile_group <= 4096 && super_group <= 4096, "hd_library_set_schedule: values must be <= 4096");
+    lib->mma_tuning.tile_group = tile_group;
+    lib->mma_tuning.super_group = super_group;
+    return HD_OK;
+}
+
 hd_status hd_query_windows(const hd_library *lib, const double *d_q_mz, const uint8_t *d_q_charge,
                            uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *d_lo, uint32_t *d_hi,
                            hd_stream stream)

@@ -51,6 +51,15 @@ struct hd_ctx {
     hd_status_word status;
 };
 
+// Schedule of the tensor-core search: tiles of 256 reference rows are grouped
+// in runs of `tile_group` (one work item per query block and group), and
+// `super_group` groups form the slice of the library the running CTAs share
+// through L2.  0 = default.
+struct hd_mma_tuning {
+    uint32_t tile_group = 0;
+    uint32_t super_group = 0;
+};
+
 struct hd_library {
     uint32_t n = 0, dim = 0, W = 0;
     int device = 0;
@@ -62,6 +71,7 @@ struct hd_library {
     uint32_t *charge_start = nullptr;   // [257] first row with charge >= c (device)
     uint8_t *x_fp8 = nullptr;      // [n][D] bipolar e4m3 rows (tensor-core form), optional
     uint8_t *x_bf16 = nullptr;     // [n][2D] bipolar bf16 rows (tensor-core form), optional
+    hd_mma_tuning mma_tuning;
     uint32_t charge_start_h[257] = {};
     hd_status_word status;
 };

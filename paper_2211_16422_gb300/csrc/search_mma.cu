@@ -145,22 +145,34 @@ __host__ __device__ constexpr uint32_t instr_desc()
 struct mma_args {
     const uint32_t *lib_orig;
     const uint32_t *lo, *hi;                    // windows, sorted query order
-    const uint32_t *blk_lo, *blk_hi, *blk_nt, *item_start;
-    const uint32_t *meta;                       // [0] tiles per item
-    uint64_t *partial;                          // [items][TM][K]
+    const uint32_t *blk_t0, *blk_t1;            // absolute tile range of each query block
+    const uint32_t *pair_start;                 // [n_pairs + 1] first item of (super-group, block)
+    uint64_t *top;                              // [n_q][K] running top-k, sorted query order
+    uint32_t *locks;                            // [n_blocks] merge locks
     uint32_t *status;
-    uint32_t n_q, n_blocks, dim, row_bytes;
+    uint32_t n_q, n_blocks, n_pairs, tg, sg, dim, row_bytes;
 };
 
-__device__ __forceinline__ uint32_t find_block(const uint32_t *item_start, uint32_t n_blocks, uint32_t item)
+// Work item -> (query block, absolute tile range [t0, t1)).  Items are
+// numbered super-group-major: pair p = G * n_blocks + b holds the groups of
+// TG tiles of block b that fall in super-group G (SG groups), so the CTAs
+// running at any moment share one slice of the library through L2.
+__device__ __forceinline__ void item_range(const mma_args &a, uint32_t item, uint32_t &b, uint32_t &t0,
+                                           uint32_t &t1)
 {
-    uint32_t a = 0, b = n_blocks;
-    while (b - a > 1) {
-        const uint32_t m = (a + b) >> 1;
-        if (item_start[m] <= item) a = m; else b = m;
+    uint32_t lo = 0, hi = a.n_pairs;
+    while (hi - lo > 1) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (a.pair_start[m] <= item) lo = m; else hi = m;
     }
-    return a;
+    const uint32_t G = lo / a.n_blocks;
+    b = lo % a.n_blocks;
+    const uint32_t g = max(a.blk_t0[b] / a.tg, G * a.sg) + (item - a.pair_start[lo]);
+    t0 = max(a.blk_t0[b], g * a.tg);
+    t1 = min(a.blk_t1[b], (g + 1) * a.tg);
 }
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 template <int K, bool FP8>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -174,7 +186,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     uint64_t *acc_empty = acc_full + 2;
     uint64_t *drain = acc_empty + 2;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_lock_ok;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -199,8 +211,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    const uint32_t total = a.item_start[a.n_blocks];
-    const uint32_t tpi = a.meta[0];
+    const uint32_t total = a.pair_start[a.n_pairs];
     const uint32_t nchunks = a.row_bytes / KB;
     volatile int *abort_flag = &s_abort;
     auto give_up = [&]() {
@@ -213,10 +224,10 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         if (lane == 0) {
             uint32_t it = 0;
             for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
-                const uint32_t b = find_block(a.item_start, a.n_blocks, item);
-                const uint32_t t0 = (item - a.item_start[b]) * tpi, t1 = min(a.blk_nt[b], t0 + tpi);
+                uint32_t b, t0, t1;
+                item_range(a, item, b, t0, t1);
                 for (uint32_t t = t0; t < t1 && !*abort_flag; ++t) {
-                    const int32_t r0 = (int32_t)(a.blk_lo[b] + t * TN);
+                    const int32_t r0 = (int32_t)(t * TN);
                     for (uint32_t c = 0; c < nchunks; ++c, ++it) {
                         const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
                         if (!mbar_wait(&empty[s], ph ^ 1u)) { give_up(); break; }
@@ -234,8 +245,8 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             constexpr uint32_t idesc = instr_desc<FP8>();
             uint32_t it = 0, acc_it = 0;
             for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
-                const uint32_t b = find_block(a.item_start, a.n_blocks, item);
-                const uint32_t t0 = (item - a.item_start[b]) * tpi, t1 = min(a.blk_nt[b], t0 + tpi);
+                uint32_t b, t0, t1;
+                item_range(a, item, b, t0, t1);
                 for (uint32_t t = t0; t < t1 && !*abort_flag; ++t, ++acc_it) {
                     const uint32_t buf = acc_it & 1u, aph = (acc_it >> 1) & 1u;
                     if (!mbar_wait(&acc_empty[buf], aph ^ 1u)) { give_up(); break; }
@@ -267,12 +278,14 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         const uint32_t quarter = warp & 3;              // TMEM lanes this warp may read
         const uint32_t row = quarter * 32 + lane;       // query row within the block
         const uint32_t lane_addr = (quarter * 32) << 16;
+        const bool leader = threadIdx.x == 64;
         uint32_t acc_it = 0;
         for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
-            const uint32_t b = find_block(a.item_start, a.n_blocks, item);
-            const uint32_t t0 = (item - a.item_start[b]) * tpi, t1 = min(a.blk_nt[b], t0 + tpi);
+            uint32_t b, t0, t1;
+            item_range(a, item, b, t0, t1);
             const uint32_t sq = b * TM + row;
             const uint32_t lo = sq < a.n_q ? a.lo[sq] : 0u, hi = sq < a.n_q ? a.hi[sq] : 0u;
+            const uint32_t span = hi > lo ? hi - lo : 0u;
             uint64_t best[K];
 #pragma unroll
             for (int i = 0; i < K; ++i) best[i] = KEY_NONE;
@@ -281,8 +294,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                 const uint32_t buf = acc_it & 1u, aph = (acc_it >> 1) & 1u;
                 if (!mbar_wait(&acc_full[buf], aph)) { give_up(); ok = false; break; }
                 tc_fence_after();
-                const uint32_t r0 = a.blk_lo[b] + t * TN;
-                const uint32_t span = hi > lo ? hi - lo : 0u;
+                const uint32_t r0 = t * TN;
 #pragma unroll 1
                 for (uint32_t cg = 0; cg < TN / 32; ++cg) {
                     uint32_t v[32];
@@ -303,16 +315,101 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                 tc_fence_before();
                 mbar_arrive(&acc_empty[buf]);
             }
-            if (!ok) break;
-            uint64_t *dst = a.partial + ((size_t)item * TM + row) * K;
+            // merge into the block's running top-k under its lock (bounded spin)
+            epi_bar();
+            if (leader) {
+                int got = 0;
+                if (ok && !*abort_flag) {
+                    const uint64_t w0 = hd_globaltimer_ns();
+                    for (uint32_t i = 0;; ++i) {
+                        if (atomicCAS(&a.locks[b], 0u, 1u) == 0u) { got = 1; break; }
+                        if ((i & 63u) == 0 && hd_globaltimer_ns() - w0 > HD_WAIT_NS) { give_up(); break; }
+                    }
+                    __threadfence();
+                }
+                s_lock_ok = got;
+            }
+            epi_bar();
+            const bool locked = s_lock_ok != 0;
+            if (locked) {
+                if (sq < a.n_q) {
+                    unsigned long long *g = reinterpret_cast<unsigned long long *>(a.top + (size_t)sq * K);
+                    uint64_t cur[K];
 #pragma unroll
-            for (int i = 0; i < K; ++i) dst[i] = best[i];
+                    for (int i = 0; i < K; ++i) cur[i] = __ldcg(g + i);
+                    topk_merge<K>(cur, best);
+#pragma unroll
+                    for (int i = 0; i < K; ++i) __stcg(g + i, (unsigned long long)cur[i]);
+                }
+                __threadfence();
+            }
+            epi_bar();
+            if (leader && locked) atomicExch(&a.locks[b], 0u);
+            if (!locked) break;
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// Work list of the L2-blocked schedule (one CTA of 1024 threads): per query
+// block the absolute tile range covering the union of its windows, then the
+// item count of every (super-group, block) pair and its exclusive scan.
+__global__ void __launch_bounds__(1024)
+k_worklist_l2(const uint32_t *__restrict__ lo, const uint32_t *__restrict__ hi, uint32_t n_q, uint32_t n_blocks,
+              uint32_t tg, uint32_t sg, uint32_t n_super, uint32_t *__restrict__ blk_t0,
+              uint32_t *__restrict__ blk_t1, uint32_t *__restrict__ pair_start)
+{
+    __shared__ uint32_t sh[33];
+    for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) {
+        uint32_t l = 0xFFFFFFFFu, h = 0;
+        const uint32_t e = min(n_q, (b + 1) * (uint32_t)TM);
+        for (uint32_t s = b * TM; s < e; ++s)
+            if (hi[s] > lo[s]) {
+                l = min(l, lo[s]);
+                h = max(h, hi[s]);
+            }
+        blk_t0[b] = h > l ? l / TN : 0u;
+        blk_t1[b] = h > l ? (h + TN - 1) / TN : 0u;
+    }
+    __syncthreads();
+    const uint32_t n_pairs = n_super * n_blocks;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < n_pairs; base += blockDim.x) {
+        const uint32_t p = base + threadIdx.x;
+        uint32_t v = 0;
+        if (p < n_pairs) {
+            const uint32_t G = p / n_blocks, b = p % n_blocks;
+            const uint32_t t0 = blk_t0[b], t1 = blk_t1[b];
+            if (t1 > t0) {
+                const uint32_t g0 = max(t0 / tg, G * sg), g1 = min((t1 - 1) / tg, G * sg + sg - 1);
+                v = g1 >= g0 ? g1 - g0 + 1 : 0u;
+            }
+        }
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, &tot, sh);
+        if (p < n_pairs) pair_start[p] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) pair_start[n_pairs] = carry;
+}
+
+// Running top-k (sorted query order) -> the caller's order.
+template <int K>
+__global__ void k_emit(const uint64_t *__restrict__ top, const uint32_t *__restrict__ perm, uint32_t n_q,
+                       uint32_t k, uint32_t *__restrict__ out_idx, uint16_t *__restrict__ out_dist)
+{
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_q) return;
+    const uint32_t q = perm[s];
+    for (uint32_t t = 0; t < k; ++t) {
+        const uint64_t key = top[(size_t)s * K + t];
+        const bool none = key == KEY_NONE;
+        out_idx[(size_t)q * k + t] = none ? 0xFFFFFFFFu : (uint32_t)key;
+        out_dist[(size_t)q * k + t] = none ? (uint16_t)0xFFFF : (uint16_t)(key >> 32);
+    }
 }
 
 // One row of packed bits per warp -> bipolar bytes (e4m3) or halves (bf16).
@@ -393,7 +490,7 @@ hd_status make_map(CUtensorMap *m, const void *base, uint64_t rows, uint32_t row
 template <int K, bool FP8>
 hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
                   uint32_t n_q, double tol, int ppm, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
-                  cudaStream_t s)
+                  cudaStream_t s, const hd_mma_tuning &tune)
 {
     const uint32_t n_blocks = (n_q + TM - 1) / TM;
     const uint32_t row_bytes = lib->dim * (FP8 ? 1u : 2u);
@@ -402,34 +499,36 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     HD_CUDA_TRY(cudaFuncSetAttribute(k_search_mma<K, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_BYTES));
     const uint32_t grid = (uint32_t)lib->num_sms;
-    const uint32_t target_items = 8 * grid;
+    const uint32_t tg = tune.tile_group, sg = tune.super_group;
+    const uint32_t n_tiles = (lib->n + TN - 1) / TN;
+    const uint32_t n_super = (n_tiles + tg * sg - 1) / (tg * sg);
+    const size_t n_pairs = (size_t)n_super * n_blocks;
+    if (n_pairs >= 0xFFFFFFFFull) return hd_fail(HD_ERR_UNSUPPORTED, "work list too large");
 
-    auto carve = [&](hd_arena &ar, uint32_t **perm, uint32_t **lo, uint32_t **hi, uint32_t **blo,
-                     uint32_t **bhi, uint32_t **bnt, uint32_t **ist, uint32_t **meta, uint64_t **part,
-                     uint8_t **qx) {
+    auto carve = [&](hd_arena &ar, uint32_t **perm, uint32_t **lo, uint32_t **hi, uint32_t **bt0,
+                     uint32_t **bt1, uint32_t **pst, uint64_t **top, uint32_t **locks, uint8_t **qx) {
         *perm = ar.take<uint32_t>(n_q);
         *lo = ar.take<uint32_t>(n_q);
         *hi = ar.take<uint32_t>(n_q);
-        *blo = ar.take<uint32_t>(n_blocks);
-        *bhi = ar.take<uint32_t>(n_blocks);
-        *bnt = ar.take<uint32_t>(n_blocks);
-        *ist = ar.take<uint32_t>(n_blocks + 1);
-        *meta = ar.take<uint32_t>(4);
-        *part = ar.take<uint64_t>((size_t)(target_items + n_blocks) * TM * K);
+        *bt0 = ar.take<uint32_t>(n_blocks);
+        *bt1 = ar.take<uint32_t>(n_blocks);
+        *pst = ar.take<uint32_t>(n_pairs + 1);
+        *top = ar.take<uint64_t>((size_t)n_q * K);
+        *locks = ar.take<uint32_t>(n_blocks);
         *qx = ar.take<uint8_t>((size_t)n_q * row_bytes);
     };
-    uint32_t *perm, *lo, *hi, *blo, *bhi, *bnt, *ist, *meta;
-    uint64_t *part;
+    uint32_t *perm, *lo, *hi, *bt0, *bt1, *pst, *locks;
+    uint64_t *top;
     uint8_t *qx;
     hd_arena plan;
-    carve(plan, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part, &qx);
+    carve(plan, &perm, &lo, &hi, &bt0, &bt1, &pst, &top, &locks, &qx);
     hd_sort_charge_mz(q_mz, q_z, n_q, nullptr, plan, s);
     hd_arena ar;
     if (cudaMallocAsync((void **)&ar.base, plan.used, s) != cudaSuccess) {
         cudaGetLastError();
         return hd_fail(HD_ERR_OOM, "tensor-core search scratch allocation failed");
     }
-    carve(ar, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part, &qx);
+    carve(ar, &perm, &lo, &hi, &bt0, &bt1, &pst, &top, &locks, &qx);
     CUtensorMap qmap, lmap;
     hd_status st = make_map(&qmap, qx, n_q, row_bytes, TM);
     if (st == HD_OK) st = make_map(&lmap, lib_x, lib->n, row_bytes, TN);
@@ -437,21 +536,21 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
         cudaFreeAsync(ar.base, s);
         return st;
     }
+    HD_CUDA_TRY(cudaMemsetAsync(top, 0xFF, (size_t)n_q * K * sizeof(uint64_t), s));
+    HD_CUDA_TRY(cudaMemsetAsync(locks, 0, (size_t)n_blocks * sizeof(uint32_t), s));
     hd_sort_charge_mz(q_mz, q_z, n_q, perm, ar, s);
     hd_count_launches(1), k_expand<FP8><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
     const double tq = ppm ? tol * 1e-6 : tol;
     hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z,
                                                                           perm, n_q, tq, ppm, lo, hi);
-    hd_count_launches(1), k_worklist<<<1, 1024, 0, s>>>(lo, hi, n_q, TM, TN, n_blocks, target_items, blo, bhi,
-                                                        bnt, ist, meta);
-    mma_args ma{lib->orig, lo, hi, blo, bhi, bnt, ist, meta, part, lib->status.dev, n_q, n_blocks, lib->dim,
-                row_bytes};
+    hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, n_blocks, tg, sg, n_super, bt0, bt1, pst);
+    mma_args ma{lib->orig, lo, hi, bt0, bt1, pst, top, locks, lib->status.dev, n_q, n_blocks, (uint32_t)n_pairs,
+                tg, sg, lib->dim, row_bytes};
     {
         hd_prof_scope timed(HD_KERNEL_SEARCH, s);
         hd_count_launches(1), k_search_mma<K, FP8><<<grid, THREADS, SMEM_BYTES, s>>>(qmap, lmap, ma);
     }
-    hd_count_launches(1), k_merge<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(part, ist, TM, perm, n_q, k, out_idx,
-                                                                          out_dist);
+    hd_count_launches(1), k_emit<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(top, perm, n_q, k, out_idx, out_dist);
     HD_CUDA_TRY(cudaGetLastError());
     HD_CUDA_TRY(cudaFreeAsync(ar.base, s));
     return HD_OK;
@@ -459,13 +558,14 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
 
 template <bool FP8>
 hd_status run_fmt(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
-                  uint32_t n_q, double tol, int ppm, uint32_t k, uint32_t *oi, uint16_t *od, cudaStream_t s)
+                  uint32_t n_q, double tol, int ppm, uint32_t k, uint32_t *oi, uint16_t *od, cudaStream_t s,
+                  const hd_mma_tuning &tu)
 {
-    if (k <= 1) return run_mma<1, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
-    if (k <= 2) return run_mma<2, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
-    if (k <= 4) return run_mma<4, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
-    if (k <= 8) return run_mma<8, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
-    return run_mma<16, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s);
+    if (k <= 1) return run_mma<1, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
+    if (k <= 2) return run_mma<2, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
+    if (k <= 4) return run_mma<4, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
+    if (k <= 8) return run_mma<8, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
+    return run_mma<16, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
 }
 
 }  // namespace
@@ -493,6 +593,9 @@ hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_h
                             uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s)
 {
     if (lib->n == 0) return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
-    if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
-    return run_fmt<false>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
+    hd_mma_tuning tu = lib->mma_tuning;
+    if (tu.tile_group == 0) tu.tile_group = 8;
+    if (tu.super_group == 0) tu.super_group = 4;
+    if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s, tu);
+    return run_fmt<false>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s, tu);
 }

@@ -61,6 +61,7 @@ _SIGS = {
     "hd_library_export": ([P, P, P, P, P, P], i32),
     "hd_library_status": ([P], i32),
     "hd_library_prepare": ([P, i32], i32),
+    "hd_library_set_schedule": ([P, u32, u32], i32),
     "hd_query_windows": ([P, P, P, u32, dbl, i32, P, P, P], i32),
     "hd_search_open": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_search_open_ex": ([P, P, P, P, u32, dbl, i32, u32, i32, P, P, P], i32),
@@ -233,6 +234,11 @@ def hd_build_library(ctx: Ctx, hv, prec_mz, charge) -> Library:
 def hd_library_prepare(lib: Library, form: str):
     """Build the library's copy for a tensor-core form ('tc_fp8' or 'tc_bf16')."""
     _check(load().hd_library_prepare(lib.handle, FORMS[form]))
+
+
+def hd_library_set_schedule(lib: Library, tile_group: int = 0, super_group: int = 0):
+    """Work-item shape of the tensor-core forms (0 = default)."""
+    _check(load().hd_library_set_schedule(lib.handle, int(tile_group), int(super_group)))
 
 
 def hd_library_export(lib: Library, stream=None):

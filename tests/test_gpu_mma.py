@@ -150,3 +150,30 @@ def test_auto_prefers_prepared_tc_form(hd):
     i1, d1 = hd.hd_search_open(lib, q, qm, qz, 100.0, "da", 3, form="auto")
     torch.cuda.synchronize()
     assert torch.equal(i0, i1) and torch.equal(d0, d1)
+
+
+@pytest.mark.parametrize("tg,sg", [(1, 1), (2, 3), (64, 64), (8, 4)])
+def test_tc_schedule_does_not_change_results(hd, tg, sg):
+    """Work-item shape (tiles per item, groups per L2 slice) is a pure
+    performance knob: the top-k must not move."""
+    rng = np.random.Generator(np.random.PCG64(17))
+    refs = synth.make_references(9000, (2, 3), (0.7, 0.3), rng, decoy_fraction=0.5)
+    qs = synth.make_queries(refs, 700, rng)
+    D, Q, k = 2048, 16, 4
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, 2)
+
+    def enc(sp):
+        return hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(sp.offsets), dev(sp.mz), dev(sp.intensity), **pp))
+
+    r_hv, q_hv = enc(refs), enc(qs)
+    lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+    hd.hd_library_prepare(lib, "tc_fp8")
+    hd.hd_library_set_schedule(lib, tg, sg)
+    i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), 500.0, "da", k, form="tc_fp8")
+    torch.cuda.synchronize()
+    lib.status()
+    oi, od = oracle.search(D, hd.as_u64(r_hv), refs.precursor_mz, refs.charge, hd.as_u64(q_hv),
+                           qs.precursor_mz, qs.charge, 500.0, "da", k)
+    assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
