@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=("full", "batched", "serving"), default="full",
+                    help="full: the headline line; batched / serving: the extra workloads")
     return ap.parse_args()
 
 
@@ -342,6 +344,180 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
+# ------------------------------------------------ batched uneven workload
+def run_batched(args):
+    """200 log-uniform query batches (10..20,000 spectra), charge 1-5, windows
+    round-robin over 20 ppm / 150 Da / 500 Da, against a 2,000,000-reference
+    library, at D=4096 and D=8192: autotune, capture encode + search of every
+    batch as one CUDA graph, time its replays.  One JSON line per D."""
+    import torch
+    from paper_2211_16422_gb300 import build, hd
+    build.build()
+    spec = synth.WORKLOADS["batched"]
+    rng = np.random.Generator(np.random.PCG64(spec["seed"]))
+    n_r = max(1000, int(spec["n_refs"] * args.scale))
+    refs = synth.make_references(n_r, spec["charges"], spec["weights"], rng, decoy_fraction=spec["decoy_fraction"])
+    hi = max(20, int(spec["batch_hi"] * args.scale))
+    sizes = synth.batch_sizes(spec["n_batches"], spec["batch_lo"], hi, rng)
+    qs = synth.make_queries(refs, int(sizes.sum()), rng)
+    windows = [(t, u) for t, u in spec["windows"]]
+    cls = np.repeat(np.arange(len(sizes)) % len(windows), sizes).astype(np.uint8)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32
+                                     else np.ascontiguousarray(a)).cuda()
+    for D in spec["dims"]:
+        Q = spec["n_levels"]
+        pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+                  max_peaks=synth.MAX_PEAKS, n_levels=Q)
+        ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, seed=0)
+        r_hv = hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp))
+        lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+        del r_hv
+        hd.hd_library_prepare(lib, "tc_fp8")
+        off, bins, lv = hd.hd_preprocess(ctx, dev(qs.offsets), dev(qs.mz), dev(qs.intensity), **pp)
+        nnz = int(hd.as_u32(off)[-1])
+        q_mz, q_z, q_cls = dev(qs.precursor_mz), dev(qs.charge), dev(cls)
+        # comparisons: in-window candidates of every query under its own window
+        comparisons = 0
+        for c, (tol, unit) in enumerate(windows):
+            sel = torch.from_numpy(np.nonzero(cls == c)[0]).cuda()
+            lo, hi_ = hd.hd_query_windows(lib, q_mz[sel].contiguous(), q_z[sel].contiguous(), tol, unit)
+            comparisons += int((hd.as_u32(hi_).astype(np.int64) - hd.as_u32(lo).astype(np.int64)).sum())
+        # autotune on a seeded 20% query sample
+        q_hv = hd.hd_encode(ctx, off, bins, lv)
+        samp = torch.from_numpy(np.sort(np.random.default_rng(1).choice(qs.n, max(1, qs.n // 5), replace=False))).cuda()
+        best, table = hd.hd_library_autotune(lib, q_hv[samp].contiguous(), q_mz[samp].contiguous(),
+                                             q_z[samp].contiguous(), q_cls[samp].contiguous(), windows, spec["k"])
+        del q_hv
+        plan = hd.Plan(ctx, lib, off, bins[:nnz], lv[:nnz], q_mz, q_z, q_cls, windows, k=spec["k"], form="auto")
+        stream = torch.cuda.current_stream()
+        for _ in range(args.warmup):
+            plan.launch()
+        torch.cuda.synchronize()
+        lib.status()
+        hd.hd_profile_enable(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clocks:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                plan.launch()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        hd.hd_profile_enable(False)
+        search_ms, search_n = hd.hd_profile_collect(hd.HD_KERNEL_SEARCH)
+        hd.hd_profile_collect(hd.HD_KERNEL_ENCODE)
+        ms = ev0.elapsed_time(ev1) / args.steps
+        line = {"metric": "Hamming comparisons/s, batched uneven windows (200 batches, 20 ppm / 150 Da / 500 Da)",
+                "value": comparisons / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": f"{n_r}-reference library x {len(sizes)} batches "
+                                       f"({int(sizes.sum())} queries, sizes {int(sizes.min())}..{int(sizes.max())}), "
+                                       f"D={D}, charge 1-5, windows round-robin", "dim": D,
+                           "n_queries": int(qs.n), "n_batches": int(len(sizes))},
+                "queries_per_s": qs.n / (ms / 1e3), "comparisons_per_step": comparisons,
+                "batch_latency_ms": {"all_batches_one_graph": ms},
+                "graph_kernel_nodes": plan.kernel_nodes, "gpu_launches": plan.kernel_nodes * args.steps,
+                "autotune": {"best": best, "candidates": len(table)},
+                "search_kernel_ms": search_ms / max(1, search_n), "clocks": clocks.summary()}
+        print(json.dumps(line), flush=True)
+        plan.close()
+        lib.close()
+        ctx.close()
+        torch.cuda.empty_cache()
+
+
+# ----------------------------------------------------------------- serving
+def run_serving(args):
+    """Continuous-batching server on the resident 1,000,000-reference D=8192
+    library: Poisson-arriving requests of 1..5000 spectra (log-uniform), +-500,
+    top-5, offered at 50..2000 requests/s.  Per load: p50/p99 latency (submit
+    to results in host memory) and sustained queries/s.  One JSON line."""
+    import torch
+    from paper_2211_16422_gb300 import build, hd
+    build.build()
+    spec = synth.WORKLOADS["serving"]
+    rng = np.random.Generator(np.random.PCG64(spec["seed"]))
+    n_r = max(1000, int(spec["n_refs"] * args.scale))
+    refs = synth.make_references(n_r, spec["charges"], spec["weights"], rng, decoy_fraction=spec["decoy_fraction"])
+    pool = synth.make_queries(refs, max(6000, int(60000 * args.scale)), rng)
+    D, Q, k = spec["dim"], spec["n_levels"], spec["k"]
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=Q)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32
+                                     else np.ascontiguousarray(a)).cuda()
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, seed=0)
+    r_hv = hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp))
+    lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+    del r_hv
+    hd.hd_library_prepare(lib, "tc_fp8")
+    off_t, bins_t, lv_t = hd.hd_preprocess(ctx, dev(pool.offsets), dev(pool.mz), dev(pool.intensity), **pp)
+    off = hd.as_u32(off_t)
+    nnz = int(off[-1])
+    bins, lv = hd.as_u32(bins_t[:nnz]), lv_t[:nnz].cpu().numpy()
+    hi_req = max(2, int(spec["req_hi"] * min(1.0, args.scale * 10)))
+    srv = hd.Server(ctx, lib, k=k, slots=3, max_batch_queries=16384)
+
+    def make_request(size, r):
+        a = int(r.integers(0, pool.n - size))
+        b = a + size
+        return (off[a:b + 1] - off[a], bins[off[a]:off[b]], lv[off[a]:off[b]], pool.precursor_mz[a:b],
+                pool.charge[a:b])
+
+    # warm-up: a few requests of each size class
+    wr = np.random.default_rng(1)
+    for s in (1, 100, 1000, 5000):
+        s = min(s, hi_req, pool.n - 1)
+        srv.wait(srv.submit(*make_request(s, wr), spec["tol"], spec["unit"]))
+    loads = []
+    for lam in (50, 100, 200, 500, 1000, 2000):
+        r = np.random.default_rng(100 + lam)
+        n_req = int(min(2000, max(100, lam * 6 * min(1.0, args.scale * 10))))
+        sizes = synth.batch_sizes(n_req, spec["req_lo"], hi_req, r)
+        reqs = [make_request(int(s), r) for s in sizes]
+        gaps = r.exponential(1.0 / lam, n_req)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        ids = [None] * n_req
+        t0 = time.perf_counter()
+
+        def submitter():
+            for j in range(n_req):
+                delay = t0 + arrivals[j] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                ids[j] = srv.submit(*reqs[j], spec["tol"], spec["unit"])
+
+        st0 = srv.stats()
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, qn = [], 0
+        for j in range(n_req):
+            while ids[j] is None:
+                time.sleep(0.0002)
+            _, _, info = srv.wait(ids[j])
+            lat.append(info["latency_s"])
+            qn += info["n_queries"]
+        t_end = time.perf_counter()
+        th.join()
+        st1 = srv.stats()
+        lat_ms = np.asarray(lat) * 1e3
+        loads.append({"offered_req_per_s": lam, "requests": n_req, "queries": qn,
+                      "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                      "mean_ms": float(lat_ms.mean()), "completed_req_per_s": n_req / (t_end - t0),
+                      "queries_per_s": qn / (t_end - t0), "batches": st1["batches"] - st0["batches"],
+                      "max_inflight_batches": st1["max_inflight"]})
+        print(json.dumps({"load": loads[-1]}), file=sys.stderr, flush=True)
+    srv.close()
+    best = max(l["queries_per_s"] for l in loads)
+    line = {"metric": "serving: sustained queries/s and p50/p99 request latency under Poisson load, D=8192, +-500",
+            "value": best, "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{n_r}-reference resident library, requests of {spec['req_lo']}..{hi_req} "
+                                   "spectra (log-uniform), Poisson arrivals", "dim": D, "k": k,
+                       "server": {"slots": 3, "max_batch_queries": 16384, "form": "tc_fp8"}},
+            "loads": loads}
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The oracle, as it stands, on the host cores (the paper publishes no
@@ -375,6 +551,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args, rank, world, local_rank)
 

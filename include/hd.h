@@ -205,6 +205,101 @@ HD_API hd_status hd_search_open_ex(const hd_library *lib, const uint64_t *d_q_hv
                             uint32_t k, hd_search_form form, uint32_t *d_out_idx,
                             uint16_t *d_out_dist, hd_stream stream);
 
+/* Candidate window of a class of queries (Section 3.4, Table 1): half-width
+ * `tol` in m/z units (HD_TOL_DA) or ppm of the query's precursor m/z. */
+typedef struct {
+    double tol;
+    hd_tol_unit unit;
+} hd_window;
+#define HD_MAX_WINDOWS 16
+
+/* Open search where each query carries its own window: query q uses
+ * windows[d_q_class[q]] (d_q_class NULL: every query uses windows[0]),
+ * 1 <= n_windows <= HD_MAX_WINDOWS; classes beyond n_windows-1 use the last.
+ * Queries are ordered by (class, charge, m/z) so that a block of queries
+ * shares one window width (Table 1's narrow 20 ppm and wide 500 Da searches
+ * can run in one call).  Results and padding as hd_search_open.  Async. */
+HD_API hd_status hd_search_open_multi(const hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                                      const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                                      const hd_window *windows, uint32_t n_windows, uint32_t k,
+                                      hd_search_form form, uint32_t *d_out_idx, uint16_t *d_out_dist,
+                                      hd_stream stream);
+
+/* Batched plan (no counterpart in the paper, which batches to fill memory,
+ * Section 4.1): encoding (Eq. 1) of a fixed set of query batches plus the
+ * multi-window search of all of them, captured once into a CUDA graph whose
+ * search is a single persistent launch over every batch.  The plan binds the
+ * given device buffers: refill their contents and call hd_plan_launch to run
+ * again.  d_q_hv_work [n_q][D/64] receives the query HVs.  The library's
+ * current form and schedule are frozen into the plan. */
+typedef struct hd_plan hd_plan;
+HD_API hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_offsets,
+                                const uint32_t *d_bins, const uint8_t *d_levels, const double *d_q_mz,
+                                const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                                const hd_window *windows, uint32_t n_windows, uint32_t k, hd_search_form form,
+                                uint64_t *d_q_hv_work, uint32_t *d_out_idx, uint16_t *d_out_dist,
+                                hd_plan **out);
+HD_API hd_status hd_plan_launch(hd_plan *plan, hd_stream stream);
+/* Kernel nodes in the plan's graph (the launches one hd_plan_launch makes). */
+HD_API hd_status hd_plan_info(const hd_plan *plan, uint32_t *kernel_nodes);
+HD_API void hd_plan_destroy(hd_plan *plan);
+
+/* Autotuner (no counterpart in the paper): times each search form the library
+ * is prepared for and, for the tensor-core forms, work-item shapes
+ * tile_group x super_group in {4, 8, 16} x {2, 4, 8}, on the given queries
+ * (a representative sample), and keeps the fastest as the library's
+ * HD_FORM_AUTO form and schedule.  `all` (capacity `cap`) receives every
+ * timing.  Synchronous; results never depend on the choice. */
+typedef struct {
+    hd_search_form form;
+    uint32_t tile_group, super_group;
+    double ms;
+} hd_tune_result;
+HD_API hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                                     const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                                     const hd_window *windows, uint32_t n_windows, uint32_t k,
+                                     hd_tune_result *best, hd_tune_result *all, uint32_t cap,
+                                     uint32_t *n_all);
+
+/* Continuous-batching server (no counterpart in the paper, which batches to
+ * fill memory, Section 4.1).  A scheduler thread keeps the library resident
+ * and coalesces the pending requests into batches whenever one of `slots`
+ * execution slots (each its own stream) is free and the device-memory budget
+ * allows; batches in different slots overlap on the device.  Each request's
+ * results equal those of searching it alone. */
+typedef struct hd_server hd_server;
+typedef struct {
+    uint32_t slots;               /* batches in flight at once, 1..64 */
+    uint32_t max_batch_queries;   /* most queries coalesced into one batch (a larger request runs alone) */
+    uint64_t mem_budget_bytes;    /* device bytes in-flight batches may hold; 0 = half the free memory */
+    uint32_t k;                   /* top-k of every request, 1..16 */
+    hd_search_form form;          /* scoring form of every batch */
+} hd_server_params;
+typedef struct {
+    double latency_s;             /* submit -> results in the caller's buffers */
+    double queue_s;               /* submit -> its batch started */
+    uint32_t n_queries, batch_queries;
+} hd_request_info;
+typedef struct {
+    uint64_t submitted, completed, queries, batches;
+    uint32_t max_inflight;        /* most batches seen in flight at once */
+} hd_server_stats;
+HD_API hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_params *params,
+                                  hd_server **out);
+/* Queues one request: a CSR batch of n_q spectra (h_offsets [n_q+1] into
+ * h_bins / h_levels), precursor m/z and charges, and its window.  Inputs are
+ * copied before returning; h_out_idx / h_out_dist [n_q][k] must stay valid
+ * until hd_server_wait returns for this request. */
+HD_API hd_status hd_server_submit(hd_server *srv, const uint32_t *h_offsets, const uint32_t *h_bins,
+                                  const uint8_t *h_levels, const double *h_q_mz, const uint8_t *h_q_charge,
+                                  uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *h_out_idx,
+                                  uint16_t *h_out_dist, uint64_t *request_id);
+/* Blocks until the request is done (HD_ERR_TIMEOUT after timeout_s > 0). */
+HD_API hd_status hd_server_wait(hd_server *srv, uint64_t request_id, double timeout_s, hd_request_info *info);
+HD_API hd_status hd_server_stats_get(hd_server *srv, hd_server_stats *out);
+/* Drains every queued request, then stops the scheduler. */
+HD_API void hd_server_destroy(hd_server *srv);
+
 /* End to end from host memory: copies a CSR query batch (h_offsets [n_q+1],
  * h_bins / h_levels [h_offsets[n_q]]), its precursor m/z and charges to the
  * device, encodes it with `ctx`, searches `lib`, copies the results to

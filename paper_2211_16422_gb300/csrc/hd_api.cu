@@ -137,6 +137,43 @@ struct scoped_stream {
 
 }  // namespace
 
+hd_status hd_make_qwin(const uint8_t *cls, const hd_window *windows, uint32_t n_windows, hd_qwin *out)
+{
+    HD_CHECK(windows && n_windows >= 1 && n_windows <= HD_MAX_WINDOWS,
+             "windows: need 1..16 window descriptions");
+    hd_qwin w;
+    w.cls = n_windows > 1 ? cls : nullptr;
+    w.n = n_windows;
+    for (uint32_t i = 0; i < n_windows; ++i) {
+        HD_CHECK(tol_ok(windows[i].tol), "windows: tol must be finite and >= 0");
+        HD_CHECK(windows[i].unit == HD_TOL_DA || windows[i].unit == HD_TOL_PPM, "windows: bad unit");
+        const int ppm = windows[i].unit == HD_TOL_PPM;
+        w.w[i].tol = ppm ? windows[i].tol * 1e-6 : windows[i].tol;
+        w.w[i].ppm = ppm;
+    }
+    *out = w;
+    return HD_OK;
+}
+
+hd_status hd_search_dispatch(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_charge,
+                             uint32_t n_q, const hd_qwin &win, uint32_t k, hd_search_form form, uint32_t *out_idx,
+                             uint16_t *out_dist, cudaStream_t s)
+{
+    if (form == HD_FORM_AUTO) {
+        form = lib->auto_form;
+        const bool ok = form == HD_FORM_POPC || (form == HD_FORM_TC_FP8 && lib->x_fp8) ||
+                        (form == HD_FORM_TC_BF16 && lib->x_bf16);
+        if (!ok) form = lib->x_fp8 ? HD_FORM_TC_FP8 : (lib->x_bf16 ? HD_FORM_TC_BF16 : HD_FORM_POPC);
+    }
+    if (form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16) {
+        const bool fp8 = form == HD_FORM_TC_FP8;
+        HD_CHECK(fp8 ? lib->x_fp8 != nullptr || lib->n == 0 : lib->x_bf16 != nullptr || lib->n == 0,
+                 "hd_search_open: call hd_library_prepare for this form first");
+        return hd_search_mma_run(lib, fp8, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
+    }
+    return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
+}
+
 extern "C" {
 
 const char *hd_status_string(hd_status s)
@@ -288,14 +325,14 @@ hd_status hd_build_library(hd_ctx *ctx, const uint64_t *d_hv, const double *d_pr
     if (n_refs > 0) {
         hd_arena plan;
         uint32_t *perm = plan.take<uint32_t>(n_refs);
-        hd_sort_charge_mz(d_prec_mz, d_charge, n_refs, nullptr, plan, ss.s);
+        hd_sort_charge_mz(d_prec_mz, d_charge, nullptr, n_refs, nullptr, plan, ss.s);
         hd_arena ar;
         if (cudaMallocAsync((void **)&ar.base, plan.used, ss.s) != cudaSuccess) {
             cudaGetLastError();
             return fail(hd_fail(HD_ERR_OOM, "hd_build_library: scratch allocation failed"));
         }
         perm = ar.take<uint32_t>(n_refs);
-        hd_sort_charge_mz(d_prec_mz, d_charge, n_refs, perm, ar, ss.s);
+        hd_sort_charge_mz(d_prec_mz, d_charge, nullptr, n_refs, perm, ar, ss.s);
         hd_count_launches(1), k_gather_rows<<<hd_ceil_div(n_refs, 8), 256, 0, ss.s>>>(d_hv, d_prec_mz, d_charge, perm, n_refs,
                                                                 lib->W, lib->hv, lib->mz, lib->charge,
                                                                 lib->orig, lib->status.dev);
@@ -381,7 +418,7 @@ hd_status hd_query_windows(const hd_library *lib, const double *d_q_mz, const ui
     HD_CHECK(d_q_mz && d_q_charge && d_lo && d_hi, "hd_query_windows: null buffer");
     hd_status st = check_device(lib->device);
     if (st != HD_OK) return st;
-    hd_windows_launch(lib, d_q_mz, d_q_charge, nullptr, n_q, tol, unit == HD_TOL_PPM, d_lo, d_hi,
+    hd_windows_launch(lib, d_q_mz, d_q_charge, nullptr, n_q, hd_single_window(tol, unit == HD_TOL_PPM), d_lo, d_hi,
                       (cudaStream_t)stream);
     HD_CUDA_TRY(cudaGetLastError());
     return HD_OK;
@@ -403,16 +440,29 @@ hd_status hd_search_open_ex(const hd_library *lib, const uint64_t *d_q_hv, const
     HD_CHECK(aligned16(d_q_hv), "hd_search_open: d_q_hv must be 16-byte aligned");
     hd_status st = check_device(lib->device);
     if (st != HD_OK) return st;
-    if (form == HD_FORM_AUTO) form = lib->x_fp8 ? HD_FORM_TC_FP8 : (lib->x_bf16 ? HD_FORM_TC_BF16 : HD_FORM_POPC);
-    if (form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16) {
-        const bool fp8 = form == HD_FORM_TC_FP8;
-        HD_CHECK(fp8 ? lib->x_fp8 != nullptr || lib->n == 0 : lib->x_bf16 != nullptr || lib->n == 0,
-                 "hd_search_open: call hd_library_prepare for this form first");
-        return hd_search_mma_run(lib, fp8, d_q_hv, d_q_mz, d_q_charge, n_q, tol, unit == HD_TOL_PPM, k, d_out_idx,
-                                 d_out_dist, (cudaStream_t)stream);
-    }
-    return hd_search_popc_run(lib, d_q_hv, d_q_mz, d_q_charge, n_q, tol, unit == HD_TOL_PPM, k, d_out_idx,
-                              d_out_dist, (cudaStream_t)stream);
+    return hd_search_dispatch(lib, d_q_hv, d_q_mz, d_q_charge, n_q, hd_single_window(tol, unit == HD_TOL_PPM), k,
+                              form, d_out_idx, d_out_dist, (cudaStream_t)stream);
+}
+
+hd_status hd_search_open_multi(const hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                               const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                               const hd_window *windows, uint32_t n_windows, uint32_t k, hd_search_form form,
+                               uint32_t *d_out_idx, uint16_t *d_out_dist, hd_stream stream)
+{
+    HD_CHECK(lib, "hd_search_open_multi: null library");
+    HD_CHECK(k >= 1 && k <= 16, "hd_search_open_multi: k must be in [1, 16]");
+    HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
+             "hd_search_open_multi: unknown form");
+    hd_qwin win;
+    hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
+    if (st != HD_OK) return st;
+    if (n_q == 0) return HD_OK;
+    HD_CHECK(d_q_hv && d_q_mz && d_q_charge && d_out_idx && d_out_dist, "hd_search_open_multi: null buffer");
+    HD_CHECK(aligned16(d_q_hv), "hd_search_open_multi: d_q_hv must be 16-byte aligned");
+    st = check_device(lib->device);
+    if (st != HD_OK) return st;
+    return hd_search_dispatch(lib, d_q_hv, d_q_mz, d_q_charge, n_q, win, k, form, d_out_idx, d_out_dist,
+                              (cudaStream_t)stream);
 }
 
 hd_status hd_search_open(const hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
@@ -474,7 +524,8 @@ hd_status hd_search_host(hd_ctx *ctx, const hd_library *lib, const uint32_t *h_o
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        st = hd_search_popc_run(lib, hv, mz, z, n_q, tol, unit == HD_TOL_PPM, k, oi, od, s);
+        st = hd_search_dispatch(lib, hv, mz, z, n_q, hd_single_window(tol, unit == HD_TOL_PPM), k, HD_FORM_AUTO,
+                                oi, od, s);
         if (st != HD_OK) {
             cudaFreeAsync(ar.base, s);
             cudaStreamSynchronize(s);

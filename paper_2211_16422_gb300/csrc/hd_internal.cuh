@@ -72,6 +72,7 @@ struct hd_library {
     uint8_t *x_fp8 = nullptr;      // [n][D] bipolar e4m3 rows (tensor-core form), optional
     uint8_t *x_bf16 = nullptr;     // [n][2D] bipolar bf16 rows (tensor-core form), optional
     hd_mma_tuning mma_tuning;
+    hd_search_form auto_form = HD_FORM_AUTO;   // set by the autotuner
     uint32_t charge_start_h[257] = {};
     hd_status_word status;
 };
@@ -128,30 +129,52 @@ hd_status hd_preprocess_launch(const hd_preprocess_params &pp, const uint32_t *r
 void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins,
                       const uint8_t *levels, uint32_t n, uint64_t *out, cudaStream_t s);
 
-// Stable sort of n items by (charge, m/z): writes the permutation `perm`
-// (perm[rank] = input index).  Scratch from `arena` (sized by a first call
-// with arena.base == nullptr).
-void hd_sort_charge_mz(const double *mz, const uint8_t *charge, uint32_t n, uint32_t *perm,
-                       hd_arena &arena, cudaStream_t s);
+// Candidate windows of a query set (Section 3.4): query q uses window
+// w[cls[q]] (w[0] when cls is null).  For ppm, `tol` holds tol * 1e-6 and the
+// window half-width is mz_q * tol.  Passed to kernels by value.
+struct hd_win {
+    double tol;
+    int ppm;
+};
+struct hd_qwin {
+    const uint8_t *cls = nullptr;
+    uint32_t n = 1;
+    hd_win w[HD_MAX_WINDOWS] = {};
+};
+hd_qwin hd_single_window(double tol, int ppm);
+
+// Stable sort of n items by (group, charge, m/z), group optional: writes the
+// permutation `perm` (perm[rank] = input index).  Scratch from `arena`
+// (sized by a first call with arena.base == nullptr).
+void hd_sort_charge_mz(const double *mz, const uint8_t *charge, const uint8_t *group, uint32_t n,
+                       uint32_t *perm, hd_arena &arena, cudaStream_t s);
 
 void hd_windows_launch(const hd_library *lib, const double *q_mz, const uint8_t *q_charge,
-                       const uint32_t *perm, uint32_t n_q, double tol, int ppm, uint32_t *lo,
+                       const uint32_t *perm, uint32_t n_q, const hd_qwin &win, uint32_t *lo,
                        uint32_t *hi, cudaStream_t s);
 
 hd_status hd_search_popc_run(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
-                             const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
+                             const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win,
                              uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);
 
 // hd_search_popc_run on caller-provided device scratch (nothing allocated);
 // fails with HD_ERR_INVALID_ARG when the request needs more than
 // `scratch_bytes`.
 hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
-                                     const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
+                                     const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win,
                                      uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s,
                                      void *scratch, size_t scratch_bytes);
 
 // Tensor-core form: the bipolar copy of the library rows, and the search.
 hd_status hd_library_expand(hd_library *lib, bool fp8, cudaStream_t s);
 hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_hv, const double *q_mz,
-                            const uint8_t *q_charge, uint32_t n_q, double tol, int ppm, uint32_t k,
+                            const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
                             uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);
+
+// Search dispatch shared by the entry points: resolves HD_FORM_AUTO and runs
+// the chosen form.
+hd_status hd_search_dispatch(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
+                             const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
+                             hd_search_form form, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);
+// Host-side validation of a window table into an hd_qwin.
+hd_status hd_make_qwin(const uint8_t *cls, const hd_window *windows, uint32_t n_windows, hd_qwin *out);

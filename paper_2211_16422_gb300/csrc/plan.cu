@@ -1,0 +1,196 @@
+// plan.cu -- batched plans (one CUDA graph for encode + search of a fixed
+// set of query batches) and the schedule autotuner.  Host code only: every
+// computation is one of libhd's kernels.
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "hd_internal.cuh"
+
+struct hd_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t kernel_nodes = 0;
+    int device = 0;
+};
+
+namespace {
+
+struct scoped_stream {
+    cudaStream_t s = nullptr;
+    ~scoped_stream()
+    {
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
+void plan_release(hd_plan *p)
+{
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_offsets, const uint32_t *d_bins,
+                         const uint8_t *d_levels, const double *d_q_mz, const uint8_t *d_q_charge,
+                         const uint8_t *d_q_class, uint32_t n_q, const hd_window *windows, uint32_t n_windows,
+                         uint32_t k, hd_search_form form, uint64_t *d_q_hv_work, uint32_t *d_out_idx,
+                         uint16_t *d_out_dist, hd_plan **out)
+{
+    if (!out) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null output");
+    *out = nullptr;
+    if (!ctx || !lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null ctx or library");
+    if (ctx->p.dim != lib->dim) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: ctx and library dims differ");
+    if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: k must be in [1, 16]");
+    if (n_q == 0) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: empty query set");
+    if (!d_offsets || !d_bins || !d_levels || !d_q_mz || !d_q_charge || !d_q_hv_work || !d_out_idx || !d_out_dist)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null buffer");
+    if (reinterpret_cast<uintptr_t>(d_q_hv_work) & 15u)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: d_q_hv_work must be 16-byte aligned");
+    hd_qwin win;
+    hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
+    if (st != HD_OK) return st;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != lib->device || dev != ctx->device)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: objects belong to another device");
+
+    scoped_stream ss;
+    HD_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+    auto body = [&]() -> hd_status {
+        hd_encode_launch(ctx, d_offsets, d_bins, d_levels, n_q, d_q_hv_work, ss.s);
+        HD_CUDA_TRY(cudaGetLastError());
+        return hd_search_dispatch(lib, d_q_hv_work, d_q_mz, d_q_charge, n_q, win, k, form, d_out_idx, d_out_dist,
+                                  ss.s);
+    };
+    // one eager run: kernel attributes and lazy module loading happen outside capture
+    st = body();
+    if (st != HD_OK) return st;
+    HD_CUDA_TRY(cudaStreamSynchronize(ss.s));
+
+    hd_plan *p = new hd_plan;
+    p->device = dev;
+    cudaError_t e = cudaStreamBeginCapture(ss.s, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        plan_release(p);
+        return hd_cuda_fail(e, "hd_plan_create: begin capture");
+    }
+    st = body();
+    e = cudaStreamEndCapture(ss.s, &p->graph);
+    if (st != HD_OK || e != cudaSuccess) {
+        plan_release(p);
+        return st != HD_OK ? st : hd_cuda_fail(e, "hd_plan_create: end capture");
+    }
+    e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (e != cudaSuccess) {
+        plan_release(p);
+        return hd_cuda_fail(e, "hd_plan_create: instantiate");
+    }
+    size_t n = 0;
+    cudaGraphGetNodes(p->graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) cudaGraphGetNodes(p->graph, nodes.data(), &n);
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++p->kernel_nodes;
+    }
+    *out = p;
+    return HD_OK;
+}
+
+hd_status hd_plan_launch(hd_plan *plan, hd_stream stream)
+{
+    if (!plan) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_launch: null plan");
+    HD_CUDA_TRY(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+    hd_count_launches(plan->kernel_nodes);
+    return HD_OK;
+}
+
+hd_status hd_plan_info(const hd_plan *plan, uint32_t *kernel_nodes)
+{
+    if (!plan) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_info: null plan");
+    if (kernel_nodes) *kernel_nodes = plan->kernel_nodes;
+    return HD_OK;
+}
+
+void hd_plan_destroy(hd_plan *plan) { plan_release(plan); }
+
+hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                              const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                              const hd_window *windows, uint32_t n_windows, uint32_t k, hd_tune_result *best,
+                              hd_tune_result *all, uint32_t cap, uint32_t *n_all)
+{
+    if (!lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: null library");
+    if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: k must be in [1, 16]");
+    if (n_q == 0 || !d_q_hv || !d_q_mz || !d_q_charge)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: empty or null query set");
+    hd_qwin win;
+    hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
+    if (st != HD_OK) return st;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != lib->device)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: library belongs to another device");
+
+    std::vector<hd_tune_result> cand;
+    cand.push_back({HD_FORM_POPC, 0, 0, 0.0});
+    const uint32_t tgs[3] = {4, 8, 16}, sgs[3] = {2, 4, 8};
+    for (hd_search_form f : {HD_FORM_TC_FP8, HD_FORM_TC_BF16}) {
+        if ((f == HD_FORM_TC_FP8 && !lib->x_fp8) || (f == HD_FORM_TC_BF16 && !lib->x_bf16)) continue;
+        for (uint32_t tg : tgs)
+            for (uint32_t sg : sgs) cand.push_back({f, tg, sg, 0.0});
+    }
+    scoped_stream ss;
+    HD_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+    uint32_t *oi = nullptr;
+    uint16_t *od = nullptr;
+    if (cudaMalloc(&oi, (size_t)n_q * k * 4) != cudaSuccess || cudaMalloc(&od, (size_t)n_q * k * 2) != cudaSuccess) {
+        cudaFree(oi);
+        cudaGetLastError();
+        return hd_fail(HD_ERR_OOM, "hd_library_autotune: output allocation failed");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const hd_mma_tuning saved = lib->mma_tuning;
+    st = HD_OK;
+    for (auto &c : cand) {
+        lib->mma_tuning.tile_group = c.tile_group;
+        lib->mma_tuning.super_group = c.super_group;
+        double bestms = 1e30;
+        for (int rep = 0; rep < 3 && st == HD_OK; ++rep) {   // first run warms up
+            cudaEventRecord(e0, ss.s);
+            st = hd_search_dispatch(lib, d_q_hv, d_q_mz, d_q_charge, n_q, win, k, c.form, oi, od, ss.s);
+            cudaEventRecord(e1, ss.s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = hd_fail(HD_ERR_CUDA, "hd_library_autotune: run failed");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) bestms = std::min(bestms, (double)ms);
+        }
+        c.ms = bestms;
+        if (st != HD_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(oi);
+    cudaFree(od);
+    if (st != HD_OK) {
+        lib->mma_tuning = saved;
+        return st;
+    }
+    const auto it = std::min_element(cand.begin(), cand.end(),
+                                     [](const hd_tune_result &a, const hd_tune_result &b) { return a.ms < b.ms; });
+    lib->mma_tuning.tile_group = it->tile_group;
+    lib->mma_tuning.super_group = it->super_group;
+    lib->auto_form = it->form;
+    if (best) *best = *it;
+    if (n_all) *n_all = (uint32_t)cand.size();
+    if (all)
+        for (uint32_t i = 0; i < cand.size() && i < cap; ++i) all[i] = cand[i];
+    return HD_OK;
+}
+
+}  // extern "C"

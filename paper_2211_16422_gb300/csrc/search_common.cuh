@@ -15,7 +15,7 @@ constexpr uint64_t KEY_NONE = ~0ull;
 // ----------------------------------------------------------------- windows
 static __global__ void k_windows(const double *__restrict__ lib_mz, const uint32_t *__restrict__ cstart,
                           const double *__restrict__ q_mz, const uint8_t *__restrict__ q_z,
-                          const uint32_t *__restrict__ perm, uint32_t n_q, double tol, int ppm,
+                          const uint32_t *__restrict__ perm, uint32_t n_q, hd_qwin win,
                           uint32_t *__restrict__ lo, uint32_t *__restrict__ hi)
 {
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -23,7 +23,9 @@ static __global__ void k_windows(const double *__restrict__ lib_mz, const uint32
     const uint32_t q = perm ? perm[s] : s;
     const double m = q_mz[q];
     const uint32_t c = q_z[q];
-    const double t = ppm ? __dmul_rn(m, tol) : tol;   // tol holds tol*1e-6 for ppm
+    const uint32_t wc = win.cls ? min((uint32_t)win.cls[q], win.n - 1) : 0u;
+    const hd_win w = win.w[wc];
+    const double t = w.ppm ? __dmul_rn(m, w.tol) : w.tol;   // tol holds tol*1e-6 for ppm
     const double nt = -t;
     const uint32_t p0 = cstart[c], p1 = cstart[c + 1];
     // first row with (mz_r - m) >= -t

@@ -489,7 +489,7 @@ hd_status make_map(CUtensorMap *m, const void *base, uint64_t rows, uint32_t row
 
 template <int K, bool FP8>
 hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
-                  uint32_t n_q, double tol, int ppm, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
+                  uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
                   cudaStream_t s, const hd_mma_tuning &tune)
 {
     const uint32_t n_blocks = (n_q + TM - 1) / TM;
@@ -522,7 +522,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     uint8_t *qx;
     hd_arena plan;
     carve(plan, &perm, &lo, &hi, &bt0, &bt1, &pst, &top, &locks, &qx);
-    hd_sort_charge_mz(q_mz, q_z, n_q, nullptr, plan, s);
+    hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, nullptr, plan, s);
     hd_arena ar;
     if (cudaMallocAsync((void **)&ar.base, plan.used, s) != cudaSuccess) {
         cudaGetLastError();
@@ -538,11 +538,10 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     }
     HD_CUDA_TRY(cudaMemsetAsync(top, 0xFF, (size_t)n_q * K * sizeof(uint64_t), s));
     HD_CUDA_TRY(cudaMemsetAsync(locks, 0, (size_t)n_blocks * sizeof(uint32_t), s));
-    hd_sort_charge_mz(q_mz, q_z, n_q, perm, ar, s);
+    hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, perm, ar, s);
     hd_count_launches(1), k_expand<FP8><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
-    const double tq = ppm ? tol * 1e-6 : tol;
     hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z,
-                                                                          perm, n_q, tq, ppm, lo, hi);
+                                                                          perm, n_q, win, lo, hi);
     hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, n_blocks, tg, sg, n_super, bt0, bt1, pst);
     mma_args ma{lib->orig, lo, hi, bt0, bt1, pst, top, locks, lib->status.dev, n_q, n_blocks, (uint32_t)n_pairs,
                 tg, sg, lib->dim, row_bytes};
@@ -558,14 +557,14 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
 
 template <bool FP8>
 hd_status run_fmt(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
-                  uint32_t n_q, double tol, int ppm, uint32_t k, uint32_t *oi, uint16_t *od, cudaStream_t s,
+                  uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *oi, uint16_t *od, cudaStream_t s,
                   const hd_mma_tuning &tu)
 {
-    if (k <= 1) return run_mma<1, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
-    if (k <= 2) return run_mma<2, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
-    if (k <= 4) return run_mma<4, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
-    if (k <= 8) return run_mma<8, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
-    return run_mma<16, FP8>(lib, q_hv, q_mz, q_z, n_q, tol, ppm, k, oi, od, s, tu);
+    if (k <= 1) return run_mma<1, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    if (k <= 2) return run_mma<2, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    if (k <= 4) return run_mma<4, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    if (k <= 8) return run_mma<8, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    return run_mma<16, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
 }
 
 }  // namespace
@@ -589,13 +588,13 @@ hd_status hd_library_expand(hd_library *lib, bool fp8, cudaStream_t s)
 }
 
 hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_hv, const double *q_mz,
-                            const uint8_t *q_charge, uint32_t n_q, double tol, int ppm, uint32_t k,
+                            const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
                             uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s)
 {
-    if (lib->n == 0) return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
+    if (lib->n == 0) return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
     hd_mma_tuning tu = lib->mma_tuning;
     if (tu.tile_group == 0) tu.tile_group = 8;
     if (tu.super_group == 0) tu.super_group = 4;
-    if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s, tu);
-    return run_fmt<false>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s, tu);
+    if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
+    return run_fmt<false>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
 }

@@ -77,7 +77,8 @@ extern "C" hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_
     void *scratch = nullptr;
     const hd_status st = scratch_address(dev, &scratch);
     if (st != HD_OK) return st;
-    return hd_search_popc_run_scratch(lib, d_q_hv, d_q_mz, d_q_charge, n_q, tol, unit == HD_TOL_PPM, k,
+    return hd_search_popc_run_scratch(lib, d_q_hv, d_q_mz, d_q_charge, n_q,
+                                      hd_single_window(tol, unit == HD_TOL_PPM), k,
                                       d_out_idx, d_out_dist, (cudaStream_t)stream, scratch,
                                       HD_NOALLOC_SCRATCH_BYTES);
 }

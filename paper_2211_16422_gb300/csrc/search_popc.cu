@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
 
 template <int K>
 hd_status run_k(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
-                const uint8_t *q_z, uint32_t n_q, double tol, int ppm, uint32_t k,
+                const uint8_t *q_z, uint32_t n_q, const hd_qwin &win, uint32_t k,
                 uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s, char *ext = nullptr,
                 size_t ext_cap = 0)
 {
@@ -248,7 +248,7 @@ hd_status run_k(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
     uint64_t *part;
     hd_arena plan;
     carve(plan, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part);
-    hd_sort_charge_mz(q_mz, q_z, n_q, nullptr, plan, s);
+    hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, nullptr, plan, s);
     hd_arena ar;
     if (ext) {   // caller-provided scratch: nothing is allocated
         if (plan.used > ext_cap)
@@ -261,10 +261,9 @@ hd_status run_k(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
         if (e != cudaSuccess) return hd_fail(HD_ERR_OOM, "search scratch allocation failed");
     }
     carve(ar, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part);
-    hd_sort_charge_mz(q_mz, q_z, n_q, perm, ar, s);
-    const double tq = ppm ? tol * 1e-6 : tol;
+    hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, perm, ar, s);
     hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z, perm, n_q,
-                                                    tq, ppm, lo, hi);
+                                                    win, lo, hi);
     hd_count_launches(1), k_worklist<<<1, 1024, 0, s>>>(lo, hi, n_q, BQ, BR, n_blocks, target_items, blo, bhi, bnt, ist, meta);
     search_args sa{lib->hv, lib->orig, q_hv, perm, lo, hi, blo, bhi, bnt, ist, meta, part,
                    lib->status.dev, n_q, n_blocks, lib->W};
@@ -281,32 +280,40 @@ hd_status run_k(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
 }  // namespace
 
 void hd_windows_launch(const hd_library *lib, const double *q_mz, const uint8_t *q_charge,
-                       const uint32_t *perm, uint32_t n_q, double tol, int ppm, uint32_t *lo,
+                       const uint32_t *perm, uint32_t n_q, const hd_qwin &win, uint32_t *lo,
                        uint32_t *hi, cudaStream_t s)
 {
-    const double tq = ppm ? tol * 1e-6 : tol;
     hd_count_launches(1), hd_search::k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_charge, perm,
-                                                    n_q, tq, ppm, lo, hi);
+                                                    n_q, win, lo, hi);
+}
+
+hd_qwin hd_single_window(double tol, int ppm)
+{
+    hd_qwin w;
+    w.n = 1;
+    w.w[0].tol = ppm ? tol * 1e-6 : tol;
+    w.w[0].ppm = ppm;
+    return w;
 }
 
 hd_status hd_search_popc_run(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
-                             const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
+                             const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win,
                              uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s)
 {
-    if (k <= 1) return run_k<1>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
-    if (k <= 2) return run_k<2>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
-    if (k <= 4) return run_k<4>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
-    if (k <= 8) return run_k<8>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
-    return run_k<16>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s);
+    if (k <= 1) return run_k<1>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
+    if (k <= 2) return run_k<2>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
+    if (k <= 4) return run_k<4>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
+    if (k <= 8) return run_k<8>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
+    return run_k<16>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
 }
 
 hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
-                                     const uint8_t *q_charge, uint32_t n_q, double tol, int ppm,
+                                     const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win,
                                      uint32_t k, uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s,
                                      void *scratch, size_t scratch_bytes)
 {
     char *x = static_cast<char *>(scratch);
-#define HD_RUN_K(KK) run_k<KK>(lib, q_hv, q_mz, q_charge, n_q, tol, ppm, k, out_idx, out_dist, s, x, scratch_bytes)
+#define HD_RUN_K(KK) run_k<KK>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, x, scratch_bytes)
     if (k <= 1) return HD_RUN_K(1);
     if (k <= 2) return HD_RUN_K(2);
     if (k <= 4) return HD_RUN_K(4);

@@ -115,15 +115,16 @@ __global__ void k_make_keys(const double *__restrict__ mz, uint32_t n, uint64_t 
     }
 }
 
-template <bool CHARGE>
+// BYTE_KEY: the digit is aux[idx[i]] (charge or group); else a byte of keys[i].
+template <bool BYTE_KEY>
 __device__ __forceinline__ uint32_t digit_of(const uint64_t *keys, const uint32_t *idx,
-                                             const uint8_t *charge, uint32_t i, int shift)
+                                             const uint8_t *aux, uint32_t i, int shift)
 {
-    if (CHARGE) return charge[idx[i]];
+    if (BYTE_KEY) return aux[idx[i]];
     return (uint32_t)(keys[i] >> shift) & 0xFFu;
 }
 
-template <bool CHARGE>
+template <bool BYTE_KEY>
 __global__ void __launch_bounds__(RS_THREADS)
 k_hist(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx,
        const uint8_t *__restrict__ charge, uint32_t n, int shift, uint32_t *__restrict__ hist)
@@ -134,13 +135,13 @@ k_hist(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ idx,
     const uint32_t base = blockIdx.x * RS_TILE;
     for (int r = 0; r < RS_ROUNDS; ++r) {
         const uint32_t i = base + r * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[digit_of<CHARGE>(keys, idx, charge, i, shift)], 1u);
+        if (i < n) atomicAdd(&h[digit_of<BYTE_KEY>(keys, idx, charge, i, shift)], 1u);
     }
     __syncthreads();
     hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-template <bool CHARGE>
+template <bool BYTE_KEY>
 __global__ void __launch_bounds__(RS_THREADS)
 k_scatter(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ idx_in,
           const uint8_t *__restrict__ charge, uint32_t n, int shift,
@@ -157,7 +158,7 @@ k_scatter(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ idx
     for (int r = 0; r < RS_ROUNDS; ++r) {
         const uint32_t i = base + r * RS_THREADS + threadIdx.x;
         const bool ok = i < n;
-        const uint32_t d = ok ? digit_of<CHARGE>(keys_in, idx_in, charge, i, shift) : 256u + lane;
+        const uint32_t d = ok ? digit_of<BYTE_KEY>(keys_in, idx_in, charge, i, shift) : 256u + lane;
 #pragma unroll
         for (int j = 0; j < NW; ++j) wcnt[j][threadIdx.x] = 0;
         __syncthreads();
@@ -168,7 +169,7 @@ k_scatter(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ idx
         if (ok) {
             uint32_t pos = run[d] + rank;
             for (int j = 0; j < w; ++j) pos += wcnt[j][d];
-            if (!CHARGE) keys_out[pos] = keys_in[i];
+            if (!BYTE_KEY) keys_out[pos] = keys_in[i];
             idx_out[pos] = idx_in[i];
         }
         __syncthreads();
@@ -182,8 +183,8 @@ k_scatter(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ idx
 
 }  // namespace
 
-void hd_sort_charge_mz(const double *mz, const uint8_t *charge, uint32_t n, uint32_t *perm,
-                       hd_arena &arena, cudaStream_t s)
+void hd_sort_charge_mz(const double *mz, const uint8_t *charge, const uint8_t *group, uint32_t n,
+                       uint32_t *perm, hd_arena &arena, cudaStream_t s)
 {
     const uint32_t tiles = (n + RS_TILE - 1) / RS_TILE;
     uint64_t *ka = arena.take<uint64_t>(n), *kb = arena.take<uint64_t>(n);
@@ -210,5 +211,11 @@ void hd_sort_charge_mz(const double *mz, const uint8_t *charge, uint32_t n, uint
     }
     hd_count_launches(1), k_hist<true><<<tiles, RS_THREADS, 0, s>>>(ka, ia, charge, n, 0, hist);
     scan();
-    hd_count_launches(1), k_scatter<true><<<tiles, RS_THREADS, 0, s>>>(ka, ia, charge, n, 0, offs, kb, perm);
+    hd_count_launches(1), k_scatter<true><<<tiles, RS_THREADS, 0, s>>>(ka, ia, charge, n, 0, offs, kb,
+                                                                        group ? ib : perm);
+    if (group) {   // most significant key last
+        hd_count_launches(1), k_hist<true><<<tiles, RS_THREADS, 0, s>>>(ka, ib, group, n, 0, hist);
+        scan();
+        hd_count_launches(1), k_scatter<true><<<tiles, RS_THREADS, 0, s>>>(ka, ib, group, n, 0, offs, kb, perm);
+    }
 }

@@ -41,6 +41,22 @@ class _PPParams(C.Structure):
                 ("max_peaks", C.c_uint32), ("n_levels", C.c_uint32)]
 
 
+class _Window(C.Structure):
+    _fields_ = [("tol", C.c_double), ("unit", C.c_int)]
+
+
+class _TuneResult(C.Structure):
+    _fields_ = [("form", C.c_int), ("tile_group", C.c_uint32), ("super_group", C.c_uint32), ("ms", C.c_double)]
+
+
+def _windows(windows):
+    """[(tol, 'da'|'ppm'), ...] -> ctypes array of hd_window."""
+    arr = (_Window * len(windows))()
+    for i, (tol, unit) in enumerate(windows):
+        arr[i].tol, arr[i].unit = float(tol), _unit(unit)
+    return arr
+
+
 _lib = None
 _lock = threading.Lock()
 P, u32, u64, dbl, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_double, C.c_int
@@ -67,6 +83,17 @@ _SIGS = {
     "hd_search_open_ex": ([P, P, P, P, u32, dbl, i32, u32, i32, P, P, P], i32),
     "hd_search_host": ([P, P, P, P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_search_open_noalloc": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
+    "hd_search_open_multi": ([P, P, P, P, P, u32, P, u32, u32, i32, P, P, P], i32),
+    "hd_plan_create": ([P, P, P, P, P, P, P, P, u32, P, u32, u32, i32, P, P, P, P], i32),
+    "hd_plan_launch": ([P, P], i32),
+    "hd_plan_info": ([P, P], i32),
+    "hd_plan_destroy": ([P], None),
+    "hd_library_autotune": ([P, P, P, P, P, u32, P, u32, u32, P, P, u32, P], i32),
+    "hd_server_create": ([P, P, P, P], i32),
+    "hd_server_submit": ([P, P, P, P, P, P, u32, dbl, i32, P, P, P], i32),
+    "hd_server_wait": ([P, u64, dbl, P], i32),
+    "hd_server_stats_get": ([P, P], i32),
+    "hd_server_destroy": ([P], None),
     "hd_profile_enable": ([i32], i32),
     "hd_profile_collect": ([i32, P, P], i32),
     "hd_launch_count": ([], u64),
@@ -297,6 +324,155 @@ def hd_search_open_noalloc(lib: Library, q_hv, q_mz, q_charge, tol, unit="da", k
     _check(load().hd_search_open_noalloc(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), n, float(tol),
                                          _unit(unit), int(k), _ptr(out_idx), _ptr(out_dist), _stream(stream)))
     return out_idx, out_dist
+
+
+def hd_search_open_multi(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=1, form="auto",
+                         out_idx=None, out_dist=None, stream=None):
+    """Search with a window per query: query q uses windows[q_class[q]]; `windows` is a list of
+    (tol, unit) pairs (at most 16); q_class a uint8 CUDA tensor or None."""
+    q_hv = _dev(q_hv, torch.int64, "q_hv")
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    if q_class is not None:
+        q_class = _dev(q_class, torch.uint8, "q_class")
+    n = q_mz.numel()
+    if out_idx is None:
+        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    if out_dist is None:
+        out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
+    w = _windows(windows)
+    _check(load().hd_search_open_multi(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), _ptr(q_class), n, w,
+                                       len(windows), int(k), FORMS[form], _ptr(out_idx), _ptr(out_dist),
+                                       _stream(stream)))
+    return out_idx, out_dist
+
+
+class Plan:
+    """Encode + multi-window search of a fixed query set, captured as one CUDA graph.
+    Keeps references to every bound buffer; refill them in place and call launch()."""
+
+    def __init__(self, ctx: Ctx, lib: Library, offsets, bins, levels, q_mz, q_charge, q_class, windows, k=1,
+                 form="auto"):
+        self.offsets = _dev(offsets, torch.int32, "offsets")
+        self.bins = _dev(bins, torch.int32, "bins")
+        self.levels = _dev(levels, torch.uint8, "levels")
+        self.q_mz = _dev(q_mz, torch.float64, "q_mz")
+        self.q_charge = _dev(q_charge, torch.uint8, "q_charge")
+        self.q_class = None if q_class is None else _dev(q_class, torch.uint8, "q_class")
+        n = self.q_mz.numel()
+        self.q_hv = torch.empty((n, ctx.dim // 64), dtype=torch.int64, device="cuda")
+        self.out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+        self.out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
+        self._keep = (ctx, lib)
+        w = _windows(windows)
+        h = C.c_void_p()
+        torch.cuda.current_stream().synchronize()
+        _check(load().hd_plan_create(ctx.handle, lib.handle, _ptr(self.offsets), _ptr(self.bins),
+                                     _ptr(self.levels), _ptr(self.q_mz), _ptr(self.q_charge), _ptr(self.q_class),
+                                     n, w, len(windows), int(k), FORMS[form], _ptr(self.q_hv),
+                                     _ptr(self.out_idx), _ptr(self.out_dist), C.byref(h)))
+        self._h = h
+        nodes = C.c_uint32()
+        _check(load().hd_plan_info(h, C.byref(nodes)))
+        self.kernel_nodes = nodes.value
+
+    def launch(self, stream=None):
+        _check(load().hd_plan_launch(self._h, _stream(stream)))
+        return self.out_idx, self.out_dist
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hd_plan_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def hd_library_autotune(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=1):
+    """Times every prepared form and schedule; keeps the fastest as the library's 'auto'.
+    Returns (best, all) as dicts."""
+    q_hv = _dev(q_hv, torch.int64, "q_hv")
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    if q_class is not None:
+        q_class = _dev(q_class, torch.uint8, "q_class")
+    torch.cuda.current_stream().synchronize()
+    best = _TuneResult()
+    allr = (_TuneResult * 64)()
+    n_all = C.c_uint32()
+    w = _windows(windows)
+    _check(load().hd_library_autotune(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), _ptr(q_class),
+                                      q_mz.numel(), w, len(windows), int(k), C.byref(best), allr, 64,
+                                      C.byref(n_all)))
+    names = {v: k_ for k_, v in FORMS.items()}
+    conv = lambda r: {"form": names[r.form], "tile_group": r.tile_group, "super_group": r.super_group, "ms": r.ms}
+    return conv(best), [conv(allr[i]) for i in range(min(64, n_all.value))]
+
+
+class _ServerParams(C.Structure):
+    _fields_ = [("slots", C.c_uint32), ("max_batch_queries", C.c_uint32), ("mem_budget_bytes", C.c_uint64),
+                ("k", C.c_uint32), ("form", C.c_int)]
+
+
+class _RequestInfo(C.Structure):
+    _fields_ = [("latency_s", C.c_double), ("queue_s", C.c_double), ("n_queries", C.c_uint32),
+                ("batch_queries", C.c_uint32)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("queries", C.c_uint64),
+                ("batches", C.c_uint64), ("max_inflight", C.c_uint32)]
+
+
+class Server:
+    """Continuous-batching server (hd_server_*) on a resident library."""
+
+    def __init__(self, ctx: Ctx, lib: Library, k=5, slots=3, max_batch_queries=8192, mem_budget_bytes=0,
+                 form="auto"):
+        self.k = int(k)
+        self._keep = (ctx, lib)
+        self._pending = {}
+        p = _ServerParams(int(slots), int(max_batch_queries), int(mem_budget_bytes), self.k, FORMS[form])
+        h = C.c_void_p()
+        _check(load().hd_server_create(ctx.handle, lib.handle, C.byref(p), C.byref(h)))
+        self._h = h
+
+    def submit(self, offsets, bins, levels, q_mz, q_charge, tol, unit="da"):
+        """Queue one request (host arrays); returns its id."""
+        off = np.ascontiguousarray(offsets, np.uint32)
+        b = np.ascontiguousarray(bins, np.uint32)
+        lv = np.ascontiguousarray(levels, np.uint8)
+        mz = np.ascontiguousarray(q_mz, np.float64)
+        z = np.ascontiguousarray(q_charge, np.uint8)
+        n = mz.size
+        oi = np.empty((n, self.k), np.uint32)
+        od = np.empty((n, self.k), np.uint16)
+        rid = C.c_uint64()
+        _check(load().hd_server_submit(self._h, _ptr(off), _ptr(b), _ptr(lv), _ptr(mz), _ptr(z), n, float(tol),
+                                       _unit(unit), _ptr(oi), _ptr(od), C.byref(rid)))
+        self._pending[rid.value] = (oi, od)
+        return rid.value
+
+    def wait(self, rid, timeout_s=120.0):
+        """(idx [n, k] u32, dist [n, k] u16, info dict) once the request is done."""
+        info = _RequestInfo()
+        oi, od = self._pending[rid]
+        _check(load().hd_server_wait(self._h, C.c_uint64(rid), float(timeout_s), C.byref(info)))
+        del self._pending[rid]
+        return oi, od, {"latency_s": info.latency_s, "queue_s": info.queue_s, "n_queries": info.n_queries,
+                        "batch_queries": info.batch_queries}
+
+    def stats(self):
+        st = _ServerStats()
+        _check(load().hd_server_stats_get(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hd_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
 
 
 def hd_search_host(ctx: Ctx, lib: Library, offsets, bins, levels, q_mz, q_charge, tol, unit="da", k=1,

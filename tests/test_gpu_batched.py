@@ -1,0 +1,147 @@
+"""Batched uneven workload (many query batches, each with its own window:
+Table 1's 20 ppm narrow search next to 150 and 500 Da open searches) through
+the multi-window search, the CUDA-graph plan and the autotuner, against the
+oracle answering each window class separately."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_16422_gb300 import synth
+from tests import oracle_side
+
+pytestmark = pytest.mark.gpu
+WINDOWS = [(20.0, "ppm"), (150.0, "da"), (500.0, "da")]
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_16422_gb300 import build, hd as _hd
+    build.build()
+    return _hd
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    elif a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).cuda()
+
+
+def _batched_workload(seed, n_refs, n_batches, lo, hi):
+    """Library + concatenated query batches (log-uniform sizes), class per
+    query = its batch's window, round-robin over WINDOWS."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    spec = synth.WORKLOADS["batched"]
+    refs = synth.make_references(n_refs, spec["charges"], spec["weights"], rng, decoy_fraction=0.5)
+    sizes = synth.batch_sizes(n_batches, lo, hi, rng)
+    qs = synth.make_queries(refs, int(sizes.sum()), rng)
+    cls = np.repeat(np.arange(n_batches) % len(WINDOWS), sizes).astype(np.uint8)
+    return refs, qs, cls, sizes
+
+
+def _oracle_by_class(D, r_hv, refs, q_hv, qs, cls, k, which=None):
+    n = qs.n
+    oi = np.full((n, k), 0xFFFFFFFF, np.uint32)
+    od = np.full((n, k), 0xFFFF, np.uint16)
+    for c, (tol, unit) in enumerate(WINDOWS):
+        idx = np.nonzero(cls == c)[0]
+        if which is not None:
+            idx = np.intersect1d(idx, which)
+        if idx.size == 0:
+            continue
+        i, d = oracle.search(D, r_hv, refs.precursor_mz, refs.charge, q_hv, qs.precursor_mz, qs.charge, tol, unit,
+                             k, which=idx.astype(np.uint32))
+        oi[idx], od[idx] = i, d
+    return oi, od
+
+
+def _setup(hd, refs, qs, D, Q, seed=0):
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, seed)
+    r_csr = hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp)
+    q_csr = hd.hd_preprocess(ctx, dev(qs.offsets), dev(qs.mz), dev(qs.intensity), **pp)
+    r_hv = hd.hd_encode(ctx, *r_csr)
+    lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+    return ctx, lib, r_hv, q_csr
+
+
+@pytest.mark.parametrize("D", [4096, 8192])
+def test_multi_window_all_forms_exact(hd, D):
+    refs, qs, cls, _ = _batched_workload(D, 8000, 12, 10, 200)
+    ctx, lib, r_hv, q_csr = _setup(hd, refs, qs, D, 32)
+    q_hv = hd.hd_encode(ctx, *q_csr)
+    for f in ("tc_fp8", "tc_bf16"):
+        hd.hd_library_prepare(lib, f)
+    oi, od = _oracle_by_class(D, oracle_side.hvs(refs, D, 32, 0), refs, oracle_side.hvs(qs, D, 32, 0), qs, cls, 5)
+    for form in ("popc", "tc_fp8", "tc_bf16"):
+        i, d = hd.hd_search_open_multi(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, 5,
+                                       form=form)
+        torch.cuda.synchronize()
+        lib.status()
+        assert np.array_equal(hd.as_u32(i), oi), form
+        assert np.array_equal(hd.as_u16(d), od), form
+    # one class for everybody equals hd_search_open
+    i1, d1 = hd.hd_search_open_multi(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), None, [(150.0, "da")], 3)
+    i2, d2 = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), 150.0, "da", 3)
+    torch.cuda.synchronize()
+    assert torch.equal(i1, i2) and torch.equal(d1, d2)
+
+
+def test_plan_graph_matches_eager_and_refills(hd):
+    D = 4096
+    refs, qs, cls, _ = _batched_workload(7, 6000, 20, 10, 300)
+    ctx, lib, r_hv, q_csr = _setup(hd, refs, qs, D, 32)
+    hd.hd_library_prepare(lib, "tc_fp8")
+    off, bins, lv = q_csr
+    nnz = int(hd.as_u32(off)[-1])
+    plan = hd.Plan(ctx, lib, off, bins[:nnz], lv[:nnz], dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS,
+                   k=5, form="tc_fp8")
+    assert plan.kernel_nodes > 5
+    for _ in range(2):
+        i, d = plan.launch()
+        torch.cuda.synchronize()
+        lib.status()
+        oi, od = _oracle_by_class(D, oracle_side.hvs(refs, D, 32, 0), refs, oracle_side.hvs(qs, D, 32, 0), qs,
+                                  cls, 5)
+        assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
+    # refill the bound buffers with another query set of the same shape
+    rng = np.random.Generator(np.random.PCG64(99))
+    qs2 = synth.make_queries(refs, qs.n, rng)
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=32)
+    off2, bins2, lv2 = oracle.preprocess(qs2.offsets, qs2.mz, qs2.intensity, **pp)
+    nnz2 = int(off2[-1])
+    # the plan reads the CSR through its offsets: a refill may use fewer peaks
+    if nnz2 <= nnz:
+        plan.offsets.copy_(dev(off2))
+        plan.bins[:nnz2].copy_(dev(bins2))
+        plan.levels[:nnz2].copy_(dev(lv2))
+        plan.q_mz.copy_(dev(qs2.precursor_mz))
+        plan.q_charge.copy_(dev(qs2.charge))
+        i, d = plan.launch()
+        torch.cuda.synchronize()
+        oi, od = _oracle_by_class(D, oracle_side.hvs(refs, D, 32, 0), refs, oracle_side.hvs(qs2, D, 32, 0), qs2,
+                                  cls, 5)
+        assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
+
+
+def test_autotune_keeps_results(hd):
+    D = 4096
+    refs, qs, cls, _ = _batched_workload(11, 12000, 9, 50, 400)
+    ctx, lib, r_hv, q_csr = _setup(hd, refs, qs, D, 32)
+    q_hv = hd.hd_encode(ctx, *q_csr)
+    hd.hd_library_prepare(lib, "tc_fp8")
+    args = (lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
+    i0, d0 = hd.hd_search_open_multi(*args, 5, form="popc")
+    best, allr = hd.hd_library_autotune(*args, 5)
+    assert best["ms"] > 0 and len(allr) == 1 + 9
+    assert best["ms"] == min(r["ms"] for r in allr)
+    i1, d1 = hd.hd_search_open_multi(*args, 5, form="auto")
+    torch.cuda.synchronize()
+    assert torch.equal(i0, i1) and torch.equal(d0, d1)

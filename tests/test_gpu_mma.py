@@ -11,6 +11,7 @@ import torch
 
 import oracle
 from paper_2211_16422_gb300 import synth
+from tests import oracle_side
 
 pytestmark = pytest.mark.gpu
 FORMS = ("tc_fp8", "tc_bf16")
@@ -128,7 +129,8 @@ def test_tc_forms_workload_exact(hd, D, k):
             i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), tol, unit, k, form=form)
             torch.cuda.synchronize()
             res[form] = (hd.as_u32(i), hd.as_u16(d))
-        oi, od = oracle.search(D, hd.as_u64(r_hv), refs.precursor_mz, refs.charge, hd.as_u64(q_hv),
+        o_r, o_q = oracle_side.hvs(refs, D, Q, 1), oracle_side.hvs(qs, D, Q, 1)
+        oi, od = oracle.search(D, o_r, refs.precursor_mz, refs.charge, o_q,
                                qs.precursor_mz, qs.charge, tol, unit, k)
         for form, (i, d) in res.items():
             assert np.array_equal(i, oi), form
@@ -174,6 +176,7 @@ def test_tc_schedule_does_not_change_results(hd, tg, sg):
     i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), 500.0, "da", k, form="tc_fp8")
     torch.cuda.synchronize()
     lib.status()
-    oi, od = oracle.search(D, hd.as_u64(r_hv), refs.precursor_mz, refs.charge, hd.as_u64(q_hv),
+    o_r, o_q = oracle_side.hvs(refs, D, Q, 2), oracle_side.hvs(qs, D, Q, 2)
+    oi, od = oracle.search(D, o_r, refs.precursor_mz, refs.charge, o_q,
                            qs.precursor_mz, qs.charge, 500.0, "da", k)
     assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)

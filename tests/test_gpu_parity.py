@@ -12,6 +12,7 @@ import torch
 
 import oracle
 from paper_2211_16422_gb300 import synth
+from tests import oracle_side
 
 pytestmark = pytest.mark.gpu
 
@@ -212,7 +213,9 @@ def test_search_bit_exact(hd, D, k, tol, unit):
     refs, qs = _medium(D + k)
     Q = 32
     _, lib, r_hv, q_hv, idx, dist = _pipeline(hd, refs, qs, D, Q, k, tol, unit)
-    oi, od = oracle.search(D, hd.as_u64(r_hv), refs.precursor_mz, refs.charge, hd.as_u64(q_hv), qs.precursor_mz,
+    o_r, o_q = oracle_side.hvs(refs, D, Q, 0), oracle_side.hvs(qs, D, Q, 0)
+    assert np.array_equal(hd.as_u64(r_hv), o_r) and np.array_equal(hd.as_u64(q_hv), o_q)
+    oi, od = oracle.search(D, o_r, refs.precursor_mz, refs.charge, o_q, qs.precursor_mz,
                            qs.charge, tol, unit, k)
     assert np.array_equal(idx, oi)
     assert np.array_equal(dist, od)
@@ -309,11 +312,15 @@ def test_full_size_sampled(hd):
     sub = refs.subset(rs)
     o_csr = oracle.preprocess(sub.offsets, sub.mz, sub.intensity, **pp)
     assert np.array_equal(hd.as_u64(r_hv[torch.from_numpy(rs).cuda()]), oracle.encode(D, F, L, *o_csr))
-    # search: a sample of queries by brute force over the whole library
+    # search: a sample of queries by brute force over the whole library, on
+    # the oracle's own encoding of every reference and of the sampled queries
     which = np.sort(rng.choice(qs.n, 48, replace=False)).astype(np.uint32)
-    r_np, q_np = hd.as_u64(r_hv), hd.as_u64(q_hv)
-    oi, od = oracle.search(D, r_np, refs.precursor_mz, refs.charge, q_np, qs.precursor_mz, qs.charge,
-                           spec["tol"], spec["unit"], k, which=which)
+    r_np = oracle_side.hvs(refs, D, Q, 0)
+    q_sub = qs.subset(which)
+    q_np = oracle_side.hvs(q_sub, D, Q, 0)
+    assert np.array_equal(hd.as_u64(q_hv[torch.from_numpy(which.astype(np.int64)).cuda()]), q_np)
+    oi, od = oracle.search(D, r_np, refs.precursor_mz, refs.charge, q_np, q_sub.precursor_mz, q_sub.charge,
+                           spec["tol"], spec["unit"], k)
     gi, gd = hd.as_u32(idx), hd.as_u16(dist)
     assert np.array_equal(gi[which], oi)
     assert np.array_equal(gd[which], od)

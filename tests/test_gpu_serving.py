@@ -1,0 +1,123 @@
+"""Continuous-batching server: every request's top-k is exactly what the
+request gets when searched alone, whether it ran coalesced with others, in an
+overlapping batch on another stream, or squeezed by a small memory budget."""
+import threading
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_16422_gb300 import synth
+from tests import oracle_side
+
+pytestmark = pytest.mark.gpu
+D, Q, K = 4096, 32, 5
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_16422_gb300 import build, hd as _hd
+    build.build()
+    return _hd
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).cuda()
+
+
+@pytest.fixture(scope="module")
+def world(hd):
+    rng = np.random.Generator(np.random.PCG64(41))
+    refs = synth.make_references(15000, (2, 3, 4), (0.6, 0.3, 0.1), rng, decoy_fraction=0.5)
+    pool = synth.make_queries(refs, 6000, rng)
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, 0)
+    r_hv = hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp))
+    lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+    hd.hd_library_prepare(lib, "tc_fp8")
+    csr = oracle.preprocess(pool.offsets, pool.mz, pool.intensity, **pp)
+    return ctx, lib, refs, pool, csr, r_hv
+
+
+def _requests(pool, csr, n_req, rng, lo=1, hi=400):
+    sizes = synth.batch_sizes(n_req, lo, hi, rng)
+    off, bins, lv = csr
+    out = []
+    for i, s in enumerate(sizes):
+        a = int(rng.integers(0, pool.n - s))
+        b = a + int(s)
+        o = off[a:b + 1] - off[a]
+        win = (500.0, "da") if i % 3 else (20.0, "ppm")
+        out.append((o, bins[off[a]:off[b]], lv[off[a]:off[b]], pool.precursor_mz[a:b], pool.charge[a:b], win))
+    return out
+
+
+def _alone(hd, ctx, lib, req):
+    o, b, lv, mz, z, (tol, unit) = req
+    q_hv = hd.hd_encode(ctx, dev(o), dev(b), dev(lv))
+    i, d = hd.hd_search_open(lib, q_hv, dev(mz), dev(z), tol, unit, K)
+    torch.cuda.synchronize()
+    return hd.as_u32(i), hd.as_u16(d)
+
+
+def test_server_results_equal_alone(hd, world):
+    ctx, lib, refs, pool, csr, r_hv = world
+    reqs = _requests(pool, csr, 60, np.random.default_rng(3))
+    srv = hd.Server(ctx, lib, k=K, slots=3, max_batch_queries=3000)
+    ids = [None] * len(reqs)
+
+    def submit(part):
+        for j in part:
+            o, b, lv, mz, z, (tol, unit) = reqs[j]
+            ids[j] = srv.submit(o, b, lv, mz, z, tol, unit)
+
+    th = [threading.Thread(target=submit, args=(range(t, len(reqs), 2),)) for t in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    got = [srv.wait(r) for r in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["batches"] < len(reqs)
+    for req, (i, d, info) in zip(reqs, got):
+        ai, ad = _alone(hd, ctx, lib, req)
+        assert np.array_equal(i, ai) and np.array_equal(d, ad)
+        assert info["n_queries"] == len(req[3]) and info["latency_s"] >= info["queue_s"] >= 0
+
+
+def test_server_matches_oracle_sample(hd, world):
+    ctx, lib, refs, pool, csr, r_hv = world
+    req = _requests(pool, csr, 1, np.random.default_rng(5), 200, 200)[0]
+    srv = hd.Server(ctx, lib, k=K, slots=2)
+    rid = srv.submit(*req[:5], *req[5])
+    i, d, _ = srv.wait(rid)
+    srv.close()
+    o, b, lv, mz, z, (tol, unit) = req
+    F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, 0)
+    q_hv = oracle.encode(D, F, L, o, b, lv)
+    oi, od = oracle.search(D, oracle_side.hvs(refs, D, Q, 0), refs.precursor_mz, refs.charge, q_hv, mz, z, tol,
+                           unit, K)
+    assert np.array_equal(i, oi) and np.array_equal(d, od)
+
+
+def test_server_small_memory_budget(hd, world):
+    """A budget of ~2 requests' worth forces many small batches, never a stall."""
+    ctx, lib, refs, pool, csr, r_hv = world
+    reqs = _requests(pool, csr, 25, np.random.default_rng(9), 50, 300)
+    srv = hd.Server(ctx, lib, k=K, slots=4, mem_budget_bytes=300 * (D // 8 + 2 * D + 1024 + K * 32))
+    ids = [srv.submit(*r[:5], *r[5]) for r in reqs]
+    got = [srv.wait(r) for r in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs)
+    for req, (i, d, info) in zip(reqs, got):
+        ai, ad = _alone(hd, ctx, lib, req)
+        assert np.array_equal(i, ai) and np.array_equal(d, ad)
