@@ -398,12 +398,15 @@ hd_status hd_library_prepare(hd_library *lib, hd_search_form form)
     return HD_OK;
 }
 
-hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group)
+hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group, uint32_t cluster)
 {
     HD_CHECK(lib, "hd_library_set_schedule: null library");
     HD_CHECK(tile_group <= 4096 && super_group <= 4096, "hd_library_set_schedule: values must be <= 4096");
+    HD_CHECK(cluster == 0 || cluster == 1 || cluster == 2 || cluster == 4,
+             "hd_library_set_schedule: cluster must be 0, 1, 2 or 4");
     lib->mma_tuning.tile_group = tile_group;
     lib->mma_tuning.super_group = super_group;
+    lib->mma_tuning.cluster = cluster;
     return HD_OK;
 }
 

@@ -58,6 +58,7 @@ struct hd_ctx {
 struct hd_mma_tuning {
     uint32_t tile_group = 0;
     uint32_t super_group = 0;
+    uint32_t cluster = 0;    // CTAs per cluster sharing reference tiles by multicast: 1, 2, 4
 };
 
 struct hd_library {

@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "hd_internal.cuh"
@@ -34,16 +35,24 @@ namespace {
 
 using namespace hd_search;
 
+#ifndef HD_MMA_TN
+#define HD_MMA_TN 256
+#endif
+#ifndef HD_MMA_STAGES
+#define HD_MMA_STAGES 4
+#endif
 constexpr int TM = 128;                 // queries per block (MMA M)
-constexpr int TN = 256;                 // reference rows per tile (MMA N)
+constexpr int TN = HD_MMA_TN;           // reference rows per tile (MMA N)
 constexpr int KB = 128;                 // bytes of K per stage (one 128B swizzle atom)
-constexpr int STAGES = 4;
+constexpr int STAGES = HD_MMA_STAGES;
 constexpr int THREADS = 192;
 constexpr uint32_t A_BYTES = TM * KB;
 constexpr uint32_t B_BYTES = TN * KB;
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
 constexpr uint32_t TMEM_COLS = 2 * TN;
+static_assert(TN % 32 == 0 && TN <= 256 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "tile shape");
+static_assert(STAGES * STAGE_BYTES + 1280 <= 232448, "shared memory");
 
 // ------------------------------------------------------------ tcgen05 PTX
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
@@ -121,6 +130,40 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// The same load delivered to the same shared-memory offset (and mbarrier) of
+// every CTA in `mask` of the cluster.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                               uint64_t *bar, uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)), "h"(mask)
+        : "memory");
+}
+
+// tcgen05.commit arriving on the same-offset mbarrier of every CTA in `mask`.
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_addr(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
 // 1024 bytes (stride byte offset), descriptor version 1.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
@@ -174,7 +217,11 @@ __device__ __forceinline__ void item_range(const mma_args &a, uint32_t item, uin
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-template <int K, bool FP8>
+// CS > 1: clusters of CS CTAs take CS consecutive query blocks of one work
+// item and sweep the same reference tiles; each CTA loads 1/CS of every B
+// tile and multicasts it into all of them, so L2 serves each tile once per
+// cluster.  Stage-free barriers count the MMA commits of every CTA.
+template <int K, bool FP8, int CS>
 __global__ void __launch_bounds__(THREADS, 1)
 k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
@@ -192,7 +239,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], CS);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
@@ -208,8 +255,13 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     }
     tc_fence_before();
     __syncthreads();
+    if (CS > 1) cluster_sync();   // peers' barriers are initialised before any multicast
     tc_fence_after();
     const uint32_t tmem = s_tmem;
+    const uint32_t crank = CS > 1 ? cluster_rank() : 0u;
+    const uint32_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+    constexpr uint16_t CMASK = (uint16_t)((1u << CS) - 1u);
+    constexpr uint32_t B_PART = B_BYTES / CS;
 
     const uint32_t total = a.pair_start[a.n_pairs];
     const uint32_t nchunks = a.row_bytes / KB;
@@ -223,7 +275,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         // ------------------------------------------------------- producer
         if (lane == 0) {
             uint32_t it = 0;
-            for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
+            for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
                 uint32_t b, t0, t1;
                 item_range(a, item, b, t0, t1);
                 for (uint32_t t = t0; t < t1 && !*abort_flag; ++t) {
@@ -233,8 +285,12 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                         if (!mbar_wait(&empty[s], ph ^ 1u)) { give_up(); break; }
                         uint8_t *sa = smem + s * STAGE_BYTES, *sb = sa + A_BYTES;
                         mbar_expect_tx(&full[s], STAGE_BYTES);
-                        tma_load_2d(sa, &qmap, (int32_t)(c * KB), (int32_t)(b * TM), &full[s]);
-                        tma_load_2d(sb, &lmap, (int32_t)(c * KB), r0, &full[s]);
+                        tma_load_2d(sa, &qmap, (int32_t)(c * KB), (int32_t)((b * CS + crank) * TM), &full[s]);
+                        if (CS == 1)
+                            tma_load_2d(sb, &lmap, (int32_t)(c * KB), r0, &full[s]);
+                        else
+                            tma_load_2d_mc(sb + crank * B_PART, &lmap, (int32_t)(c * KB),
+                                           r0 + (int32_t)(crank * (TN / CS)), &full[s], CMASK);
                     }
                 }
             }
@@ -244,7 +300,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         if (lane == 0) {
             constexpr uint32_t idesc = instr_desc<FP8>();
             uint32_t it = 0, acc_it = 0;
-            for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
+            for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
                 uint32_t b, t0, t1;
                 item_range(a, item, b, t0, t1);
                 for (uint32_t t = t0; t < t1 && !*abort_flag; ++t, ++acc_it) {
@@ -262,7 +318,8 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
 #pragma unroll
                         for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
                             mma_issue<FP8>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
-                        mma_commit(&empty[s]);
+                        if (CS == 1) mma_commit(&empty[s]);
+                        else mma_commit_mc(&empty[s], CMASK);
                     }
                     if (!ok) break;
                     mma_commit(&acc_full[buf]);
@@ -280,10 +337,11 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         const uint32_t lane_addr = (quarter * 32) << 16;
         const bool leader = threadIdx.x == 64;
         uint32_t acc_it = 0;
-        for (uint32_t item = blockIdx.x; item < total && !*abort_flag; item += gridDim.x) {
+        for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
             uint32_t b, t0, t1;
             item_range(a, item, b, t0, t1);
-            const uint32_t sq = b * TM + row;
+            const uint32_t sb_ = b * CS + crank;     // this CTA's query block
+            const uint32_t sq = sb_ * TM + row;
             const uint32_t lo = sq < a.n_q ? a.lo[sq] : 0u, hi = sq < a.n_q ? a.hi[sq] : 0u;
             const uint32_t span = hi > lo ? hi - lo : 0u;
             uint64_t best[K];
@@ -322,7 +380,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                 if (ok && !*abort_flag) {
                     const uint64_t w0 = hd_globaltimer_ns();
                     for (uint32_t i = 0;; ++i) {
-                        if (atomicCAS(&a.locks[b], 0u, 1u) == 0u) { got = 1; break; }
+                        if (atomicCAS(&a.locks[sb_], 0u, 1u) == 0u) { got = 1; break; }
                         if ((i & 63u) == 0 && hd_globaltimer_ns() - w0 > HD_WAIT_NS) { give_up(); break; }
                     }
                     __threadfence();
@@ -344,12 +402,13 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                 __threadfence();
             }
             epi_bar();
-            if (leader && locked) atomicExch(&a.locks[b], 0u);
+            if (leader && locked) atomicExch(&a.locks[sb_], 0u);
             if (!locked) break;
         }
     }
     tc_fence_before();
     __syncthreads();
+    if (CS > 1) cluster_sync();   // no peer multicasts into this CTA once it leaves
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
@@ -358,15 +417,15 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
 // block the absolute tile range covering the union of its windows, then the
 // item count of every (super-group, block) pair and its exclusive scan.
 __global__ void __launch_bounds__(1024)
-k_worklist_l2(const uint32_t *__restrict__ lo, const uint32_t *__restrict__ hi, uint32_t n_q, uint32_t n_blocks,
-              uint32_t tg, uint32_t sg, uint32_t n_super, uint32_t *__restrict__ blk_t0,
+k_worklist_l2(const uint32_t *__restrict__ lo, const uint32_t *__restrict__ hi, uint32_t n_q, uint32_t bq,
+              uint32_t n_blocks, uint32_t tg, uint32_t sg, uint32_t n_super, uint32_t *__restrict__ blk_t0,
               uint32_t *__restrict__ blk_t1, uint32_t *__restrict__ pair_start)
 {
     __shared__ uint32_t sh[33];
     for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) {
         uint32_t l = 0xFFFFFFFFu, h = 0;
-        const uint32_t e = min(n_q, (b + 1) * (uint32_t)TM);
-        for (uint32_t s = b * TM; s < e; ++s)
+        const uint32_t e = min(n_q, (b + 1) * bq);
+        for (uint32_t s = b * bq; s < e; ++s)
             if (hi[s] > lo[s]) {
                 l = min(l, lo[s]);
                 h = max(h, hi[s]);
@@ -492,13 +551,32 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
                   uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
                   cudaStream_t s, const hd_mma_tuning &tune)
 {
-    const uint32_t n_blocks = (n_q + TM - 1) / TM;
+    const uint32_t cs = tune.cluster;   // 1, 2 or 4 CTAs per cluster
+    const uint32_t n_blocks = (n_q + TM * cs - 1) / (TM * cs);
     const uint32_t row_bytes = lib->dim * (FP8 ? 1u : 2u);
     const uint8_t *lib_x = FP8 ? lib->x_fp8 : lib->x_bf16;
     if (!lib_x) return hd_fail(HD_ERR_INVALID_ARG, "library not prepared for this tensor-core form");
-    HD_CUDA_TRY(cudaFuncSetAttribute(k_search_mma<K, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES));
-    const uint32_t grid = (uint32_t)lib->num_sms;
+    auto kern = cs == 4 ? k_search_mma<K, FP8, 4> : (cs == 2 ? k_search_mma<K, FP8, 2> : k_search_mma<K, FP8, 1>);
+    HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    if (cs > 1) HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    uint32_t grid = (uint32_t)lib->num_sms / cs * cs;
+    if (cs > 1) {   // only co-resident clusters: a persistent grid must not wait for SMs
+        cudaLaunchConfig_t qc = {};
+        qc.gridDim = dim3(grid);
+        qc.blockDim = dim3(THREADS);
+        qc.dynamicSmemBytes = SMEM_BYTES;
+        cudaLaunchAttribute qa[1];
+        qa[0].id = cudaLaunchAttributeClusterDimension;
+        qa[0].val.clusterDim.x = cs;
+        qa[0].val.clusterDim.y = 1;
+        qa[0].val.clusterDim.z = 1;
+        qc.attrs = qa;
+        qc.numAttrs = 1;
+        int n_cl = 0;
+        HD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n_cl, kern, &qc));
+        if (n_cl < 1) return hd_fail(HD_ERR_UNSUPPORTED, "cluster launch does not fit on this GPU");
+        grid = std::min(grid, (uint32_t)n_cl * cs);
+    }
     const uint32_t tg = tune.tile_group, sg = tune.super_group;
     const uint32_t n_tiles = (lib->n + TN - 1) / TN;
     const uint32_t n_super = (n_tiles + tg * sg - 1) / (tg * sg);
@@ -514,7 +592,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
         *bt1 = ar.take<uint32_t>(n_blocks);
         *pst = ar.take<uint32_t>(n_pairs + 1);
         *top = ar.take<uint64_t>((size_t)n_q * K);
-        *locks = ar.take<uint32_t>(n_blocks);
+        *locks = ar.take<uint32_t>((size_t)n_blocks * cs);
         *qx = ar.take<uint8_t>((size_t)n_q * row_bytes);
     };
     uint32_t *perm, *lo, *hi, *bt0, *bt1, *pst, *locks;
@@ -531,23 +609,36 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     carve(ar, &perm, &lo, &hi, &bt0, &bt1, &pst, &top, &locks, &qx);
     CUtensorMap qmap, lmap;
     hd_status st = make_map(&qmap, qx, n_q, row_bytes, TM);
-    if (st == HD_OK) st = make_map(&lmap, lib_x, lib->n, row_bytes, TN);
+    if (st == HD_OK) st = make_map(&lmap, lib_x, lib->n, row_bytes, TN / cs);
     if (st != HD_OK) {
         cudaFreeAsync(ar.base, s);
         return st;
     }
     HD_CUDA_TRY(cudaMemsetAsync(top, 0xFF, (size_t)n_q * K * sizeof(uint64_t), s));
-    HD_CUDA_TRY(cudaMemsetAsync(locks, 0, (size_t)n_blocks * sizeof(uint32_t), s));
+    HD_CUDA_TRY(cudaMemsetAsync(locks, 0, (size_t)n_blocks * cs * sizeof(uint32_t), s));
     hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, perm, ar, s);
     hd_count_launches(1), k_expand<FP8><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
     hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z,
                                                                           perm, n_q, win, lo, hi);
-    hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, n_blocks, tg, sg, n_super, bt0, bt1, pst);
+    hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, TM * cs, n_blocks, tg, sg, n_super, bt0, bt1, pst);
     mma_args ma{lib->orig, lo, hi, bt0, bt1, pst, top, locks, lib->status.dev, n_q, n_blocks, (uint32_t)n_pairs,
                 tg, sg, lib->dim, row_bytes};
     {
         hd_prof_scope timed(HD_KERNEL_SEARCH, s);
-        hd_count_launches(1), k_search_mma<K, FP8><<<grid, THREADS, SMEM_BYTES, s>>>(qmap, lmap, ma);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        hd_count_launches(1);
+        HD_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, qmap, lmap, ma));
     }
     hd_count_launches(1), k_emit<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(top, perm, n_q, k, out_idx, out_dist);
     HD_CUDA_TRY(cudaGetLastError());
@@ -593,8 +684,9 @@ hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_h
 {
     if (lib->n == 0) return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
     hd_mma_tuning tu = lib->mma_tuning;
-    if (tu.tile_group == 0) tu.tile_group = 8;
-    if (tu.super_group == 0) tu.super_group = 4;
+    if (tu.tile_group == 0) tu.tile_group = 16;
+    if (tu.super_group == 0) tu.super_group = 8;
+    if (tu.cluster != 1 && tu.cluster != 2 && tu.cluster != 4) tu.cluster = 2;
     if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
     return run_fmt<false>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
 }

@@ -154,8 +154,8 @@ def test_auto_prefers_prepared_tc_form(hd):
     assert torch.equal(i0, i1) and torch.equal(d0, d1)
 
 
-@pytest.mark.parametrize("tg,sg", [(1, 1), (2, 3), (64, 64), (8, 4)])
-def test_tc_schedule_does_not_change_results(hd, tg, sg):
+@pytest.mark.parametrize("tg,sg,cs", [(1, 1, 1), (2, 3, 2), (64, 64, 4), (8, 4, 2), (16, 8, 4), (3, 5, 1)])
+def test_tc_schedule_does_not_change_results(hd, tg, sg, cs):
     """Work-item shape (tiles per item, groups per L2 slice) is a pure
     performance knob: the top-k must not move."""
     rng = np.random.Generator(np.random.PCG64(17))
@@ -172,7 +172,7 @@ def test_tc_schedule_does_not_change_results(hd, tg, sg):
     r_hv, q_hv = enc(refs), enc(qs)
     lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
     hd.hd_library_prepare(lib, "tc_fp8")
-    hd.hd_library_set_schedule(lib, tg, sg)
+    hd.hd_library_set_schedule(lib, tg, sg, cs)
     i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), 500.0, "da", k, form="tc_fp8")
     torch.cuda.synchronize()
     lib.status()
