@@ -330,6 +330,17 @@ HD_API hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_t *d
                                         double tol, hd_tol_unit unit, uint32_t k, uint32_t *d_out_idx,
                                         uint16_t *d_out_dist, hd_stream stream);
 
+/* Failure-detection hooks (no counterpart in the paper).  Every device wait
+ * of a search (stage loads, tensor-core commits, merge locks) gives up after
+ * a bounded time, records HD_ERR_TIMEOUT in the library's status word and
+ * lets its kernel return, leaving the CUDA context usable.
+ * hd_library_set_wait_limit sets that bound (0: 2 s; otherwise >= 1 ms).
+ * hd_library_inject_stall makes the next n searches on this library arm one
+ * stage barrier and never issue its load, so that a wait does run out: the
+ * test hook for that path.  No trap, fault or endless loop is involved. */
+HD_API hd_status hd_library_set_wait_limit(hd_library *lib, uint64_t ns);
+HD_API hd_status hd_library_inject_stall(hd_library *lib, uint32_t n_searches);
+
 /* Measurement hooks (no counterpart in the paper).  While enabled, libhd
  * records a CUDA event pair around every launch of the given kernel kind, on
  * the stream the kernel runs on.  hd_profile_collect() waits for the

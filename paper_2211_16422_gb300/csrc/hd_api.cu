@@ -174,6 +174,15 @@ hd_status hd_search_dispatch(const hd_library *lib, const uint64_t *q_hv, const 
     return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
 }
 
+bool hd_take_injected_stall(const hd_library *lib)
+{
+    uint32_t n = __atomic_load_n(&lib->inject_stalls, __ATOMIC_SEQ_CST);
+    while (n > 0)
+        if (__atomic_compare_exchange_n(&lib->inject_stalls, &n, n - 1, false, __ATOMIC_SEQ_CST, __ATOMIC_SEQ_CST))
+            return true;
+    return false;
+}
+
 extern "C" {
 
 const char *hd_status_string(hd_status s)
@@ -395,6 +404,21 @@ hd_status hd_library_prepare(hd_library *lib, hd_search_form form)
     st = hd_library_expand(lib, form == HD_FORM_TC_FP8, ss.s);
     if (st != HD_OK) return st;
     HD_CUDA_TRY(cudaStreamSynchronize(ss.s));
+    return HD_OK;
+}
+
+hd_status hd_library_set_wait_limit(hd_library *lib, uint64_t ns)
+{
+    HD_CHECK(lib, "hd_library_set_wait_limit: null library");
+    HD_CHECK(ns == 0 || ns >= 1000000ull, "hd_library_set_wait_limit: limit must be 0 or >= 1 ms");
+    lib->wait_ns = ns;
+    return HD_OK;
+}
+
+hd_status hd_library_inject_stall(hd_library *lib, uint32_t n_searches)
+{
+    HD_CHECK(lib, "hd_library_inject_stall: null library");
+    __atomic_store_n(&lib->inject_stalls, n_searches, __ATOMIC_SEQ_CST);
     return HD_OK;
 }
 

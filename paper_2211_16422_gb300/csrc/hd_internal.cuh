@@ -74,6 +74,8 @@ struct hd_library {
     uint8_t *x_bf16 = nullptr;     // [n][2D] bipolar bf16 rows (tensor-core form), optional
     hd_mma_tuning mma_tuning;
     hd_search_form auto_form = HD_FORM_AUTO;   // set by the autotuner
+    uint64_t wait_ns = 0;                      // device wait limit (0: HD_WAIT_NS)
+    mutable uint32_t inject_stalls = 0;        // test hook: searches that drop their first load
     uint32_t charge_start_h[257] = {};
     hd_status_word status;
 };
@@ -143,6 +145,11 @@ struct hd_qwin {
     hd_win w[HD_MAX_WINDOWS] = {};
 };
 hd_qwin hd_single_window(double tol, int ppm);
+
+// Test hook: true (and one fewer pending) when this search must drop its
+// first stage load so that a bounded device wait runs out.
+bool hd_take_injected_stall(const hd_library *lib);
+inline uint64_t hd_wait_limit(const hd_library *lib) { return lib->wait_ns ? lib->wait_ns : HD_WAIT_NS; }
 
 // Stable sort of n items by (group, charge, m/z), group optional: writes the
 // permutation `perm` (perm[rank] = input index).  Scratch from `arena`

@@ -147,14 +147,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: false once HD_WAIT_NS of wall time passed without the phase.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Bounded wait: false once `limit_ns` of wall time passed without the phase.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = HD_WAIT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = hd_globaltimer_ns();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63u) == 0 && hd_globaltimer_ns() - t0 > HD_WAIT_NS) return false;
+        if ((i & 63u) == 0 && hd_globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 

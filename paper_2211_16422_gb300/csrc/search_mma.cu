@@ -194,6 +194,8 @@ struct mma_args {
     uint32_t *locks;                            // [n_blocks] merge locks
     uint32_t *status;
     uint32_t n_q, n_blocks, n_pairs, tg, sg, dim, row_bytes;
+    uint64_t wait_ns;      // bound of every device wait
+    uint32_t stall;        // test hook: drop the first stage load
 };
 
 // Work item -> (query block, absolute tile range [t0, t1)).  Items are
@@ -282,9 +284,10 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                     const int32_t r0 = (int32_t)(t * TN);
                     for (uint32_t c = 0; c < nchunks; ++c, ++it) {
                         const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
-                        if (!mbar_wait(&empty[s], ph ^ 1u)) { give_up(); break; }
+                        if (!mbar_wait(&empty[s], ph ^ 1u, a.wait_ns)) { give_up(); break; }
                         uint8_t *sa = smem + s * STAGE_BYTES, *sb = sa + A_BYTES;
                         mbar_expect_tx(&full[s], STAGE_BYTES);
+                        if (a.stall && it == 0) continue;   // nothing ever completes this stage
                         tma_load_2d(sa, &qmap, (int32_t)(c * KB), (int32_t)((b * CS + crank) * TM), &full[s]);
                         if (CS == 1)
                             tma_load_2d(sb, &lmap, (int32_t)(c * KB), r0, &full[s]);
@@ -305,13 +308,13 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                 item_range(a, item, b, t0, t1);
                 for (uint32_t t = t0; t < t1 && !*abort_flag; ++t, ++acc_it) {
                     const uint32_t buf = acc_it & 1u, aph = (acc_it >> 1) & 1u;
-                    if (!mbar_wait(&acc_empty[buf], aph ^ 1u)) { give_up(); break; }
+                    if (!mbar_wait(&acc_empty[buf], aph ^ 1u, a.wait_ns)) { give_up(); break; }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + buf * TN;
                     bool ok = true;
                     for (uint32_t c = 0; c < nchunks; ++c, ++it) {
                         const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
-                        if (!mbar_wait(&full[s], ph)) { give_up(); ok = false; break; }
+                        if (!mbar_wait(&full[s], ph, a.wait_ns)) { give_up(); ok = false; break; }
                         tc_fence_after();
                         const uint32_t sa = smem_addr(smem + s * STAGE_BYTES), sb = sa + A_BYTES;
                         const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
@@ -327,7 +330,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             }
             // every issued MMA has finished before TMEM is released
             mma_commit(drain);
-            mbar_wait(drain, 0);
+            mbar_wait(drain, 0, a.wait_ns);
         }
         __syncwarp();
     } else {
@@ -350,7 +353,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             bool ok = true;
             for (uint32_t t = t0; t < t1; ++t, ++acc_it) {
                 const uint32_t buf = acc_it & 1u, aph = (acc_it >> 1) & 1u;
-                if (!mbar_wait(&acc_full[buf], aph)) { give_up(); ok = false; break; }
+                if (!mbar_wait(&acc_full[buf], aph, a.wait_ns)) { give_up(); ok = false; break; }
                 tc_fence_after();
                 const uint32_t r0 = t * TN;
 #pragma unroll 1
@@ -381,7 +384,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                     const uint64_t w0 = hd_globaltimer_ns();
                     for (uint32_t i = 0;; ++i) {
                         if (atomicCAS(&a.locks[sb_], 0u, 1u) == 0u) { got = 1; break; }
-                        if ((i & 63u) == 0 && hd_globaltimer_ns() - w0 > HD_WAIT_NS) { give_up(); break; }
+                        if ((i & 63u) == 0 && hd_globaltimer_ns() - w0 > a.wait_ns) { give_up(); break; }
                     }
                     __threadfence();
                 }
@@ -622,7 +625,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
                                                                           perm, n_q, win, lo, hi);
     hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, TM * cs, n_blocks, tg, sg, n_super, bt0, bt1, pst);
     mma_args ma{lib->orig, lo, hi, bt0, bt1, pst, top, locks, lib->status.dev, n_q, n_blocks, (uint32_t)n_pairs,
-                tg, sg, lib->dim, row_bytes};
+                tg, sg, lib->dim, row_bytes, hd_wait_limit(lib), hd_take_injected_stall(lib) ? 1u : 0u};
     {
         hd_prof_scope timed(HD_KERNEL_SEARCH, s);
         cudaLaunchConfig_t cfg = {};

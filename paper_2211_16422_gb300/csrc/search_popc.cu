@@ -45,6 +45,8 @@ struct search_args {
     uint64_t *partial;         // [items][BQ][K]
     uint32_t *status;
     uint32_t n_q, n_blocks, W64;
+    uint64_t wait_ns;      // bound of every device wait
+    uint32_t stall;        // test hook: drop the first stage copies
 };
 
 // ------------------------------------------------------------ search kernel
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
     const uint32_t total_items = a.item_start[a.n_blocks];
     const uint32_t tpi = a.meta[0];
     uint32_t parity = 0;   // bit st: phase parity expected next on stage st
+    bool first_item = true;
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(&a.meta[1], 1u);
@@ -123,6 +126,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
             uint8_t *stage = smem + (st_step & 1) * STAGE_B;
             if (lane == 0) mbar_expect_tx(&bar[st_step & 1], (nq + nr) * rb);
             __syncwarp();
+            if (a.stall && first_item && st_step == 0) return;   // nothing completes this stage
             for (uint32_t x = lane; x < nq; x += 32)
                 bulk_load(stage + x * PITCH_B,
                           a.q_hv + (size_t)a.perm[q0 + x] * a.W64 + ch * (CHUNK_W32 / 2), rb,
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
         bool aborted = false;
         for (uint32_t s = 0; s < steps; ++s) {
             const uint32_t st = s & 1;
-            const bool ok = mbar_wait(&bar[st], (parity >> st) & 1u);
+            const bool ok = mbar_wait(&bar[st], (parity >> st) & 1u, a.wait_ns);
             parity ^= 1u << st;
             ++waited;
             if (__syncthreads_or(!ok)) {
@@ -192,7 +196,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
             // let copies still in flight land before the CTA's memory is released
             const uint32_t issued = min(steps, waited + 1);
             for (uint32_t s = waited; s < issued; ++s) {
-                mbar_wait(&bar[s & 1], (parity >> (s & 1)) & 1u);
+                mbar_wait(&bar[s & 1], (parity >> (s & 1)) & 1u, a.wait_ns);
                 parity ^= 1u << (s & 1);
             }
             return;
@@ -214,6 +218,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
                 for (int t = 0; t < K; ++t) dst[t] = best[i][t];
             }
         }
+        first_item = false;
     }
 }
 
@@ -266,7 +271,8 @@ hd_status run_k(const hd_library *lib, const uint64_t *q_hv, const double *q_mz,
                                                     win, lo, hi);
     hd_count_launches(1), k_worklist<<<1, 1024, 0, s>>>(lo, hi, n_q, BQ, BR, n_blocks, target_items, blo, bhi, bnt, ist, meta);
     search_args sa{lib->hv, lib->orig, q_hv, perm, lo, hi, blo, bhi, bnt, ist, meta, part,
-                   lib->status.dev, n_q, n_blocks, lib->W};
+                   lib->status.dev, n_q, n_blocks, lib->W, hd_wait_limit(lib),
+                   hd_take_injected_stall(lib) ? 1u : 0u};
     {
         hd_prof_scope timed(HD_KERNEL_SEARCH, s);
         hd_count_launches(1), k_search_popc<K><<<grid, THREADS, SMEM_B, s>>>(sa);

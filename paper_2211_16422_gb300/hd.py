@@ -79,6 +79,8 @@ _SIGS = {
     "hd_library_status": ([P], i32),
     "hd_library_prepare": ([P, i32], i32),
     "hd_library_set_schedule": ([P, u32, u32, u32], i32),
+    "hd_library_set_wait_limit": ([P, u64], i32),
+    "hd_library_inject_stall": ([P, u32], i32),
     "hd_query_windows": ([P, P, P, u32, dbl, i32, P, P, P], i32),
     "hd_search_open": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_search_open_ex": ([P, P, P, P, u32, dbl, i32, u32, i32, P, P, P], i32),
@@ -267,6 +269,16 @@ def hd_library_prepare(lib: Library, form: str):
 def hd_library_set_schedule(lib: Library, tile_group: int = 0, super_group: int = 0, cluster: int = 0):
     """Work-item shape and multicast cluster size of the tensor-core forms (0 = default)."""
     _check(load().hd_library_set_schedule(lib.handle, int(tile_group), int(super_group), int(cluster)))
+
+
+def hd_library_set_wait_limit(lib: Library, seconds: float = 0.0):
+    """Bound of every device wait of searches on `lib` (0: the 2 s default)."""
+    _check(load().hd_library_set_wait_limit(lib.handle, int(seconds * 1e9)))
+
+
+def hd_library_inject_stall(lib: Library, n_searches: int = 1):
+    """Test hook: the next n searches on `lib` stall one stage until their bounded wait runs out."""
+    _check(load().hd_library_inject_stall(lib.handle, int(n_searches)))
 
 
 def hd_library_export(lib: Library, stream=None):
