@@ -177,11 +177,14 @@ HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
  * items are ordered so that the CTAs running at once share `super_group`
  * consecutive groups of tiles through L2.  `cluster` (1, 2 or 4) CTAs of a
  * thread-block cluster take adjacent query blocks and share each reference
- * tile by TMA multicast.  0 keeps the default (16, 8, 2).
+ * tile by TMA multicast.  `cta_group` 2 pairs the two CTAs of a cluster of
+ * 2 on neighbouring SMs into one M = 256 tensor-core operation (each SM
+ * stages half of every reference tile); it requires cluster 0 or 2.  0 keeps
+ * the default (16, 8, 2, 2; cta_group 0 with cluster 1 or 4 means 1).
  * Results do not depend on the schedule.  Not to be changed while a search
  * on this library is in flight. */
 HD_API hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group,
-                                         uint32_t cluster);
+                                         uint32_t cluster, uint32_t cta_group);
 
 /* Candidate windows (Section 3.4, Table 1): for each query, rows [lo, hi) of
  * the sorted library whose charge equals the query's and whose precursor
@@ -249,14 +252,15 @@ HD_API void hd_plan_destroy(hd_plan *plan);
 
 /* Autotuner (no counterpart in the paper): times each search form the library
  * is prepared for and, for the tensor-core forms, work-item shapes
- * tile_group x super_group x cluster in {4, 16} x {2, 8} x {1, 2, 4}, on the
+ * tile_group x super_group x (cluster, cta_group) in {4, 16} x {2, 8} x
+ * {(1, 1), (2, 1), (4, 1), (2, 2)}, on the
  * given queries
  * (a representative sample), and keeps the fastest as the library's
  * HD_FORM_AUTO form and schedule.  `all` (capacity `cap`) receives every
  * timing.  Synchronous; results never depend on the choice. */
 typedef struct {
     hd_search_form form;
-    uint32_t tile_group, super_group, cluster;
+    uint32_t tile_group, super_group, cluster, cta_group;
     double ms;
 } hd_tune_result;
 HD_API hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,

@@ -49,6 +49,8 @@ hd_status status_take(hd_status_word &w, const char *who)
     const uint32_t v = __atomic_exchange_n(w.host, 0u, __ATOMIC_SEQ_CST);
     if (v & HD_DEV_TIMEOUT)
         return hd_fail(HD_ERR_TIMEOUT, std::string(who) + ": a bounded device wait expired");
+    if (v & HD_DEV_TMEM)
+        return hd_fail(HD_ERR_CUDA, std::string(who) + ": paired CTAs hold different tensor-memory columns");
     if (v & HD_DEV_BAD_INPUT)
         return hd_fail(HD_ERR_INVALID_ARG, std::string(who) + ": malformed input found on the device");
     return HD_OK;
@@ -422,15 +424,20 @@ hd_status hd_library_inject_stall(hd_library *lib, uint32_t n_searches)
     return HD_OK;
 }
 
-hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group, uint32_t cluster)
+hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group, uint32_t cluster,
+                                  uint32_t cta_group)
 {
     HD_CHECK(lib, "hd_library_set_schedule: null library");
     HD_CHECK(tile_group <= 4096 && super_group <= 4096, "hd_library_set_schedule: values must be <= 4096");
     HD_CHECK(cluster == 0 || cluster == 1 || cluster == 2 || cluster == 4,
              "hd_library_set_schedule: cluster must be 0, 1, 2 or 4");
+    HD_CHECK(cta_group <= 2, "hd_library_set_schedule: cta_group must be 0, 1 or 2");
+    HD_CHECK(cta_group != 2 || cluster == 0 || cluster == 2,
+             "hd_library_set_schedule: cta_group 2 needs a cluster of 2");
     lib->mma_tuning.tile_group = tile_group;
     lib->mma_tuning.super_group = super_group;
-    lib->mma_tuning.cluster = cluster;
+    lib->mma_tuning.cluster = cta_group == 2 ? 2u : cluster;
+    lib->mma_tuning.cta_group = cta_group;
     return HD_OK;
 }
 

@@ -15,7 +15,8 @@
 // ---------------------------------------------------------------------------
 enum : uint32_t {
     HD_DEV_BAD_INPUT = 1u,   // malformed CSR row, bin or level out of range, ...
-    HD_DEV_TIMEOUT = 2u      // a bounded wait (mbarrier, work queue) expired
+    HD_DEV_TIMEOUT = 2u,     // a bounded wait (mbarrier, work queue) expired
+    HD_DEV_TMEM = 4u         // the two CTAs of a pair were given different tensor-memory columns
 };
 
 __device__ __forceinline__ void hd_flag(uint32_t *status, uint32_t bits)
@@ -59,6 +60,7 @@ struct hd_mma_tuning {
     uint32_t tile_group = 0;
     uint32_t super_group = 0;
     uint32_t cluster = 0;    // CTAs per cluster sharing reference tiles by multicast: 1, 2, 4
+    uint32_t cta_group = 0;  // 2: SM pairs issue M = 256 MMAs (cluster of 2); 0/1: one SM per MMA
 };
 
 struct hd_library {

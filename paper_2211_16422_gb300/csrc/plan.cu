@@ -136,13 +136,14 @@ hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const dou
         return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: library belongs to another device");
 
     std::vector<hd_tune_result> cand;
-    cand.push_back({HD_FORM_POPC, 0, 0, 0, 0.0});
-    const uint32_t tgs[2] = {4, 16}, sgs[2] = {2, 8}, css[3] = {1, 2, 4};
+    cand.push_back({HD_FORM_POPC, 0, 0, 0, 0, 0.0});
+    const uint32_t tgs[2] = {4, 16}, sgs[2] = {2, 8};
+    const uint32_t shapes[4][2] = {{1, 1}, {2, 1}, {4, 1}, {2, 2}};   // (cluster, cta_group)
     for (hd_search_form f : {HD_FORM_TC_FP8, HD_FORM_TC_BF16}) {
         if ((f == HD_FORM_TC_FP8 && !lib->x_fp8) || (f == HD_FORM_TC_BF16 && !lib->x_bf16)) continue;
         for (uint32_t tg : tgs)
             for (uint32_t sg : sgs)
-                for (uint32_t cs : css) cand.push_back({f, tg, sg, cs, 0.0});
+                for (const auto &sh : shapes) cand.push_back({f, tg, sg, sh[0], sh[1], 0.0});
     }
     scoped_stream ss;
     HD_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
@@ -162,6 +163,7 @@ hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const dou
         lib->mma_tuning.tile_group = c.tile_group;
         lib->mma_tuning.super_group = c.super_group;
         lib->mma_tuning.cluster = c.cluster;
+        lib->mma_tuning.cta_group = c.cta_group;
         double bestms = 1e30;
         for (int rep = 0; rep < 3 && st == HD_OK; ++rep) {   // first run warms up
             cudaEventRecord(e0, ss.s);
@@ -188,6 +190,7 @@ hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const dou
     lib->mma_tuning.tile_group = it->tile_group;
     lib->mma_tuning.super_group = it->super_group;
     lib->mma_tuning.cluster = it->cluster;
+    lib->mma_tuning.cta_group = it->cta_group;
     lib->auto_form = it->form;
     if (best) *best = *it;
     if (n_all) *n_all = (uint32_t)cand.size();

@@ -411,9 +411,336 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     }
     tc_fence_before();
     __syncthreads();
-    if (CS > 1) cluster_sync();   // no peer multicasts into this CTA once it leaves
+    if (CS > 1) {
+        cluster_sync();   // every peer has stopped issuing multicast loads
+        // After a give-up anywhere in the grid, loads that a peer issued before
+        // the barrier may still be landing in this CTA's shared memory: pause
+        // (bounded, 200 us) so that they complete before the CTA exits.
+        if (threadIdx.x == 0 && (*abort_flag || (a.status && (atomicOr_system(a.status, 0u) & HD_DEV_TIMEOUT) != 0u))) {
+            const uint64_t w0 = hd_globaltimer_ns();
+            while (hd_globaltimer_ns() - w0 < 200000ull) __nanosleep(1000);
+        }
+        __syncthreads();
+    }
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ------------------------------------------------------------- 2-SM form
+// A cluster of two CTAs on an SM pair (cluster ranks 0 and 1) issues one
+// tcgen05.mma.cta_group::2 of M = 256, N = 256 from rank 0: each CTA holds
+// the 128 query rows of its own block (A) and 128 of the tile's 256
+// reference rows (B; rank 0 rows 0..127, rank 1 rows 128..255) in every
+// stage, and its tensor memory receives the 128 x 256 scores of its queries.
+// Per SM the tensor core reads half as many B bytes from shared memory as in
+// the 1-SM form, and the TMA writes half as many: at M = 128, N = 256 the two
+// together exceed what shared memory delivers per clock.
+constexpr uint32_t B2_BYTES = (TN / 2) * KB;
+constexpr uint32_t STAGE2_BYTES = A_BYTES + B2_BYTES;
+#ifndef HD_MMA2_STAGES
+#define HD_MMA2_STAGES 6
+#endif
+#ifndef HD_MMA2_BUFS
+#define HD_MMA2_BUFS 2
+#endif
+constexpr int STAGES2 = HD_MMA2_STAGES;
+constexpr int BUFS2 = HD_MMA2_BUFS;                 // accumulator buffers in tensor memory
+constexpr uint32_t TMEM2_COLS = BUFS2 * TN;
+// B2_BYTES of slack after the ring keep every operand read of the last stage
+// inside the allocation, whatever the split of B between the two CTAs.
+constexpr uint32_t SMEM2_BYTES = STAGES2 * STAGE2_BYTES + B2_BYTES + 1024 + 256;
+static_assert(SMEM2_BYTES <= 232448, "shared memory (2-SM form)");
+static_assert((BUFS2 == 1 || BUFS2 == 2) && TN == 256, "2-SM form: N = 256, one or two accumulators");
+
+__device__ __forceinline__ void tmem_alloc2(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish2()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+template <bool FP8>
+__device__ __forceinline__ void mma_issue2(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                           uint32_t accumulate)
+{
+    if (FP8)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+
+// Arrives on `bar` (same offset in every CTA of `mask`) once the pair's
+// tcgen05.mma issued so far by this thread are done.
+__device__ __forceinline__ void mma_commit2_mc(uint64_t *bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_addr(bar)),
+        "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit2(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+// Address of this CTA's shared variable `p` in the shared memory of cluster CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t caddr)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(caddr) : "memory");
+    return v;
+}
+
+// 2-D tensor load into this CTA's shared memory whose bytes are counted on
+// an mbarrier of either CTA of the pair (`bar` is a cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                                 uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// M = 256 (the pair), N = 256.
+template <bool FP8>
+__host__ __device__ constexpr uint32_t instr_desc2()
+{
+    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((uint32_t)(TN >> 3) << 17) |
+           ((uint32_t)((2 * TM) >> 4) << 24);
+}
+
+template <int K, bool FP8>
+__global__ void __launch_bounds__(THREADS, 1)
+k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES2 * STAGE2_BYTES + B2_BYTES);
+    uint64_t *empty = full + STAGES2;
+    uint64_t *acc_full = empty + STAGES2;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *drain = acc_empty + 2;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_lock_ok;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t crank = cluster_rank();   // 0: issues the pair's MMAs
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES2; ++i) {
+            mbar_init(&full[i], 1);    // rank 0's producer arms it for both CTAs' bytes
+            mbar_init(&empty[i], 1);   // one multicast commit per use
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 256);   // every epilogue thread of both CTAs
+        }
+        mbar_init(drain, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc2(&s_tmem, TMEM2_COLS);
+        tmem_relinquish2();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    volatile int *abort_flag = &s_abort;
+    auto give_up = [&]() {
+        *abort_flag = 1;
+        hd_flag(a.status, HD_DEV_TIMEOUT);
+    };
+    // both CTAs must hold the same tensor-memory columns; otherwise do nothing
+    if (threadIdx.x == 0 && ld_cluster_u32(cluster_addr(&s_tmem, crank ^ 1u)) != tmem) {
+        *abort_flag = 1;
+        hd_flag(a.status, HD_DEV_TMEM);
+    }
+    __syncthreads();
+    const uint32_t cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+    const uint32_t total = a.pair_start[a.n_pairs];
+    const uint32_t nchunks = a.row_bytes / KB;
+
+    if (warp == 0) {
+        // ------------------------------------------------------- producers
+        if (lane == 0) {
+            const uint32_t full0 = cluster_addr(&full[0], 0);   // rank 0's stage barriers
+            uint32_t it = 0;
+            for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
+                uint32_t b, t0, t1;
+                item_range(a, item, b, t0, t1);
+                for (uint32_t t = t0; t < t1 && !*abort_flag; ++t) {
+                    const int32_t r0 = (int32_t)(t * TN + crank * (TN / 2));
+                    for (uint32_t c = 0; c < nchunks; ++c, ++it) {
+                        const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
+                        if (!mbar_wait(&empty[s], ph ^ 1u, a.wait_ns)) { give_up(); break; }
+                        if (crank == 0) mbar_expect_tx(&full[s], 2 * STAGE2_BYTES);
+                        if (a.stall && it == 0) continue;   // nothing ever completes this stage
+                        uint8_t *sa = smem + s * STAGE2_BYTES, *sb = sa + A_BYTES;
+                        const uint32_t bar = full0 + s * 8u;
+                        tma_load_2d_pair(sa, &qmap, (int32_t)(c * KB), (int32_t)((b * 2 + crank) * TM), bar);
+                        tma_load_2d_pair(sb, &lmap, (int32_t)(c * KB), r0, bar);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------- MMA issuer (rank 0 only)
+        if (lane == 0 && crank == 0) {
+            constexpr uint32_t idesc = instr_desc2<FP8>();
+            uint32_t it = 0, acc_it = 0;
+            for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
+                uint32_t b, t0, t1;
+                item_range(a, item, b, t0, t1);
+                for (uint32_t t = t0; t < t1 && !*abort_flag; ++t, ++acc_it) {
+                    const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
+                    const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
+                    if (!mbar_wait(&acc_empty[buf], aph ^ 1u, a.wait_ns)) { give_up(); break; }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + buf * TN;
+                    bool ok = true;
+                    for (uint32_t c = 0; c < nchunks; ++c, ++it) {
+                        const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
+                        if (!mbar_wait(&full[s], ph, a.wait_ns)) { give_up(); ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sa = smem_addr(smem + s * STAGE2_BYTES), sb = sa + A_BYTES;
+                        const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
+#pragma unroll
+                        for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
+                            mma_issue2<FP8>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
+                        mma_commit2_mc(&empty[s], 0x3);
+                    }
+                    if (!ok) break;
+                    mma_commit2_mc(&acc_full[buf], 0x3);
+                }
+            }
+            // every issued MMA has finished before either CTA releases its memory
+            mma_commit2(drain);
+            mbar_wait(drain, 0, a.wait_ns);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------- epilogue
+        const uint32_t quarter = warp & 3;              // TMEM lanes this warp may read
+        const uint32_t row = quarter * 32 + lane;       // query row within the block
+        const uint32_t lane_addr = (quarter * 32) << 16;
+        const bool leader = threadIdx.x == 64;
+        const uint32_t acc_empty0 = cluster_addr(&acc_empty[0], 0);
+        uint32_t acc_it = 0;
+        for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
+            uint32_t b, t0, t1;
+            item_range(a, item, b, t0, t1);
+            const uint32_t sb_ = b * 2 + crank;      // this CTA's query block
+            const uint32_t sq = sb_ * TM + row;
+            const uint32_t lo = sq < a.n_q ? a.lo[sq] : 0u, hi = sq < a.n_q ? a.hi[sq] : 0u;
+            const uint32_t span = hi > lo ? hi - lo : 0u;
+            uint64_t best[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) best[i] = KEY_NONE;
+            bool ok = true;
+            for (uint32_t t = t0; t < t1; ++t, ++acc_it) {
+                const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
+                const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
+                if (!mbar_wait(&acc_full[buf], aph, a.wait_ns)) { give_up(); ok = false; break; }
+                tc_fence_after();
+                const uint32_t r0 = t * TN;
+#pragma unroll 1
+                for (uint32_t cg = 0; cg < TN / 32; ++cg) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
+                    tmem_ld_wait();
+                    const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const uint32_t r = r0 + cg * 32 + e;
+                        const int s = __float2int_rn(__uint_as_float(v[e]));
+                        const uint32_t d = (uint32_t)((int)a.dim - s) >> 1;
+                        if (r - lo < span && d <= thr) {
+                            const uint64_t key = ((uint64_t)d << 32) | __ldg(a.lib_orig + r);
+                            if (key < best[K - 1]) topk_insert<K>(best, key);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive_remote(acc_empty0 + buf * 8u);
+            }
+            // merge into the block's running top-k under its lock (bounded spin)
+            epi_bar();
+            if (leader) {
+                int got = 0;
+                if (ok && !*abort_flag) {
+                    const uint64_t w0 = hd_globaltimer_ns();
+                    for (uint32_t i = 0;; ++i) {
+                        if (atomicCAS(&a.locks[sb_], 0u, 1u) == 0u) { got = 1; break; }
+                        if ((i & 63u) == 0 && hd_globaltimer_ns() - w0 > a.wait_ns) { give_up(); break; }
+                    }
+                    __threadfence();
+                }
+                s_lock_ok = got;
+            }
+            epi_bar();
+            const bool locked = s_lock_ok != 0;
+            if (locked) {
+                if (sq < a.n_q) {
+                    unsigned long long *g = reinterpret_cast<unsigned long long *>(a.top + (size_t)sq * K);
+                    uint64_t cur[K];
+#pragma unroll
+                    for (int i = 0; i < K; ++i) cur[i] = __ldcg(g + i);
+                    topk_merge<K>(cur, best);
+#pragma unroll
+                    for (int i = 0; i < K; ++i) __stcg(g + i, (unsigned long long)cur[i]);
+                }
+                __threadfence();
+            }
+            epi_bar();
+            if (leader && locked) atomicExch(&a.locks[sb_], 0u);
+            if (!locked) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // rank 0's MMAs have drained; neither CTA issues loads any more
+    // after a give-up anywhere, loads issued before the barrier may still be
+    // landing in this CTA's shared memory: a bounded pause lets them complete
+    if (threadIdx.x == 0 && (*abort_flag || (a.status && (atomicOr_system(a.status, 0u) & HD_DEV_TIMEOUT) != 0u))) {
+        const uint64_t w0 = hd_globaltimer_ns();
+        while (hd_globaltimer_ns() - w0 < 200000ull) __nanosleep(1000);
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc2(tmem, TMEM2_COLS);
 }
 
 // Work list of the L2-blocked schedule (one CTA of 1024 threads): per query
@@ -554,20 +881,23 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
                   uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
                   cudaStream_t s, const hd_mma_tuning &tune)
 {
-    const uint32_t cs = tune.cluster;   // 1, 2 or 4 CTAs per cluster
+    const bool pair = tune.cta_group == 2;   // SM pairs, M = 256 (cluster of 2)
+    const uint32_t cs = pair ? 2u : tune.cluster;   // 1, 2 or 4 CTAs per cluster
     const uint32_t n_blocks = (n_q + TM * cs - 1) / (TM * cs);
     const uint32_t row_bytes = lib->dim * (FP8 ? 1u : 2u);
     const uint8_t *lib_x = FP8 ? lib->x_fp8 : lib->x_bf16;
     if (!lib_x) return hd_fail(HD_ERR_INVALID_ARG, "library not prepared for this tensor-core form");
-    auto kern = cs == 4 ? k_search_mma<K, FP8, 4> : (cs == 2 ? k_search_mma<K, FP8, 2> : k_search_mma<K, FP8, 1>);
-    HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    auto kern = pair ? k_search_mma2<K, FP8>
+                     : (cs == 4 ? k_search_mma<K, FP8, 4> : (cs == 2 ? k_search_mma<K, FP8, 2> : k_search_mma<K, FP8, 1>));
+    const uint32_t smem_bytes = pair ? SMEM2_BYTES : SMEM_BYTES;
+    HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
     if (cs > 1) HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     uint32_t grid = (uint32_t)lib->num_sms / cs * cs;
     if (cs > 1) {   // only co-resident clusters: a persistent grid must not wait for SMs
         cudaLaunchConfig_t qc = {};
         qc.gridDim = dim3(grid);
         qc.blockDim = dim3(THREADS);
-        qc.dynamicSmemBytes = SMEM_BYTES;
+        qc.dynamicSmemBytes = smem_bytes;
         cudaLaunchAttribute qa[1];
         qa[0].id = cudaLaunchAttributeClusterDimension;
         qa[0].val.clusterDim.x = cs;
@@ -631,7 +961,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(THREADS);
-        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.dynamicSmemBytes = smem_bytes;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -690,6 +1020,7 @@ hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_h
     if (tu.tile_group == 0) tu.tile_group = 16;
     if (tu.super_group == 0) tu.super_group = 8;
     if (tu.cluster != 1 && tu.cluster != 2 && tu.cluster != 4) tu.cluster = 2;
+    if (tu.cta_group == 0) tu.cta_group = tu.cluster == 2 ? 2u : 1u;   // default: SM pairs
     if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
     return run_fmt<false>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
 }

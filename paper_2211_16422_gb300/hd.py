@@ -47,7 +47,7 @@ class _Window(C.Structure):
 
 class _TuneResult(C.Structure):
     _fields_ = [("form", C.c_int), ("tile_group", C.c_uint32), ("super_group", C.c_uint32),
-                ("cluster", C.c_uint32), ("ms", C.c_double)]
+                ("cluster", C.c_uint32), ("cta_group", C.c_uint32), ("ms", C.c_double)]
 
 
 def _windows(windows):
@@ -78,7 +78,7 @@ _SIGS = {
     "hd_library_export": ([P, P, P, P, P, P], i32),
     "hd_library_status": ([P], i32),
     "hd_library_prepare": ([P, i32], i32),
-    "hd_library_set_schedule": ([P, u32, u32, u32], i32),
+    "hd_library_set_schedule": ([P, u32, u32, u32, u32], i32),
     "hd_library_set_wait_limit": ([P, u64], i32),
     "hd_library_inject_stall": ([P, u32], i32),
     "hd_query_windows": ([P, P, P, u32, dbl, i32, P, P, P], i32),
@@ -266,9 +266,12 @@ def hd_library_prepare(lib: Library, form: str):
     _check(load().hd_library_prepare(lib.handle, FORMS[form]))
 
 
-def hd_library_set_schedule(lib: Library, tile_group: int = 0, super_group: int = 0, cluster: int = 0):
-    """Work-item shape and multicast cluster size of the tensor-core forms (0 = default)."""
-    _check(load().hd_library_set_schedule(lib.handle, int(tile_group), int(super_group), int(cluster)))
+def hd_library_set_schedule(lib: Library, tile_group: int = 0, super_group: int = 0, cluster: int = 0,
+                            cta_group: int = 0):
+    """Work-item shape, multicast cluster size and SM pairing (cta_group 2) of
+    the tensor-core forms (0 = default)."""
+    _check(load().hd_library_set_schedule(lib.handle, int(tile_group), int(super_group), int(cluster),
+                                          int(cta_group)))
 
 
 def hd_library_set_wait_limit(lib: Library, seconds: float = 0.0):
@@ -419,7 +422,7 @@ def hd_library_autotune(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=
                                       C.byref(n_all)))
     names = {v: k_ for k_, v in FORMS.items()}
     conv = lambda r: {"form": names[r.form], "tile_group": r.tile_group, "super_group": r.super_group,
-                      "cluster": r.cluster, "ms": r.ms}
+                      "cluster": r.cluster, "cta_group": r.cta_group, "ms": r.ms}
     return conv(best), [conv(allr[i]) for i in range(min(64, n_all.value))]
 
 

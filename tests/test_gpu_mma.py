@@ -154,10 +154,12 @@ def test_auto_prefers_prepared_tc_form(hd):
     assert torch.equal(i0, i1) and torch.equal(d0, d1)
 
 
-@pytest.mark.parametrize("tg,sg,cs", [(1, 1, 1), (2, 3, 2), (64, 64, 4), (8, 4, 2), (16, 8, 4), (3, 5, 1)])
-def test_tc_schedule_does_not_change_results(hd, tg, sg, cs):
-    """Work-item shape (tiles per item, groups per L2 slice) is a pure
-    performance knob: the top-k must not move."""
+@pytest.mark.parametrize("tg,sg,cs,cg", [(1, 1, 1, 1), (2, 3, 2, 1), (64, 64, 4, 1), (8, 4, 2, 1), (16, 8, 4, 1),
+                                         (3, 5, 1, 1), (1, 1, 2, 2), (3, 5, 2, 2), (16, 8, 2, 2), (64, 64, 2, 2)])
+def test_tc_schedule_does_not_change_results(hd, tg, sg, cs, cg):
+    """Work-item shape (tiles per item, groups per L2 slice), multicast
+    cluster and SM pairing are pure performance knobs: the top-k must not
+    move."""
     rng = np.random.Generator(np.random.PCG64(17))
     refs = synth.make_references(9000, (2, 3), (0.7, 0.3), rng, decoy_fraction=0.5)
     qs = synth.make_queries(refs, 700, rng)
@@ -172,7 +174,7 @@ def test_tc_schedule_does_not_change_results(hd, tg, sg, cs):
     r_hv, q_hv = enc(refs), enc(qs)
     lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
     hd.hd_library_prepare(lib, "tc_fp8")
-    hd.hd_library_set_schedule(lib, tg, sg, cs)
+    hd.hd_library_set_schedule(lib, tg, sg, cs, cg)
     i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), 500.0, "da", k, form="tc_fp8")
     torch.cuda.synchronize()
     lib.status()
@@ -180,3 +182,48 @@ def test_tc_schedule_does_not_change_results(hd, tg, sg, cs):
     oi, od = oracle.search(D, o_r, refs.precursor_mz, refs.charge, o_q,
                            qs.precursor_mz, qs.charge, 500.0, "da", k)
     assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
+
+
+@pytest.mark.parametrize("D,k,n_q,tol,unit", [(2048, 1, 300, 500.0, "da"), (4096, 16, 257, 150.0, "da"),
+                                              (8192, 5, 1, 500.0, "da"), (2048, 2, 700, 20.0, "ppm")])
+def test_tc_pair_form_exact(hd, D, k, n_q, tol, unit):
+    """The 2-SM form (one M = 256 tensor-core operation per SM pair) gives the
+    oracle's top-k for both operand types, with ragged query blocks (257, 1)
+    and narrow windows."""
+    rng = np.random.Generator(np.random.PCG64(40 + k))
+    refs = synth.make_references(6000, (2, 3, 4), (0.6, 0.3, 0.1), rng, decoy_fraction=0.5)
+    qs = synth.make_queries(refs, n_q, rng)
+    Q = 16
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, 5)
+
+    def enc(sp):
+        return hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(sp.offsets), dev(sp.mz), dev(sp.intensity), **pp))
+
+    lib = hd.hd_build_library(ctx, enc(refs), dev(refs.precursor_mz), dev(refs.charge))
+    q_hv = enc(qs)
+    o_r, o_q = oracle_side.hvs(refs, D, Q, 5), oracle_side.hvs(qs, D, Q, 5)
+    oi, od = oracle.search(D, o_r, refs.precursor_mz, refs.charge, o_q, qs.precursor_mz, qs.charge, tol, unit, k)
+    for form in ("tc_fp8", "tc_bf16"):
+        hd.hd_library_prepare(lib, form)
+        hd.hd_library_set_schedule(lib, 4, 2, 2, 2)
+        i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), tol, unit, k, form=form)
+        torch.cuda.synchronize()
+        lib.status()
+        assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od), form
+
+
+def test_schedule_arguments_checked(hd):
+    rng = np.random.default_rng(3)
+    D, W, n = 2048, 32, 100
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library(ctx, dev(rng.integers(-2**63, 2**63, (n, W), dtype=np.int64)),
+                              dev(rng.uniform(400, 600, n)), dev(np.full(n, 2, np.uint8)))
+    for args in [(0, 0, 3, 1), (0, 0, 0, 3), (0, 0, 4, 2), (0, 0, 1, 2), (5000, 0, 0, 0)]:
+        with pytest.raises(hd.HDError) as e:
+            hd.hd_library_set_schedule(lib, *args)
+        assert e.value.status == hd.HD_ERR_INVALID_ARG
+    hd.hd_library_set_schedule(lib, 0, 0, 0, 2)
+    hd.hd_library_set_schedule(lib, 0, 0, 2, 2)
+    hd.hd_library_set_schedule(lib, 0, 0, 0, 0)
