@@ -45,7 +45,11 @@ L2_BYTES = 129 * 2**20
 # otherwise `traffic` is null.
 KERNEL_SOURCES = ("paper_2211_16422_gb300/csrc/search_mma.cu", "paper_2211_16422_gb300/csrc/search_common.cuh",
                   "paper_2211_16422_gb300/csrc/hd_internal.cuh")
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+    #     -k regex:k_search_mma -s 48 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
+    ("k_search_mma2", "tc_fp8", 16, 8, 2, 2): {"bytes": 493.63e9 + 0.23047e9, "sha256": "134d11aa6dc65e18"},
+}
 
 
 def kernel_source_hash():

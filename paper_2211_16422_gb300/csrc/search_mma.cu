@@ -448,7 +448,11 @@ constexpr int BUFS2 = HD_MMA2_BUFS;                 // accumulator buffers in te
 constexpr uint32_t TMEM2_COLS = BUFS2 * TN;
 // B2_BYTES of slack after the ring keep every operand read of the last stage
 // inside the allocation, whatever the split of B between the two CTAs.
-constexpr uint32_t SMEM2_BYTES = STAGES2 * STAGE2_BYTES + B2_BYTES + 1024 + 256;
+#ifndef HD_MMA2_PAD
+#define HD_MMA2_PAD 1
+#endif
+constexpr uint32_t PAD2_BYTES = HD_MMA2_PAD ? B2_BYTES : 0u;
+constexpr uint32_t SMEM2_BYTES = STAGES2 * STAGE2_BYTES + PAD2_BYTES + 1024 + 256;
 static_assert(SMEM2_BYTES <= 232448, "shared memory (2-SM form)");
 static_assert((BUFS2 == 1 || BUFS2 == 2) && TN == 256, "2-SM form: N = 256, one or two accumulators");
 
@@ -546,7 +550,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES2 * STAGE2_BYTES + B2_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES2 * STAGE2_BYTES + PAD2_BYTES);
     uint64_t *empty = full + STAGES2;
     uint64_t *acc_full = empty + STAGES2;
     uint64_t *acc_empty = acc_full + 2;
