@@ -47,8 +47,8 @@ KERNEL_SOURCES = ("paper_2211_16422_gb300/csrc/search_mma.cu", "paper_2211_16422
                   "paper_2211_16422_gb300/csrc/hd_internal.cuh")
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
-    #     -k regex:k_search_mma -s 48 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
-    ("k_search_mma2", "tc_fp8", 16, 8, 2, 2): {"bytes": 493.63e9 + 0.23047e9, "sha256": "134d11aa6dc65e18"},
+    #     -k regex:k_search_mma -s 72 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
+    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 458.54e9 + 0.06245e9, "sha256": "fb74755592a66dfb"},
 }
 
 
@@ -337,12 +337,15 @@ def run_ours(args, rank, world, local_rank):
     if form.startswith("tc_"):
         # dense +-1 contraction: 2*D flops per in-window comparison (masked tile
         # padding is not counted)
+        # the search kernel is timed alone in a sub-second region at the full
+        # SM clock: the burst bf16 figure applies (x2 for e4m3, the nominal
+        # 4.5 / 2.25 PFLOP/s dense ratio)
         peaks = measured_peaks()
-        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+        bf16 = peaks.get("bf16_tflops", 1900.0)
         peak = bf16 * (2.0 if form == "tc_fp8" else 1.0)
         achieved = comparisons * 2.0 * D / (avg_search_ms / 1e3) / 1e12
-        basis = ("measured sustained cuBLAS bf16 x 2 (nominal fp8/bf16 ratio 4.5/2.25)" if form == "tc_fp8"
-                 else "measured sustained cuBLAS bf16")
+        basis = ("measured burst cuBLAS bf16 x 2 (nominal fp8/bf16 ratio 4.5/2.25)" if form == "tc_fp8"
+                 else "measured burst cuBLAS bf16")
         sched = setup.get("autotune_choice") or {"tile_group": 16, "super_group": 8, "cluster": 2, "cta_group": 2}
         kname = "k_search_mma2" if sched.get("cta_group") == 2 else "k_search_mma"
         roofline = {"kernel": kname, "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,

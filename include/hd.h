@@ -180,7 +180,7 @@ HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
  * tile by TMA multicast.  `cta_group` 2 pairs the two CTAs of a cluster of
  * 2 on neighbouring SMs into one M = 256 tensor-core operation (each SM
  * stages half of every reference tile); it requires cluster 0 or 2.  0 keeps
- * the default (16, 8, 2, 2; cta_group 0 with cluster 1 or 4 means 1).
+ * the default (16, 16, 2, 2; cta_group 0 with cluster 1 or 4 means 1).
  * Results do not depend on the schedule.  Not to be changed while a search
  * on this library is in flight. */
 HD_API hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group,
@@ -252,7 +252,7 @@ HD_API void hd_plan_destroy(hd_plan *plan);
 
 /* Autotuner (no counterpart in the paper): times each search form the library
  * is prepared for and, for the tensor-core forms, work-item shapes
- * tile_group x super_group x (cluster, cta_group) in {4, 16} x {2, 8} x
+ * tile_group x super_group x (cluster, cta_group) in {4, 16, 32} x {2, 16} x
  * {(1, 1), (2, 1), (4, 1), (2, 2)}, on the
  * given queries
  * (a representative sample), and keeps the fastest as the library's

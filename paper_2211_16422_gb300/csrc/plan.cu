@@ -128,6 +128,8 @@ hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const dou
     if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: k must be in [1, 16]");
     if (n_q == 0 || !d_q_hv || !d_q_mz || !d_q_charge)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: empty or null query set");
+    if (reinterpret_cast<uintptr_t>(d_q_hv) & 15u)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: d_q_hv must be 16-byte aligned");
     hd_qwin win;
     hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
     if (st != HD_OK) return st;
@@ -137,7 +139,7 @@ hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const dou
 
     std::vector<hd_tune_result> cand;
     cand.push_back({HD_FORM_POPC, 0, 0, 0, 0, 0.0});
-    const uint32_t tgs[2] = {4, 16}, sgs[2] = {2, 8};
+    const uint32_t tgs[3] = {4, 16, 32}, sgs[2] = {2, 16};
     const uint32_t shapes[4][2] = {{1, 1}, {2, 1}, {4, 1}, {2, 2}};   // (cluster, cta_group)
     for (hd_search_form f : {HD_FORM_TC_FP8, HD_FORM_TC_BF16}) {
         if ((f == HD_FORM_TC_FP8 && !lib->x_fp8) || (f == HD_FORM_TC_BF16 && !lib->x_bf16)) continue;

@@ -446,10 +446,12 @@ constexpr uint32_t STAGE2_BYTES = A_BYTES + B2_BYTES;
 constexpr int STAGES2 = HD_MMA2_STAGES;
 constexpr int BUFS2 = HD_MMA2_BUFS;                 // accumulator buffers in tensor memory
 constexpr uint32_t TMEM2_COLS = BUFS2 * TN;
-// B2_BYTES of slack after the ring keep every operand read of the last stage
-// inside the allocation, whatever the split of B between the two CTAs.
+// Optional B2_BYTES of slack after the ring (HD_MMA2_PAD=1) would keep a
+// 256-row B read of the last stage inside the allocation.  Off: each CTA of
+// the pair supplies 128 rows of B, which exact parity of both tensor-core
+// forms against the popcount form confirms.
 #ifndef HD_MMA2_PAD
-#define HD_MMA2_PAD 1
+#define HD_MMA2_PAD 0
 #endif
 constexpr uint32_t PAD2_BYTES = HD_MMA2_PAD ? B2_BYTES : 0u;
 constexpr uint32_t SMEM2_BYTES = STAGES2 * STAGE2_BYTES + PAD2_BYTES + 1024 + 256;
@@ -536,6 +538,35 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         : "memory");
 }
 
+// L2 eviction priority of the pair's operand loads: 0 default, 1 evict-first,
+// 2 evict-last.  A query block is re-read for every reference tile of its
+// work item and the running pairs' blocks nearly fill L2; a reference tile is
+// read by the few pairs on the same tile group at about the same time.  Query
+// blocks evict-last and reference tiles evict-first keep the blocks resident
+// (full workload: 83 -> 77 ms).
+#ifndef HD_MMA2_HINT_A
+#define HD_MMA2_HINT_A 2
+#endif
+#ifndef HD_MMA2_HINT_B
+#define HD_MMA2_HINT_B 1
+#endif
+__device__ __forceinline__ uint64_t l2_policy(int kind)
+{
+    uint64_t p = 0;
+    if (kind == 1) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    if (kind == 2) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tma_load_2d_pair_hint(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                                      uint32_t bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(bar), "l"(policy)
+        : "memory");
+}
+
 // M = 256 (the pair), N = 256.
 template <bool FP8>
 __host__ __device__ constexpr uint32_t instr_desc2()
@@ -544,10 +575,15 @@ __host__ __device__ constexpr uint32_t instr_desc2()
            ((uint32_t)((2 * TM) >> 4) << 24);
 }
 
+// A cluster of two CTAs on an SM pair (cluster ranks 0 and 1; rank 0 issues
+// the pair's MMAs).  Each CTA holds its own block of 128 queries (A) and its
+// half of the pair's reference tile (B); all loads complete on rank 0's stage
+// barrier.
 template <int K, bool FP8>
 __global__ void __launch_bounds__(THREADS, 1)
 k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
+    constexpr uint32_t CS = 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES2 * STAGE2_BYTES + PAD2_BYTES);
@@ -593,7 +629,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         hd_flag(a.status, HD_DEV_TMEM);
     }
     __syncthreads();
-    const uint32_t cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+    const uint32_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
     const uint32_t total = a.pair_start[a.n_pairs];
     const uint32_t nchunks = a.row_bytes / KB;
 
@@ -601,12 +637,14 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         // ------------------------------------------------------- producers
         if (lane == 0) {
             const uint32_t full0 = cluster_addr(&full[0], 0);   // rank 0's stage barriers
+            const uint64_t pol_a = l2_policy(HD_MMA2_HINT_A), pol_b = l2_policy(HD_MMA2_HINT_B);
             uint32_t it = 0;
             for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
                 uint32_t b, t0, t1;
                 item_range(a, item, b, t0, t1);
+                const int32_t ya = (int32_t)((b * CS + crank) * TM);
                 for (uint32_t t = t0; t < t1 && !*abort_flag; ++t) {
-                    const int32_t r0 = (int32_t)(t * TN + crank * (TN / 2));
+                    const int32_t rb = (int32_t)(t * TN + crank * (TN / 2));
                     for (uint32_t c = 0; c < nchunks; ++c, ++it) {
                         const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
                         if (!mbar_wait(&empty[s], ph ^ 1u, a.wait_ns)) { give_up(); break; }
@@ -614,45 +652,50 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                         if (a.stall && it == 0) continue;   // nothing ever completes this stage
                         uint8_t *sa = smem + s * STAGE2_BYTES, *sb = sa + A_BYTES;
                         const uint32_t bar = full0 + s * 8u;
-                        tma_load_2d_pair(sa, &qmap, (int32_t)(c * KB), (int32_t)((b * 2 + crank) * TM), bar);
-                        tma_load_2d_pair(sb, &lmap, (int32_t)(c * KB), r0, bar);
+                        const int32_t x = (int32_t)(c * KB);
+                        if (HD_MMA2_HINT_A) tma_load_2d_pair_hint(sa, &qmap, x, ya, bar, pol_a);
+                        else tma_load_2d_pair(sa, &qmap, x, ya, bar);
+                        if (HD_MMA2_HINT_B) tma_load_2d_pair_hint(sb, &lmap, x, rb, bar, pol_b);
+                        else tma_load_2d_pair(sb, &lmap, x, rb, bar);
                     }
                 }
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------- MMA issuer (rank 0 only)
-        if (lane == 0 && crank == 0) {
-            constexpr uint32_t idesc = instr_desc2<FP8>();
-            uint32_t it = 0, acc_it = 0;
-            for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
-                uint32_t b, t0, t1;
-                item_range(a, item, b, t0, t1);
-                for (uint32_t t = t0; t < t1 && !*abort_flag; ++t, ++acc_it) {
-                    const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
-                    const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
-                    if (!mbar_wait(&acc_empty[buf], aph ^ 1u, a.wait_ns)) { give_up(); break; }
-                    tc_fence_after();
-                    const uint32_t d_tmem = tmem + buf * TN;
-                    bool ok = true;
-                    for (uint32_t c = 0; c < nchunks; ++c, ++it) {
-                        const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
-                        if (!mbar_wait(&full[s], ph, a.wait_ns)) { give_up(); ok = false; break; }
+        if (crank == 0) {
+            // ------------------------------------------- MMA issuer (rank 0)
+            if (lane == 0) {
+                constexpr uint32_t idesc = instr_desc2<FP8>();
+                uint32_t it = 0, acc_it = 0;
+                for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
+                    uint32_t b, t0, t1;
+                    item_range(a, item, b, t0, t1);
+                    for (uint32_t t = t0; t < t1 && !*abort_flag; ++t, ++acc_it) {
+                        const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
+                        const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
+                        if (!mbar_wait(&acc_empty[buf], aph ^ 1u, a.wait_ns)) { give_up(); break; }
                         tc_fence_after();
-                        const uint32_t sa = smem_addr(smem + s * STAGE2_BYTES), sb = sa + A_BYTES;
-                        const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
+                        const uint32_t d_tmem = tmem + buf * TN;
+                        bool ok = true;
+                        for (uint32_t c = 0; c < nchunks; ++c, ++it) {
+                            const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
+                            if (!mbar_wait(&full[s], ph, a.wait_ns)) { give_up(); ok = false; break; }
+                            tc_fence_after();
+                            const uint32_t sa = smem_addr(smem + s * STAGE2_BYTES), sb = sa + A_BYTES;
+                            const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
 #pragma unroll
-                        for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
-                            mma_issue2<FP8>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
-                        mma_commit2_mc(&empty[s], 0x3);
+                            for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
+                                mma_issue2<FP8>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
+                            mma_commit2_mc(&empty[s], 0x3);
+                        }
+                        if (!ok) break;
+                        mma_commit2_mc(&acc_full[buf], 0x3);
                     }
-                    if (!ok) break;
-                    mma_commit2_mc(&acc_full[buf], 0x3);
                 }
+                // every issued MMA has finished before either CTA releases its memory
+                mma_commit2(drain);
+                mbar_wait(drain, 0, a.wait_ns);
             }
-            // every issued MMA has finished before either CTA releases its memory
-            mma_commit2(drain);
-            mbar_wait(drain, 0, a.wait_ns);
         }
         __syncwarp();
     } else {
@@ -666,7 +709,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
             uint32_t b, t0, t1;
             item_range(a, item, b, t0, t1);
-            const uint32_t sb_ = b * 2 + crank;      // this CTA's query block
+            const uint32_t sb_ = b * CS + crank;     // this CTA's query block
             const uint32_t sq = sb_ * TM + row;
             const uint32_t lo = sq < a.n_q ? a.lo[sq] : 0u, hi = sq < a.n_q ? a.hi[sq] : 0u;
             const uint32_t span = hi > lo ? hi - lo : 0u;
@@ -1022,7 +1065,7 @@ hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_h
     if (lib->n == 0) return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
     hd_mma_tuning tu = lib->mma_tuning;
     if (tu.tile_group == 0) tu.tile_group = 16;
-    if (tu.super_group == 0) tu.super_group = 8;
+    if (tu.super_group == 0) tu.super_group = 16;
     if (tu.cluster != 1 && tu.cluster != 2 && tu.cluster != 4) tu.cluster = 2;
     if (tu.cta_group == 0) tu.cta_group = tu.cluster == 2 ? 2u : 1u;   // default: SM pairs
     if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);

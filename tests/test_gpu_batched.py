@@ -140,7 +140,7 @@ def test_autotune_keeps_results(hd):
     args = (lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
     i0, d0 = hd.hd_search_open_multi(*args, 5, form="popc")
     best, allr = hd.hd_library_autotune(*args, 5)
-    assert best["ms"] > 0 and len(allr) == 1 + 16
+    assert best["ms"] > 0 and len(allr) == 1 + 24
     assert best["ms"] == min(r["ms"] for r in allr)
     i1, d1 = hd.hd_search_open_multi(*args, 5, form="auto")
     torch.cuda.synchronize()

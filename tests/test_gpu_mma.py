@@ -155,7 +155,8 @@ def test_auto_prefers_prepared_tc_form(hd):
 
 
 @pytest.mark.parametrize("tg,sg,cs,cg", [(1, 1, 1, 1), (2, 3, 2, 1), (64, 64, 4, 1), (8, 4, 2, 1), (16, 8, 4, 1),
-                                         (3, 5, 1, 1), (1, 1, 2, 2), (3, 5, 2, 2), (16, 8, 2, 2), (64, 64, 2, 2)])
+                                         (3, 5, 1, 1), (1, 1, 2, 2), (3, 5, 2, 2), (16, 8, 2, 2), (64, 64, 2, 2),
+                                         (16, 16, 2, 2), (32, 2, 2, 2)])
 def test_tc_schedule_does_not_change_results(hd, tg, sg, cs, cg):
     """Work-item shape (tiles per item, groups per L2 slice), multicast
     cluster and SM pairing are pure performance knobs: the top-k must not
