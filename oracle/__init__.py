@@ -150,3 +150,71 @@ def search(dim, ref_hv, ref_mz, ref_z, q_hv, q_mz, q_z, tol, unit="da", k=1, whi
     if rc:
         raise ValueError(f"orc_search rc={rc}")
     return idx, dist
+
+
+def fdr_qvalues(scores, is_decoy):
+    """Target-decoy q-values of spectrum-spectrum matches (SSMs), the FDR
+    filter of Section 2.1 (the target-decoy strategy the paper cites).
+
+    Plain definition, written out: order the SSMs by score, highest first.
+    The threshold at score s accepts every SSM with score >= s; its FDR is
+    (decoy SSMs with score >= s) / (target SSMs with score >= s), with the
+    denominator taken as 1 when it is 0.  The q-value of an SSM with score s
+    is the smallest FDR over all thresholds s' <= s.  Equal scores share one
+    threshold.  Returns float64 q per SSM, in the input order.
+    """
+    s = np.asarray(scores, np.int64)
+    d = np.asarray(is_decoy).astype(bool)
+    n = s.size
+    if n == 0:
+        return np.zeros(0, np.float64)
+    order = np.argsort(-s, kind="stable")
+    s_sorted, d_sorted = s[order], d[order]
+    n_dec = np.cumsum(d_sorted)
+    n_tgt = np.cumsum(~d_sorted)
+    last = np.r_[np.nonzero(np.diff(s_sorted))[0], n - 1]   # last SSM of each run of equal scores
+    fdr = n_dec[last].astype(np.float64) / np.maximum(n_tgt[last], 1).astype(np.float64)
+    q_run = np.minimum.accumulate(fdr[::-1])[::-1]           # min over this and every lower threshold
+    run = np.searchsorted(last, np.arange(n))                 # run of each sorted position
+    q = np.empty(n, np.float64)
+    q[order] = q_run[run]
+    return q
+
+
+def cascade(dim, ref_hv, ref_mz, ref_z, ref_decoy, q_hv, q_mz, q_z, levels, fdr, n_threads=None):
+    """Cascade search (Section 3.4, after the cascade strategy the paper
+    cites): levels are searched in order, each with its own precursor window
+    (tol, unit).  At a level, the queries not identified so far are searched
+    (top-1, as ``search``); the level's SSMs -- those queries with at least one
+    candidate -- get q-values among themselves (``fdr_qvalues`` on the score
+    D - dist); an SSM whose reference is a target and whose q <= fdr
+    identifies its query at that level, and the query leaves the cascade.
+
+    Returns (idx u32 [n], dist u16 [n], level u8 [n], q f64 [n]): the SSM of
+    the last level each query was searched at (idx 0xFFFFFFFF, dist 0xFFFF,
+    q NaN when that level had no candidate), and the level that identified it
+    (0xFF: none).
+    """
+    dec_flags = np.asarray(ref_decoy).astype(bool)
+    n = int(np.asarray(q_mz).size)
+    idx = np.full(n, 0xFFFFFFFF, np.uint32)
+    dist = np.full(n, 0xFFFF, np.uint16)
+    level = np.full(n, 0xFF, np.uint8)
+    q = np.full(n, np.nan, np.float64)
+    active = np.arange(n, dtype=np.uint32)
+    for li, (tol, unit) in enumerate(levels):
+        if active.size == 0:
+            break
+        i1, d1 = search(dim, ref_hv, ref_mz, ref_z, q_hv, q_mz, q_z, tol, unit, k=1, which=active,
+                        n_threads=n_threads)
+        i1, d1 = i1[:, 0], d1[:, 0]
+        idx[active], dist[active], q[active] = i1, d1, np.nan
+        has = i1 != 0xFFFFFFFF
+        ssm = active[has]
+        is_dec = dec_flags[i1[has]]
+        qv = fdr_qvalues(dim - d1[has].astype(np.int64), is_dec)
+        q[ssm] = qv
+        hit = ssm[(~is_dec) & (qv <= fdr)]
+        level[hit] = li
+        active = np.setdiff1d(active, hit).astype(np.uint32)
+    return idx, dist, level, q
