@@ -231,6 +231,36 @@ HD_API hd_status hd_search_open_multi(const hd_library *lib, const uint64_t *d_q
                                       hd_search_form form, uint32_t *d_out_idx, uint16_t *d_out_dist,
                                       hd_stream stream);
 
+/* Decoy flags of the library's references (target-decoy strategy, Section
+ * 2.1): d_is_decoy [n_refs] in input order, nonzero = decoy.  Copied (the
+ * caller keeps its buffer); replaces earlier flags.  Synchronous. */
+HD_API hd_status hd_library_set_decoys(hd_library *lib, const uint8_t *d_is_decoy);
+
+/* Cascade search (Section 3.4: a narrow precursor window first, FDR
+ * filtering, then a wider window for the spectra still unidentified; FDR by
+ * the target-decoy strategy of Section 2.1).  Levels run in order, each with
+ * its window levels[l] (1 <= n_levels <= 16).  At a level, the queries not yet
+ * identified are searched with k = 1 (as hd_search_open_ex with `form`); the
+ * level's spectrum-spectrum matches (SSMs: queries with a candidate) are
+ * ranked by score D - dist; the FDR of the threshold at score s is (decoy
+ * SSMs with score >= s) / max(1, target SSMs with score >= s), and the
+ * q-value of an SSM with score s is the smallest FDR over thresholds <= s,
+ * in IEEE double.  An SSM whose reference is a target and whose q-value is
+ * <= fdr identifies its query at that level.
+ *   d_out_idx [n_q], d_out_dist [n_q]: the SSM of the last level the query
+ *     was searched at (the identifying level, else the last level);
+ *     idx 0xFFFFFFFF and dist 0xFFFF when that level had no candidate.
+ *   d_out_q [n_q]: that SSM's q-value (NaN without a candidate).
+ *   d_out_level [n_q]: the identifying level, 0xFF if none.
+ * Requires decoy flags (hd_library_set_decoys).  Query rows d_q_hv 16-byte
+ * aligned.  Scratch is allocated stream-ordered; the call synchronizes
+ * `stream` once per level (the next level's query count is read back). */
+HD_API hd_status hd_cascade_search(const hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,
+                                   const uint8_t *d_q_charge, uint32_t n_q, const hd_window *levels,
+                                   uint32_t n_levels, double fdr, hd_search_form form, uint32_t *d_out_idx,
+                                   uint16_t *d_out_dist, double *d_out_q, uint8_t *d_out_level,
+                                   hd_stream stream);
+
 /* Batched plan (no counterpart in the paper, which batches to fill memory,
  * Section 4.1): encoding (Eq. 1) of a fixed set of query batches plus the
  * multi-window search of all of them, captured once into a CUDA graph whose

@@ -2,7 +2,9 @@
 
 Python wrapper (ctypes) around ``hd_oracle.c``: a plain, slow C restatement
 of the paper's encoding (Section 3.3, Eq. 1), candidate filter and Hamming
-search (Section 3.4) and preprocessing (Section 3.2, Table 1).  Only the
+search (Section 3.4) and preprocessing (Section 3.2, Table 1); plus, in
+plain numpy on top of that search, the target-decoy q-values (Section 2.1)
+and the cascade search (Section 3.4).  Only the
 tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
 import this package.  It shares no code with the GPU library.
 """

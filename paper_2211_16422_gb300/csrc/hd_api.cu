@@ -114,6 +114,7 @@ void lib_release(hd_library *lib)
     cudaFree(lib->charge_start);
     cudaFree(lib->x_fp8);
     cudaFree(lib->x_bf16);
+    cudaFree(lib->decoy);
     status_free(lib->status);
     delete lib;
 }

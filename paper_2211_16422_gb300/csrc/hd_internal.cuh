@@ -74,6 +74,7 @@ struct hd_library {
     uint32_t *charge_start = nullptr;   // [257] first row with charge >= c (device)
     uint8_t *x_fp8 = nullptr;      // [n][D] bipolar e4m3 rows (tensor-core form), optional
     uint8_t *x_bf16 = nullptr;     // [n][2D] bipolar bf16 rows (tensor-core form), optional
+    uint8_t *decoy = nullptr;      // [n] decoy flags, input order, optional
     hd_mma_tuning mma_tuning;
     hd_search_form auto_form = HD_FORM_AUTO;   // set by the autotuner
     uint64_t wait_ns = 0;                      // device wait limit (0: HD_WAIT_NS)

@@ -87,6 +87,8 @@ _SIGS = {
     "hd_search_host": ([P, P, P, P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_search_open_noalloc": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_search_open_multi": ([P, P, P, P, P, u32, P, u32, u32, i32, P, P, P], i32),
+    "hd_library_set_decoys": ([P, P], i32),
+    "hd_cascade_search": ([P, P, P, P, u32, P, u32, dbl, i32, P, P, P, P, P], i32),
     "hd_plan_create": ([P, P, P, P, P, P, P, P, u32, P, u32, u32, i32, P, P, P, P], i32),
     "hd_plan_launch": ([P, P], i32),
     "hd_plan_info": ([P, P], i32),
@@ -361,6 +363,31 @@ def hd_search_open_multi(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k
                                        len(windows), int(k), FORMS[form], _ptr(out_idx), _ptr(out_dist),
                                        _stream(stream)))
     return out_idx, out_dist
+
+
+def hd_library_set_decoys(lib: Library, is_decoy):
+    """Decoy flags [n_refs] (uint8, input order, nonzero = decoy) for the cascade's FDR filter."""
+    f = _dev(is_decoy, torch.uint8, "is_decoy")
+    _check(load().hd_library_set_decoys(lib.handle, _ptr(f)))
+
+
+def hd_cascade_search(lib: Library, q_hv, q_mz, q_charge, levels, fdr=0.01, form="auto", stream=None):
+    """Cascade search with target-decoy FDR: `levels` is a list of (tol, unit) windows, narrow
+    first.  Returns (idx int32 [n], dist int16 [n], q float64 [n], level uint8 [n]); level 255 =
+    not identified."""
+    q_hv = _dev(q_hv, torch.int64, "q_hv")
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    n = q_mz.numel()
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    dist = torch.empty(n, dtype=torch.int16, device="cuda")
+    q = torch.empty(n, dtype=torch.float64, device="cuda")
+    level = torch.empty(n, dtype=torch.uint8, device="cuda")
+    w = _windows(levels)
+    _check(load().hd_cascade_search(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), n, w, len(levels),
+                                    float(fdr), FORMS[form], _ptr(idx), _ptr(dist), _ptr(q), _ptr(level),
+                                    _stream(stream)))
+    return idx, dist, q, level
 
 
 class Plan:

@@ -13,8 +13,10 @@ preprocessing settings (Table 1: 50 peaks, fragment m/z 101-1500):
 * reference: precursor m/z ~ U(400, 1500); charge from a per-workload
   distribution; ``n_peaks`` fragment peaks with m/z ~ U(101, 1500) and
   intensity sqrt(U(0.01, 1]) normalised to a maximum of 1;
-* decoy k (second half of the library): target k with its fragment m/z
-  values permuted within the spectrum (same precursor and charge);
+* decoy k (second half of the library): target k with its fragment peaks
+  repositioned -- new m/z ~ U(101, 1500), same intensities, precursor and
+  charge (the library's decoys come from shuffle-and-reposition, Section
+  4.1, which moves the fragments);
 * query: a copy of a uniformly drawn target; a mass shift drawn with equal
   probability from {0, +15.995, +42.011, +79.966, U(-100, 100)} Da is added
   to the precursor as shift/charge; 30% of the peaks move by shift/charge
@@ -87,7 +89,7 @@ def make_references(n, charges, weights, rng, n_peaks=50, decoy_fraction=0.0):
     mz_t = rng.uniform(FRAG_MZ_LO, FRAG_MZ_HI, (n_tgt, n_peaks))
     it_t = _intensities(rng, (n_tgt, n_peaks))
     if n_dec:
-        mz_d = rng.permuted(mz_t[:n_dec], axis=1)
+        mz_d = rng.uniform(FRAG_MZ_LO, FRAG_MZ_HI, (n_dec, n_peaks))
         mz = np.concatenate([mz_t, mz_d])
         it = np.concatenate([it_t, it_t[:n_dec]])
         prec = np.concatenate([prec_t, prec_t[:n_dec]])

@@ -22,3 +22,11 @@ def hvs(sp, D, Q, seed):
     """Oracle HVs [n, D/64] of raw spectra `sp` (synth.Spectra)."""
     F, L = item_memory(D, Q, seed)
     return oracle.encode(D, F, L, *oracle.preprocess(sp.offsets, sp.mz, sp.intensity, **pp_args(Q)))
+
+
+@functools.lru_cache(maxsize=1)
+def workload_ref_hvs(name, D, Q, seed):
+    """Oracle HVs of a named workload's references (cached: several tests use
+    the 1,000,000-reference library)."""
+    refs, _, _ = synth.make_workload(name)
+    return hvs(refs, D, Q, seed)

@@ -315,7 +315,7 @@ def test_full_size_sampled(hd):
     # search: a sample of queries by brute force over the whole library, on
     # the oracle's own encoding of every reference and of the sampled queries
     which = np.sort(rng.choice(qs.n, 48, replace=False)).astype(np.uint32)
-    r_np = oracle_side.hvs(refs, D, Q, 0)
+    r_np = oracle_side.workload_ref_hvs("full", D, Q, 0)
     q_sub = qs.subset(which)
     q_np = oracle_side.hvs(q_sub, D, Q, 0)
     assert np.array_equal(hd.as_u64(q_hv[torch.from_numpy(which.astype(np.int64)).cuda()]), q_np)
