@@ -24,7 +24,8 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-TOL_DA, TOL_PPM = 0, 1
+TOL_DA, TOL_PPM, TOL_MASS = 0, 1, 2
+_UNITS = {"da": TOL_DA, "ppm": TOL_PPM, "mass": TOL_MASS}
 
 
 def build(force: bool = False) -> str:
@@ -124,7 +125,7 @@ def window_count(ref_mz, ref_z, q_mz, q_z, tol, unit="da"):
     qm, qz = _c(q_mz, np.float64), _c(q_z, np.uint8)
     out = np.zeros(qm.size, np.uint32)
     _load().orc_window_count(rm.size, _p(rm), _p(rz), qm.size, _p(qm), _p(qz), float(tol),
-                             int(unit == "ppm"), _p(out))
+                             _UNITS[unit], _p(out))
     return out
 
 
@@ -137,7 +138,9 @@ def library_order(mz, z):
 
 def search(dim, ref_hv, ref_mz, ref_z, q_hv, q_mz, q_z, tol, unit="da", k=1, which=None,
            n_threads=None):
-    """Brute-force windowed top-k: (idx [m, k] u32, dist [m, k] u16)."""
+    """Brute-force windowed top-k: (idx [m, k] u32, dist [m, k] u16).  ``unit``:
+    "da" and "ppm" bound the precursor m/z difference, "mass" the neutral
+    precursor mass difference (mz - 1.007276) * z, in Da."""
     rh, rm, rz = _c(ref_hv, np.uint64), _c(ref_mz, np.float64), _c(ref_z, np.uint8)
     qh, qm, qz = _c(q_hv, np.uint64), _c(q_mz, np.float64), _c(q_z, np.uint8)
     w = None if which is None else _c(which, np.uint32)
@@ -147,7 +150,7 @@ def search(dim, ref_hv, ref_mz, ref_z, q_hv, q_mz, q_z, tol, unit="da", k=1, whi
     if n_threads is None:
         n_threads = os.cpu_count() or 1
     rc = _load().orc_search(dim, rm.size, _p(rh), _p(rm), _p(rz), qm.size, _p(qh), _p(qm), _p(qz),
-                            float(tol), int(unit == "ppm"), k, _p(w), 0 if w is None else w.size,
+                            float(tol), _UNITS[unit], k, _p(w), 0 if w is None else w.size,
                             _p(idx), _p(dist), n_threads)
     if rc:
         raise ValueError(f"orc_search rc={rc}")

@@ -301,23 +301,33 @@ int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L
 
 /* ---------------------------------------------------------------------------
  * Candidate predicate (Section 3.4, Table 1): same charge, and the precursor
- * m/z difference within the tolerance, bound inclusive:
+ * difference within the tolerance, bound inclusive.  unit 0 ("Da") and 1
+ * (ppm) compare precursor m/z:
  *     fabs(mz_r - mz_q) <= tol_q,
- * tol_q = tol for a tolerance in m/z units ("Da"), mz_q * (tol * 1e-6) for
- * ppm.  Reading: "500 Da" is a literal precursor m/z difference.
+ * tol_q = tol for a tolerance in m/z units, mz_q * (tol * 1e-6) for ppm
+ * (reading: "500 Da" is a literal precursor m/z difference).  unit 2 compares
+ * neutral precursor masses M = (mz - 1.007276) * z, the m/z less one proton
+ * mass per charge:
+ *     fabs(M_r - M_q) <= tol.
  * ------------------------------------------------------------------------- */
-static int is_candidate(double mz_r, uint8_t z_r, double mz_q, uint8_t z_q, double tol, int ppm)
+#define ORC_PROTON_MASS 1.007276
+
+static double neutral_mass(double mz, uint8_t z) { return (mz - ORC_PROTON_MASS) * (double)z; }
+
+static int is_candidate(double mz_r, uint8_t z_r, double mz_q, uint8_t z_q, double tol, int unit)
 {
-    double tol_q = ppm ? mz_q * (tol * 1e-6) : tol;
-    return z_r == z_q && fabs(mz_r - mz_q) <= tol_q;
+    if (z_r != z_q) return 0;
+    if (unit == 2) return fabs(neutral_mass(mz_r, z_r) - neutral_mass(mz_q, z_q)) <= tol;
+    double tol_q = unit == 1 ? mz_q * (tol * 1e-6) : tol;
+    return fabs(mz_r - mz_q) <= tol_q;
 }
 
 int orc_window_count(uint32_t n_ref, const double *ref_mz, const uint8_t *ref_z, uint32_t n_q,
-                     const double *q_mz, const uint8_t *q_z, double tol, int ppm, uint32_t *count)
+                     const double *q_mz, const uint8_t *q_z, double tol, int unit, uint32_t *count)
 {
     for (uint32_t q = 0; q < n_q; ++q) {
         uint32_t c = 0;
-        for (uint32_t r = 0; r < n_ref; ++r) c += (uint32_t)is_candidate(ref_mz[r], ref_z[r], q_mz[q], q_z[q], tol, ppm);
+        for (uint32_t r = 0; r < n_ref; ++r) c += (uint32_t)is_candidate(ref_mz[r], ref_z[r], q_mz[q], q_z[q], tol, unit);
         count[q] = c;
     }
     return 0;
@@ -361,7 +371,7 @@ typedef struct {
     const double *ref_mz, *q_mz;
     const uint8_t *ref_z, *q_z;
     const uint32_t *which;
-    double tol; int ppm;
+    double tol; int unit;
     uint32_t *out_idx; uint16_t *out_dist;
 } search_job;
 
@@ -375,7 +385,7 @@ static void *search_worker(void *arg)
         for (uint32_t s = 0; s < j->k; ++s) best[s] = UINT64_MAX;
         const uint64_t *qh = j->q_hv + (size_t)q * W;
         for (uint32_t r = 0; r < j->n_ref; ++r) {
-            if (!is_candidate(j->ref_mz[r], j->ref_z[r], j->q_mz[q], j->q_z[q], j->tol, j->ppm)) continue;
+            if (!is_candidate(j->ref_mz[r], j->ref_z[r], j->q_mz[q], j->q_z[q], j->tol, j->unit)) continue;
             const uint64_t *rh = j->ref_hv + (size_t)r * W;
             uint64_t dist = 0;
             for (uint32_t w = 0; w < W; ++w) dist += (uint64_t)__builtin_popcountll(qh[w] ^ rh[w]);
@@ -396,7 +406,7 @@ static void *search_worker(void *arg)
 
 int orc_search(uint32_t D, uint32_t n_ref, const uint64_t *ref_hv, const double *ref_mz, const uint8_t *ref_z,
                uint32_t n_q, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
-               double tol, int ppm, uint32_t k, const uint32_t *which, uint32_t n_which,
+               double tol, int unit, uint32_t k, const uint32_t *which, uint32_t n_which,
                uint32_t *out_idx, uint16_t *out_dist, uint32_t n_threads)
 {
     if (D == 0 || D % 64u || D > 65534u || k == 0 || !(tol >= 0.0)) return -1;
@@ -407,7 +417,7 @@ int orc_search(uint32_t D, uint32_t n_ref, const uint64_t *ref_hv, const double 
     if (!th || !jobs) { free(th); free(jobs); return -2; }
     for (uint32_t t = 0; t < n_threads; ++t) {
         search_job j = { D, n_ref, n_q, k, n_which, t, n_threads, ref_hv, q_hv, ref_mz, q_mz, ref_z, q_z,
-                         which, tol, ppm, out_idx, out_dist };
+                         which, tol, unit, out_idx, out_dist };
         jobs[t] = j;
     }
     uint32_t started = 0;

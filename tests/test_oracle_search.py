@@ -126,3 +126,56 @@ def test_library_order_matches_lexsort():
     z = rng.integers(1, 5, 500).astype(np.uint8)
     order = oracle.library_order(mz, z)
     assert np.array_equal(order, np.lexsort((np.arange(500), mz, z)))
+
+
+# ------------------------------------------------ neutral-mass windows (N4)
+def test_mass_window_scales_mz_window_by_charge():
+    """Within one charge z, neutral masses differ by z times the m/z
+    difference, so the +-T Da mass window selects the references of m/z
+    within T / z; checked away from the rounding boundary, for charges 1..4."""
+    rng = np.random.default_rng(41)
+    n = 4000
+    mz = rng.uniform(400, 1500, n)
+    z = rng.integers(1, 5, n).astype(np.uint8)
+    qm = rng.uniform(450, 1450, 300)
+    qz = rng.integers(1, 5, 300).astype(np.uint8)
+    for T in (0.5, 20.0, 150.0, 500.0):
+        got = oracle.window_count(mz, z, qm, qz, T, "mass")
+        for i in range(qm.size):
+            same = z == qz[i]
+            d = np.abs(mz[same] - qm[i])
+            lim = T / float(qz[i])
+            if np.any(np.abs(d - lim) < 1e-9 * max(1.0, lim)):
+                continue                                   # on the rounding boundary
+            assert got[i] == int(np.count_nonzero(d <= lim)), (T, i)
+
+
+def test_mass_window_charge_zero_and_charge_filter():
+    # charge 0: every neutral mass is 0, so every charge-0 reference is a candidate
+    mz = np.array([400.0, 900.0, 1400.0, 650.0])
+    z = np.array([0, 0, 0, 2], np.uint8)
+    assert list(oracle.window_count(mz, z, np.array([1000.0]), np.array([0], np.uint8), 0.0, "mass")) == [3]
+    # another charge never matches, however wide the window
+    assert list(oracle.window_count(mz, z, np.array([650.0]), np.array([3], np.uint8), 1e6, "mass")) == [0]
+
+
+def test_mass_window_search_brute_force():
+    rng = np.random.default_rng(42)
+    n, m = 300, 40
+    refs = _rand_hv(rng, n)
+    mz = rng.uniform(400, 600, n)
+    z = rng.integers(1, 4, n).astype(np.uint8)
+    qs = _rand_hv(rng, m)
+    qm = rng.uniform(400, 600, m)
+    qz = rng.integers(1, 4, m).astype(np.uint8)
+    idx, dist = oracle.search(D, refs, mz, z, qs, qm, qz, 30.0, "mass", k=4)
+    dm = hamming_matrix(qs, refs)
+    for i in range(m):
+        cand = [r for r in range(n) if z[r] == qz[i] and abs((mz[r] - qm[i]) * float(qz[i])) <= 30.0 * (1 - 1e-12)]
+        edge = [r for r in range(n) if z[r] == qz[i] and abs(abs((mz[r] - qm[i]) * float(qz[i])) - 30.0) < 1e-6]
+        if edge:
+            continue
+        best = sorted(cand, key=lambda r: (dm[i, r], r))[:4]
+        got = [int(x) for x in idx[i] if x != 0xFFFFFFFF]
+        assert got == best
+        assert [int(dm[i, r]) for r in best] == [int(x) for x in dist[i][:len(best)]]
