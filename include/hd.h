@@ -60,7 +60,10 @@ typedef enum {
     HD_ERR_UNSUPPORTED = 5    /* valid request this build or GPU does not serve */
 } hd_status;
 
-typedef enum { HD_TOL_DA = 0, HD_TOL_PPM = 1 } hd_tol_unit;
+/* Precursor tolerance units.  HD_TOL_DA and HD_TOL_PPM bound the precursor
+ * m/z difference (Section 3.4, Table 1); HD_TOL_MASS bounds the neutral
+ * precursor mass difference, mass = (mz - 1.007276) * charge, in Da. */
+typedef enum { HD_TOL_DA = 0, HD_TOL_PPM = 1, HD_TOL_MASS = 2 } hd_tol_unit;
 
 /* Item-memory parameters (Section 3.3).
  *  dim      D, multiple of 128, 128..32768 (paper: 8192, Section 4.2)
@@ -162,6 +165,19 @@ HD_API hd_status hd_build_library(hd_ctx *ctx, const uint64_t *d_hv, const doubl
                            const uint8_t *d_charge, uint32_t n_refs, hd_library **out);
 HD_API void hd_library_free(hd_library *lib);
 HD_API hd_status hd_library_info(const hd_library *lib, uint32_t *n_refs, uint32_t *dim);
+/* Saves the library to `path` and loads it back (reference HVs are encoded
+ * once and reused by later runs, Section 3.3).  File, little-endian: the
+ * 8-byte magic "HDLIB001"; u32 dim, n_levels, n_bins, alpha and u64 seed of
+ * the context that encoded the rows; u32 n, u32 flags (bit 0: decoy flags
+ * follow); then hv [n][D/64] u64 in sorted row order, mz [n] f64, charge [n]
+ * u8, orig [n] u32, decoy [n] u8 (input order, if flagged); then a u64
+ * FNV-1a hash of every preceding byte.  Tensor-core copies are not stored
+ * (hd_library_prepare rebuilds them).  Load requires a context with the same
+ * parameters, checks the hash and the row order (charge, then m/z,
+ * ascending, m/z finite), and fails with HD_ERR_INVALID_ARG otherwise.  Both
+ * calls are synchronous. */
+HD_API hd_status hd_library_save(const hd_library *lib, const hd_ctx *ctx, const char *path);
+HD_API hd_status hd_library_load(hd_ctx *ctx, const char *path, hd_library **out);
 /* Copies the sorted rows out (any pointer may be NULL): d_hv [n][D/64],
  * d_mz [n], d_charge [n], d_orig [n] (input index of each row). */
 HD_API hd_status hd_library_export(const hd_library *lib, uint64_t *d_hv, double *d_mz,
@@ -189,8 +205,10 @@ HD_API hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, u
 /* Candidate windows (Section 3.4, Table 1): for each query, rows [lo, hi) of
  * the sorted library whose charge equals the query's and whose precursor
  * m/z satisfies fabs(mz_r - mz_q) <= tol_q in IEEE double, tol_q = tol
- * (HD_TOL_DA, an m/z difference) or mz_q * (tol * 1e-6) (HD_TOL_PPM).  A
- * query with no candidate gets lo == hi.  tol >= 0 and finite. */
+ * (HD_TOL_DA, an m/z difference) or mz_q * (tol * 1e-6) (HD_TOL_PPM); with
+ * HD_TOL_MASS, fabs(M_r - M_q) <= tol for M = (mz - 1.007276) * charge in
+ * IEEE double.  A query with no candidate gets lo == hi.  tol >= 0 and
+ * finite. */
 HD_API hd_status hd_query_windows(const hd_library *lib, const double *d_q_mz, const uint8_t *d_q_charge,
                            uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *d_lo,
                            uint32_t *d_hi, hd_stream stream);

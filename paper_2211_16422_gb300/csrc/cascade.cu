@@ -256,7 +256,7 @@ hd_status hd_cascade_search(const hd_library *lib, const uint64_t *d_q_hv, const
             qm = mz;
             qz = z;
         }
-        const hd_qwin win = hd_single_window(levels[l].tol, levels[l].unit == HD_TOL_PPM);
+        const hd_qwin win = hd_single_window(levels[l].tol, levels[l].unit);
         hd_status st = hd_search_dispatch(lib, qh, qm, qz, n_act, win, 1, form, idx, dist, s);
         if (st != HD_OK) return fail(st);
         const uint32_t ga = hd_ceil_div(n_act, 256);

@@ -3,7 +3,9 @@
 // kernels of the other translation units.
 #include <cmath>
 #include <cstring>
+#include <cstdio>
 #include <string>
+#include <vector>
 
 #include "hd_internal.cuh"
 
@@ -65,6 +67,7 @@ hd_status check_device(int want)
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool unit_ok(hd_tol_unit u) { return u == HD_TOL_DA || u == HD_TOL_PPM || u == HD_TOL_MASS; }
 
 bool tol_ok(double tol) { return std::isfinite(tol) && tol >= 0.0; }
 
@@ -149,10 +152,8 @@ hd_status hd_make_qwin(const uint8_t *cls, const hd_window *windows, uint32_t n_
     w.n = n_windows;
     for (uint32_t i = 0; i < n_windows; ++i) {
         HD_CHECK(tol_ok(windows[i].tol), "windows: tol must be finite and >= 0");
-        HD_CHECK(windows[i].unit == HD_TOL_DA || windows[i].unit == HD_TOL_PPM, "windows: bad unit");
-        const int ppm = windows[i].unit == HD_TOL_PPM;
-        w.w[i].tol = ppm ? windows[i].tol * 1e-6 : windows[i].tol;
-        w.w[i].ppm = ppm;
+        HD_CHECK(unit_ok(windows[i].unit), "windows: bad unit");
+        w.w[i] = hd_single_window(windows[i].tol, windows[i].unit).w[0];
     }
     *out = w;
     return HD_OK;
@@ -388,6 +389,167 @@ hd_status hd_library_export(const hd_library *lib, uint64_t *d_hv, double *d_mz,
     return HD_OK;
 }
 
+namespace {
+
+const char LIB_MAGIC[8] = {'H', 'D', 'L', 'I', 'B', '0', '0', '1'};
+
+struct lib_header {
+    char magic[8];
+    uint32_t dim, n_levels, n_bins, alpha;
+    uint64_t seed;
+    uint32_t n, flags;
+};
+
+struct fnv64 {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n)
+    {
+        const uint8_t *b = static_cast<const uint8_t *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+};
+
+struct file_closer {
+    FILE *f = nullptr;
+    ~file_closer()
+    {
+        if (f) fclose(f);
+    }
+};
+
+}  // namespace
+
+hd_status hd_library_save(const hd_library *lib, const hd_ctx *ctx, const char *path)
+{
+    HD_CHECK(lib && ctx && path, "hd_library_save: null argument");
+    HD_CHECK(ctx->p.dim == lib->dim, "hd_library_save: ctx and library dims differ");
+    hd_status st = check_device(lib->device);
+    if (st != HD_OK) return st;
+    const size_t n = lib->n, W = lib->W;
+    std::vector<uint64_t> hv(n * W);
+    std::vector<double> mz(n);
+    std::vector<uint8_t> z(n), dec(lib->decoy ? n : 0);
+    std::vector<uint32_t> orig(n);
+    if (n) {
+        HD_CUDA_TRY(cudaMemcpy(hv.data(), lib->hv, n * W * 8, cudaMemcpyDeviceToHost));
+        HD_CUDA_TRY(cudaMemcpy(mz.data(), lib->mz, n * 8, cudaMemcpyDeviceToHost));
+        HD_CUDA_TRY(cudaMemcpy(z.data(), lib->charge, n, cudaMemcpyDeviceToHost));
+        HD_CUDA_TRY(cudaMemcpy(orig.data(), lib->orig, n * 4, cudaMemcpyDeviceToHost));
+        if (lib->decoy) HD_CUDA_TRY(cudaMemcpy(dec.data(), lib->decoy, n, cudaMemcpyDeviceToHost));
+    }
+    lib_header h{};
+    std::memcpy(h.magic, LIB_MAGIC, 8);
+    h.dim = ctx->p.dim;
+    h.n_levels = ctx->p.n_levels;
+    h.n_bins = ctx->p.n_bins;
+    h.alpha = ctx->p.alpha;
+    h.seed = ctx->p.seed;
+    h.n = lib->n;
+    h.flags = lib->decoy ? 1u : 0u;
+    file_closer fc;
+    fc.f = std::fopen(path, "wb");
+    if (!fc.f) return hd_fail(HD_ERR_INVALID_ARG, std::string("hd_library_save: cannot open ") + path);
+    fnv64 hash;
+    bool ok = true;
+    auto put = [&](const void *p, size_t bytes) {
+        if (!ok || bytes == 0) return;
+        hash.add(p, bytes);
+        ok = std::fwrite(p, 1, bytes, fc.f) == bytes;
+    };
+    put(&h, sizeof(h));
+    put(hv.data(), hv.size() * 8);
+    put(mz.data(), mz.size() * 8);
+    put(z.data(), z.size());
+    put(orig.data(), orig.size() * 4);
+    put(dec.data(), dec.size());
+    const uint64_t digest = hash.h;
+    if (ok) ok = std::fwrite(&digest, 1, 8, fc.f) == 8;
+    if (ok) ok = std::fclose(fc.f) == 0;
+    fc.f = nullptr;
+    if (!ok) return hd_fail(HD_ERR_INVALID_ARG, std::string("hd_library_save: write failed: ") + path);
+    return HD_OK;
+}
+
+hd_status hd_library_load(hd_ctx *ctx, const char *path, hd_library **out)
+{
+    HD_CHECK(ctx && path && out, "hd_library_load: null argument");
+    *out = nullptr;
+    hd_status st = check_device(ctx->device);
+    if (st != HD_OK) return st;
+    file_closer fc;
+    fc.f = std::fopen(path, "rb");
+    if (!fc.f) return hd_fail(HD_ERR_INVALID_ARG, std::string("hd_library_load: cannot open ") + path);
+    fnv64 hash;
+    bool ok = true;
+    auto get = [&](void *p, size_t bytes) {
+        if (!ok || bytes == 0) return;
+        ok = std::fread(p, 1, bytes, fc.f) == bytes;
+        if (ok) hash.add(p, bytes);
+    };
+    lib_header h{};
+    get(&h, sizeof(h));
+    if (!ok || std::memcmp(h.magic, LIB_MAGIC, 8) != 0)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_library_load: not a library file");
+    if (h.dim != ctx->p.dim || h.n_levels != ctx->p.n_levels || h.n_bins != ctx->p.n_bins ||
+        h.alpha != ctx->p.alpha || h.seed != ctx->p.seed)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_library_load: the file was encoded with other item-memory parameters");
+    const size_t n = h.n, W = ctx->W;
+    std::vector<uint64_t> hv(n * W);
+    std::vector<double> mz(n);
+    std::vector<uint8_t> z(n), dec((h.flags & 1u) ? n : 0);
+    std::vector<uint32_t> orig(n);
+    get(hv.data(), hv.size() * 8);
+    get(mz.data(), mz.size() * 8);
+    get(z.data(), z.size());
+    get(orig.data(), orig.size() * 4);
+    get(dec.data(), dec.size());
+    uint64_t digest = 0;
+    if (ok) ok = std::fread(&digest, 1, 8, fc.f) == 8;
+    if (!ok || digest != hash.h) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_load: truncated or corrupted file");
+    std::vector<uint8_t> seen(n, 0);
+    for (size_t i = 0; i < n; ++i) {
+        const bool order = i == 0 || z[i] > z[i - 1] || (z[i] == z[i - 1] && mz[i] >= mz[i - 1]);
+        if (!order || !std::isfinite(mz[i]) || orig[i] >= n || seen[orig[i]])
+            return hd_fail(HD_ERR_INVALID_ARG, "hd_library_load: rows out of order or bad index");
+        seen[orig[i]] = 1;
+    }
+    hd_library *lib = new hd_library;
+    lib->n = h.n;
+    lib->dim = ctx->p.dim;
+    lib->W = ctx->W;
+    lib->device = ctx->device;
+    lib->num_sms = ctx->num_sms;
+    auto fail = [&](hd_status s) {
+        lib_release(lib);
+        return s;
+    };
+    const size_t n1 = n ? n : 1;
+    if (cudaMalloc(&lib->hv, n1 * W * 8) != cudaSuccess || cudaMalloc(&lib->mz, n1 * 8) != cudaSuccess ||
+        cudaMalloc(&lib->charge, n1) != cudaSuccess || cudaMalloc(&lib->orig, n1 * 4) != cudaSuccess ||
+        cudaMalloc(&lib->charge_start, 257 * 4) != cudaSuccess ||
+        (!dec.empty() && cudaMalloc(&lib->decoy, n) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(hd_fail(HD_ERR_OOM, "hd_library_load: allocation failed"));
+    }
+    st = status_alloc(lib->status);
+    if (st != HD_OK) return fail(st);
+    cudaError_t e = cudaSuccess;
+    if (n) {
+        e = cudaMemcpy(lib->hv, hv.data(), n * W * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(lib->mz, mz.data(), n * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(lib->charge, z.data(), n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(lib->orig, orig.data(), n * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !dec.empty()) e = cudaMemcpy(lib->decoy, dec.data(), n, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return fail(hd_cuda_fail(e, "hd_library_load: upload"));
+    hd_count_launches(1), k_charge_start<<<1, 288>>>(lib->charge, h.n, lib->charge_start);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(lib->charge_start_h, lib->charge_start, 257 * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(hd_cuda_fail(e, "hd_library_load"));
+    *out = lib;
+    return HD_OK;
+}
+
 hd_status hd_library_status(hd_library *lib)
 {
     HD_CHECK(lib, "hd_library_status: null library");
@@ -448,12 +610,12 @@ hd_status hd_query_windows(const hd_library *lib, const double *d_q_mz, const ui
 {
     HD_CHECK(lib, "hd_query_windows: null library");
     HD_CHECK(tol_ok(tol), "hd_query_windows: tol must be finite and >= 0");
-    HD_CHECK(unit == HD_TOL_DA || unit == HD_TOL_PPM, "hd_query_windows: bad unit");
+    HD_CHECK(unit_ok(unit), "hd_query_windows: bad unit");
     if (n_q == 0) return HD_OK;
     HD_CHECK(d_q_mz && d_q_charge && d_lo && d_hi, "hd_query_windows: null buffer");
     hd_status st = check_device(lib->device);
     if (st != HD_OK) return st;
-    hd_windows_launch(lib, d_q_mz, d_q_charge, nullptr, n_q, hd_single_window(tol, unit == HD_TOL_PPM), d_lo, d_hi,
+    hd_windows_launch(lib, d_q_mz, d_q_charge, nullptr, n_q, hd_single_window(tol, unit), d_lo, d_hi,
                       (cudaStream_t)stream);
     HD_CUDA_TRY(cudaGetLastError());
     return HD_OK;
@@ -467,7 +629,7 @@ hd_status hd_search_open_ex(const hd_library *lib, const uint64_t *d_q_hv, const
     HD_CHECK(lib, "hd_search_open: null library");
     HD_CHECK(k >= 1 && k <= 16, "hd_search_open: k must be in [1, 16]");
     HD_CHECK(tol_ok(tol), "hd_search_open: tol must be finite and >= 0");
-    HD_CHECK(unit == HD_TOL_DA || unit == HD_TOL_PPM, "hd_search_open: bad unit");
+    HD_CHECK(unit_ok(unit), "hd_search_open: bad unit");
     HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
              "hd_search_open: unknown form");
     if (n_q == 0) return HD_OK;
@@ -475,7 +637,7 @@ hd_status hd_search_open_ex(const hd_library *lib, const uint64_t *d_q_hv, const
     HD_CHECK(aligned16(d_q_hv), "hd_search_open: d_q_hv must be 16-byte aligned");
     hd_status st = check_device(lib->device);
     if (st != HD_OK) return st;
-    return hd_search_dispatch(lib, d_q_hv, d_q_mz, d_q_charge, n_q, hd_single_window(tol, unit == HD_TOL_PPM), k,
+    return hd_search_dispatch(lib, d_q_hv, d_q_mz, d_q_charge, n_q, hd_single_window(tol, unit), k,
                               form, d_out_idx, d_out_dist, (cudaStream_t)stream);
 }
 
@@ -559,7 +721,7 @@ hd_status hd_search_host(hd_ctx *ctx, const hd_library *lib, const uint32_t *h_o
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        st = hd_search_dispatch(lib, hv, mz, z, n_q, hd_single_window(tol, unit == HD_TOL_PPM), k, HD_FORM_AUTO,
+        st = hd_search_dispatch(lib, hv, mz, z, n_q, hd_single_window(tol, unit), k, HD_FORM_AUTO,
                                 oi, od, s);
         if (st != HD_OK) {
             cudaFreeAsync(ar.base, s);

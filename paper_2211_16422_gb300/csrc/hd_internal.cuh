@@ -136,18 +136,20 @@ void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bi
                       const uint8_t *levels, uint32_t n, uint64_t *out, cudaStream_t s);
 
 // Candidate windows of a query set (Section 3.4): query q uses window
-// w[cls[q]] (w[0] when cls is null).  For ppm, `tol` holds tol * 1e-6 and the
-// window half-width is mz_q * tol.  Passed to kernels by value.
+// w[cls[q]] (w[0] when cls is null).  `unit` is an hd_tol_unit.  For ppm,
+// `tol` holds tol * 1e-6 and the window half-width is mz_q * tol; for
+// neutral masses the half-width applies to (mz - 1.007276) * charge.  Passed
+// to kernels by value.
 struct hd_win {
     double tol;
-    int ppm;
+    int unit;
 };
 struct hd_qwin {
     const uint8_t *cls = nullptr;
     uint32_t n = 1;
     hd_win w[HD_MAX_WINDOWS] = {};
 };
-hd_qwin hd_single_window(double tol, int ppm);
+hd_qwin hd_single_window(double tol, hd_tol_unit unit);
 
 // Test hook: true (and one fewer pending) when this search must drop its
 // first stage load so that a bounded device wait runs out.

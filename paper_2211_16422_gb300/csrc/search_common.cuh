@@ -25,21 +25,30 @@ static __global__ void k_windows(const double *__restrict__ lib_mz, const uint32
     const uint32_t c = q_z[q];
     const uint32_t wc = win.cls ? min((uint32_t)win.cls[q], win.n - 1) : 0u;
     const hd_win w = win.w[wc];
-    const double t = w.ppm ? __dmul_rn(m, w.tol) : w.tol;   // tol holds tol*1e-6 for ppm
-    const double nt = -t;
     const uint32_t p0 = cstart[c], p1 = cstart[c + 1];
-    // first row with (mz_r - m) >= -t
+    // Within one charge the compared quantity is non-decreasing in the row's
+    // m/z (IEEE subtraction and multiplication by a charge >= 0 are monotone),
+    // so each bound is the first row where a monotone predicate turns true.
+    auto delta = [&](uint32_t r) -> double {
+        if (w.unit == HD_TOL_MASS)   // neutral masses (mz - 1.007276) * z
+            return __dsub_rn(__dmul_rn(__dsub_rn(lib_mz[r], 1.007276), (double)c),
+                             __dmul_rn(__dsub_rn(m, 1.007276), (double)c));
+        return __dsub_rn(lib_mz[r], m);
+    };
+    const double t = w.unit == HD_TOL_PPM ? __dmul_rn(m, w.tol) : w.tol;   // tol holds tol*1e-6 for ppm
+    const double nt = -t;
+    // first row with delta >= -t
     uint32_t a = p0, b = p1;
     while (a < b) {
         const uint32_t mid = a + ((b - a) >> 1);
-        if (__dsub_rn(lib_mz[mid], m) >= nt) b = mid; else a = mid + 1;
+        if (delta(mid) >= nt) b = mid; else a = mid + 1;
     }
     const uint32_t l = a;
-    // first row with (mz_r - m) > t
+    // first row with delta > t
     b = p1;
     while (a < b) {
         const uint32_t mid = a + ((b - a) >> 1);
-        if (__dsub_rn(lib_mz[mid], m) > t) b = mid; else a = mid + 1;
+        if (delta(mid) > t) b = mid; else a = mid + 1;
     }
     lo[s] = l;
     hi[s] = a;

@@ -64,7 +64,7 @@ extern "C" hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_
     if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: k must be in [1, 16]");
     if (!(tol >= 0.0) || tol > 1.7976931348623157e308)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: tol must be finite and >= 0");
-    if (unit != HD_TOL_DA && unit != HD_TOL_PPM)
+    if (unit != HD_TOL_DA && unit != HD_TOL_PPM && unit != HD_TOL_MASS)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: bad unit");
     if (n_q == 0) return HD_OK;
     if (!d_q_hv || !d_q_mz || !d_q_charge || !d_out_idx || !d_out_dist)
@@ -78,7 +78,7 @@ extern "C" hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_
     const hd_status st = scratch_address(dev, &scratch);
     if (st != HD_OK) return st;
     return hd_search_popc_run_scratch(lib, d_q_hv, d_q_mz, d_q_charge, n_q,
-                                      hd_single_window(tol, unit == HD_TOL_PPM), k,
+                                      hd_single_window(tol, unit), k,
                                       d_out_idx, d_out_dist, (cudaStream_t)stream, scratch,
                                       HD_NOALLOC_SCRATCH_BYTES);
 }

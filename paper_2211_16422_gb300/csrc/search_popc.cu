@@ -293,12 +293,12 @@ void hd_windows_launch(const hd_library *lib, const double *q_mz, const uint8_t 
                                                     n_q, win, lo, hi);
 }
 
-hd_qwin hd_single_window(double tol, int ppm)
+hd_qwin hd_single_window(double tol, hd_tol_unit unit)
 {
     hd_qwin w;
     w.n = 1;
-    w.w[0].tol = ppm ? tol * 1e-6 : tol;
-    w.w[0].ppm = ppm;
+    w.w[0].tol = unit == HD_TOL_PPM ? tol * 1e-6 : tol;
+    w.w[0].unit = (int)unit;
     return w;
 }
 

@@ -319,7 +319,7 @@ hd_status hd_server_submit(hd_server *s, const uint32_t *h_offsets, const uint32
     if (!s || !request_id) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: null argument");
     if (n_q == 0 || !h_offsets || !h_q_mz || !h_q_charge || !h_out_idx || !h_out_dist)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: empty request or null buffer");
-    if (!(tol >= 0.0) || tol > 1.7976931348623157e308 || (unit != HD_TOL_DA && unit != HD_TOL_PPM))
+    if (!(tol >= 0.0) || tol > 1.7976931348623157e308 || (unit != HD_TOL_DA && unit != HD_TOL_PPM && unit != HD_TOL_MASS))
         return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: bad window");
     const uint32_t nnz = h_offsets[n_q] - h_offsets[0];
     if (nnz && (!h_bins || !h_levels)) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: null CSR buffer");

@@ -18,7 +18,7 @@ import torch
 from . import build as _build
 
 HD_OK, HD_ERR_INVALID_ARG, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_TIMEOUT, HD_ERR_UNSUPPORTED = range(6)
-HD_TOL_DA, HD_TOL_PPM = 0, 1
+HD_TOL_DA, HD_TOL_PPM, HD_TOL_MASS = 0, 1, 2
 HD_FORM_AUTO, HD_FORM_POPC, HD_FORM_TC_FP8, HD_FORM_TC_BF16 = 0, 1, 2, 3
 FORMS = {"auto": HD_FORM_AUTO, "popc": HD_FORM_POPC, "tc_fp8": HD_FORM_TC_FP8, "tc_bf16": HD_FORM_TC_BF16}
 NO_IDX, NO_DIST = 0xFFFFFFFF, 0xFFFF
@@ -88,6 +88,8 @@ _SIGS = {
     "hd_search_open_noalloc": ([P, P, P, P, u32, dbl, i32, u32, P, P, P], i32),
     "hd_search_open_multi": ([P, P, P, P, P, u32, P, u32, u32, i32, P, P, P], i32),
     "hd_library_set_decoys": ([P, P], i32),
+    "hd_library_save": ([P, P, C.c_char_p], i32),
+    "hd_library_load": ([P, C.c_char_p, P], i32),
     "hd_cascade_search": ([P, P, P, P, u32, P, u32, dbl, i32, P, P, P, P, P], i32),
     "hd_plan_create": ([P, P, P, P, P, P, P, P, u32, P, u32, u32, i32, P, P, P, P], i32),
     "hd_plan_launch": ([P, P], i32),
@@ -157,7 +159,11 @@ def _dev(t, dtype, name):
 
 
 def _unit(unit) -> int:
-    return HD_TOL_PPM if unit in ("ppm", HD_TOL_PPM) else HD_TOL_DA
+    units = {"da": HD_TOL_DA, "ppm": HD_TOL_PPM, "mass": HD_TOL_MASS,
+             HD_TOL_DA: HD_TOL_DA, HD_TOL_PPM: HD_TOL_PPM, HD_TOL_MASS: HD_TOL_MASS}
+    if unit not in units:
+        raise ValueError(f"unknown tolerance unit {unit!r}")
+    return units[unit]
 
 
 class Ctx:
@@ -363,6 +369,20 @@ def hd_search_open_multi(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k
                                        len(windows), int(k), FORMS[form], _ptr(out_idx), _ptr(out_dist),
                                        _stream(stream)))
     return out_idx, out_dist
+
+
+def hd_library_save(lib: Library, ctx: Ctx, path: str):
+    """Write the library (sorted rows, decoy flags, item-memory parameters) to `path`."""
+    _check(load().hd_library_save(lib.handle, ctx.handle, os.fsencode(path)))
+
+
+def hd_library_load(ctx: Ctx, path: str) -> "Library":
+    """Read a library written by hd_library_save; ctx must have the same parameters."""
+    h = C.c_void_p()
+    _check(load().hd_library_load(ctx.handle, os.fsencode(path), C.byref(h)))
+    n, dim = C.c_uint32(), C.c_uint32()
+    _check(load().hd_library_info(h, C.byref(n), C.byref(dim)))
+    return Library(h, n.value, dim.value)
 
 
 def hd_library_set_decoys(lib: Library, is_decoy):

@@ -145,3 +145,32 @@ def test_autotune_keeps_results(hd):
     i1, d1 = hd.hd_search_open_multi(*args, 5, form="auto")
     torch.cuda.synchronize()
     assert torch.equal(i0, i1) and torch.equal(d0, d1)
+
+
+def test_multi_window_mixed_units_exact(hd):
+    """Window classes mixing m/z (Da, ppm) and neutral-mass tolerances in one
+    launch give, per class, the oracle's top-k for that window."""
+    windows = [(20.0, "ppm"), (300.0, "mass"), (150.0, "da"), (1000.0, "mass")]
+    D = 2048
+    rng = np.random.Generator(np.random.PCG64(77))
+    spec = synth.WORKLOADS["batched"]
+    refs = synth.make_references(6000, spec["charges"], spec["weights"], rng, decoy_fraction=0.5)
+    qs = synth.make_queries(refs, 900, rng)
+    cls = (np.arange(qs.n) % len(windows)).astype(np.uint8)
+    ctx, lib, r_hv, q_csr = _setup(hd, refs, qs, D, 16)
+    q_hv = hd.hd_encode(ctx, *q_csr)
+    hd.hd_library_prepare(lib, "tc_fp8")
+    o_r, o_q = oracle_side.hvs(refs, D, 16, 0), oracle_side.hvs(qs, D, 16, 0)
+    oi = np.full((qs.n, 4), 0xFFFFFFFF, np.uint32)
+    od = np.full((qs.n, 4), 0xFFFF, np.uint16)
+    for c, (tol, unit) in enumerate(windows):
+        idx = np.nonzero(cls == c)[0].astype(np.uint32)
+        oi[idx], od[idx] = oracle.search(D, o_r, refs.precursor_mz, refs.charge, o_q, qs.precursor_mz, qs.charge,
+                                         tol, unit, 4, which=idx)
+    for form in ("popc", "tc_fp8"):
+        i, d = hd.hd_search_open_multi(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), windows, 4,
+                                       form=form)
+        torch.cuda.synchronize()
+        lib.status()
+        assert np.array_equal(hd.as_u32(i), oi), form
+        assert np.array_equal(hd.as_u16(d), od), form

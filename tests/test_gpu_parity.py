@@ -145,7 +145,8 @@ def test_library_rejects_nan_mz(hd):
 
 
 # --------------------------------------------------------------- windows
-@pytest.mark.parametrize("tol,unit", [(500.0, "da"), (150.0, "da"), (20.0, "ppm"), (0.0, "da"), (0.05, "da")])
+@pytest.mark.parametrize("tol,unit", [(500.0, "da"), (150.0, "da"), (20.0, "ppm"), (0.0, "da"), (0.05, "da"),
+                                      (500.0, "mass"), (37.5, "mass"), (0.0, "mass")])
 def test_windows_match_oracle(hd, tol, unit):
     rng = np.random.default_rng(4)
     n = 5000
@@ -208,7 +209,7 @@ def _medium(seed, n_refs=3000, n_q=500):
 
 @pytest.mark.parametrize("D,k,tol,unit", [(2048, 1, 500.0, "da"), (8192, 5, 500.0, "da"), (8192, 16, 150.0, "da"),
                                           (12288, 3, 500.0, "da"), (4096, 5, 20.0, "ppm"), (2048, 2, 0.0, "da"),
-                                          (128, 8, 1e6, "da")])
+                                          (128, 8, 1e6, "da"), (4096, 5, 300.0, "mass"), (2048, 3, 1000.0, "mass")])
 def test_search_bit_exact(hd, D, k, tol, unit):
     refs, qs = _medium(D + k)
     Q = 32
