@@ -47,10 +47,10 @@ def _load():
             P = C.c_void_p
             u32, u64, dbl, i32 = C.c_uint32, C.c_uint64, C.c_double, C.c_int
             lib.orc_philox4x32_10.argtypes = [P, P, P]
-            lib.orc_item_memory.argtypes = [u32, u32, u32, u32, u64, P, P, P, P]
+            lib.orc_item_memory.argtypes = [u32, u32, u32, u32, u64, u32, P, P, P, P]
             lib.orc_preprocess.argtypes = [u32, P, P, P, dbl, dbl, dbl, u32, u32, dbl, u32, P, P, P]
             lib.orc_preprocess.restype = C.c_longlong
-            lib.orc_encode.argtypes = [u32, P, u32, P, u32, u32, P, P, P, P, u32]
+            lib.orc_encode.argtypes = [u32, P, u32, P, u32, u32, P, P, P, P, u32, u32]
             lib.orc_window_count.argtypes = [u32, P, P, u32, P, P, dbl, i32, P]
             lib.orc_library_order.argtypes = [u32, P, P, P]
             lib.orc_search.argtypes = [u32, u32, P, P, P, u32, P, P, P, dbl, i32, u32, P, u32, P, P, u32]
@@ -74,14 +74,16 @@ def philox4x32_10(ctr, key):
     return out
 
 
-def item_memory(dim, n_levels, n_bins, alpha, seed):
-    """(F [f, D/64] u64, L [Q, D/64] u64, rank_F [D], rank_L [D])."""
+def item_memory(dim, n_levels, n_bins, alpha, seed, mode=0):
+    """(F [f, D/64] u64, L [Q, D/64] u64, rank_F [D], rank_L [D]).  ``mode``: 0 nested
+    position flips (alpha in total), 1 random walk (alpha flips per step), 2 independent
+    random position HVs."""
     W = dim // 64
     F = np.zeros((n_bins, W), np.uint64)
     L = np.zeros((n_levels, W), np.uint64)
     rF = np.zeros(dim, np.uint32)
     rL = np.zeros(dim, np.uint32)
-    rc = _load().orc_item_memory(dim, n_levels, n_bins, alpha, seed, _p(F), _p(L), _p(rF), _p(rL))
+    rc = _load().orc_item_memory(dim, n_levels, n_bins, alpha, seed, mode, _p(F), _p(L), _p(rF), _p(rL))
     if rc:
         raise ValueError(f"orc_item_memory rc={rc}")
     return F, L, rF, rL
@@ -104,8 +106,9 @@ def preprocess(offsets, mz, intensity, *, mz_min, mz_max, bin_width, n_bins, max
     return o_off, o_bin[:nnz].copy(), o_lvl[:nnz].copy()
 
 
-def encode(dim, F, L, offsets, bins, levels, n_threads=None):
-    """Binary HVs [n, D/64] u64 of CSR spectrum vectors (Eq. 1 + sign)."""
+def encode(dim, F, L, offsets, bins, levels, n_threads=None, encoder=0):
+    """Binary HVs [n, D/64] u64 of CSR spectrum vectors: encoder 0 = Eq. 1 + sign,
+    1 = random projection with weights level + 1."""
     off = _c(offsets, np.uint32)
     n = off.size - 1
     out = np.zeros((n, dim // 64), np.uint64)
@@ -114,7 +117,7 @@ def encode(dim, F, L, offsets, bins, levels, n_threads=None):
     if n_threads is None:
         n_threads = os.cpu_count() or 1
     rc = _load().orc_encode(dim, _p(F), F.shape[0], _p(L), L.shape[0], n, _p(off), _p(b), _p(lv), _p(out),
-                            n_threads)
+                            n_threads, encoder)
     if rc:
         raise ValueError(f"orc_encode rc={rc}")
     return out

@@ -115,21 +115,60 @@ static void make_base(uint32_t D, uint64_t seed, uint32_t stream, uint64_t *hv)
         set_bit(hv, d, (int)((stream_word(seed, stream, d >> 5) >> (d & 31u)) & 1u));
 }
 
-int orc_item_memory(uint32_t D, uint32_t Q, uint32_t f, uint32_t alpha, uint64_t seed,
+/* Encoder variants compared in Section 4.2 ("Encoding strategy"):
+ *  mode 0 -- the nested flips above;
+ *  mode 1 -- reading B of Section 3.3.1, a random walk: F_i is F_{i-1} with
+ *           exactly `alpha` components flipped (alpha <= 256) at distinct
+ *           positions drawn by Floyd's sampling algorithm: for k = 0..alpha-1,
+ *           j = D - alpha + k, t = word(stream 4, i * 256 + k) mod (j + 1);
+ *           take t unless already taken, else take j;
+ *  mode 2 -- ID-Level HDC: independent random F_i, bit d of F_i = bit d%32 of
+ *           word(stream 5, i * D/32 + d/32).
+ * The level HVs are the same in every mode. */
+static int in_set(const uint32_t *s, uint32_t n, uint32_t v)
+{
+    for (uint32_t i = 0; i < n; ++i) if (s[i] == v) return 1;
+    return 0;
+}
+
+int orc_item_memory(uint32_t D, uint32_t Q, uint32_t f, uint32_t alpha, uint64_t seed, uint32_t mode,
                     uint64_t *F, uint64_t *L, uint32_t *rank_F, uint32_t *rank_L)
 {
-    if (D == 0 || D % 64u || Q < 2 || f == 0 || alpha > D) return -1;
+    if (D == 0 || D % 64u || Q < 2 || f == 0 || alpha > D || mode > 2) return -1;
+    if (mode == 1 && (alpha > 256u || f > (1u << 24))) return -1;           /* counters i * 256 + k */
+    if (mode == 2 && (uint64_t)f * (D / 32u) > 0xFFFFFFFFull) return -1;  /* counters i * D/32 + w */
     const uint32_t W = D / 64u;
     uint64_t *F0 = (uint64_t *)calloc(W, 8), *L0 = (uint64_t *)calloc(W, 8);
     if (!F0 || !L0) { free(F0); free(L0); return -2; }
     make_base(D, seed, 0, F0);
     make_base(D, seed, 2, L0);
     if (make_rank(D, seed, 1, rank_F) || make_rank(D, seed, 3, rank_L)) { free(F0); free(L0); return -2; }
-    for (uint32_t i = 0; i < f; ++i) {
-        uint64_t m = (f > 1) ? ((uint64_t)i * alpha) / (uint64_t)(f - 1) : 0;
-        uint64_t *Fi = F + (size_t)i * W;
-        for (uint32_t d = 0; d < D; ++d)
-            set_bit(Fi, d, get_bit(F0, d) ^ (rank_F[d] < m));
+    if (mode == 0) {
+        for (uint32_t i = 0; i < f; ++i) {
+            uint64_t m = (f > 1) ? ((uint64_t)i * alpha) / (uint64_t)(f - 1) : 0;
+            uint64_t *Fi = F + (size_t)i * W;
+            for (uint32_t d = 0; d < D; ++d)
+                set_bit(Fi, d, get_bit(F0, d) ^ (rank_F[d] < m));
+        }
+    } else if (mode == 1) {
+        uint32_t chosen[256];
+        memcpy(F, F0, (size_t)W * 8);
+        for (uint32_t i = 1; i < f; ++i) {
+            uint64_t *Fi = F + (size_t)i * W;
+            memcpy(Fi, Fi - W, (size_t)W * 8);
+            for (uint32_t k = 0; k < alpha; ++k) {
+                uint32_t j = D - alpha + k;
+                uint32_t t = stream_word(seed, 4, i * 256u + k) % (j + 1u);
+                chosen[k] = in_set(chosen, k, t) ? j : t;
+                set_bit(Fi, chosen[k], !get_bit(Fi, chosen[k]));
+            }
+        }
+    } else {
+        for (uint32_t i = 0; i < f; ++i) {
+            uint64_t *Fi = F + (size_t)i * W;
+            for (uint32_t d = 0; d < D; ++d)
+                set_bit(Fi, d, (int)((stream_word(seed, 5, i * (D / 32u) + d / 32u) >> (d & 31u)) & 1u));
+        }
     }
     for (uint32_t j = 0; j < Q; ++j) {
         uint64_t n = ((uint64_t)j * (D / 2u)) / (uint64_t)(Q - 1);
@@ -236,9 +275,13 @@ long long orc_preprocess(uint32_t n_spec, const uint32_t *raw_off, const double 
  * Encoding, Eq. 1 and the binarisation after it (Section 3.3): in bipolar
  * arithmetic I = sum over peaks (i, j) of F_i (.) L_j, then component d of
  * the output is +1 when I_d > 0 and -1 otherwise.
+ * encoder 1 -- the random-projection LSH baseline of Section 4.2: the
+ * spectrum vector (value level + 1 at each peak's bin) projected on D random
+ * +-1 directions, direction d taking component d of F_bin for each bin:
+ * I_d = sum over peaks of (level + 1) * F_bin[d], then the same sign rule.
  * ------------------------------------------------------------------------- */
 typedef struct {
-    uint32_t D, n_bins, n_levels, s0, s1;
+    uint32_t D, n_bins, n_levels, s0, s1, encoder;
     const uint64_t *F, *L;
     const uint32_t *off, *bin;
     const uint8_t *level;
@@ -259,7 +302,7 @@ static void *encode_worker(void *arg)
             const uint64_t *Fi = j->F + (size_t)j->bin[p] * W, *Lj = j->L + (size_t)j->level[p] * W;
             for (uint32_t d = 0; d < D; ++d) {
                 int f = 1 - 2 * get_bit(Fi, d), l = 1 - 2 * get_bit(Lj, d);
-                I[d] += f * l;
+                I[d] += j->encoder == 1 ? f * ((int)j->level[p] + 1) : f * l;
             }
         }
         uint64_t *o = j->out + (size_t)s * W;
@@ -272,9 +315,9 @@ static void *encode_worker(void *arg)
 /* Spectra are split into `n_threads` contiguous ranges, one per thread. */
 int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L, uint32_t n_levels,
                uint32_t n_spec, const uint32_t *off, const uint32_t *bin, const uint8_t *level,
-               uint64_t *out, uint32_t n_threads)
+               uint64_t *out, uint32_t n_threads, uint32_t encoder)
 {
-    if (D == 0 || D % 64u) return -1;
+    if (D == 0 || D % 64u || encoder > 1) return -1;
     for (uint32_t s = 0; s < n_spec; ++s) if (off[s + 1] < off[s]) return -1;
     if (n_threads == 0) n_threads = 1;
     if (n_threads > n_spec) n_threads = n_spec ? n_spec : 1;
@@ -284,7 +327,7 @@ int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L
     if (!th || !jobs || !started) { free(th); free(jobs); free(started); return -2; }
     for (uint32_t t = 0; t < n_threads; ++t) {
         encode_job j = { D, n_bins, n_levels, (uint32_t)((uint64_t)n_spec * t / n_threads),
-                         (uint32_t)((uint64_t)n_spec * (t + 1) / n_threads), F, L, off, bin, level, out, 0 };
+                         (uint32_t)((uint64_t)n_spec * (t + 1) / n_threads), encoder, F, L, off, bin, level, out, 0 };
         jobs[t] = j;
     }
     for (uint32_t t = 1; t < n_threads; ++t) started[t] = pthread_create(&th[t], NULL, encode_worker, &jobs[t]) == 0;
