@@ -65,19 +65,40 @@ typedef enum {
  * precursor mass difference, mass = (mz - 1.007276) * charge, in Da. */
 typedef enum { HD_TOL_DA = 0, HD_TOL_PPM = 1, HD_TOL_MASS = 2 } hd_tol_unit;
 
+/* Position-HV generation (Section 3.3.1; variants compared in Section 4.2).
+ *  HD_POS_NESTED  F_i = F_0 with the floor(i * alpha / (f - 1)) lowest-ranked
+ *                 components of one random permutation flipped (alpha in
+ *                 total from the first to the last bin) -- the default
+ *  HD_POS_WALK    F_i = F_{i-1} with exactly alpha (<= 256) components flipped
+ *                 at distinct random positions (Floyd's sampling on Philox
+ *                 stream 4, counter i * 256 + k)
+ *  HD_POS_RANDOM  independent random F_i (ID-Level HDC; Philox stream 5) */
+typedef enum { HD_POS_NESTED = 0, HD_POS_WALK = 1, HD_POS_RANDOM = 2 } hd_position_mode;
+/* Spectrum encoder (Section 3.3, Eq. 1; baseline of Section 4.2).
+ *  HD_ENC_ID_LEVEL    sign of sum over peaks of F_bin (.) L_level (Eq. 1)
+ *  HD_ENC_PROJECTION  random-projection LSH: sign of sum over peaks of
+ *                     (level + 1) * F_bin, F_bin as +-1 directions
+ * Both map a sum <= 0 to -1 (bit 1). */
+typedef enum { HD_ENC_ID_LEVEL = 0, HD_ENC_PROJECTION = 1 } hd_encoder_kind;
+
 /* Item-memory parameters (Section 3.3).
  *  dim      D, multiple of 128, 128..32768 (paper: 8192, Section 4.2)
  *  n_levels Q intensity levels 0..Q-1, 2..256 (paper: 16)
  *  n_bins   f spectrum-vector dimensionality (m/z bins), >= 1
- *  alpha    total position flips from the first to the last bin, <= D
- *           (paper: D/2, Section 4.2)
- *  seed     Philox4x32-10 key of the random base vectors and permutations */
+ *  alpha    HD_POS_NESTED: total position flips from the first to the last
+ *           bin, <= D (paper: D/2, Section 4.2); HD_POS_WALK: flips per
+ *           step, <= 256; HD_POS_RANDOM: unused
+ *  seed     Philox4x32-10 key of the random base vectors and permutations
+ *  position_mode  an hd_position_mode (0: the paper's, as read here)
+ *  encoder        an hd_encoder_kind (0: Eq. 1) */
 typedef struct {
     uint32_t dim;
     uint32_t n_levels;
     uint32_t n_bins;
     uint32_t alpha;
     uint64_t seed;
+    uint32_t position_mode;
+    uint32_t encoder;
 } hd_params;
 
 /* Preprocessing parameters (Section 3.2, Table 1). */
@@ -167,8 +188,9 @@ HD_API void hd_library_free(hd_library *lib);
 HD_API hd_status hd_library_info(const hd_library *lib, uint32_t *n_refs, uint32_t *dim);
 /* Saves the library to `path` and loads it back (reference HVs are encoded
  * once and reused by later runs, Section 3.3).  File, little-endian: the
- * 8-byte magic "HDLIB001"; u32 dim, n_levels, n_bins, alpha and u64 seed of
- * the context that encoded the rows; u32 n, u32 flags (bit 0: decoy flags
+ * 8-byte magic "HDLIB001"; u32 dim, n_levels, n_bins, alpha, u64 seed and u32
+ * position_mode, encoder of the context that encoded the rows; u32 n, u32
+ * flags (bit 0: decoy flags
  * follow); then hv [n][D/64] u64 in sorted row order, mz [n] f64, charge [n]
  * u8, orig [n] u32, decoy [n] u8 (input order, if flagged); then a u64
  * FNV-1a hash of every preceding byte.  Tensor-core copies are not stored

@@ -1,4 +1,5 @@
-// encode.cu -- spectrum vectors -> binary hypervectors (Section 3.3, Eq. 1).
+// encode.cu -- spectrum vectors -> binary hypervectors (Section 3.3, Eq. 1;
+// the random-projection baseline of Section 4.2 as a second encoder).
 //
 // out_d = [2 c_d >= n], with c_d the number of peaks whose bound bit
 // F_bin XOR L_level is 1 at d (Eq. 1's bipolar sum is n - 2 c_d and the
@@ -83,6 +84,48 @@ k_encode(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__rest
     }
 }
 
+// Random-projection encoder (the LSH baseline of Section 4.2): out_d = [I_d <= 0]
+// with I_d = sum over peaks of (level + 1) * (1 - 2 F_bin[d]).  One warp per
+// spectrum; each lane owns one 64-bit word at a time and keeps its 64 sums in
+// registers.
+__global__ void __launch_bounds__(ENC_WARPS * 32)
+k_encode_projection(const uint64_t *__restrict__ F, uint32_t n_bins, uint32_t n_levels, uint32_t W,
+                    const uint32_t *__restrict__ off, const uint32_t *__restrict__ bins,
+                    const uint8_t *__restrict__ levels, uint32_t n_spec, uint64_t *__restrict__ out,
+                    uint32_t *status)
+{
+    const uint32_t sp = blockIdx.x * ENC_WARPS + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31;
+    if (sp >= n_spec) return;
+    uint32_t beg = off[sp], end = off[sp + 1];
+    if (end < beg || end - beg > ENC_MAX_PEAKS) {
+        if (lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
+        end = beg;   // encode as an empty row
+    }
+    bool any_bad = false;
+    for (uint32_t w = lane; w < W; w += 32) {
+        int32_t acc[64];
+#pragma unroll
+        for (int b = 0; b < 64; ++b) acc[b] = 0;
+        for (uint32_t p = beg; p < end; ++p) {
+            const uint32_t bn = __ldg(bins + p), l = __ldg(levels + p);
+            if (bn >= n_bins || l >= n_levels) {
+                any_bad = true;
+                continue;
+            }
+            const uint64_t x = __ldg(F + (size_t)bn * W + w);
+            const int32_t wt = (int32_t)l + 1;
+#pragma unroll
+            for (int b = 0; b < 64; ++b) acc[b] += ((x >> b) & 1ull) ? -wt : wt;
+        }
+        uint64_t o = 0;
+#pragma unroll
+        for (int b = 0; b < 64; ++b) o |= (uint64_t)(acc[b] <= 0) << b;
+        out[(size_t)sp * W + w] = o;
+    }
+    if (any_bad) hd_flag(status, HD_DEV_BAD_INPUT);
+}
+
 }  // namespace
 
 void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins,
@@ -92,7 +135,11 @@ void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bi
     const unsigned grid = hd_ceil_div(n, ENC_WARPS);
     const uint32_t *st = ctx->status.dev;
     hd_prof_scope timed(HD_KERNEL_ENCODE, s);
-    if (W >= 128)
+    if (ctx->p.encoder == HD_ENC_PROJECTION)
+        hd_count_launches(1), k_encode_projection<<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins,
+                                                                              ctx->p.n_levels, W, off, bins,
+                                                                              levels, n, out, (uint32_t *)st);
+    else if (W >= 128)
         hd_count_launches(1), k_encode<4><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
                                                     W, off, bins, levels, n, out, (uint32_t *)st);
     else if (W >= 64)

@@ -215,6 +215,12 @@ hd_status hd_ctx_create(const hd_params *p, hd_ctx **out)
     HD_CHECK(p->n_levels >= 2 && p->n_levels <= 256, "hd_ctx_create: n_levels must be in [2, 256]");
     HD_CHECK(p->n_bins >= 1, "hd_ctx_create: n_bins must be >= 1");
     HD_CHECK(p->alpha <= p->dim, "hd_ctx_create: alpha must be <= dim");
+    HD_CHECK(p->position_mode <= HD_POS_RANDOM, "hd_ctx_create: unknown position_mode");
+    HD_CHECK(p->encoder <= HD_ENC_PROJECTION, "hd_ctx_create: unknown encoder");
+    HD_CHECK(p->position_mode != HD_POS_WALK || (p->alpha <= 256 && p->n_bins <= (1u << 24)),
+             "hd_ctx_create: a position walk takes alpha <= 256 flips per step and n_bins <= 2^24");
+    HD_CHECK(p->position_mode != HD_POS_RANDOM || (uint64_t)p->n_bins * (p->dim / 32) <= 0xFFFFFFFFull,
+             "hd_ctx_create: n_bins * dim / 32 must fit 32 bits for random position HVs");
     hd_ctx *c = new hd_ctx;
     c->p = *p;
     c->W = p->dim / 64;
@@ -397,6 +403,7 @@ struct lib_header {
     char magic[8];
     uint32_t dim, n_levels, n_bins, alpha;
     uint64_t seed;
+    uint32_t position_mode, encoder;
     uint32_t n, flags;
 };
 
@@ -444,6 +451,8 @@ hd_status hd_library_save(const hd_library *lib, const hd_ctx *ctx, const char *
     h.n_bins = ctx->p.n_bins;
     h.alpha = ctx->p.alpha;
     h.seed = ctx->p.seed;
+    h.position_mode = ctx->p.position_mode;
+    h.encoder = ctx->p.encoder;
     h.n = lib->n;
     h.flags = lib->decoy ? 1u : 0u;
     file_closer fc;
@@ -491,7 +500,8 @@ hd_status hd_library_load(hd_ctx *ctx, const char *path, hd_library **out)
     if (!ok || std::memcmp(h.magic, LIB_MAGIC, 8) != 0)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_library_load: not a library file");
     if (h.dim != ctx->p.dim || h.n_levels != ctx->p.n_levels || h.n_bins != ctx->p.n_bins ||
-        h.alpha != ctx->p.alpha || h.seed != ctx->p.seed)
+        h.alpha != ctx->p.alpha || h.seed != ctx->p.seed || h.position_mode != ctx->p.position_mode ||
+        h.encoder != ctx->p.encoder)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_library_load: the file was encoded with other item-memory parameters");
     const size_t n = h.n, W = ctx->W;
     std::vector<uint64_t> hv(n * W);

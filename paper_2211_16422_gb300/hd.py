@@ -32,7 +32,8 @@ class HDError(RuntimeError):
 
 class _Params(C.Structure):
     _fields_ = [("dim", C.c_uint32), ("n_levels", C.c_uint32), ("n_bins", C.c_uint32),
-                ("alpha", C.c_uint32), ("seed", C.c_uint64)]
+                ("alpha", C.c_uint32), ("seed", C.c_uint64), ("position_mode", C.c_uint32),
+                ("encoder", C.c_uint32)]
 
 
 class _PPParams(C.Structure):
@@ -169,11 +170,15 @@ def _unit(unit) -> int:
 class Ctx:
     """Item memory (hd_ctx) on the current CUDA device."""
 
-    def __init__(self, dim, n_levels, n_bins, alpha=None, seed=0):
+    POSITION_MODES = {"nested": 0, "walk": 1, "random": 2}
+    ENCODERS = {"id_level": 0, "projection": 1}
+
+    def __init__(self, dim, n_levels, n_bins, alpha=None, seed=0, position_mode="nested", encoder="id_level"):
         lib = load()
         self.dim, self.n_levels, self.n_bins = int(dim), int(n_levels), int(n_bins)
         self.alpha = self.dim // 2 if alpha is None else int(alpha)
-        p = _Params(self.dim, self.n_levels, self.n_bins, self.alpha, int(seed))
+        p = _Params(self.dim, self.n_levels, self.n_bins, self.alpha, int(seed),
+                    self.POSITION_MODES[position_mode], self.ENCODERS[encoder])
         h = C.c_void_p()
         _check(lib.hd_ctx_create(C.byref(p), C.byref(h)))
         self._h = h
