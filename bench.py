@@ -200,6 +200,23 @@ def cpu_oracle_rate(refs, queries, spec, target_s, lib_fraction=0.05, seed=5):
     return per_step, threads, sample, step
 
 
+# ------------------------------------------------------- multi-rank reduce
+def reduce_over_ranks(seconds, units, device=None):
+    """Whole-job figures of a weak-scaling step: the slowest rank's time and the
+    units (comparisons, queries) of all ranks summed.  With no process group
+    the rank's own figures are returned.  `device` holds the reduction tensors
+    (cuda for NCCL; None = CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds), int(units)
+    tt = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cc = torch.tensor([int(units)], dtype=torch.int64, device=device)
+    dist.all_reduce(cc)
+    return float(tt.item()), int(cc.item())
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -286,16 +303,7 @@ def run_ours(args, rank, world, local_rank):
     ctx.status()
     lib.status()
     ms = ev0.elapsed_time(ev1) / args.steps
-    if dist_on:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        cc = torch.tensor([comparisons], device="cuda", dtype=torch.int64)
-        dist.all_reduce(cc)
-        total_comparisons = int(cc.item())
-    else:
-        total_comparisons = comparisons
+    ms, total_comparisons = reduce_over_ranks(ms, comparisons, device="cuda")
     value = total_comparisons / (ms / 1e3)
     qps = nq * world / (ms / 1e3)
 
@@ -316,11 +324,7 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.steps):
             e2e_step()
         e2e_s = (time.perf_counter() - t) / args.steps
-        if dist_on:
-            import torch.distributed as dist
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s, _ = reduce_over_ranks(e2e_s, 0, device="cuda")
         h2d = sum(t_.numel() * t_.element_size() for t_ in (h_off, h_bins, h_lv, h_mz, h_z))
         d2h = nq * k * (4 + 2)
         e2e = {"value": total_comparisons / e2e_s, "unit": UNIT, "queries_per_s": nq * world / e2e_s,
