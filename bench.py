@@ -47,8 +47,10 @@ KERNEL_SOURCES = ("paper_2211_16422_gb300/csrc/search_mma.cu", "paper_2211_16422
                   "paper_2211_16422_gb300/csrc/hd_internal.cuh")
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
-    #     -k regex:k_search_mma -s 72 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
-    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 457.25e9 + 0.07484e9, "sha256": "1b17b84d993c61ca"},
+    #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
+    #     --form tc_fp8 --schedule <tile_group,super_group,cluster,cta_group>
+    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 460.00e9 + 0.06307e9, "sha256": "0918cc4046e77fe2"},
+    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 462.04e9 + 0.04146e9, "sha256": "0918cc4046e77fe2"},
 }
 
 
@@ -68,6 +70,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", default="auto")
+    ap.add_argument("--schedule", default=None,
+                    help="tile_group,super_group,cluster,cta_group of the tensor-core form (with --form; "
+                         "default: the library's 16,16,2,2)")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -257,6 +262,10 @@ def run_ours(args, rank, world, local_rank):
         t = time.perf_counter()
         hd.hd_library_prepare(lib, form)
         setup["prepare_" + form + "_s"] = time.perf_counter() - t
+    if args.schedule:
+        tg_, sg_, cs_, cg_ = (int(x) for x in args.schedule.split(","))
+        hd.hd_library_set_schedule(lib, tg_, sg_, cs_, cg_)
+        setup["schedule"] = {"tile_group": tg_, "super_group": sg_, "cluster": cs_, "cta_group": cg_}
     q_mz, q_z = dev(queries.precursor_mz), dev(queries.charge)
     if args.form == "auto":
         # the library's autotuner picks form and schedule on this query batch (setup, not timed)
@@ -350,7 +359,8 @@ def run_ours(args, rank, world, local_rank):
         achieved = comparisons * 2.0 * D / (avg_search_ms / 1e3) / 1e12
         basis = ("measured burst cuBLAS bf16 x 2 (nominal fp8/bf16 ratio 4.5/2.25)" if form == "tc_fp8"
                  else "measured burst cuBLAS bf16")
-        sched = setup.get("autotune_choice") or {"tile_group": 16, "super_group": 8, "cluster": 2, "cta_group": 2}
+        sched = (setup.get("autotune_choice") or setup.get("schedule")
+                 or {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2})
         kname = "k_search_mma2" if sched.get("cta_group") == 2 else "k_search_mma"
         roofline = {"kernel": kname, "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
                     "peak": peak, "frac": achieved / peak, "peak_basis": basis + " (of measured)",

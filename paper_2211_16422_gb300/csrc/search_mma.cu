@@ -550,11 +550,15 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
 #ifndef HD_MMA2_HINT_B
 #define HD_MMA2_HINT_B 1
 #endif
+#ifndef HD_MMA2_HINT_FRAC
+#define HD_MMA2_HINT_FRAC 1.0
+#endif
 __device__ __forceinline__ uint64_t l2_policy(int kind)
 {
     uint64_t p = 0;
-    if (kind == 1) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    if (kind == 2) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    const float frac = HD_MMA2_HINT_FRAC;
+    if (kind == 1) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, %1;" : "=l"(p) : "f"(frac));
+    if (kind == 2) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, %1;" : "=l"(p) : "f"(frac));
     return p;
 }
 __device__ __forceinline__ void tma_load_2d_pair_hint(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
