@@ -48,9 +48,11 @@ KERNEL_SOURCES = ("paper_2211_16422_gb300/csrc/search_mma.cu", "paper_2211_16422
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
-    #     --form tc_fp8 --schedule <tile_group,super_group,cluster,cta_group>
-    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 460.00e9 + 0.06307e9, "sha256": "0918cc4046e77fe2"},
-    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 462.04e9 + 0.04146e9, "sha256": "0918cc4046e77fe2"},
+    #     --form <form> --schedule <tile_group,super_group,cluster,cta_group>
+    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 243.34e9 + 0.01459e9, "sha256": "4f6780bb9139726a"},
+    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 244.46e9 + 0.02192e9, "sha256": "4f6780bb9139726a"},
+    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 457.72e9 + 0.04105e9, "sha256": "4f6780bb9139726a"},
+    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 459.31e9 + 0.07186e9, "sha256": "4f6780bb9139726a"},
 }
 
 
@@ -257,11 +259,12 @@ def run_ours(args, rank, world, local_rank):
     lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
     setup["build_library_s"] = time.perf_counter() - t
     del r_hv
-    form = args.form if args.form != "auto" else "tc_fp8"
-    if form.startswith("tc_"):
+    form = args.form
+    # the autotuner chooses among the prepared tensor-core forms (and popc)
+    for f in (("tc_fp4", "tc_fp8") if form == "auto" else ((form,) if form.startswith("tc_") else ())):
         t = time.perf_counter()
-        hd.hd_library_prepare(lib, form)
-        setup["prepare_" + form + "_s"] = time.perf_counter() - t
+        hd.hd_library_prepare(lib, f)
+        setup["prepare_" + f + "_s"] = time.perf_counter() - t
     if args.schedule:
         tg_, sg_, cs_, cg_ = (int(x) for x in args.schedule.split(","))
         hd.hd_library_set_schedule(lib, tg_, sg_, cs_, cg_)
@@ -355,10 +358,11 @@ def run_ours(args, rank, world, local_rank):
         # 4.5 / 2.25 PFLOP/s dense ratio)
         peaks = measured_peaks()
         bf16 = peaks.get("bf16_tflops", 1900.0)
-        peak = bf16 * (2.0 if form == "tc_fp8" else 1.0)
+        eight_bit_kind = form in ("tc_fp8", "tc_fp4")   # kind::f8f6f4 runs e2m1 at the e4m3 rate
+        peak = bf16 * (2.0 if eight_bit_kind else 1.0)
         achieved = comparisons * 2.0 * D / (avg_search_ms / 1e3) / 1e12
-        basis = ("measured burst cuBLAS bf16 x 2 (nominal fp8/bf16 ratio 4.5/2.25)" if form == "tc_fp8"
-                 else "measured burst cuBLAS bf16")
+        basis = ("measured burst cuBLAS bf16 x 2 (nominal fp8/bf16 ratio 4.5/2.25; tcgen05 kind::f8f6f4 runs "
+                 "e4m3 and e2m1 operands at the same rate)" if eight_bit_kind else "measured burst cuBLAS bf16")
         sched = (setup.get("autotune_choice") or setup.get("schedule")
                  or {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2})
         kname = "k_search_mma2" if sched.get("cta_group") == 2 else "k_search_mma"
@@ -431,6 +435,7 @@ def run_batched(args):
         r_hv = hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp))
         lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
         del r_hv
+        hd.hd_library_prepare(lib, "tc_fp4")
         hd.hd_library_prepare(lib, "tc_fp8")
         off, bins, lv = hd.hd_preprocess(ctx, dev(qs.offsets), dev(qs.mz), dev(qs.intensity), **pp)
         nnz = int(hd.as_u32(off)[-1])
@@ -473,7 +478,8 @@ def run_batched(args):
         hd.hd_profile_enable(False)
         search_ms, search_n = hd.hd_profile_collect(hd.HD_KERNEL_SEARCH)
         achieved = comparisons * 2.0 * D / (search_ms / max(1, search_n) / 1e3) / 1e12
-        peak = measured_peaks().get("bf16_tflops_sustained", 1700.0) * (2.0 if best["form"] == "tc_fp8" else 1.0)
+        peak = measured_peaks().get("bf16_tflops_sustained", 1700.0) * (2.0 if best["form"] in ("tc_fp8", "tc_fp4")
+                                                                         else 1.0)
         line = {"metric": "Hamming comparisons/s, batched uneven windows (200 batches, 20 ppm / 150 Da / 500 Da)",
                 "value": comparisons / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -523,7 +529,7 @@ def run_serving(args):
     r_hv = hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp))
     lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
     del r_hv
-    hd.hd_library_prepare(lib, "tc_fp8")
+    hd.hd_library_prepare(lib, "tc_fp4")
     off_t, bins_t, lv_t = hd.hd_preprocess(ctx, dev(pool.offsets), dev(pool.mz), dev(pool.intensity), **pp)
     off = hd.as_u32(off_t)
     nnz = int(off[-1])
@@ -587,7 +593,7 @@ def run_serving(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": f"{n_r}-reference resident library, requests of {spec['req_lo']}..{hi_req} "
                                    "spectra (log-uniform), Poisson arrivals", "dim": D, "k": k,
-                       "server": {"slots": 3, "max_batch_queries": 16384, "form": "tc_fp8"}},
+                       "server": {"slots": 3, "max_batch_queries": 16384, "form": "tc_fp4"}},
             "loads": loads}
     print(json.dumps(line), flush=True)
 
@@ -613,7 +619,7 @@ def run_cascade(args):
     lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
     del r_hv
     hd.hd_library_set_decoys(lib, dev(refs.decoy))
-    hd.hd_library_prepare(lib, "tc_fp8")
+    hd.hd_library_prepare(lib, "tc_fp4")
     q_csr = hd.hd_preprocess(ctx, dev(queries.offsets), dev(queries.mz), dev(queries.intensity), **pp_args(spec))
     q_mz, q_z = dev(queries.precursor_mz), dev(queries.charge)
     nq = queries.n
@@ -621,7 +627,7 @@ def run_cascade(args):
 
     def step():
         hd.hd_encode(ctx, *q_csr, out=q_hv)
-        return hd.hd_cascade_search(lib, q_hv, q_mz, q_z, levels, fdr, form="tc_fp8")
+        return hd.hd_cascade_search(lib, q_hv, q_mz, q_z, levels, fdr, form="tc_fp4")
 
     for _ in range(args.warmup):
         out = step()
@@ -649,7 +655,7 @@ def run_cascade(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded generator; decoys are targets with repositioned fragments)",
             "config": {"workload": f"{refs.n}-reference library (50% decoys) x {nq} queries, D={D}, Q={Q}, "
-                                   "levels 20 ppm / +-500 Da, top-1, FDR 1%", "form": "tc_fp8",
+                                   "levels 20 ppm / +-500 Da, top-1, FDR 1%", "form": "tc_fp4",
                        "l2": "library and query set exceed L2: no flush needed"},
             "identified_per_level": ident, "identified_fraction": sum(ident) / nq,
             "search_ms_per_step": search_ms / args.steps, "search_launches_per_step": search_n / args.steps,

@@ -121,7 +121,9 @@ typedef enum {
     HD_FORM_AUTO = 0,     /* fastest form the library was prepared for */
     HD_FORM_POPC = 1,     /* XOR + population count on the integer pipes */
     HD_FORM_TC_FP8 = 2,   /* tcgen05 kind::f8f6f4, +-1 as e4m3 (library: D bytes/row) */
-    HD_FORM_TC_BF16 = 3   /* tcgen05 kind::f16, +-1 as bf16 (library: 2D bytes/row) */
+    HD_FORM_TC_BF16 = 3,  /* tcgen05 kind::f16, +-1 as bf16 (library: 2D bytes/row) */
+    HD_FORM_TC_FP4 = 4    /* tcgen05 kind::f8f6f4, +-1 as e2m1 packed two per byte
+                             (library: D/2 bytes/row; the TMA unpacks into shared memory) */
 } hd_search_form;
 
 HD_API const char *hd_status_string(hd_status s);
@@ -206,8 +208,9 @@ HD_API hd_status hd_library_export(const hd_library *lib, uint64_t *d_hv, double
                             uint8_t *d_charge, uint32_t *d_orig, hd_stream stream);
 HD_API hd_status hd_library_status(hd_library *lib);
 /* Builds the bipolar copy of the library a tensor-core form scores
- * (HD_FORM_TC_FP8: n*D bytes; HD_FORM_TC_BF16: n*2D bytes of device memory,
- * owned by the library).  HD_FORM_POPC needs nothing.  Synchronous; idempotent. */
+ * (HD_FORM_TC_FP8: n*D bytes; HD_FORM_TC_BF16: n*2D bytes; HD_FORM_TC_FP4:
+ * n*D/2 bytes of device memory, owned by the library).  HD_FORM_POPC needs
+ * nothing.  Synchronous; idempotent. */
 HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
 /* Schedule of the tensor-core forms (no counterpart in the paper).  Reference
  * rows form tiles of 256 on a grid fixed to row 0; one work item scores one

@@ -67,6 +67,10 @@ hd_status check_device(int want)
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool form_ok(hd_search_form f)
+{
+    return f == HD_FORM_AUTO || f == HD_FORM_POPC || f == HD_FORM_TC_FP8 || f == HD_FORM_TC_BF16 || f == HD_FORM_TC_FP4;
+}
 bool unit_ok(hd_tol_unit u) { return u == HD_TOL_DA || u == HD_TOL_PPM || u == HD_TOL_MASS; }
 
 bool tol_ok(double tol) { return std::isfinite(tol) && tol >= 0.0; }
@@ -117,6 +121,7 @@ void lib_release(hd_library *lib)
     cudaFree(lib->charge_start);
     cudaFree(lib->x_fp8);
     cudaFree(lib->x_bf16);
+    cudaFree(lib->x_fp4);
     cudaFree(lib->decoy);
     status_free(lib->status);
     delete lib;
@@ -163,17 +168,19 @@ hd_status hd_search_dispatch(const hd_library *lib, const uint64_t *q_hv, const 
                              uint32_t n_q, const hd_qwin &win, uint32_t k, hd_search_form form, uint32_t *out_idx,
                              uint16_t *out_dist, cudaStream_t s)
 {
+    auto copy_of = [&](hd_search_form f) -> const uint8_t * {
+        return f == HD_FORM_TC_FP8 ? lib->x_fp8 : (f == HD_FORM_TC_BF16 ? lib->x_bf16 : lib->x_fp4);
+    };
     if (form == HD_FORM_AUTO) {
         form = lib->auto_form;
-        const bool ok = form == HD_FORM_POPC || (form == HD_FORM_TC_FP8 && lib->x_fp8) ||
-                        (form == HD_FORM_TC_BF16 && lib->x_bf16);
-        if (!ok) form = lib->x_fp8 ? HD_FORM_TC_FP8 : (lib->x_bf16 ? HD_FORM_TC_BF16 : HD_FORM_POPC);
+        const bool ok = form == HD_FORM_POPC || (form != HD_FORM_AUTO && copy_of(form));
+        if (!ok)
+            form = lib->x_fp4 ? HD_FORM_TC_FP4
+                              : (lib->x_fp8 ? HD_FORM_TC_FP8 : (lib->x_bf16 ? HD_FORM_TC_BF16 : HD_FORM_POPC));
     }
-    if (form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16) {
-        const bool fp8 = form == HD_FORM_TC_FP8;
-        HD_CHECK(fp8 ? lib->x_fp8 != nullptr || lib->n == 0 : lib->x_bf16 != nullptr || lib->n == 0,
-                 "hd_search_open: call hd_library_prepare for this form first");
-        return hd_search_mma_run(lib, fp8, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
+    if (form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16 || form == HD_FORM_TC_FP4) {
+        HD_CHECK(copy_of(form) != nullptr || lib->n == 0, "hd_search_open: call hd_library_prepare for this form first");
+        return hd_search_mma_run(lib, form, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
     }
     return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
 }
@@ -569,14 +576,14 @@ hd_status hd_library_status(hd_library *lib)
 hd_status hd_library_prepare(hd_library *lib, hd_search_form form)
 {
     HD_CHECK(lib, "hd_library_prepare: null library");
-    HD_CHECK(form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
+    HD_CHECK(form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16 || form == HD_FORM_TC_FP4,
              "hd_library_prepare: unknown form");
     hd_status st = check_device(lib->device);
     if (st != HD_OK || form == HD_FORM_POPC) return st;
     scoped_stream ss;
     if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess)
         return hd_fail(HD_ERR_CUDA, "hd_library_prepare: stream creation failed");
-    st = hd_library_expand(lib, form == HD_FORM_TC_FP8, ss.s);
+    st = hd_library_expand(lib, form, ss.s);
     if (st != HD_OK) return st;
     HD_CUDA_TRY(cudaStreamSynchronize(ss.s));
     return HD_OK;
@@ -640,7 +647,7 @@ hd_status hd_search_open_ex(const hd_library *lib, const uint64_t *d_q_hv, const
     HD_CHECK(k >= 1 && k <= 16, "hd_search_open: k must be in [1, 16]");
     HD_CHECK(tol_ok(tol), "hd_search_open: tol must be finite and >= 0");
     HD_CHECK(unit_ok(unit), "hd_search_open: bad unit");
-    HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
+    HD_CHECK(form_ok(form),
              "hd_search_open: unknown form");
     if (n_q == 0) return HD_OK;
     HD_CHECK(d_q_hv && d_q_mz && d_q_charge && d_out_idx && d_out_dist, "hd_search_open: null buffer");
@@ -658,7 +665,7 @@ hd_status hd_search_open_multi(const hd_library *lib, const uint64_t *d_q_hv, co
 {
     HD_CHECK(lib, "hd_search_open_multi: null library");
     HD_CHECK(k >= 1 && k <= 16, "hd_search_open_multi: k must be in [1, 16]");
-    HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
+    HD_CHECK(form_ok(form),
              "hd_search_open_multi: unknown form");
     hd_qwin win;
     hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);

@@ -74,6 +74,7 @@ struct hd_library {
     uint32_t *charge_start = nullptr;   // [257] first row with charge >= c (device)
     uint8_t *x_fp8 = nullptr;      // [n][D] bipolar e4m3 rows (tensor-core form), optional
     uint8_t *x_bf16 = nullptr;     // [n][2D] bipolar bf16 rows (tensor-core form), optional
+    uint8_t *x_fp4 = nullptr;      // [n][D/2] bipolar e2m1 rows, two per byte (tensor-core form), optional
     uint8_t *decoy = nullptr;      // [n] decoy flags, input order, optional
     hd_mma_tuning mma_tuning;
     hd_search_form auto_form = HD_FORM_AUTO;   // set by the autotuner
@@ -179,8 +180,8 @@ hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv
                                      void *scratch, size_t scratch_bytes);
 
 // Tensor-core form: the bipolar copy of the library rows, and the search.
-hd_status hd_library_expand(hd_library *lib, bool fp8, cudaStream_t s);
-hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_hv, const double *q_mz,
+hd_status hd_library_expand(hd_library *lib, hd_search_form form, cudaStream_t s);
+hd_status hd_search_mma_run(const hd_library *lib, hd_search_form form, const uint64_t *q_hv, const double *q_mz,
                             const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
                             uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);
 

@@ -41,6 +41,19 @@ using namespace hd_search;
 #ifndef HD_MMA_STAGES
 #define HD_MMA_STAGES 4
 #endif
+// Operand formats of +-1: FMT_BF16 (kind::f16, 2 bytes), FMT_E4M3 (kind::f8f6f4,
+// 1 byte), FMT_E2M1 (kind::f8f6f4, 4 bits packed in HBM and unpacked by the TMA
+// into 16-byte shared-memory containers of 16 values, so the shared-memory
+// image of a K-chunk is that of e4m3 while HBM and L2 carry half the bytes).
+constexpr int FMT_BF16 = 0, FMT_E4M3 = 1, FMT_E2M1 = 2;
+// instruction-descriptor A/B format code of each operand format
+__host__ __device__ constexpr uint32_t fmt_code(int fmt) { return fmt == FMT_BF16 ? 1u : (fmt == FMT_E4M3 ? 0u : 5u); }
+// Transaction bytes a load of `smem_bytes` of operand counts on its mbarrier:
+// the bytes read from global memory, half the unpacked footprint for e2m1.
+__host__ __device__ constexpr uint32_t tx_bytes(int fmt, uint32_t smem_bytes)
+{
+    return fmt == FMT_E2M1 ? smem_bytes / 2 : smem_bytes;
+}
 constexpr int TM = 128;                 // queries per block (MMA M)
 constexpr int TN = HD_MMA_TN;           // reference rows per tile (MMA N)
 constexpr int KB = 128;                 // bytes of K per stage (one 128B swizzle atom)
@@ -72,11 +85,11 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-template <bool FP8>
+template <int FMT>
 __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                           uint32_t accumulate)
 {
-    if (FP8)
+    if (FMT != FMT_BF16)
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -176,12 +189,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor: fp32 accumulator, A/B e4m3 (kind::f8f6f4) or bf16
-// (kind::f16), both K-major, M = 128, N = 256.
-template <bool FP8>
+// Instruction descriptor: fp32 accumulator, A/B e4m3 or e2m1 (kind::f8f6f4) or
+// bf16 (kind::f16), both K-major, M = 128, N = 256.
+template <int FMT>
 __host__ __device__ constexpr uint32_t instr_desc()
 {
-    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((uint32_t)(TN >> 3) << 17) |
+    return (1u << 4) | (fmt_code(FMT) << 7) | (fmt_code(FMT) << 10) | ((uint32_t)(TN >> 3) << 17) |
            ((uint32_t)(TM >> 4) << 24);
 }
 
@@ -223,7 +236,7 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 // item and sweep the same reference tiles; each CTA loads 1/CS of every B
 // tile and multicasts it into all of them, so L2 serves each tile once per
 // cluster.  Stage-free barriers count the MMA commits of every CTA.
-template <int K, bool FP8, int CS>
+template <int K, int FMT, int CS>
 __global__ void __launch_bounds__(THREADS, 1)
 k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
@@ -286,7 +299,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                         const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
                         if (!mbar_wait(&empty[s], ph ^ 1u, a.wait_ns)) { give_up(); break; }
                         uint8_t *sa = smem + s * STAGE_BYTES, *sb = sa + A_BYTES;
-                        mbar_expect_tx(&full[s], STAGE_BYTES);
+                        mbar_expect_tx(&full[s], tx_bytes(FMT, STAGE_BYTES));
                         if (a.stall && it == 0) continue;   // nothing ever completes this stage
                         tma_load_2d(sa, &qmap, (int32_t)(c * KB), (int32_t)((b * CS + crank) * TM), &full[s]);
                         if (CS == 1)
@@ -301,7 +314,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     } else if (warp == 1) {
         // ----------------------------------------------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = instr_desc<FP8>();
+            constexpr uint32_t idesc = instr_desc<FMT>();
             uint32_t it = 0, acc_it = 0;
             for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
                 uint32_t b, t0, t1;
@@ -320,7 +333,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                         const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
 #pragma unroll
                         for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
-                            mma_issue<FP8>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
+                            mma_issue<FMT>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
                         if (CS == 1) mma_commit(&empty[s]);
                         else mma_commit_mc(&empty[s], CMASK);
                     }
@@ -473,11 +486,11 @@ __device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols)
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-template <bool FP8>
+template <int FMT>
 __device__ __forceinline__ void mma_issue2(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                            uint32_t accumulate)
 {
-    if (FP8)
+    if (FMT != FMT_BF16)
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
@@ -572,10 +585,10 @@ __device__ __forceinline__ void tma_load_2d_pair_hint(void *dst, const CUtensorM
 }
 
 // M = 256 (the pair), N = 256.
-template <bool FP8>
+template <int FMT>
 __host__ __device__ constexpr uint32_t instr_desc2()
 {
-    return (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((uint32_t)(TN >> 3) << 17) |
+    return (1u << 4) | (fmt_code(FMT) << 7) | (fmt_code(FMT) << 10) | ((uint32_t)(TN >> 3) << 17) |
            ((uint32_t)((2 * TM) >> 4) << 24);
 }
 
@@ -583,7 +596,7 @@ __host__ __device__ constexpr uint32_t instr_desc2()
 // the pair's MMAs).  Each CTA holds its own block of 128 queries (A) and its
 // half of the pair's reference tile (B); all loads complete on rank 0's stage
 // barrier.
-template <int K, bool FP8>
+template <int K, int FMT>
 __global__ void __launch_bounds__(THREADS, 1)
 k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
@@ -652,7 +665,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                     for (uint32_t c = 0; c < nchunks; ++c, ++it) {
                         const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
                         if (!mbar_wait(&empty[s], ph ^ 1u, a.wait_ns)) { give_up(); break; }
-                        if (crank == 0) mbar_expect_tx(&full[s], 2 * STAGE2_BYTES);
+                        if (crank == 0) mbar_expect_tx(&full[s], tx_bytes(FMT, 2 * STAGE2_BYTES));
                         if (a.stall && it == 0) continue;   // nothing ever completes this stage
                         uint8_t *sa = smem + s * STAGE2_BYTES, *sb = sa + A_BYTES;
                         const uint32_t bar = full0 + s * 8u;
@@ -669,7 +682,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         if (crank == 0) {
             // ------------------------------------------- MMA issuer (rank 0)
             if (lane == 0) {
-                constexpr uint32_t idesc = instr_desc2<FP8>();
+                constexpr uint32_t idesc = instr_desc2<FMT>();
                 uint32_t it = 0, acc_it = 0;
                 for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
                     uint32_t b, t0, t1;
@@ -689,7 +702,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                             const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
 #pragma unroll
                             for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
-                                mma_issue2<FP8>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
+                                mma_issue2<FMT>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
                             mma_commit2_mc(&empty[s], 0x3);
                         }
                         if (!ok) break;
@@ -852,8 +865,10 @@ __global__ void k_emit(const uint64_t *__restrict__ top, const uint32_t *__restr
     }
 }
 
-// One row of packed bits per warp -> bipolar bytes (e4m3) or halves (bf16).
-template <bool FP8>
+// One row of packed bits per warp -> +-1 in the operand format: bytes (e4m3:
+// 0x38 / 0xB8), halves (bf16: 0x3F80 / 0xBF80) or nibbles (e2m1: 0x2 / 0xA,
+// element 2i in the low nibble of byte i).
+template <int FMT>
 __global__ void k_expand(const uint64_t *__restrict__ hv, const uint32_t *__restrict__ perm, uint32_t n,
                          uint32_t W, uint8_t *__restrict__ out)
 {
@@ -861,28 +876,34 @@ __global__ void k_expand(const uint64_t *__restrict__ hv, const uint32_t *__rest
     const uint32_t lane = threadIdx.x & 31;
     if (r >= n) return;
     const uint64_t *src = hv + (size_t)(perm ? perm[r] : r) * W;
-    constexpr uint32_t EB = FP8 ? 1 : 2;
-    uint8_t *dst = out + (size_t)r * W * 64 * EB;
+    constexpr uint32_t WB = FMT == FMT_BF16 ? 128 : (FMT == FMT_E4M3 ? 64 : 32);   // bytes per 64 bits
+    uint8_t *dst = out + (size_t)r * W * WB;
     for (uint32_t w = lane; w < W; w += 32) {
         const uint64_t x = src[w];
-        uint4 *o = reinterpret_cast<uint4 *>(dst + (size_t)w * 64 * EB);
+        uint4 *o = reinterpret_cast<uint4 *>(dst + (size_t)w * WB);
 #pragma unroll
-        for (int q = 0; q < 4 * (int)EB; ++q) {
+        for (int q = 0; q < (int)(WB / 16); ++q) {
             uint32_t p[4];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 uint32_t word = 0;
-                if (FP8) {
+                if (FMT == FMT_E4M3) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const uint32_t bit = (uint32_t)(x >> (q * 16 + h * 4 + j)) & 1u;
                         word |= (0x38u | (bit << 7)) << (8 * j);
                     }
-                } else {
+                } else if (FMT == FMT_BF16) {
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
                         const uint32_t bit = (uint32_t)(x >> (q * 8 + h * 2 + j)) & 1u;
                         word |= (0x3F80u | (bit << 15)) << (16 * j);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const uint32_t bit = (uint32_t)(x >> (q * 32 + h * 8 + j)) & 1u;
+                        word |= (0x2u | (bit << 3)) << (4 * j);
                     }
                 }
                 p[h] = word;
@@ -927,7 +948,28 @@ hd_status make_map(CUtensorMap *m, const void *base, uint64_t rows, uint32_t row
     return HD_OK;
 }
 
-template <int K, bool FP8>
+// Rows of `dim` e2m1 values packed two per byte (dim / 2 bytes); boxes of 128
+// values x box_rows rows, unpacked into 16-byte containers of 16 values (128
+// bytes of shared memory per row), 128B swizzle, rows past `rows` read as 0.
+hd_status make_map_e2m1(CUtensorMap *m, const void *base, uint64_t rows, uint32_t dim, uint32_t box_rows)
+{
+    encode_fn enc = tensor_map_encoder();
+    if (!enc) return hd_fail(HD_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[2] = {dim, rows};
+    const cuuint64_t strides[1] = {dim / 2};
+    const cuuint32_t box[2] = {128u, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_16U4_ALIGN16B, 2, const_cast<void *>(base), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return hd_fail(HD_ERR_CUDA, "cuTensorMapEncodeTiled (e2m1) failed");
+    return HD_OK;
+}
+
+template <int FMT>
+constexpr uint32_t global_row_bytes(uint32_t dim) { return FMT == FMT_BF16 ? 2 * dim : (FMT == FMT_E4M3 ? dim : dim / 2); }
+
+template <int K, int FMT>
 hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
                   uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
                   cudaStream_t s, const hd_mma_tuning &tune)
@@ -935,11 +977,13 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     const bool pair = tune.cta_group == 2;   // SM pairs, M = 256 (cluster of 2)
     const uint32_t cs = pair ? 2u : tune.cluster;   // 1, 2 or 4 CTAs per cluster
     const uint32_t n_blocks = (n_q + TM * cs - 1) / (TM * cs);
-    const uint32_t row_bytes = lib->dim * (FP8 ? 1u : 2u);
-    const uint8_t *lib_x = FP8 ? lib->x_fp8 : lib->x_bf16;
+    // shared-memory bytes of one operand row (the K extent the kernel walks) and HBM bytes
+    const uint32_t row_bytes = lib->dim * (FMT == FMT_BF16 ? 2u : 1u);
+    const uint32_t g_row_bytes = global_row_bytes<FMT>(lib->dim);
+    const uint8_t *lib_x = FMT == FMT_BF16 ? lib->x_bf16 : (FMT == FMT_E4M3 ? lib->x_fp8 : lib->x_fp4);
     if (!lib_x) return hd_fail(HD_ERR_INVALID_ARG, "library not prepared for this tensor-core form");
-    auto kern = pair ? k_search_mma2<K, FP8>
-                     : (cs == 4 ? k_search_mma<K, FP8, 4> : (cs == 2 ? k_search_mma<K, FP8, 2> : k_search_mma<K, FP8, 1>));
+    auto kern = pair ? k_search_mma2<K, FMT>
+                     : (cs == 4 ? k_search_mma<K, FMT, 4> : (cs == 2 ? k_search_mma<K, FMT, 2> : k_search_mma<K, FMT, 1>));
     const uint32_t smem_bytes = pair ? SMEM2_BYTES : SMEM_BYTES;
     HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
     if (cs > 1) HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -977,7 +1021,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
         *pst = ar.take<uint32_t>(n_pairs + 1);
         *top = ar.take<uint64_t>((size_t)n_q * K);
         *locks = ar.take<uint32_t>((size_t)n_blocks * cs);
-        *qx = ar.take<uint8_t>((size_t)n_q * row_bytes);
+        *qx = ar.take<uint8_t>((size_t)n_q * g_row_bytes);
     };
     uint32_t *perm, *lo, *hi, *bt0, *bt1, *pst, *locks;
     uint64_t *top;
@@ -992,8 +1036,11 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     }
     carve(ar, &perm, &lo, &hi, &bt0, &bt1, &pst, &top, &locks, &qx);
     CUtensorMap qmap, lmap;
-    hd_status st = make_map(&qmap, qx, n_q, row_bytes, TM);
-    if (st == HD_OK) st = make_map(&lmap, lib_x, lib->n, row_bytes, TN / cs);
+    hd_status st = FMT == FMT_E2M1 ? make_map_e2m1(&qmap, qx, n_q, lib->dim, TM)
+                                   : make_map(&qmap, qx, n_q, row_bytes, TM);
+    if (st == HD_OK)
+        st = FMT == FMT_E2M1 ? make_map_e2m1(&lmap, lib_x, lib->n, lib->dim, TN / cs)
+                             : make_map(&lmap, lib_x, lib->n, row_bytes, TN / cs);
     if (st != HD_OK) {
         cudaFreeAsync(ar.base, s);
         return st;
@@ -1001,7 +1048,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     HD_CUDA_TRY(cudaMemsetAsync(top, 0xFF, (size_t)n_q * K * sizeof(uint64_t), s));
     HD_CUDA_TRY(cudaMemsetAsync(locks, 0, (size_t)n_blocks * cs * sizeof(uint32_t), s));
     hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, perm, ar, s);
-    hd_count_launches(1), k_expand<FP8><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
+    hd_count_launches(1), k_expand<FMT><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
     hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z,
                                                                           perm, n_q, win, lo, hi);
     hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, TM * cs, n_blocks, tg, sg, n_super, bt0, bt1, pst);
@@ -1030,39 +1077,52 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     return HD_OK;
 }
 
-template <bool FP8>
+template <int FMT>
 hd_status run_fmt(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
                   uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *oi, uint16_t *od, cudaStream_t s,
                   const hd_mma_tuning &tu)
 {
-    if (k <= 1) return run_mma<1, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
-    if (k <= 2) return run_mma<2, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
-    if (k <= 4) return run_mma<4, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
-    if (k <= 8) return run_mma<8, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
-    return run_mma<16, FP8>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    if (k <= 1) return run_mma<1, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    if (k <= 2) return run_mma<2, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    if (k <= 4) return run_mma<4, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    if (k <= 8) return run_mma<8, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    return run_mma<16, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
 }
 
 }  // namespace
 
-hd_status hd_library_expand(hd_library *lib, bool fp8, cudaStream_t s)
+namespace {
+int form_fmt(hd_search_form form)
 {
-    uint8_t *&dst = fp8 ? lib->x_fp8 : lib->x_bf16;
+    return form == HD_FORM_TC_BF16 ? FMT_BF16 : (form == HD_FORM_TC_FP8 ? FMT_E4M3 : FMT_E2M1);
+}
+}  // namespace
+
+hd_status hd_library_expand(hd_library *lib, hd_search_form form, cudaStream_t s)
+{
+    const int fmt = form_fmt(form);
+    uint8_t *&dst = fmt == FMT_BF16 ? lib->x_bf16 : (fmt == FMT_E4M3 ? lib->x_fp8 : lib->x_fp4);
     if (dst || lib->n == 0) return HD_OK;
-    const size_t bytes = (size_t)lib->n * lib->dim * (fp8 ? 1 : 2);
+    const size_t bytes = (size_t)lib->n * (fmt == FMT_BF16 ? global_row_bytes<FMT_BF16>(lib->dim)
+                                           : fmt == FMT_E4M3 ? global_row_bytes<FMT_E4M3>(lib->dim)
+                                                             : global_row_bytes<FMT_E2M1>(lib->dim));
     if (cudaMalloc(&dst, bytes) != cudaSuccess) {
         cudaGetLastError();
         dst = nullptr;
         return hd_fail(HD_ERR_OOM, "expanded library allocation failed");
     }
-    if (fp8)
-        hd_count_launches(1), k_expand<true><<<hd_ceil_div(lib->n, 8), 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
+    const unsigned g = hd_ceil_div(lib->n, 8);
+    if (fmt == FMT_E4M3)
+        hd_count_launches(1), k_expand<FMT_E4M3><<<g, 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
+    else if (fmt == FMT_BF16)
+        hd_count_launches(1), k_expand<FMT_BF16><<<g, 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
     else
-        hd_count_launches(1), k_expand<false><<<hd_ceil_div(lib->n, 8), 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
+        hd_count_launches(1), k_expand<FMT_E2M1><<<g, 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
     HD_CUDA_TRY(cudaGetLastError());
     return HD_OK;
 }
 
-hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_hv, const double *q_mz,
+hd_status hd_search_mma_run(const hd_library *lib, hd_search_form form, const uint64_t *q_hv, const double *q_mz,
                             const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
                             uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s)
 {
@@ -1072,6 +1132,8 @@ hd_status hd_search_mma_run(const hd_library *lib, bool fp8, const uint64_t *q_h
     if (tu.super_group == 0) tu.super_group = 16;
     if (tu.cluster != 1 && tu.cluster != 2 && tu.cluster != 4) tu.cluster = 2;
     if (tu.cta_group == 0) tu.cta_group = tu.cluster == 2 ? 2u : 1u;   // default: SM pairs
-    if (fp8) return run_fmt<true>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
-    return run_fmt<false>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
+    const int fmt = form_fmt(form);
+    if (fmt == FMT_E4M3) return run_fmt<FMT_E4M3>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
+    if (fmt == FMT_BF16) return run_fmt<FMT_BF16>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
+    return run_fmt<FMT_E2M1>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
 }

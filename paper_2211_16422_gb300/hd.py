@@ -19,8 +19,9 @@ from . import build as _build
 
 HD_OK, HD_ERR_INVALID_ARG, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_TIMEOUT, HD_ERR_UNSUPPORTED = range(6)
 HD_TOL_DA, HD_TOL_PPM, HD_TOL_MASS = 0, 1, 2
-HD_FORM_AUTO, HD_FORM_POPC, HD_FORM_TC_FP8, HD_FORM_TC_BF16 = 0, 1, 2, 3
-FORMS = {"auto": HD_FORM_AUTO, "popc": HD_FORM_POPC, "tc_fp8": HD_FORM_TC_FP8, "tc_bf16": HD_FORM_TC_BF16}
+HD_FORM_AUTO, HD_FORM_POPC, HD_FORM_TC_FP8, HD_FORM_TC_BF16, HD_FORM_TC_FP4 = 0, 1, 2, 3, 4
+FORMS = {"auto": HD_FORM_AUTO, "popc": HD_FORM_POPC, "tc_fp8": HD_FORM_TC_FP8, "tc_bf16": HD_FORM_TC_BF16,
+         "tc_fp4": HD_FORM_TC_FP4}
 NO_IDX, NO_DIST = 0xFFFFFFFF, 0xFFFF
 
 

@@ -76,10 +76,10 @@ def test_multi_window_all_forms_exact(hd, D):
     refs, qs, cls, _ = _batched_workload(D, 8000, 12, 10, 200)
     ctx, lib, r_hv, q_csr = _setup(hd, refs, qs, D, 32)
     q_hv = hd.hd_encode(ctx, *q_csr)
-    for f in ("tc_fp8", "tc_bf16"):
+    for f in ("tc_fp8", "tc_bf16", "tc_fp4"):
         hd.hd_library_prepare(lib, f)
     oi, od = _oracle_by_class(D, oracle_side.hvs(refs, D, 32, 0), refs, oracle_side.hvs(qs, D, 32, 0), qs, cls, 5)
-    for form in ("popc", "tc_fp8", "tc_bf16"):
+    for form in ("popc", "tc_fp8", "tc_bf16", "tc_fp4"):
         i, d = hd.hd_search_open_multi(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, 5,
                                        form=form)
         torch.cuda.synchronize()

@@ -14,7 +14,7 @@ from paper_2211_16422_gb300 import synth
 from tests import oracle_side
 
 pytestmark = pytest.mark.gpu
-FORMS = ("tc_fp8", "tc_bf16")
+FORMS = ("tc_fp8", "tc_bf16", "tc_fp4")
 
 
 @pytest.fixture(scope="module")
@@ -206,7 +206,7 @@ def test_tc_pair_form_exact(hd, D, k, n_q, tol, unit):
     q_hv = enc(qs)
     o_r, o_q = oracle_side.hvs(refs, D, Q, 5), oracle_side.hvs(qs, D, Q, 5)
     oi, od = oracle.search(D, o_r, refs.precursor_mz, refs.charge, o_q, qs.precursor_mz, qs.charge, tol, unit, k)
-    for form in ("tc_fp8", "tc_bf16"):
+    for form in FORMS:
         hd.hd_library_prepare(lib, form)
         hd.hd_library_set_schedule(lib, 4, 2, 2, 2)
         i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), tol, unit, k, form=form)
@@ -228,3 +228,24 @@ def test_schedule_arguments_checked(hd):
     hd.hd_library_set_schedule(lib, 0, 0, 0, 2)
     hd.hd_library_set_schedule(lib, 0, 0, 2, 2)
     hd.hd_library_set_schedule(lib, 0, 0, 0, 0)
+
+
+@pytest.mark.parametrize("tg,sg,cs,cg", [(1, 1, 1, 1), (8, 4, 4, 1), (3, 5, 2, 2), (16, 16, 2, 2)])
+def test_e2m1_schedules_exact(hd, tg, sg, cs, cg):
+    """The e2m1 form (4-bit operands in HBM, unpacked by the TMA) under the
+    1-SM schedules with and without multicast and the SM-pair schedule."""
+    rng = np.random.default_rng(90 + tg)
+    D, n, m = 2048, 5000, 333
+    refs = _rand_hv(rng, n, D // 64)
+    mz = rng.uniform(400, 700, n)
+    z = rng.integers(2, 4, n).astype(np.uint8)
+    q = refs[:m] ^ (_rand_hv(rng, m, D // 64) & np.uint64(0x0000FFFF0000FFFF))
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
+    hd.hd_library_prepare(lib, "tc_fp4")
+    hd.hd_library_set_schedule(lib, tg, sg, cs, cg)
+    i, d = hd.hd_search_open(lib, dev(q), dev(mz[:m]), dev(z[:m]), 100.0, "da", 4, form="tc_fp4")
+    torch.cuda.synchronize()
+    lib.status()
+    oi, od = oracle.search(D, refs, mz, z, q, mz[:m], z[:m], 100.0, "da", 4)
+    assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
