@@ -1,24 +1,31 @@
 // search_mma.cu -- open-modification Hamming search (Section 3.4) on the
 // 5th-generation tensor cores (tcgen05), exact.
 //
-// Bits become bipolar values (bit 0 -> +1, bit 1 -> -1) stored as 8-bit e4m3
-// (+1 = 0x38, -1 = 0xB8) or bf16 (0x3F80 / 0xBF80).  For a query x and a
-// reference y the tensor core computes S = sum_d x_d y_d = D - 2 dist(x, y)
-// with fp32 accumulation in tensor memory.  Every product is +-1 and every
-// partial sum an integer of magnitude <= D <= 32768 < 2^24, so the sum is
-// exact and dist = (D - S) / 2 matches the popcount form bit for bit.
+// Bits become bipolar values (bit 0 -> +1, bit 1 -> -1) stored as e2m1 (4 bits,
+// 0x2 / 0xA, two per byte), e4m3 (0x38 / 0xB8) or bf16 (0x3F80 / 0xBF80).  For
+// a query x and a reference y the tensor core computes S = sum_d x_d y_d =
+// D - 2 dist(x, y) with fp32 accumulation in tensor memory.  Every product is
+// +-1 and every partial sum an integer of magnitude <= D <= 32768 < 2^24, so
+// the sum is exact and dist = (D - S) / 2 matches the popcount form bit for
+// bit.
 //
-// Kernel layout (one persistent CTA per SM, 192 threads):
-//   warp 0      TMA producer: 2-D tensor loads of 128-byte K-slices of a
-//               query block (A: 128 rows) and a reference tile (B: 256 rows)
-//               into a 4-stage ring, 128B-swizzled for the MMA descriptors;
-//   warp 1      allocates 512 TMEM columns and issues tcgen05.mma
-//               (M=128, N=256, 32 bytes of K per instruction) into one of two
-//               accumulator buffers, committing stages and tiles to mbarriers;
-//   warps 2..5  epilogue: tcgen05.ld of the finished 128x256 accumulator,
-//               one query row per thread, window mask, top-k of (dist, input
-//               index) keys; the buffer is handed back while the next tile is
-//               being accumulated in the other one.
+// Two kernels share the warp roles (192 threads per CTA, one persistent CTA
+// per SM):
+//   warp 0      TMA producer: 2-D tensor loads of 128-component K-slices of a
+//               query block (A: 128 rows) and a reference tile into a ring of
+//               stages, 128B-swizzled for the MMA descriptors;
+//   warp 1      allocates 512 TMEM columns and issues tcgen05.mma (32
+//               components of K per instruction) into one of two accumulator
+//               buffers, committing stages and tiles to mbarriers;
+//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator, one query row
+//               per thread, window mask, top-k of (dist, input index) keys; the
+//               buffer is handed back while the next tile is accumulated in
+//               the other one.
+// k_search_mma: M = 128, N = 256 per CTA, 4 stages of 48 KB; clusters of 1, 2
+// or 4 CTAs share each reference tile by TMA multicast.
+// k_search_mma2 (default): SM pairs, tcgen05.mma.cta_group::2 with M = 256,
+// N = 256 issued by the even CTA; each CTA stages its own query block and half
+// of the tile, 6 stages of 32 KB.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
