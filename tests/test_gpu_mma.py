@@ -49,7 +49,7 @@ def _search_all(hd, lib, q, qmz, qz, tol, unit, k):
     return out
 
 
-@pytest.mark.parametrize("D", [128, 2048, 8192])
+@pytest.mark.parametrize("D", [128, 2048, 8192, 16384, 32768])
 def test_tc_forms_small_exact(hd, D):
     rng = np.random.default_rng(D)
     W = D // 64
