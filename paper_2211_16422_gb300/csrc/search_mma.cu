@@ -9,23 +9,24 @@
 // the sum is exact and dist = (D - S) / 2 matches the popcount form bit for
 // bit.
 //
-// Two kernels share the warp roles (192 threads per CTA, one persistent CTA
-// per SM):
+// Two kernels share the warp roles (one persistent CTA per SM):
 //   warp 0      TMA producer: 2-D tensor loads of 128-component K-slices of a
 //               query block (A: 128 rows) and a reference tile into a ring of
 //               stages, 128B-swizzled for the MMA descriptors;
 //   warp 1      allocates 512 TMEM columns and issues tcgen05.mma (32
 //               components of K per instruction) into one of two accumulator
 //               buffers, committing stages and tiles to mbarriers;
-//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator, one query row
-//               per thread, window mask, top-k of (dist, input index) keys; the
-//               buffer is handed back while the next tile is accumulated in
-//               the other one.
-// k_search_mma: M = 128, N = 256 per CTA, 4 stages of 48 KB; clusters of 1, 2
-// or 4 CTAs share each reference tile by TMA multicast.
-// k_search_mma2 (default): SM pairs, tcgen05.mma.cta_group::2 with M = 256,
-// N = 256 issued by the even CTA; each CTA stages its own query block and half
-// of the tile, 6 stages of 32 KB.
+//   warps 2..    epilogue: tcgen05.ld of the finished accumulator, one query
+//               row per thread, window mask, top-k of (dist, input index) keys;
+//               the buffer is handed back while the next tile is accumulated
+//               in the other one.
+// k_search_mma: 192 threads (4 epilogue warps), M = 128, N = 256 per CTA, 4
+// stages of 48 KB; clusters of 1, 2 or 4 CTAs share each reference tile by
+// TMA multicast.
+// k_search_mma2 (default): 320 threads (8 epilogue warps, two per 32 query
+// rows, each on 128 of the 256 columns), SM pairs, tcgen05.mma.cta_group::2
+// with M = 256, N = 256 issued by the even CTA; each CTA stages its own query
+// block and half of the tile, 6 stages of 32 KB.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -71,6 +72,12 @@ constexpr uint32_t B_BYTES = TN * KB;
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
 constexpr uint32_t TMEM_COLS = 2 * TN;
+// Epilogue warps of the pair kernel: two per tensor-memory lane quarter, each
+// scoring half of the 256 columns of its 32 query rows, so the scoring of a
+// tile keeps up with its MMAs at D = 4096 as well.
+constexpr int EPI2_WARPS = 8;
+constexpr int THREADS2 = 64 + 32 * EPI2_WARPS;
+constexpr uint32_t EPI2_THREADS = 32 * EPI2_WARPS;
 static_assert(TN % 32 == 0 && TN <= 256 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "tile shape");
 static_assert(STAGES * STAGE_BYTES + 1280 <= 232448, "shared memory");
 
@@ -238,6 +245,7 @@ __device__ __forceinline__ void item_range(const mma_args &a, uint32_t item, uin
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar2() { asm volatile("bar.sync 1, %0;" ::"r"(EPI2_THREADS) : "memory"); }
 
 // CS > 1: clusters of CS CTAs take CS consecutive query blocks of one work
 // item and sweep the same reference tiles; each CTA loads 1/CS of every B
@@ -604,7 +612,7 @@ __host__ __device__ constexpr uint32_t instr_desc2()
 // half of the pair's reference tile (B); all loads complete on rank 0's stage
 // barrier.
 template <int K, int FMT>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS2, 1)
 k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
     constexpr uint32_t CS = 2;
@@ -627,7 +635,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 256);   // every epilogue thread of both CTAs
+            mbar_init(&acc_empty[i], 2 * EPI2_THREADS);   // every epilogue thread of both CTAs
         }
         mbar_init(drain, 1);
         s_abort = 0;
@@ -725,6 +733,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
     } else {
         // ------------------------------------------------------- epilogue
         const uint32_t quarter = warp & 3;              // TMEM lanes this warp may read
+        const uint32_t half = (uint32_t)(warp - 2) >> 2;  // which 128 of the 256 columns
         const uint32_t row = quarter * 32 + lane;       // query row within the block
         const uint32_t lane_addr = (quarter * 32) << 16;
         const bool leader = threadIdx.x == 64;
@@ -748,7 +757,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 tc_fence_after();
                 const uint32_t r0 = t * TN;
 #pragma unroll 1
-                for (uint32_t cg = 0; cg < TN / 32; ++cg) {
+                for (uint32_t cg = half * (TN / 64); cg < (half + 1) * (TN / 64); ++cg) {
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
@@ -767,8 +776,9 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 tc_fence_before();
                 mbar_arrive_remote(acc_empty0 + buf * 8u);
             }
-            // merge into the block's running top-k under its lock (bounded spin)
-            epi_bar();
+            // merge into the block's running top-k under its lock (bounded spin),
+            // the two halves of each row one after the other
+            epi_bar2();
             if (leader) {
                 int got = 0;
                 if (ok && !*abort_flag) {
@@ -781,21 +791,23 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 }
                 s_lock_ok = got;
             }
-            epi_bar();
+            epi_bar2();
             const bool locked = s_lock_ok != 0;
-            if (locked) {
-                if (sq < a.n_q) {
-                    unsigned long long *g = reinterpret_cast<unsigned long long *>(a.top + (size_t)sq * K);
-                    uint64_t cur[K];
+            for (uint32_t ph = 0; ph < 2; ++ph) {
+                if (locked && half == ph) {
+                    if (sq < a.n_q) {
+                        unsigned long long *g = reinterpret_cast<unsigned long long *>(a.top + (size_t)sq * K);
+                        uint64_t cur[K];
 #pragma unroll
-                    for (int i = 0; i < K; ++i) cur[i] = __ldcg(g + i);
-                    topk_merge<K>(cur, best);
+                        for (int i = 0; i < K; ++i) cur[i] = __ldcg(g + i);
+                        topk_merge<K>(cur, best);
 #pragma unroll
-                    for (int i = 0; i < K; ++i) __stcg(g + i, (unsigned long long)cur[i]);
+                        for (int i = 0; i < K; ++i) __stcg(g + i, (unsigned long long)cur[i]);
+                    }
+                    __threadfence();
                 }
-                __threadfence();
+                epi_bar2();
             }
-            epi_bar();
             if (leader && locked) atomicExch(&a.locks[sb_], 0u);
             if (!locked) break;
         }
@@ -992,13 +1004,14 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     auto kern = pair ? k_search_mma2<K, FMT>
                      : (cs == 4 ? k_search_mma<K, FMT, 4> : (cs == 2 ? k_search_mma<K, FMT, 2> : k_search_mma<K, FMT, 1>));
     const uint32_t smem_bytes = pair ? SMEM2_BYTES : SMEM_BYTES;
+    const uint32_t threads = pair ? (uint32_t)THREADS2 : (uint32_t)THREADS;
     HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
     if (cs > 1) HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     uint32_t grid = (uint32_t)lib->num_sms / cs * cs;
     if (cs > 1) {   // only co-resident clusters: a persistent grid must not wait for SMs
         cudaLaunchConfig_t qc = {};
         qc.gridDim = dim3(grid);
-        qc.blockDim = dim3(THREADS);
+        qc.blockDim = dim3(threads);
         qc.dynamicSmemBytes = smem_bytes;
         cudaLaunchAttribute qa[1];
         qa[0].id = cudaLaunchAttributeClusterDimension;
@@ -1065,7 +1078,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
         hd_prof_scope timed(HD_KERNEL_SEARCH, s);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(THREADS);
+        cfg.blockDim = dim3(threads);
         cfg.dynamicSmemBytes = smem_bytes;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
