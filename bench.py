@@ -49,10 +49,10 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
     #     --form <form> --schedule <tile_group,super_group,cluster,cta_group>
-    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 243.34e9 + 0.01459e9, "sha256": "5a671dd6dd33bb95"},
-    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 244.46e9 + 0.02192e9, "sha256": "5a671dd6dd33bb95"},
-    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 457.72e9 + 0.04105e9, "sha256": "5a671dd6dd33bb95"},
-    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 459.31e9 + 0.07186e9, "sha256": "5a671dd6dd33bb95"},
+    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 241.97e9 + 0.01489e9, "sha256": "373e9b9b6e7112da"},
+    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 245.13e9 + 0.02122e9, "sha256": "373e9b9b6e7112da"},
+    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 468.56e9 + 0.04449e9, "sha256": "373e9b9b6e7112da"},
+    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 458.08e9 + 0.06646e9, "sha256": "373e9b9b6e7112da"},
 }
 
 
