@@ -72,10 +72,16 @@ constexpr uint32_t B_BYTES = TN * KB;
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
 constexpr uint32_t TMEM_COLS = 2 * TN;
-// Epilogue warps of the pair kernel: two per tensor-memory lane quarter, each
-// scoring half of the 256 columns of its 32 query rows, so the scoring of a
-// tile keeps up with its MMAs at D = 4096 as well.
-constexpr int EPI2_WARPS = 8;
+// Epilogue warps of the pair kernel: EPI2_SPLIT per tensor-memory lane
+// quarter, each scoring 1/EPI2_SPLIT of the 256 columns of its 32 query rows,
+// so the scoring of a tile keeps up with its MMAs at D = 4096 as well.
+#ifndef HD_MMA2_EPI_WARPS
+#define HD_MMA2_EPI_WARPS 8
+#endif
+constexpr int EPI2_WARPS = HD_MMA2_EPI_WARPS;
+constexpr int EPI2_SPLIT = EPI2_WARPS / 4;
+constexpr int EPI2_COLS = TN / EPI2_SPLIT;   // accumulator columns per epilogue warp
+static_assert(EPI2_WARPS % 4 == 0 && (TN / 32) % EPI2_SPLIT == 0, "epilogue split");
 constexpr int THREADS2 = 64 + 32 * EPI2_WARPS;
 constexpr uint32_t EPI2_THREADS = 32 * EPI2_WARPS;
 static_assert(TN % 32 == 0 && TN <= 256 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "tile shape");
@@ -368,7 +374,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         const uint32_t lane_addr = (quarter * 32) << 16;
         const bool leader = threadIdx.x == 64;
         uint32_t acc_it = 0;
-        for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
+        for (uint32_t item = cid; item < total && !__any_sync(0xFFFFFFFFu, *abort_flag != 0); item += ncl) {
             uint32_t b, t0, t1;
             item_range(a, item, b, t0, t1);
             const uint32_t sb_ = b * CS + crank;     // this CTA's query block
@@ -381,7 +387,8 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             bool ok = true;
             for (uint32_t t = t0; t < t1; ++t, ++acc_it) {
                 const uint32_t buf = acc_it & 1u, aph = (acc_it >> 1) & 1u;
-                if (!mbar_wait(&acc_full[buf], aph, a.wait_ns)) { give_up(); ok = false; break; }
+                // warp-uniform outcome: the tensor-memory loads below are .sync.aligned
+                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&acc_full[buf], aph, a.wait_ns))) { give_up(); ok = false; break; }
                 tc_fence_after();
                 const uint32_t r0 = t * TN;
 #pragma unroll 1
@@ -733,13 +740,13 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
     } else {
         // ------------------------------------------------------- epilogue
         const uint32_t quarter = warp & 3;              // TMEM lanes this warp may read
-        const uint32_t half = (uint32_t)(warp - 2) >> 2;  // which 128 of the 256 columns
+        const uint32_t slice = (uint32_t)(warp - 2) >> 2;  // which EPI2_COLS of the TN columns
         const uint32_t row = quarter * 32 + lane;       // query row within the block
         const uint32_t lane_addr = (quarter * 32) << 16;
         const bool leader = threadIdx.x == 64;
         const uint32_t acc_empty0 = cluster_addr(&acc_empty[0], 0);
         uint32_t acc_it = 0;
-        for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
+        for (uint32_t item = cid; item < total && !__any_sync(0xFFFFFFFFu, *abort_flag != 0); item += ncl) {
             uint32_t b, t0, t1;
             item_range(a, item, b, t0, t1);
             const uint32_t sb_ = b * CS + crank;     // this CTA's query block
@@ -753,11 +760,12 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
             for (uint32_t t = t0; t < t1; ++t, ++acc_it) {
                 const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
                 const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
-                if (!mbar_wait(&acc_full[buf], aph, a.wait_ns)) { give_up(); ok = false; break; }
-                tc_fence_after();
                 const uint32_t r0 = t * TN;
+                // warp-uniform outcome: the tensor-memory loads below are .sync.aligned
+                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&acc_full[buf], aph, a.wait_ns))) { give_up(); ok = false; break; }
+                tc_fence_after();
 #pragma unroll 1
-                for (uint32_t cg = half * (TN / 64); cg < (half + 1) * (TN / 64); ++cg) {
+                for (uint32_t cg = slice * (EPI2_COLS / 32); cg < (slice + 1) * (EPI2_COLS / 32); ++cg) {
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
@@ -777,7 +785,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 mbar_arrive_remote(acc_empty0 + buf * 8u);
             }
             // merge into the block's running top-k under its lock (bounded spin),
-            // the two halves of each row one after the other
+            // the EPI2_SPLIT partial lists of each row one after the other
             epi_bar2();
             if (leader) {
                 int got = 0;
@@ -793,8 +801,8 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
             }
             epi_bar2();
             const bool locked = s_lock_ok != 0;
-            for (uint32_t ph = 0; ph < 2; ++ph) {
-                if (locked && half == ph) {
+            for (uint32_t ph = 0; ph < (uint32_t)EPI2_SPLIT; ++ph) {
+                if (locked && slice == ph) {
                     if (sq < a.n_q) {
                         unsigned long long *g = reinterpret_cast<unsigned long long *>(a.top + (size_t)sq * K);
                         uint64_t cur[K];
