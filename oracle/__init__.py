@@ -2,7 +2,8 @@
 
 Python wrapper (ctypes) around ``hd_oracle.c``: a plain, slow C restatement
 of the paper's encoding (Section 3.3, Eq. 1), candidate filter and Hamming
-search (Section 3.4) and preprocessing (Section 3.2, Table 1); plus, in
+search (Section 3.4) and preprocessing (Section 3.2, Table 1), and the
+multi-bit components and their dot-product search (Section 4.3); plus, in
 plain numpy on top of that search, the target-decoy q-values (Section 2.1)
 and the cascade search (Section 3.4).  Only the
 tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
@@ -54,6 +55,8 @@ def _load():
             lib.orc_window_count.argtypes = [u32, P, P, u32, P, P, dbl, i32, P]
             lib.orc_library_order.argtypes = [u32, P, P, P]
             lib.orc_search.argtypes = [u32, u32, P, P, P, u32, P, P, P, dbl, i32, u32, P, u32, P, P, u32]
+            lib.orc_encode_multibit.argtypes = [u32, P, u32, P, u32, u32, P, P, P, u32, P, u32, u32]
+            lib.orc_search_dot.argtypes = [u32, u32, P, P, P, u32, P, P, P, dbl, i32, u32, P, u32, P, P, u32]
             _lib = lib
     return _lib
 
@@ -121,6 +124,46 @@ def encode(dim, F, L, offsets, bins, levels, n_threads=None, encoder=0):
     if rc:
         raise ValueError(f"orc_encode rc={rc}")
     return out
+
+
+def encode_multibit(dim, F, L, offsets, bins, levels, bits, n_threads=None, encoder=0):
+    """Multi-bit components [n, D] int8 in [-m, m], m = 2^(bits-1) - 1: the
+    bundle I of ``encode`` (Eq. 1, or the projection sum for encoder 1)
+    quantised with the spectrum's own step max|I| / m, halves rounded up in
+    magnitude (reading of Section 4.3's higher-precision components)."""
+    off = _c(offsets, np.uint32)
+    n = off.size - 1
+    out = np.zeros((n, dim), np.int8)
+    F, L = _c(F, np.uint64), _c(L, np.uint64)
+    b, lv = _c(bins, np.uint32), _c(levels, np.uint8)
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    rc = _load().orc_encode_multibit(dim, _p(F), F.shape[0], _p(L), L.shape[0], n, _p(off), _p(b), _p(lv),
+                                     int(bits), _p(out), n_threads, encoder)
+    if rc:
+        raise ValueError(f"orc_encode_multibit rc={rc}")
+    return out
+
+
+def search_dot(ref, ref_mz, ref_z, qv, q_mz, q_z, tol, unit="da", k=1, which=None, n_threads=None):
+    """Brute-force windowed top-k by the dot product of integer components:
+    (idx [m, k] u32, score [m, k] i32), higher score first, the lower reference
+    index on a tie; missing slots hold 0xFFFFFFFF / INT32_MIN."""
+    rv, rm, rz = _c(ref, np.int8), _c(ref_mz, np.float64), _c(ref_z, np.uint8)
+    qq, qm, qz = _c(qv, np.int8), _c(q_mz, np.float64), _c(q_z, np.uint8)
+    dim = rv.shape[1] if rv.ndim == 2 and rv.shape[0] else qq.shape[1]
+    w = None if which is None else _c(which, np.uint32)
+    m = qm.size if w is None else w.size
+    idx = np.zeros((m, k), np.uint32)
+    score = np.zeros((m, k), np.int32)
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    rc = _load().orc_search_dot(dim, rm.size, _p(rv), _p(rm), _p(rz), qm.size, _p(qq), _p(qm), _p(qz),
+                                float(tol), _UNITS[unit], k, _p(w), 0 if w is None else w.size,
+                                _p(idx), _p(score), n_threads)
+    if rc:
+        raise ValueError(f"orc_search_dot rc={rc}")
+    return idx, score
 
 
 def window_count(ref_mz, ref_z, q_mz, q_z, tol, unit="da"):

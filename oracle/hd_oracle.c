@@ -279,13 +279,22 @@ long long orc_preprocess(uint32_t n_spec, const uint32_t *raw_off, const double 
  * spectrum vector (value level + 1 at each peak's bin) projected on D random
  * +-1 directions, direction d taking component d of F_bin for each bin:
  * I_d = sum over peaks of (level + 1) * F_bin[d], then the same sign rule.
+ *
+ * Multi-bit components (bits > 1; Section 4.3 names a higher precision per
+ * HV component as a way to raise the identification rate, without a
+ * quantiser).  Reading: the same sum I is quantised symmetrically to
+ * m = 2^(bits-1) - 1 magnitude levels with the spectrum's own step M / m,
+ * M = max_d |I_d|:
+ *     h_d = sign(I_d) * round(m * |I_d| / M), halves rounded up in magnitude,
+ * computed in integers as floor((2 m |I_d| + M) / (2 M)); h = 0 when M = 0.
  * ------------------------------------------------------------------------- */
 typedef struct {
-    uint32_t D, n_bins, n_levels, s0, s1, encoder;
+    uint32_t D, n_bins, n_levels, s0, s1, encoder, bits;
     const uint64_t *F, *L;
     const uint32_t *off, *bin;
     const uint8_t *level;
-    uint64_t *out;
+    uint64_t *out;      /* bits == 1: [n][D/64] */
+    int8_t *out_mb;     /* bits > 1: [n][D] */
     int rc;
 } encode_job;
 
@@ -305,19 +314,37 @@ static void *encode_worker(void *arg)
                 I[d] += j->encoder == 1 ? f * ((int)j->level[p] + 1) : f * l;
             }
         }
-        uint64_t *o = j->out + (size_t)s * W;
-        for (uint32_t d = 0; d < D; ++d) set_bit(o, d, I[d] > 0 ? 0 : 1);
+        if (j->bits == 1) {
+            uint64_t *o = j->out + (size_t)s * W;
+            for (uint32_t d = 0; d < D; ++d) set_bit(o, d, I[d] > 0 ? 0 : 1);
+        } else {
+            const int64_t m = ((int64_t)1 << (j->bits - 1)) - 1;
+            int64_t M = 0;
+            for (uint32_t d = 0; d < D; ++d) {
+                int64_t a = I[d] < 0 ? -(int64_t)I[d] : (int64_t)I[d];
+                if (a > M) M = a;
+            }
+            int8_t *o = j->out_mb + (size_t)s * D;
+            for (uint32_t d = 0; d < D; ++d) {
+                if (M == 0) { o[d] = 0; continue; }
+                int64_t a = I[d] < 0 ? -(int64_t)I[d] : (int64_t)I[d];
+                int64_t h = (2 * m * a + M) / (2 * M);
+                o[d] = (int8_t)(I[d] < 0 ? -h : h);
+            }
+        }
     }
     free(I);
     return NULL;
 }
 
-/* Spectra are split into `n_threads` contiguous ranges, one per thread. */
-int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L, uint32_t n_levels,
-               uint32_t n_spec, const uint32_t *off, const uint32_t *bin, const uint8_t *level,
-               uint64_t *out, uint32_t n_threads, uint32_t encoder)
+/* Spectra are split into `n_threads` contiguous ranges, one per thread.
+ * bits == 1 writes binary HVs to `out`, bits in 2..8 multi-bit components to
+ * `out_mb`. */
+static int encode_any(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L, uint32_t n_levels,
+                      uint32_t n_spec, const uint32_t *off, const uint32_t *bin, const uint8_t *level,
+                      uint64_t *out, int8_t *out_mb, uint32_t bits, uint32_t n_threads, uint32_t encoder)
 {
-    if (D == 0 || D % 64u || encoder > 1) return -1;
+    if (D == 0 || D % 64u || encoder > 1 || bits == 0 || bits > 8) return -1;
     for (uint32_t s = 0; s < n_spec; ++s) if (off[s + 1] < off[s]) return -1;
     if (n_threads == 0) n_threads = 1;
     if (n_threads > n_spec) n_threads = n_spec ? n_spec : 1;
@@ -327,7 +354,8 @@ int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L
     if (!th || !jobs || !started) { free(th); free(jobs); free(started); return -2; }
     for (uint32_t t = 0; t < n_threads; ++t) {
         encode_job j = { D, n_bins, n_levels, (uint32_t)((uint64_t)n_spec * t / n_threads),
-                         (uint32_t)((uint64_t)n_spec * (t + 1) / n_threads), encoder, F, L, off, bin, level, out, 0 };
+                         (uint32_t)((uint64_t)n_spec * (t + 1) / n_threads), encoder, bits, F, L, off, bin, level,
+                         out, out_mb, 0 };
         jobs[t] = j;
     }
     for (uint32_t t = 1; t < n_threads; ++t) started[t] = pthread_create(&th[t], NULL, encode_worker, &jobs[t]) == 0;
@@ -340,6 +368,21 @@ int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L
     }
     free(th); free(jobs); free(started);
     return rc;
+}
+
+int orc_encode(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L, uint32_t n_levels,
+               uint32_t n_spec, const uint32_t *off, const uint32_t *bin, const uint8_t *level,
+               uint64_t *out, uint32_t n_threads, uint32_t encoder)
+{
+    return encode_any(D, F, n_bins, L, n_levels, n_spec, off, bin, level, out, NULL, 1, n_threads, encoder);
+}
+
+int orc_encode_multibit(uint32_t D, const uint64_t *F, uint32_t n_bins, const uint64_t *L, uint32_t n_levels,
+                        uint32_t n_spec, const uint32_t *off, const uint32_t *bin, const uint8_t *level,
+                        uint32_t bits, int8_t *out, uint32_t n_threads, uint32_t encoder)
+{
+    if (bits < 2) return -1;
+    return encode_any(D, F, n_bins, L, n_levels, n_spec, off, bin, level, NULL, out, bits, n_threads, encoder);
 }
 
 /* ---------------------------------------------------------------------------
@@ -470,6 +513,83 @@ int orc_search(uint32_t D, uint32_t n_ref, const uint64_t *ref_hv, const double 
     if (started + 1 < n_threads)
         for (uint32_t t = started + 1; t < n_threads; ++t) search_worker(&jobs[t]);
     search_worker(&jobs[0]);
+    for (uint32_t t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    free(th); free(jobs);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Search over multi-bit components (the Section 4.3 variant above).  With
+ * integer components the Hamming similarity generalises to the dot product
+ *     S(x, y) = sum_d x_d * y_d,
+ * which for +-1 components equals D - 2 * dist.  For each query every
+ * candidate (the same predicate as orc_search) is scored and the k best are
+ * kept: higher S first, the lower reference index on a tie.  With fewer than
+ * k candidates the remaining slots hold idx 0xFFFFFFFF and score INT32_MIN.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t D, n_ref, k, n_which, tid, n_threads;
+    const int8_t *ref, *qv;
+    const double *ref_mz, *q_mz;
+    const uint8_t *ref_z, *q_z;
+    const uint32_t *which;
+    double tol; int unit;
+    uint32_t *out_idx; int32_t *out_score;
+} dot_job;
+
+static void *dot_worker(void *arg)
+{
+    dot_job *j = (dot_job *)arg;
+    int64_t *bs = (int64_t *)malloc(sizeof(int64_t) * j->k);
+    uint32_t *bi = (uint32_t *)malloc(sizeof(uint32_t) * j->k);
+    for (uint32_t t = j->tid; t < j->n_which; t += j->n_threads) {
+        uint32_t q = j->which ? j->which[t] : t, filled = 0;
+        const int8_t *qh = j->qv + (size_t)q * j->D;
+        for (uint32_t r = 0; r < j->n_ref; ++r) {
+            if (!is_candidate(j->ref_mz[r], j->ref_z[r], j->q_mz[q], j->q_z[q], j->tol, j->unit)) continue;
+            const int8_t *rh = j->ref + (size_t)r * j->D;
+            int64_t S = 0;
+            for (uint32_t d = 0; d < j->D; ++d) S += (int64_t)qh[d] * (int64_t)rh[d];
+            /* position of (S, r) among the kept entries, best first */
+            uint32_t pos = filled;
+            while (pos > 0 && (bs[pos - 1] < S || (bs[pos - 1] == S && bi[pos - 1] > r))) --pos;
+            if (pos >= j->k) continue;
+            uint32_t last = filled < j->k ? filled : j->k - 1;
+            for (uint32_t u = last; u > pos; --u) { bs[u] = bs[u - 1]; bi[u] = bi[u - 1]; }
+            bs[pos] = S; bi[pos] = r;
+            if (filled < j->k) ++filled;
+        }
+        for (uint32_t s = 0; s < j->k; ++s) {
+            j->out_idx[(size_t)t * j->k + s] = s < filled ? bi[s] : 0xFFFFFFFFu;
+            j->out_score[(size_t)t * j->k + s] = s < filled ? (int32_t)bs[s] : INT32_MIN;
+        }
+    }
+    free(bs); free(bi);
+    return NULL;
+}
+
+int orc_search_dot(uint32_t D, uint32_t n_ref, const int8_t *ref, const double *ref_mz, const uint8_t *ref_z,
+                   uint32_t n_q, const int8_t *qv, const double *q_mz, const uint8_t *q_z,
+                   double tol, int unit, uint32_t k, const uint32_t *which, uint32_t n_which,
+                   uint32_t *out_idx, int32_t *out_score, uint32_t n_threads)
+{
+    if (D == 0 || k == 0 || !(tol >= 0.0)) return -1;
+    if (!which) n_which = n_q;
+    if (n_threads == 0) n_threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * n_threads);
+    dot_job *jobs = (dot_job *)malloc(sizeof(dot_job) * n_threads);
+    if (!th || !jobs) { free(th); free(jobs); return -2; }
+    for (uint32_t t = 0; t < n_threads; ++t) {
+        dot_job j = { D, n_ref, k, n_which, t, n_threads, ref, qv, ref_mz, q_mz, ref_z, q_z, which, tol, unit,
+                      out_idx, out_score };
+        jobs[t] = j;
+    }
+    uint32_t started = 0;
+    for (uint32_t t = 1; t < n_threads; ++t)
+        if (pthread_create(&th[t], NULL, dot_worker, &jobs[t]) == 0) ++started; else break;
+    if (started + 1 < n_threads)
+        for (uint32_t t = started + 1; t < n_threads; ++t) dot_worker(&jobs[t]);
+    dot_worker(&jobs[0]);
     for (uint32_t t = 1; t <= started; ++t) pthread_join(th[t], NULL);
     free(th); free(jobs);
     return 0;
