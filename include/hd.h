@@ -407,6 +407,47 @@ HD_API hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_t *d
                                         double tol, hd_tol_unit unit, uint32_t k, uint32_t *d_out_idx,
                                         uint16_t *d_out_dist, hd_stream stream);
 
+/* Multi-bit HV components (Section 4.3: a higher precision per component
+ * is the paper's second way to raise the identification rate; it names no
+ * quantiser).  Reading: the encoder's integer bundle I (Eq. 1, or the
+ * projection sum when the context's encoder is HD_ENC_PROJECTION) is
+ * quantised with the spectrum's own step, M = max_d |I_d|,
+ * m = 2^(bits-1) - 1:
+ *     h_d = sign(I_d) * floor((2 m |I_d| + M) / (2 M))    (h = 0 if M = 0),
+ * i.e. m |I_d| / M rounded half up in magnitude; h_d in [-m, m].  Two
+ * spectra score by the dot product S = sum_d h_q,d h_r,d, which for +-1
+ * components is D - 2 dist; higher is better.
+ *
+ * hd_encode_multibit writes d_out [n_spectra][D] int8 (16-byte aligned),
+ * bits in 2..5; same CSR input and errors as hd_encode.
+ * hd_build_library_multibit sorts and copies such rows like hd_build_library
+ * (d_comp [n_refs][D] int8, 16-byte aligned, components in [-m, m]; rows out
+ * of range fail with HD_ERR_INVALID_ARG) and prepares the tensor-core copy
+ * HD_FORM_TC_FP4 (bits <= 3: every |h| <= 3 is exact in e2m1) or
+ * HD_FORM_TC_FP8 (e4m3 holds the integers up to 16 exactly);
+ * hd_library_prepare adds HD_FORM_TC_FP8 or HD_FORM_TC_BF16 (and
+ * HD_FORM_TC_FP4 for bits <= 3).  Every partial sum is an integer of size at
+ * most D m^2 < 2^24, so the fp32 accumulation is exact.  Such a library is
+ * searched only with hd_search_dot; the binary entry points (hd_search_*,
+ * cascade, plan, server, autotune, save, export) reject it with
+ * HD_ERR_INVALID_ARG, and HD_FORM_POPC does not apply.
+ * hd_search_dot: windows as hd_search_open (Section 3.4); per query the k
+ * best candidates by S, higher first, the lower input index on a tie; d_q_comp
+ * [n_q][D] int8 (16-byte aligned, components in [-m, m]; others flag
+ * HD_ERR_INVALID_ARG on the library's status), d_out_idx / d_out_score
+ * [n_q][k]; missing slots hold 0xFFFFFFFF / INT32_MIN.  Asynchronous. */
+HD_API hd_status hd_encode_multibit(hd_ctx *ctx, const uint32_t *d_offsets, const uint32_t *d_bins,
+                                    const uint8_t *d_levels, uint32_t n_spectra, uint32_t bits, int8_t *d_out,
+                                    hd_stream stream);
+HD_API hd_status hd_build_library_multibit(hd_ctx *ctx, const int8_t *d_comp, const double *d_prec_mz,
+                                           const uint8_t *d_charge, uint32_t n_refs, uint32_t bits,
+                                           hd_library **out);
+/* Component bits of a library: 1 for binary HVs. */
+HD_API hd_status hd_library_component_bits(const hd_library *lib, uint32_t *bits);
+HD_API hd_status hd_search_dot(const hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
+                               const uint8_t *d_q_charge, uint32_t n_q, double tol, hd_tol_unit unit, uint32_t k,
+                               hd_search_form form, uint32_t *d_out_idx, int32_t *d_out_score, hd_stream stream);
+
 /* Failure-detection hooks (no counterpart in the paper).  Every device wait
  * of a search (stage loads, tensor-core commits, merge locks) gives up after
  * a bounded time, records HD_ERR_TIMEOUT in the library's status word and

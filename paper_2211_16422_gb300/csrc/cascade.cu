@@ -179,6 +179,7 @@ hd_status hd_cascade_search(const hd_library *lib, const uint64_t *d_q_hv, const
                             double *d_out_q, uint8_t *d_out_level, hd_stream stream)
 {
     if (!lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_cascade_search: null library");
+    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_cascade_search: multi-bit library (binary HVs only)");
     if (n_q == 0) return HD_OK;
     if (!d_q_hv || !d_q_mz || !d_q_charge || !d_out_idx || !d_out_dist || !d_out_q || !d_out_level)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_cascade_search: null buffer");

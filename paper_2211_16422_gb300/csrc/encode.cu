@@ -1,5 +1,6 @@
 // encode.cu -- spectrum vectors -> binary hypervectors (Section 3.3, Eq. 1;
-// the random-projection baseline of Section 4.2 as a second encoder).
+// the random-projection baseline of Section 4.2 as a second encoder), and
+// multi-bit components (Section 4.3).
 //
 // out_d = [2 c_d >= n], with c_d the number of peaks whose bound bit
 // F_bin XOR L_level is 1 at d (Eq. 1's bipolar sum is n - 2 c_d and the
@@ -126,7 +127,94 @@ k_encode_projection(const uint64_t *__restrict__ F, uint32_t n_bins, uint32_t n_
     if (any_bad) hd_flag(status, HD_DEV_BAD_INPUT);
 }
 
+// Multi-bit components (Section 4.3 reading): h_d = sign(I_d) *
+// floor((2 m |I_d| + M) / (2 M)), M = max_d |I_d|, h = 0 when M = 0, with
+// I_d = sum over peaks of w (1 - 2 x_d): x = F_bin XOR L_level and w = 1
+// (Eq. 1), or x = F_bin and w = level + 1 (projection).  One warp per
+// spectrum and two passes over its peaks: the first finds M, the second
+// recomputes each 64-bit word's sums and writes them quantised, component d
+// at byte d of the row.
+template <bool PROJ>
+__device__ __forceinline__ bool word_sums(const uint64_t *__restrict__ F, uint32_t n_bins,
+                                          const uint64_t *__restrict__ L, uint32_t n_levels, uint32_t W,
+                                          const uint32_t *__restrict__ bins, const uint8_t *__restrict__ levels,
+                                          uint32_t beg, uint32_t end, uint32_t w, int32_t (&acc)[64])
+{
+    bool bad = false;
+#pragma unroll
+    for (int b = 0; b < 64; ++b) acc[b] = 0;
+    for (uint32_t p = beg; p < end; ++p) {
+        const uint32_t bn = __ldg(bins + p), l = __ldg(levels + p);
+        if (bn >= n_bins || l >= n_levels) {
+            bad = true;
+            continue;
+        }
+        const uint64_t x = PROJ ? __ldg(F + (size_t)bn * W + w) : (__ldg(F + (size_t)bn * W + w) ^ __ldg(L + (size_t)l * W + w));
+        const int32_t wt = PROJ ? (int32_t)l + 1 : 1;
+#pragma unroll
+        for (int b = 0; b < 64; ++b) acc[b] += ((x >> b) & 1ull) ? -wt : wt;
+    }
+    return bad;
+}
+
+template <bool PROJ>
+__global__ void __launch_bounds__(ENC_WARPS * 32)
+k_encode_mb(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__restrict__ L, uint32_t n_levels,
+            uint32_t W, const uint32_t *__restrict__ off, const uint32_t *__restrict__ bins,
+            const uint8_t *__restrict__ levels, uint32_t n_spec, uint32_t m, int8_t *__restrict__ out,
+            uint32_t *status)
+{
+    const uint32_t sp = blockIdx.x * ENC_WARPS + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31;
+    if (sp >= n_spec) return;
+    uint32_t beg = off[sp], end = off[sp + 1];
+    if (end < beg || end - beg > ENC_MAX_PEAKS) {
+        if (lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
+        end = beg;   // encode as an empty row
+    }
+    bool bad = false;
+    int32_t acc[64];
+    uint32_t M = 0;
+    for (uint32_t w = lane; w < W; w += 32) {
+        bad |= word_sums<PROJ>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w, acc);
+#pragma unroll
+        for (int b = 0; b < 64; ++b) M = max(M, (uint32_t)abs(acc[b]));
+    }
+    M = __reduce_max_sync(0xFFFFFFFFu, M);
+    for (uint32_t w = lane; w < W; w += 32) {
+        word_sums<PROJ>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w, acc);
+        uint32_t p[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) p[i] = 0;
+#pragma unroll
+        for (int b = 0; b < 64; ++b) {
+            const uint32_t a = (uint32_t)abs(acc[b]);
+            const int32_t h = M ? (int32_t)((2u * m * a + M) / (2u * M)) : 0;
+            p[b >> 2] |= (uint32_t)(uint8_t)(int8_t)(acc[b] < 0 ? -h : h) << (8 * (b & 3));
+        }
+        uint4 *o = reinterpret_cast<uint4 *>(out + (size_t)sp * W * 64 + (size_t)w * 64);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_uint4(p[4 * i], p[4 * i + 1], p[4 * i + 2], p[4 * i + 3]);
+    }
+    if (bad) hd_flag(status, HD_DEV_BAD_INPUT);
+}
+
 }  // namespace
+
+void hd_encode_mb_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins, const uint8_t *levels,
+                         uint32_t n, uint32_t bits, int8_t *out, cudaStream_t s)
+{
+    const unsigned grid = hd_ceil_div(n, ENC_WARPS);
+    uint32_t *st = ctx->status.dev;
+    const uint32_t m = hd_comp_max(bits);
+    hd_prof_scope timed(HD_KERNEL_ENCODE, s);
+    if (ctx->p.encoder == HD_ENC_PROJECTION)
+        hd_count_launches(1), k_encode_mb<true><<<grid, ENC_WARPS * 32, 0, s>>>(
+            ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
+    else
+        hd_count_launches(1), k_encode_mb<false><<<grid, ENC_WARPS * 32, 0, s>>>(
+            ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
+}
 
 void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins,
                       const uint8_t *levels, uint32_t n, uint64_t *out, cudaStream_t s)

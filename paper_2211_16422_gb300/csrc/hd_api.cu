@@ -123,6 +123,7 @@ void lib_release(hd_library *lib)
     cudaFree(lib->x_bf16);
     cudaFree(lib->x_fp4);
     cudaFree(lib->decoy);
+    cudaFree(lib->comp);
     status_free(lib->status);
     delete lib;
 }
@@ -168,6 +169,7 @@ hd_status hd_search_dispatch(const hd_library *lib, const uint64_t *q_hv, const 
                              uint32_t n_q, const hd_qwin &win, uint32_t k, hd_search_form form, uint32_t *out_idx,
                              uint16_t *out_dist, cudaStream_t s)
 {
+    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "multi-bit library: search it with hd_search_dot");
     auto copy_of = [&](hd_search_form f) -> const uint8_t * {
         return f == HD_FORM_TC_FP8 ? lib->x_fp8 : (f == HD_FORM_TC_BF16 ? lib->x_bf16 : lib->x_fp4);
     };
@@ -193,6 +195,80 @@ bool hd_take_injected_stall(const hd_library *lib)
             return true;
     return false;
 }
+
+namespace {
+
+// Shared by the binary and multi-bit builds: sorts the references by (charge,
+// precursor m/z, input index) and gathers `row_words` 64-bit words of each row
+// (binary HVs: D/64; int8 components: D/8) into the library's sorted rows.
+hd_status build_rows(hd_ctx *ctx, const uint64_t *d_rows, uint32_t bits, const double *d_prec_mz,
+                     const uint8_t *d_charge, uint32_t n_refs, hd_library **out, const char *fn)
+{
+    hd_library *lib = new hd_library;
+    lib->n = n_refs;
+    lib->dim = ctx->p.dim;
+    lib->W = ctx->W;
+    lib->bits = bits;
+    lib->device = ctx->device;
+    lib->num_sms = ctx->num_sms;
+    auto fail = [&](hd_status s) {
+        lib_release(lib);
+        return s;
+    };
+    const size_t n1 = n_refs ? n_refs : 1;
+    const uint32_t row_words = bits == 1 ? lib->W : lib->dim / 8;
+    uint64_t *rows = nullptr;
+    if (cudaMalloc(&rows, n1 * row_words * 8) != cudaSuccess || cudaMalloc(&lib->mz, n1 * 8) != cudaSuccess ||
+        cudaMalloc(&lib->charge, n1) != cudaSuccess || cudaMalloc(&lib->orig, n1 * 4) != cudaSuccess ||
+        cudaMalloc(&lib->charge_start, 257 * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(rows);
+        return fail(hd_fail(HD_ERR_OOM, std::string(fn) + ": allocation failed"));
+    }
+    if (bits == 1) lib->hv = rows;
+    else lib->comp = reinterpret_cast<int8_t *>(rows);
+    hd_status st = status_alloc(lib->status);
+    if (st != HD_OK) return fail(st);
+    scoped_stream ss;
+    if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(hd_fail(HD_ERR_CUDA, std::string(fn) + ": stream creation failed"));
+    if (n_refs > 0) {
+        hd_arena plan;
+        uint32_t *perm = plan.take<uint32_t>(n_refs);
+        hd_sort_charge_mz(d_prec_mz, d_charge, nullptr, n_refs, nullptr, plan, ss.s);
+        hd_arena ar;
+        if (cudaMallocAsync((void **)&ar.base, plan.used, ss.s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(hd_fail(HD_ERR_OOM, std::string(fn) + ": scratch allocation failed"));
+        }
+        perm = ar.take<uint32_t>(n_refs);
+        hd_sort_charge_mz(d_prec_mz, d_charge, nullptr, n_refs, perm, ar, ss.s);
+        hd_count_launches(1), k_gather_rows<<<hd_ceil_div(n_refs, 8), 256, 0, ss.s>>>(d_rows, d_prec_mz, d_charge, perm, n_refs,
+                                                                row_words, rows, lib->mz, lib->charge,
+                                                                lib->orig, lib->status.dev);
+        cudaFreeAsync(ar.base, ss.s);
+    }
+    hd_count_launches(1), k_charge_start<<<1, 288, 0, ss.s>>>(lib->charge, n_refs, lib->charge_start);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lib->charge_start_h, lib->charge_start, 257 * 4,
+                                              cudaMemcpyDeviceToHost, ss.s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ss.s);
+    if (e != cudaSuccess) return fail(hd_cuda_fail(e, fn));
+    st = status_take(lib->status, fn);
+    if (st != HD_OK) return fail(hd_fail(st, std::string(fn) + ": precursor m/z must be finite"));
+    if (bits > 1) {   // the default tensor-core copy; it also checks the component range
+        st = hd_library_expand(lib, bits <= 3 ? HD_FORM_TC_FP4 : HD_FORM_TC_FP8, ss.s);
+        if (st != HD_OK) return fail(st);
+        e = cudaStreamSynchronize(ss.s);
+        if (e != cudaSuccess) return fail(hd_cuda_fail(e, fn));
+        st = status_take(lib->status, fn);
+        if (st != HD_OK) return fail(hd_fail(st, std::string(fn) + ": components must lie in [-m, m]"));
+    }
+    *out = lib;
+    return HD_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -318,6 +394,7 @@ hd_status hd_encode(hd_ctx *ctx, const uint32_t *d_offsets, const uint32_t *d_bi
     return HD_OK;
 }
 
+
 hd_status hd_build_library(hd_ctx *ctx, const uint64_t *d_hv, const double *d_prec_mz,
                            const uint8_t *d_charge, uint32_t n_refs, hd_library **out)
 {
@@ -326,54 +403,68 @@ hd_status hd_build_library(hd_ctx *ctx, const uint64_t *d_hv, const double *d_pr
     HD_CHECK(n_refs == 0 || (d_hv && d_prec_mz && d_charge), "hd_build_library: null buffer");
     hd_status st = check_device(ctx->device);
     if (st != HD_OK) return st;
-    hd_library *lib = new hd_library;
-    lib->n = n_refs;
-    lib->dim = ctx->p.dim;
-    lib->W = ctx->W;
-    lib->device = ctx->device;
-    lib->num_sms = ctx->num_sms;
-    auto fail = [&](hd_status s) {
-        lib_release(lib);
-        return s;
-    };
-    const size_t n1 = n_refs ? n_refs : 1;
-    if (cudaMalloc(&lib->hv, n1 * lib->W * 8) != cudaSuccess || cudaMalloc(&lib->mz, n1 * 8) != cudaSuccess ||
-        cudaMalloc(&lib->charge, n1) != cudaSuccess || cudaMalloc(&lib->orig, n1 * 4) != cudaSuccess ||
-        cudaMalloc(&lib->charge_start, 257 * 4) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(hd_fail(HD_ERR_OOM, "hd_build_library: allocation failed"));
-    }
-    st = status_alloc(lib->status);
-    if (st != HD_OK) return fail(st);
-    scoped_stream ss;
-    if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess)
-        return fail(hd_fail(HD_ERR_CUDA, "hd_build_library: stream creation failed"));
-    if (n_refs > 0) {
-        hd_arena plan;
-        uint32_t *perm = plan.take<uint32_t>(n_refs);
-        hd_sort_charge_mz(d_prec_mz, d_charge, nullptr, n_refs, nullptr, plan, ss.s);
-        hd_arena ar;
-        if (cudaMallocAsync((void **)&ar.base, plan.used, ss.s) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(hd_fail(HD_ERR_OOM, "hd_build_library: scratch allocation failed"));
-        }
-        perm = ar.take<uint32_t>(n_refs);
-        hd_sort_charge_mz(d_prec_mz, d_charge, nullptr, n_refs, perm, ar, ss.s);
-        hd_count_launches(1), k_gather_rows<<<hd_ceil_div(n_refs, 8), 256, 0, ss.s>>>(d_hv, d_prec_mz, d_charge, perm, n_refs,
-                                                                lib->W, lib->hv, lib->mz, lib->charge,
-                                                                lib->orig, lib->status.dev);
-        cudaFreeAsync(ar.base, ss.s);
-    }
-    hd_count_launches(1), k_charge_start<<<1, 288, 0, ss.s>>>(lib->charge, n_refs, lib->charge_start);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(lib->charge_start_h, lib->charge_start, 257 * 4,
-                                              cudaMemcpyDeviceToHost, ss.s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ss.s);
-    if (e != cudaSuccess) return fail(hd_cuda_fail(e, "hd_build_library"));
-    st = status_take(lib->status, "hd_build_library");
-    if (st != HD_OK) return fail(hd_fail(st, "hd_build_library: precursor m/z must be finite"));
-    *out = lib;
+    return build_rows(ctx, d_hv, 1, d_prec_mz, d_charge, n_refs, out, "hd_build_library");
+}
+
+hd_status hd_encode_multibit(hd_ctx *ctx, const uint32_t *d_offsets, const uint32_t *d_bins,
+                             const uint8_t *d_levels, uint32_t n_spectra, uint32_t bits, int8_t *d_out,
+                             hd_stream stream)
+{
+    HD_CHECK(ctx, "hd_encode_multibit: null ctx");
+    HD_CHECK(bits >= 2 && bits <= 5, "hd_encode_multibit: bits must be in [2, 5]");
+    if (n_spectra == 0) return HD_OK;
+    HD_CHECK(d_offsets && d_bins && d_levels && d_out, "hd_encode_multibit: null buffer");
+    HD_CHECK(aligned16(d_out), "hd_encode_multibit: d_out must be 16-byte aligned");
+    hd_status st = check_device(ctx->device);
+    if (st != HD_OK) return st;
+    hd_encode_mb_launch(ctx, d_offsets, d_bins, d_levels, n_spectra, bits, d_out, (cudaStream_t)stream);
+    HD_CUDA_TRY(cudaGetLastError());
     return HD_OK;
+}
+
+hd_status hd_build_library_multibit(hd_ctx *ctx, const int8_t *d_comp, const double *d_prec_mz,
+                                    const uint8_t *d_charge, uint32_t n_refs, uint32_t bits, hd_library **out)
+{
+    HD_CHECK(ctx && out, "hd_build_library_multibit: null argument");
+    *out = nullptr;
+    HD_CHECK(bits >= 2 && bits <= 5, "hd_build_library_multibit: bits must be in [2, 5]");
+    HD_CHECK(n_refs == 0 || (d_comp && d_prec_mz && d_charge), "hd_build_library_multibit: null buffer");
+    HD_CHECK(aligned16(d_comp), "hd_build_library_multibit: d_comp must be 16-byte aligned");
+    hd_status st = check_device(ctx->device);
+    if (st != HD_OK) return st;
+    return build_rows(ctx, reinterpret_cast<const uint64_t *>(d_comp), bits, d_prec_mz, d_charge, n_refs, out,
+                      "hd_build_library_multibit");
+}
+
+hd_status hd_library_component_bits(const hd_library *lib, uint32_t *bits)
+{
+    HD_CHECK(lib && bits, "hd_library_component_bits: null argument");
+    *bits = lib->bits;
+    return HD_OK;
+}
+
+hd_status hd_search_dot(const hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
+                        const uint8_t *d_q_charge, uint32_t n_q, double tol, hd_tol_unit unit, uint32_t k,
+                        hd_search_form form, uint32_t *d_out_idx, int32_t *d_out_score, hd_stream stream)
+{
+    HD_CHECK(lib, "hd_search_dot: null library");
+    HD_CHECK(lib->bits > 1, "hd_search_dot: binary library (use hd_search_open)");
+    HD_CHECK(k >= 1 && k <= 16, "hd_search_dot: k must be in [1, 16]");
+    HD_CHECK(tol_ok(tol), "hd_search_dot: tol must be finite and >= 0");
+    HD_CHECK(unit_ok(unit), "hd_search_dot: bad unit");
+    HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_TC_FP4 || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
+             "hd_search_dot: form must be AUTO or a tensor-core form");
+    if (form == HD_FORM_AUTO)
+        form = lib->x_fp4 ? HD_FORM_TC_FP4 : (lib->x_fp8 ? HD_FORM_TC_FP8 : HD_FORM_TC_BF16);
+    const uint8_t *copy = form == HD_FORM_TC_FP8 ? lib->x_fp8 : (form == HD_FORM_TC_BF16 ? lib->x_bf16 : lib->x_fp4);
+    HD_CHECK(copy || lib->n == 0, "hd_search_dot: call hd_library_prepare for this form first");
+    if (n_q == 0) return HD_OK;
+    HD_CHECK(d_q_comp && d_q_mz && d_q_charge && d_out_idx && d_out_score, "hd_search_dot: null buffer");
+    HD_CHECK(aligned16(d_q_comp), "hd_search_dot: d_q_comp must be 16-byte aligned");
+    hd_status st = check_device(lib->device);
+    if (st != HD_OK) return st;
+    return hd_search_mma_dot_run(lib, form, d_q_comp, d_q_mz, d_q_charge, n_q, hd_single_window(tol, unit), k,
+                                 d_out_idx, d_out_score, (cudaStream_t)stream);
 }
 
 void hd_library_free(hd_library *lib) { lib_release(lib); }
@@ -390,6 +481,7 @@ hd_status hd_library_export(const hd_library *lib, uint64_t *d_hv, double *d_mz,
                             uint32_t *d_orig, hd_stream stream)
 {
     HD_CHECK(lib, "hd_library_export: null library");
+    HD_CHECK(hd_lib_binary(lib), "hd_library_export: multi-bit library (binary HVs only)");
     hd_status st = check_device(lib->device);
     if (st != HD_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -436,6 +528,7 @@ struct file_closer {
 hd_status hd_library_save(const hd_library *lib, const hd_ctx *ctx, const char *path)
 {
     HD_CHECK(lib && ctx && path, "hd_library_save: null argument");
+    HD_CHECK(hd_lib_binary(lib), "hd_library_save: multi-bit library (binary HVs only)");
     HD_CHECK(ctx->p.dim == lib->dim, "hd_library_save: ctx and library dims differ");
     hd_status st = check_device(lib->device);
     if (st != HD_OK) return st;
@@ -578,6 +671,7 @@ hd_status hd_library_prepare(hd_library *lib, hd_search_form form)
     HD_CHECK(lib, "hd_library_prepare: null library");
     HD_CHECK(form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16 || form == HD_FORM_TC_FP4,
              "hd_library_prepare: unknown form");
+    HD_CHECK(form != HD_FORM_POPC || hd_lib_binary(lib), "hd_library_prepare: popc scores binary HVs only");
     hd_status st = check_device(lib->device);
     if (st != HD_OK || form == HD_FORM_POPC) return st;
     scoped_stream ss;

@@ -76,6 +76,8 @@ struct hd_library {
     uint8_t *x_bf16 = nullptr;     // [n][2D] bipolar bf16 rows (tensor-core form), optional
     uint8_t *x_fp4 = nullptr;      // [n][D/2] bipolar e2m1 rows, two per byte (tensor-core form), optional
     uint8_t *decoy = nullptr;      // [n] decoy flags, input order, optional
+    uint32_t bits = 1;             // component bits: 1 = binary rows in hv; 2..5 = int8 rows in comp
+    int8_t *comp = nullptr;        // [n][D] multi-bit components, sorted rows (bits > 1)
     hd_mma_tuning mma_tuning;
     hd_search_form auto_form = HD_FORM_AUTO;   // set by the autotuner
     uint64_t wait_ns = 0;                      // device wait limit (0: HD_WAIT_NS)
@@ -184,6 +186,17 @@ hd_status hd_library_expand(hd_library *lib, hd_search_form form, cudaStream_t s
 hd_status hd_search_mma_run(const hd_library *lib, hd_search_form form, const uint64_t *q_hv, const double *q_mz,
                             const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
                             uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);
+
+// Multi-bit components: encode, and the dot-product search on the tensor-core
+// forms (scores S = sum_d h_q,d h_r,d; keys (D m^2 - S, orig)).
+void hd_encode_mb_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins, const uint8_t *levels,
+                         uint32_t n, uint32_t bits, int8_t *out, cudaStream_t s);
+hd_status hd_search_mma_dot_run(const hd_library *lib, hd_search_form form, const int8_t *q_comp,
+                                const double *q_mz, const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win,
+                                uint32_t k, uint32_t *out_idx, int32_t *out_score, cudaStream_t s);
+inline uint32_t hd_comp_max(uint32_t bits) { return (1u << (bits - 1)) - 1u; }
+// Entry points that score binary HVs refuse a multi-bit library.
+inline bool hd_lib_binary(const hd_library *lib) { return lib->bits == 1; }
 
 // Search dispatch shared by the entry points: resolves HD_FORM_AUTO and runs
 // the chosen form.

@@ -45,6 +45,7 @@ hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_o
     if (!out) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null output");
     *out = nullptr;
     if (!ctx || !lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null ctx or library");
+    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: multi-bit library (binary HVs only)");
     if (ctx->p.dim != lib->dim) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: ctx and library dims differ");
     if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: k must be in [1, 16]");
     if (n_q == 0) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: empty query set");
@@ -125,6 +126,7 @@ hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const dou
                               hd_tune_result *all, uint32_t cap, uint32_t *n_all)
 {
     if (!lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: null library");
+    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: multi-bit library (binary HVs only)");
     if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: k must be in [1, 16]");
     if (n_q == 0 || !d_q_hv || !d_q_mz || !d_q_charge)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune: empty or null query set");

@@ -229,6 +229,9 @@ struct mma_args {
     uint32_t n_q, n_blocks, n_pairs, tg, sg, dim, row_bytes;
     uint64_t wait_ns;      // bound of every device wait
     uint32_t stall;        // test hook: drop the first stage load
+    // key distance (bias - S) >> shift of a score S: binary rows (D - S) / 2,
+    // the Hamming distance; multi-bit rows D m^2 - S
+    uint32_t bias, shift;
 };
 
 // Work item -> (query block, absolute tile range [t0, t1)).  Items are
@@ -401,7 +404,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                     for (int e = 0; e < 32; ++e) {
                         const uint32_t r = r0 + cg * 32 + e;
                         const int s = __float2int_rn(__uint_as_float(v[e]));
-                        const uint32_t d = (uint32_t)((int)a.dim - s) >> 1;
+                        const uint32_t d = (uint32_t)((int)a.bias - s) >> a.shift;
                         if (r - lo < span && d <= thr) {
                             const uint64_t key = ((uint64_t)d << 32) | __ldg(a.lib_orig + r);
                             if (key < best[K - 1]) topk_insert<K>(best, key);
@@ -774,7 +777,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                     for (int e = 0; e < 32; ++e) {
                         const uint32_t r = r0 + cg * 32 + e;
                         const int s = __float2int_rn(__uint_as_float(v[e]));
-                        const uint32_t d = (uint32_t)((int)a.dim - s) >> 1;
+                        const uint32_t d = (uint32_t)((int)a.bias - s) >> a.shift;
                         if (r - lo < span && d <= thr) {
                             const uint64_t key = ((uint64_t)d << 32) | __ldg(a.lib_orig + r);
                             if (key < best[K - 1]) topk_insert<K>(best, key);
@@ -892,6 +895,97 @@ __global__ void k_emit(const uint64_t *__restrict__ top, const uint32_t *__restr
     }
 }
 
+// Multi-bit form: scores S = bias - key distance, in the caller's order.
+template <int K>
+__global__ void k_emit_score(const uint64_t *__restrict__ top, const uint32_t *__restrict__ perm, uint32_t n_q,
+                             uint32_t k, uint32_t bias, uint32_t *__restrict__ out_idx,
+                             int32_t *__restrict__ out_score)
+{
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_q) return;
+    const uint32_t q = perm[s];
+    for (uint32_t t = 0; t < k; ++t) {
+        const uint64_t key = top[(size_t)s * K + t];
+        const bool none = key == KEY_NONE;
+        out_idx[(size_t)q * k + t] = none ? 0xFFFFFFFFu : (uint32_t)key;
+        out_score[(size_t)q * k + t] = none ? INT32_MIN : (int32_t)((int64_t)bias - (int64_t)(key >> 32));
+    }
+}
+
+__global__ void k_fill_none(uint32_t *__restrict__ out_idx, int32_t *__restrict__ out_score, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        out_idx[i] = 0xFFFFFFFFu;
+        out_score[i] = INT32_MIN;
+    }
+}
+
+// Operand codes of small integers, from the IEEE single bits of the value:
+// an integer of at most four significant bits (|v| <= 15) is exact in e4m3
+// (sign, 4-bit exponent of bias 7, top 3 mantissa bits), |v| <= 3 in e2m1
+// (sign, 2-bit exponent of bias 1, top mantissa bit), and bf16 is the
+// single's upper half.
+__device__ __forceinline__ uint32_t int_to_e4m3(int v)
+{
+    if (v == 0) return 0u;
+    const uint32_t f = __float_as_uint((float)v);
+    return ((f >> 31) << 7) | ((((f >> 23) & 0xFFu) - 120u) << 3) | ((f >> 20) & 7u);
+}
+__device__ __forceinline__ uint32_t int_to_e2m1(int v)
+{
+    if (v == 0) return 0u;
+    const uint32_t f = __float_as_uint((float)v);
+    return ((f >> 31) << 3) | ((((f >> 23) & 0xFFu) - 126u) << 1) | ((f >> 22) & 1u);
+}
+__device__ __forceinline__ uint32_t int_to_bf16(int v) { return __float_as_uint((float)v) >> 16; }
+
+// One row of int8 components in [-m, m] per warp -> the operand format (e4m3
+// bytes, bf16 halves, or e2m1 nibbles with element 2i in the low nibble of
+// byte i).  A component outside [-m, m] is written as 0 and flags the
+// status word.  `perm` (optional) picks the source row of output row r.
+template <int FMT>
+__global__ void k_expand_comp(const int8_t *__restrict__ comp, const uint32_t *__restrict__ perm, uint32_t n,
+                              uint32_t D, int m, uint8_t *__restrict__ out, uint32_t *status)
+{
+    const uint32_t r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const uint32_t lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int8_t *src = comp + (size_t)(perm ? perm[r] : r) * D;
+    bool bad = false;
+    for (uint32_t c = lane; c < D / 16; c += 32) {
+        const uint4 in = *reinterpret_cast<const uint4 *>(src + (size_t)c * 16);
+        const uint32_t wv[4] = {in.x, in.y, in.z, in.w};
+        int v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            v[i] = (int)(int8_t)(uint8_t)(wv[i >> 2] >> (8 * (i & 3)));
+            if (v[i] < -m || v[i] > m) {
+                bad = true;
+                v[i] = 0;
+            }
+        }
+        if (FMT == FMT_E4M3) {
+            uint32_t p[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int i = 0; i < 16; ++i) p[i >> 2] |= int_to_e4m3(v[i]) << (8 * (i & 3));
+            *reinterpret_cast<uint4 *>(out + (size_t)r * D + (size_t)c * 16) = make_uint4(p[0], p[1], p[2], p[3]);
+        } else if (FMT == FMT_BF16) {
+            uint32_t p[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) p[i] = int_to_bf16(v[2 * i]) | (int_to_bf16(v[2 * i + 1]) << 16);
+            uint4 *o = reinterpret_cast<uint4 *>(out + (size_t)r * 2 * D + (size_t)c * 32);
+            o[0] = make_uint4(p[0], p[1], p[2], p[3]);
+            o[1] = make_uint4(p[4], p[5], p[6], p[7]);
+        } else {
+            uint32_t p[2] = {0, 0};
+#pragma unroll
+            for (int i = 0; i < 16; ++i) p[i >> 3] |= int_to_e2m1(v[i]) << (4 * (i & 7));
+            *reinterpret_cast<uint2 *>(out + (size_t)r * (D / 2) + (size_t)c * 8) = make_uint2(p[0], p[1]);
+        }
+    }
+    if (bad) hd_flag(status, HD_DEV_BAD_INPUT);
+}
+
 // One row of packed bits per warp -> +-1 in the operand format: bytes (e4m3:
 // 0x38 / 0xB8), halves (bf16: 0x3F80 / 0xBF80) or nibbles (e2m1: 0x2 / 0xA,
 // element 2i in the low nibble of byte i).
@@ -993,13 +1087,19 @@ hd_status make_map_e2m1(CUtensorMap *m, const void *base, uint64_t rows, uint32_
     return HD_OK;
 }
 
+// Multi-bit search I/O: int8 query components in, scores out.
+struct dot_io {
+    const int8_t *q_comp;
+    int32_t *out_score;
+};
+
 template <int FMT>
 constexpr uint32_t global_row_bytes(uint32_t dim) { return FMT == FMT_BF16 ? 2 * dim : (FMT == FMT_E4M3 ? dim : dim / 2); }
 
 template <int K, int FMT>
 hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
                   uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
-                  cudaStream_t s, const hd_mma_tuning &tune)
+                  cudaStream_t s, const hd_mma_tuning &tune, const dot_io *dot = nullptr)
 {
     const bool pair = tune.cta_group == 2;   // SM pairs, M = 256 (cluster of 2)
     const uint32_t cs = pair ? 2u : tune.cluster;   // 1, 2 or 4 CTAs per cluster
@@ -1076,12 +1176,19 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     HD_CUDA_TRY(cudaMemsetAsync(top, 0xFF, (size_t)n_q * K * sizeof(uint64_t), s));
     HD_CUDA_TRY(cudaMemsetAsync(locks, 0, (size_t)n_blocks * cs * sizeof(uint32_t), s));
     hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, perm, ar, s);
-    hd_count_launches(1), k_expand<FMT><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
+    if (dot)
+        hd_count_launches(1), k_expand_comp<FMT><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(
+            dot->q_comp, perm, n_q, lib->dim, (int)hd_comp_max(lib->bits), qx, lib->status.dev);
+    else
+        hd_count_launches(1), k_expand<FMT><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
+    const uint32_t mq = hd_comp_max(lib->bits);
+    const uint32_t bias = dot ? lib->dim * mq * mq : lib->dim, shift = dot ? 0u : 1u;
     hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z,
                                                                           perm, n_q, win, lo, hi);
     hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, TM * cs, n_blocks, tg, sg, n_super, bt0, bt1, pst);
     mma_args ma{lib->orig, lo, hi, bt0, bt1, pst, top, locks, lib->status.dev, n_q, n_blocks, (uint32_t)n_pairs,
-                tg, sg, lib->dim, row_bytes, hd_wait_limit(lib), hd_take_injected_stall(lib) ? 1u : 0u};
+                tg, sg, lib->dim, row_bytes, hd_wait_limit(lib), hd_take_injected_stall(lib) ? 1u : 0u,
+                bias, shift};
     {
         hd_prof_scope timed(HD_KERNEL_SEARCH, s);
         cudaLaunchConfig_t cfg = {};
@@ -1099,7 +1206,11 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
         hd_count_launches(1);
         HD_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, qmap, lmap, ma));
     }
-    hd_count_launches(1), k_emit<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(top, perm, n_q, k, out_idx, out_dist);
+    if (dot)
+        hd_count_launches(1), k_emit_score<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(top, perm, n_q, k, bias, out_idx,
+                                                                                 dot->out_score);
+    else
+        hd_count_launches(1), k_emit<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(top, perm, n_q, k, out_idx, out_dist);
     HD_CUDA_TRY(cudaGetLastError());
     HD_CUDA_TRY(cudaFreeAsync(ar.base, s));
     return HD_OK;
@@ -1108,13 +1219,13 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
 template <int FMT>
 hd_status run_fmt(const hd_library *lib, const uint64_t *q_hv, const double *q_mz, const uint8_t *q_z,
                   uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *oi, uint16_t *od, cudaStream_t s,
-                  const hd_mma_tuning &tu)
+                  const hd_mma_tuning &tu, const dot_io *dot = nullptr)
 {
-    if (k <= 1) return run_mma<1, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
-    if (k <= 2) return run_mma<2, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
-    if (k <= 4) return run_mma<4, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
-    if (k <= 8) return run_mma<8, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
-    return run_mma<16, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu);
+    if (k <= 1) return run_mma<1, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu, dot);
+    if (k <= 2) return run_mma<2, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu, dot);
+    if (k <= 4) return run_mma<4, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu, dot);
+    if (k <= 8) return run_mma<8, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu, dot);
+    return run_mma<16, FMT>(lib, q_hv, q_mz, q_z, n_q, win, k, oi, od, s, tu, dot);
 }
 
 }  // namespace
@@ -1129,6 +1240,8 @@ int form_fmt(hd_search_form form)
 hd_status hd_library_expand(hd_library *lib, hd_search_form form, cudaStream_t s)
 {
     const int fmt = form_fmt(form);
+    if (fmt == FMT_E2M1 && lib->bits > 3)
+        return hd_fail(HD_ERR_UNSUPPORTED, "e2m1 holds components up to 3 only (bits <= 3)");
     uint8_t *&dst = fmt == FMT_BF16 ? lib->x_bf16 : (fmt == FMT_E4M3 ? lib->x_fp8 : lib->x_fp4);
     if (dst || lib->n == 0) return HD_OK;
     const size_t bytes = (size_t)lib->n * (fmt == FMT_BF16 ? global_row_bytes<FMT_BF16>(lib->dim)
@@ -1140,7 +1253,18 @@ hd_status hd_library_expand(hd_library *lib, hd_search_form form, cudaStream_t s
         return hd_fail(HD_ERR_OOM, "expanded library allocation failed");
     }
     const unsigned g = hd_ceil_div(lib->n, 8);
-    if (fmt == FMT_E4M3)
+    if (lib->bits > 1) {   // multi-bit components; range violations flag the library's status
+        const int m = (int)hd_comp_max(lib->bits);
+        if (fmt == FMT_E4M3)
+            hd_count_launches(1), k_expand_comp<FMT_E4M3><<<g, 256, 0, s>>>(lib->comp, nullptr, lib->n, lib->dim, m,
+                                                                           dst, lib->status.dev);
+        else if (fmt == FMT_BF16)
+            hd_count_launches(1), k_expand_comp<FMT_BF16><<<g, 256, 0, s>>>(lib->comp, nullptr, lib->n, lib->dim, m,
+                                                                           dst, lib->status.dev);
+        else
+            hd_count_launches(1), k_expand_comp<FMT_E2M1><<<g, 256, 0, s>>>(lib->comp, nullptr, lib->n, lib->dim, m,
+                                                                           dst, lib->status.dev);
+    } else if (fmt == FMT_E4M3)
         hd_count_launches(1), k_expand<FMT_E4M3><<<g, 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
     else if (fmt == FMT_BF16)
         hd_count_launches(1), k_expand<FMT_BF16><<<g, 256, 0, s>>>(lib->hv, nullptr, lib->n, lib->W, dst);
@@ -1164,4 +1288,26 @@ hd_status hd_search_mma_run(const hd_library *lib, hd_search_form form, const ui
     if (fmt == FMT_E4M3) return run_fmt<FMT_E4M3>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
     if (fmt == FMT_BF16) return run_fmt<FMT_BF16>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
     return run_fmt<FMT_E2M1>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
+}
+
+hd_status hd_search_mma_dot_run(const hd_library *lib, hd_search_form form, const int8_t *q_comp,
+                                const double *q_mz, const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win,
+                                uint32_t k, uint32_t *out_idx, int32_t *out_score, cudaStream_t s)
+{
+    if (lib->n == 0) {   // no candidates anywhere
+        hd_count_launches(1), k_fill_none<<<hd_ceil_div((size_t)n_q * k, 256), 256, 0, s>>>(out_idx, out_score,
+                                                                                          (size_t)n_q * k);
+        HD_CUDA_TRY(cudaGetLastError());
+        return HD_OK;
+    }
+    hd_mma_tuning tu = lib->mma_tuning;
+    if (tu.tile_group == 0) tu.tile_group = 16;
+    if (tu.super_group == 0) tu.super_group = 16;
+    if (tu.cluster != 1 && tu.cluster != 2 && tu.cluster != 4) tu.cluster = 2;
+    if (tu.cta_group == 0) tu.cta_group = tu.cluster == 2 ? 2u : 1u;
+    const dot_io io{q_comp, out_score};
+    const int fmt = form_fmt(form);
+    if (fmt == FMT_E4M3) return run_fmt<FMT_E4M3>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
+    if (fmt == FMT_BF16) return run_fmt<FMT_BF16>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
+    return run_fmt<FMT_E2M1>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
 }

@@ -61,6 +61,7 @@ extern "C" hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_
                                             hd_stream stream)
 {
     if (!lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: null library");
+    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: multi-bit library (binary HVs only)");
     if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: k must be in [1, 16]");
     if (!(tol >= 0.0) || tol > 1.7976931348623157e308)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: tol must be finite and >= 0");

@@ -283,6 +283,7 @@ hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_p
     if (!out) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: null output");
     *out = nullptr;
     if (!ctx || !lib || !params) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: null argument");
+    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: multi-bit library (binary HVs only)");
     if (ctx->p.dim != lib->dim) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: ctx and library dims differ");
     if (params->k < 1 || params->k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: k must be in [1, 16]");
     if (params->slots < 1 || params->slots > 64)

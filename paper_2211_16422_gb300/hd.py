@@ -106,6 +106,10 @@ _SIGS = {
     "hd_profile_enable": ([i32], i32),
     "hd_profile_collect": ([i32, P, P], i32),
     "hd_launch_count": ([], u64),
+    "hd_encode_multibit": ([P, P, P, P, u32, u32, P, P], i32),
+    "hd_build_library_multibit": ([P, P, P, P, u32, u32, P], i32),
+    "hd_library_component_bits": ([P, P], i32),
+    "hd_search_dot": ([P, P, P, P, u32, dbl, i32, u32, i32, P, P, P], i32),
 }
 HD_KERNEL_ENCODE, HD_KERNEL_SEARCH = 0, 1
 
@@ -273,6 +277,55 @@ def hd_build_library(ctx: Ctx, hv, prec_mz, charge) -> Library:
     h = C.c_void_p()
     _check(load().hd_build_library(ctx.handle, _ptr(hv), _ptr(prec_mz), _ptr(charge), n, C.byref(h)))
     return Library(h, n, ctx.dim)
+
+
+def hd_encode_multibit(ctx: Ctx, offsets, bins, levels, bits, out=None, stream=None):
+    """Multi-bit components [n, D] int8 in [-m, m], m = 2^(bits-1) - 1 (bits 2..5)."""
+    offsets = _dev(offsets, torch.int32, "offsets")
+    bins = _dev(bins, torch.int32, "bins")
+    levels = _dev(levels, torch.uint8, "levels")
+    n = offsets.numel() - 1
+    if out is None:
+        out = torch.empty((n, ctx.dim), dtype=torch.int8, device="cuda")
+    _check(load().hd_encode_multibit(ctx.handle, _ptr(offsets), _ptr(bins), _ptr(levels), n, int(bits), _ptr(out),
+                                     _stream(stream)))
+    return out
+
+
+def hd_build_library_multibit(ctx: Ctx, comp, prec_mz, charge, bits) -> Library:
+    """Library of multi-bit component rows (int8 [n, D]); prepares its default tensor-core copy."""
+    comp = _dev(comp, torch.int8, "comp")
+    prec_mz = _dev(prec_mz, torch.float64, "prec_mz")
+    charge = _dev(charge, torch.uint8, "charge")
+    n = prec_mz.numel()
+    torch.cuda.current_stream().synchronize()
+    h = C.c_void_p()
+    _check(load().hd_build_library_multibit(ctx.handle, _ptr(comp), _ptr(prec_mz), _ptr(charge), n, int(bits),
+                                            C.byref(h)))
+    return Library(h, n, ctx.dim)
+
+
+def hd_library_component_bits(lib: Library) -> int:
+    b = C.c_uint32()
+    _check(load().hd_library_component_bits(lib.handle, C.byref(b)))
+    return int(b.value)
+
+
+def hd_search_dot(lib: Library, q_comp, q_mz, q_charge, tol, unit="da", k=1, form="auto",
+                  out_idx=None, out_score=None, stream=None):
+    """Dot-product top-k over multi-bit components: (idx i32 [n_q, k], score i32 [n_q, k]);
+    padding idx -1 (0xFFFFFFFF) and score INT32_MIN."""
+    q_comp = _dev(q_comp, torch.int8, "q_comp")
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    n = q_mz.numel()
+    if out_idx is None:
+        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    if out_score is None:
+        out_score = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    _check(load().hd_search_dot(lib.handle, _ptr(q_comp), _ptr(q_mz), _ptr(q_charge), n, float(tol), _unit(unit),
+                                int(k), FORMS[form], _ptr(out_idx), _ptr(out_score), _stream(stream)))
+    return out_idx, out_score
 
 
 def hd_library_prepare(lib: Library, form: str):

@@ -1,0 +1,206 @@
+"""Multi-bit HV components (Section 4.3) on the GPU against the oracle:
+the encoder bit for bit (both encoders, bits 2..5, empty and long spectra),
+and the dot-product search through every tensor-core form and schedule,
+with exact indices and scores, on encoded spectra and on random components
+with ties and extreme scores; plus the boundary's argument checks."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_16422_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_16422_gb300 import build, hd as _hd
+    build.build()
+    return _hd
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    elif a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).cuda()
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def random_csr(rng, n, f, Q, lens):
+    off = np.zeros(n + 1, np.uint32)
+    off[1:] = np.cumsum(lens)
+    b = np.concatenate([np.sort(rng.choice(f, l, replace=False)) for l in lens]).astype(np.uint32) \
+        if sum(lens) else np.zeros(0, np.uint32)
+    lv = rng.integers(0, Q, int(off[-1])).astype(np.uint8)
+    return off, b, lv
+
+
+@pytest.mark.parametrize("D,Q,f,encoder", [(128, 4, 60, "id_level"), (2048, 16, 3000, "id_level"),
+                                           (8192, 32, synth.N_BINS, "id_level"), (1024, 64, 2000, "projection"),
+                                           (4096, 256, 5000, "projection")])
+def test_encode_multibit_bit_exact(hd, D, Q, f, encoder):
+    rng = np.random.default_rng(D + Q)
+    lens = [0, 1, 2, 3, 50, min(1023, f)] + list(rng.integers(0, 120, 90))
+    lens = [min(l, f) for l in lens]
+    off, b, lv = random_csr(rng, len(lens), f, Q, lens)
+    ctx = hd.Ctx(D, Q, f, D // 2, 3, encoder=encoder)
+    F, L, _, _ = oracle.item_memory(D, Q, f, D // 2, 3)
+    enc = 1 if encoder == "projection" else 0
+    for bits in (2, 3, 4, 5):
+        got = hd.hd_encode_multibit(ctx, dev(off), dev(b), dev(lv), bits)
+        torch.cuda.synchronize()
+        ctx.status()
+        want = oracle.encode_multibit(D, F, L, off, b, lv, bits, encoder=enc)
+        assert np.array_equal(got.cpu().numpy(), want), bits
+
+
+def windowed(rng, n_ref, n_q, lo=400.0, hi=460.0):
+    ref_mz = rng.uniform(lo, hi, n_ref)
+    ref_z = rng.integers(2, 4, n_ref).astype(np.uint8)
+    q_mz = rng.uniform(lo, hi, n_q)
+    q_z = rng.integers(2, 4, n_q).astype(np.uint8)
+    return ref_mz, ref_z, q_mz, q_z
+
+
+def check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, tol, unit, k, form):
+    gi, gs = hd.hd_search_dot(lib, dev(Qv), dev(q_mz), dev(q_z), tol, unit, k, form)
+    torch.cuda.synchronize()
+    lib.status()
+    oi, osc = oracle.search_dot(R, ref_mz, ref_z, Qv, q_mz, q_z, tol, unit, k)
+    assert np.array_equal(u32(gi), oi), (form, unit, k)
+    assert np.array_equal(gs.cpu().numpy(), osc), (form, unit, k)
+    return oi
+
+
+@pytest.mark.parametrize("bits", [2, 3, 4, 5])
+def test_search_dot_encoded_spectra(hd, bits):
+    """Encoded synthetic-style spectra: 3000 references (12 tiles, ragged), 700
+    queries, every applicable form, three window units, k 1 / 5 / 16."""
+    D, Q, f = 2048, 16, 4000
+    rng = np.random.default_rng(bits)
+    n_ref, n_q = 3000, 700
+    r_off, r_b, r_lv = random_csr(rng, n_ref, f, Q, list(rng.integers(1, 60, n_ref)))
+    q_off, q_b, q_lv = random_csr(rng, n_q, f, Q, list(rng.integers(0, 60, n_q)))
+    ctx = hd.Ctx(D, Q, f, D // 2, 9)
+    r_gpu = hd.hd_encode_multibit(ctx, dev(r_off), dev(r_b), dev(r_lv), bits)
+    q_gpu = hd.hd_encode_multibit(ctx, dev(q_off), dev(q_b), dev(q_lv), bits)
+    F, L, _, _ = oracle.item_memory(D, Q, f, D // 2, 9)
+    R = oracle.encode_multibit(D, F, L, r_off, r_b, r_lv, bits)
+    Qv = oracle.encode_multibit(D, F, L, q_off, q_b, q_lv, bits)
+    assert np.array_equal(r_gpu.cpu().numpy(), R) and np.array_equal(q_gpu.cpu().numpy(), Qv)
+    ref_mz, ref_z, q_mz, q_z = windowed(rng, n_ref, n_q)
+    lib = hd.hd_build_library_multibit(ctx, r_gpu, dev(ref_mz), dev(ref_z), bits)
+    assert hd.hd_library_component_bits(lib) == bits
+    forms = ["tc_fp8", "tc_bf16"] + (["tc_fp4"] if bits <= 3 else [])
+    for form in forms:
+        hd.hd_library_prepare(lib, form)
+    for form in forms:
+        for unit, tol, k in (("da", 6.0, 5), ("ppm", 9000.0, 1), ("mass", 15.0, 16)):
+            check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, tol, unit, k, form)
+    # 'auto' takes e2m1 when the library holds it, else e4m3
+    oi = check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, 6.0, "da", 5, "auto")
+    assert np.mean(oi[:, 0] != 0xFFFFFFFF) > 0.9
+
+
+@pytest.mark.parametrize("cluster,cta_group", [(2, 2), (1, 1), (4, 1), (2, 1)])
+@pytest.mark.parametrize("form,bits", [("tc_fp4", 3), ("tc_fp8", 4)])
+def test_search_dot_random_components_schedules(hd, form, bits, cluster, cta_group):
+    """Random components in [-m, m], duplicate rows (ties go to the lower input
+    index) and rows of all +m / all -m (scores D m^2 and -D m^2, the ends of
+    the key range), under the pair and 1-SM schedules."""
+    D, m = 1024, 2 ** (bits - 1) - 1
+    rng = np.random.default_rng(bits * 10 + cluster + cta_group)
+    n_ref, n_q = 2600, 450
+    R = rng.integers(-m, m + 1, (n_ref, D)).astype(np.int8)
+    Qv = rng.integers(-m, m + 1, (n_q, D)).astype(np.int8)
+    ref_mz, ref_z, q_mz, q_z = windowed(rng, n_ref, n_q, 400.0, 410.0)
+    for a, b_ in ((100, 5), (2000, 7), (611, 2599)):     # duplicate rows b_ of rows a
+        R[b_], ref_mz[b_], ref_z[b_] = R[a], ref_mz[a], ref_z[a]
+    R[10], R[11] = m, -m
+    ref_z[11], ref_mz[11] = ref_z[10], ref_mz[10]
+    Qv[0], q_mz[0], q_z[0] = m, ref_mz[10], ref_z[10]    # S = D m^2 with row 10, -D m^2 with row 11
+    Qv[1], q_mz[1], q_z[1] = R[100], ref_mz[100], ref_z[100]
+    ctx = hd.Ctx(D, 8, 100, D // 2, 1)
+    lib = hd.hd_build_library_multibit(ctx, dev(R), dev(ref_mz), dev(ref_z), bits)
+    hd.hd_library_prepare(lib, form)
+    hd.hd_library_set_schedule(lib, 4, 2, cluster, cta_group)
+    oi = check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, 1.5, "da", 16, form)
+    assert oi[0, 0] == 10 and oi[1, 0] == 5 and oi[1, 1] == 100
+    gi, gs = hd.hd_search_dot(lib, dev(Qv[:1]), dev(q_mz[:1]), dev(q_z[:1]), 0.0, "da", 16, form)
+    s = gs.cpu().numpy()[0]
+    assert s[0] == D * m * m and s[u32(gi)[0] == 11][0] == -D * m * m
+
+
+def test_search_dot_d8192_tiles_and_tail(hd):
+    """D = 8192 (64 K-chunks per tile), 100,003 references: many tiles and a
+    ragged last tile; 40 queries over wide windows checked in full."""
+    D, bits, m = 8192, 3, 3
+    rng = np.random.default_rng(77)
+    n_ref, n_q = 100003, 40
+    R = rng.integers(-m, m + 1, (n_ref, D), dtype=np.int8)
+    Qv = rng.integers(-m, m + 1, (n_q, D), dtype=np.int8)
+    ref_mz = rng.uniform(400, 1500, n_ref)
+    ref_z = rng.integers(2, 4, n_ref).astype(np.uint8)
+    q_mz = rng.uniform(400, 1500, n_q)
+    q_z = rng.integers(2, 4, n_q).astype(np.uint8)
+    ctx = hd.Ctx(D, 8, 100, D // 2, 1)
+    lib = hd.hd_build_library_multibit(ctx, dev(R), dev(ref_mz), dev(ref_z), bits)
+    for form in ("tc_fp4", "tc_fp8"):
+        hd.hd_library_prepare(lib, form)
+        check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, 500.0, "da", 5, form)
+
+
+def test_multibit_argument_checks(hd):
+    D = 256
+    rng = np.random.default_rng(0)
+    ctx = hd.Ctx(D, 8, 100, D // 2, 1)
+    R = rng.integers(-3, 4, (300, D)).astype(np.int8)
+    mz = rng.uniform(400, 401, 300)
+    z = np.full(300, 2, np.uint8)
+    with pytest.raises(hd.HDError):                    # bits out of range
+        hd.hd_build_library_multibit(ctx, dev(R), dev(mz), dev(z), 6)
+    bad = R.copy()
+    bad[17, 5] = 4                                     # |h| > m for bits 3
+    with pytest.raises(hd.HDError) as e:
+        hd.hd_build_library_multibit(ctx, dev(bad), dev(mz), dev(z), 3)
+    assert e.value.status == 1
+    lib = hd.hd_build_library_multibit(ctx, dev(R), dev(mz), dev(z), 3)
+    lib4 = hd.hd_build_library_multibit(ctx, dev(R), dev(mz), dev(z), 4)
+    with pytest.raises(hd.HDError) as e:               # e2m1 cannot hold 4..7
+        hd.hd_library_prepare(lib4, "tc_fp4")
+    assert e.value.status == 5
+    with pytest.raises(hd.HDError):                    # binary entry points refuse it
+        hd.hd_search_open(lib, torch.zeros((4, D // 64), dtype=torch.int64, device="cuda"),
+                          dev(mz[:4]), dev(z[:4]), 1.0, "da", 1)
+    with pytest.raises(hd.HDError):
+        hd.hd_library_prepare(lib, "popc")
+    binary = hd.hd_build_library(ctx, torch.zeros((300, D // 64), dtype=torch.int64, device="cuda"),
+                                 dev(mz), dev(z))
+    with pytest.raises(hd.HDError):                    # hd_search_dot refuses a binary library
+        hd.hd_search_dot(binary, dev(R[:4]), dev(mz[:4]), dev(z[:4]), 1.0, "da", 1)
+    with pytest.raises(hd.HDError):                    # not prepared for this form
+        hd.hd_search_dot(lib, dev(R[:4]), dev(mz[:4]), dev(z[:4]), 1.0, "da", 1, "tc_bf16")
+    # a query component out of range flags the library's status
+    q = R[:4].copy()
+    q[2, 9] = -5
+    hd.hd_search_dot(lib, dev(q), dev(mz[:4]), dev(z[:4]), 1.0, "da", 1, "tc_fp4")
+    torch.cuda.synchronize()
+    with pytest.raises(hd.HDError):
+        lib.status()
+    lib.status()                                       # the flag is consumed
+    # no queries, and an empty library: every slot padded
+    gi, gs = hd.hd_search_dot(lib, dev(R[:0]), dev(mz[:0]), dev(z[:0]), 1.0, "da", 3)
+    assert gi.shape == (0, 3)
+    empty = hd.hd_build_library_multibit(ctx, dev(R[:0]), dev(mz[:0]), dev(z[:0]), 3)
+    gi, gs = hd.hd_search_dot(empty, dev(R[:5]), dev(mz[:5]), dev(z[:5]), 1.0, "da", 3)
+    torch.cuda.synchronize()
+    assert np.all(u32(gi) == 0xFFFFFFFF) and np.all(gs.cpu().numpy() == np.iinfo(np.int32).min)
