@@ -49,10 +49,10 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
     #     --form <form> --schedule <tile_group,super_group,cluster,cta_group>
-    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 241.97e9 + 0.01489e9, "sha256": "373e9b9b6e7112da"},
-    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 245.13e9 + 0.02122e9, "sha256": "373e9b9b6e7112da"},
-    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 468.56e9 + 0.04449e9, "sha256": "373e9b9b6e7112da"},
-    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 458.08e9 + 0.06646e9, "sha256": "373e9b9b6e7112da"},
+    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 239.35e9 + 0.01444e9, "sha256": "6f3db4798d42cca9"},
+    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 245.77e9 + 0.02128e9, "sha256": "6f3db4798d42cca9"},
+    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 463.04e9 + 0.04653e9, "sha256": "6f3db4798d42cca9"},
+    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 454.55e9 + 0.05802e9, "sha256": "6f3db4798d42cca9"},
 }
 
 
@@ -85,8 +85,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=("full", "batched", "serving", "cascade"), default="full",
-                    help="full: the headline line; batched / serving / cascade: the extra workloads")
+    ap.add_argument("--workload", choices=("full", "batched", "serving", "cascade", "multibit"), default="full",
+                    help="full: the headline line; batched / serving / cascade / multibit: the extra workloads")
+    ap.add_argument("--bits", type=int, default=3, help="component bits of --workload multibit (2..5)")
     return ap.parse_args()
 
 
@@ -177,9 +178,10 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(refs, queries, spec, target_s, lib_fraction=0.05, seed=5):
+def cpu_oracle_rate(refs, queries, spec, target_s, lib_fraction=0.05, seed=5, bits=1):
     """The oracle's brute-force windowed top-k search on the host cores, on a
-    uniform library sample; returns (comparisons/s, threads, sample text, step fn)."""
+    uniform library sample; returns (comparisons/s, threads, sample text, step fn).
+    bits > 1: multi-bit components and the dot-product search."""
     import oracle
     rng = np.random.default_rng(seed)
     n_lib = max(1000, int(refs.n * lib_fraction))
@@ -187,18 +189,25 @@ def cpu_oracle_rate(refs, queries, spec, target_s, lib_fraction=0.05, seed=5):
     rsub = refs.subset(rsel)
     D, Q = spec["dim"], spec["n_levels"]
     F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, 0)
-    r_hv = oracle.encode(D, F, L, *oracle.preprocess(rsub.offsets, rsub.mz, rsub.intensity, **pp_args(spec)))
+    enc = ((lambda *csr: oracle.encode(D, F, L, *csr)) if bits == 1
+           else (lambda *csr: oracle.encode_multibit(D, F, L, *csr, bits)))
+    r_hv = enc(*oracle.preprocess(rsub.offsets, rsub.mz, rsub.intensity, **pp_args(spec)))
     threads = os.cpu_count() or 1
     q_all = queries.subset(np.arange(min(queries.n, 20000)))
-    q_hv = oracle.encode(D, F, L, *oracle.preprocess(q_all.offsets, q_all.mz, q_all.intensity, **pp_args(spec)))
+    q_hv = enc(*oracle.preprocess(q_all.offsets, q_all.mz, q_all.intensity, **pp_args(spec)))
     wc = oracle.window_count(rsub.precursor_mz, rsub.charge, q_all.precursor_mz, q_all.charge, spec["tol"],
                              spec["unit"]).astype(np.int64)
 
     def step(m, offset=0):
         which = (np.arange(m) + offset) % q_all.n
         t = time.perf_counter()
-        oracle.search(D, r_hv, rsub.precursor_mz, rsub.charge, q_hv, q_all.precursor_mz, q_all.charge,
-                      spec["tol"], spec["unit"], spec["k"], which=which.astype(np.uint32), n_threads=threads)
+        if bits == 1:
+            oracle.search(D, r_hv, rsub.precursor_mz, rsub.charge, q_hv, q_all.precursor_mz, q_all.charge,
+                          spec["tol"], spec["unit"], spec["k"], which=which.astype(np.uint32), n_threads=threads)
+        else:
+            oracle.search_dot(r_hv, rsub.precursor_mz, rsub.charge, q_hv, q_all.precursor_mz, q_all.charge,
+                              spec["tol"], spec["unit"], spec["k"], which=which.astype(np.uint32),
+                              n_threads=threads)
         return int(wc[which].sum()), time.perf_counter() - t
 
     m = 256
@@ -207,7 +216,8 @@ def cpu_oracle_rate(refs, queries, spec, target_s, lib_fraction=0.05, seed=5):
         m = min(q_all.n, m * 4)
         comps, dt = step(m)
     per_step = max(1, min(q_all.n, int(m * max(1.0, target_s / 4) / max(dt, 1e-3))))
-    sample = (f"oracle brute-force top-{spec['k']} search of {per_step} queries against a uniform "
+    kind = "search" if bits == 1 else f"dot-product search ({bits}-bit components)"
+    sample = (f"oracle brute-force top-{spec['k']} {kind} of {per_step} queries against a uniform "
               f"{n_lib}-reference sample ({lib_fraction:.0%}) of the library, D={D}, +-{spec['tol']:g}; "
               f"oracle encoding of the sample is setup, not timed")
     return per_step, threads, sample, step
@@ -669,6 +679,100 @@ def run_cascade(args):
     print(json.dumps(line), flush=True)
 
 
+def run_multibit(args):
+    """Multi-bit HV components (Section 4.3) on the headline workload: the
+    1,000,000 references encoded once with `--bits` bits per component and
+    kept as e2m1 (bits <= 3) or e4m3; a step encodes the 50,000 queries and
+    runs the windowed dot-product top-5 search.  One JSON line: in-window
+    comparisons/s, with the search kernel's roofline and the oracle's
+    dot-product search as the CPU baseline."""
+    import torch
+    from paper_2211_16422_gb300 import build, hd
+    build.build()
+    bits = args.bits
+    refs, queries, spec = workload(args.scale, 0)
+    D, Q, k, tol, unit = spec["dim"], spec["n_levels"], spec["k"], spec["tol"], spec["unit"]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32
+                                     else np.ascontiguousarray(a)).cuda()
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, seed=0)
+    r_csr = hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp_args(spec))
+    r_comp = hd.hd_encode_multibit(ctx, *r_csr, bits)
+    lib = hd.hd_build_library_multibit(ctx, r_comp, dev(refs.precursor_mz), dev(refs.charge), bits)
+    del r_comp
+    form = args.form if args.form != "auto" else ("tc_fp4" if bits <= 3 else "tc_fp8")
+    hd.hd_library_prepare(lib, form)
+    sched = {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2}
+    if args.schedule:
+        tg_, sg_, cs_, cg_ = (int(x) for x in args.schedule.split(","))
+        sched = {"tile_group": tg_, "super_group": sg_, "cluster": cs_, "cta_group": cg_}
+    hd.hd_library_set_schedule(lib, sched["tile_group"], sched["super_group"], sched["cluster"],
+                               sched["cta_group"])
+    q_csr = hd.hd_preprocess(ctx, dev(queries.offsets), dev(queries.mz), dev(queries.intensity), **pp_args(spec))
+    q_mz, q_z = dev(queries.precursor_mz), dev(queries.charge)
+    lo, hi = hd.hd_query_windows(lib, q_mz, q_z, tol, unit)
+    comparisons = int((hd.as_u32(hi).astype(np.int64) - hd.as_u32(lo).astype(np.int64)).sum())
+    nq = queries.n
+    q_comp = torch.empty((nq, D), dtype=torch.int8, device="cuda")
+    out_idx = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    out_score = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+
+    def step():
+        hd.hd_encode_multibit(ctx, *q_csr, bits, out=q_comp)
+        hd.hd_search_dot(lib, q_comp, q_mz, q_z, tol, unit, k, form, out_idx=out_idx, out_score=out_score)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.status()
+    lib.status()
+    hd.hd_profile_enable(True)
+    launches0 = hd.hd_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+    launches = hd.hd_launch_count() - launches0
+    hd.hd_profile_enable(False)
+    search_ms, search_n = hd.hd_profile_collect(hd.HD_KERNEL_SEARCH)
+    encode_ms, _ = hd.hd_profile_collect(hd.HD_KERNEL_ENCODE)
+    ctx.status()
+    lib.status()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    avg_search_ms = search_ms / max(1, search_n)
+    bf16 = measured_peaks().get("bf16_tflops", 1900.0)
+    peak = bf16 * (2.0 if form in ("tc_fp8", "tc_fp4") else 1.0)
+    achieved = comparisons * 2.0 * D / (avg_search_ms / 1e3) / 1e12
+    roofline = {"kernel": "k_search_mma2" if sched["cta_group"] == 2 else "k_search_mma", "bound": "tensor",
+                "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "peak_basis": "measured burst cuBLAS bf16" + (" x 2 (kind::f8f6f4)" if peak > bf16 else "")
+                              + " (of measured)",
+                "schedule": sched, "traffic": None, "avg_launch_ms": avg_search_ms, "launches": search_n,
+                "step_share": search_ms / (ms * args.steps)}
+    cpu = None
+    if not args.no_cpu_baseline:
+        per_step, threads, sample, cstep = cpu_oracle_rate(refs, queries, spec, args.cpu_seconds, bits=bits)
+        tot_c, tot_t, off = 0, 0.0, 0
+        while tot_t < args.cpu_seconds:
+            c_, t_ = cstep(per_step, off)
+            tot_c, tot_t, off = tot_c + c_, tot_t + t_, off + per_step
+        cpu = {"value": tot_c / tot_t, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+               "seconds": tot_t}
+    line = {"metric": f"in-window comparisons/s, dot-product search over {bits}-bit HV components (Section 4.3)",
+            "value": comparisons / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i8", "data": "synthetic (seeded generator)",
+            "config": {"workload": f"{refs.n}-reference library x {nq} queries, D={D}, {bits}-bit components "
+                                   f"(|h| <= {2 ** (bits - 1) - 1}), +-500 open window, top-5", "form": form,
+                       "l2": "library and query set exceed L2: no flush needed"},
+            "queries_per_s": nq / (ms / 1e3), "comparisons_per_step": comparisons,
+            "kernel_ms_per_step": {"search": search_ms / args.steps, "encode": encode_ms / args.steps},
+            "roofline": roofline, "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     """The oracle, as it stands, on the host cores (the paper publishes no
@@ -708,6 +812,8 @@ def main():
         run_serving(args)
     elif args.workload == "cascade":
         run_cascade(args)
+    elif args.workload == "multibit":
+        run_multibit(args)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -377,7 +377,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         const uint32_t lane_addr = (quarter * 32) << 16;
         const bool leader = threadIdx.x == 64;
         uint32_t acc_it = 0;
-        for (uint32_t item = cid; item < total && !__any_sync(0xFFFFFFFFu, *abort_flag != 0); item += ncl) {
+        for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
             uint32_t b, t0, t1;
             item_range(a, item, b, t0, t1);
             const uint32_t sb_ = b * CS + crank;     // this CTA's query block
@@ -390,8 +390,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             bool ok = true;
             for (uint32_t t = t0; t < t1; ++t, ++acc_it) {
                 const uint32_t buf = acc_it & 1u, aph = (acc_it >> 1) & 1u;
-                // warp-uniform outcome: the tensor-memory loads below are .sync.aligned
-                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&acc_full[buf], aph, a.wait_ns))) { give_up(); ok = false; break; }
+                if (!mbar_wait(&acc_full[buf], aph, a.wait_ns)) { give_up(); ok = false; break; }
                 tc_fence_after();
                 const uint32_t r0 = t * TN;
 #pragma unroll 1
@@ -399,14 +398,17 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
+                    // x >> shift <= thr  <=>  x <= ((thr + 1) << shift) - 1; an empty
+                    // list (thr = ~0) admits every x
                     const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
+                    const uint32_t lim = ((thr + 1u) << a.shift) - 1u;
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
                         const uint32_t r = r0 + cg * 32 + e;
                         const int s = __float2int_rn(__uint_as_float(v[e]));
-                        const uint32_t d = (uint32_t)((int)a.bias - s) >> a.shift;
-                        if (r - lo < span && d <= thr) {
-                            const uint64_t key = ((uint64_t)d << 32) | __ldg(a.lib_orig + r);
+                        const uint32_t x = (uint32_t)((int)a.bias - s);
+                        if (r - lo < span && x <= lim) {
+                            const uint64_t key = ((uint64_t)(x >> a.shift) << 32) | __ldg(a.lib_orig + r);
                             if (key < best[K - 1]) topk_insert<K>(best, key);
                         }
                     }
@@ -749,7 +751,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         const bool leader = threadIdx.x == 64;
         const uint32_t acc_empty0 = cluster_addr(&acc_empty[0], 0);
         uint32_t acc_it = 0;
-        for (uint32_t item = cid; item < total && !__any_sync(0xFFFFFFFFu, *abort_flag != 0); item += ncl) {
+        for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
             uint32_t b, t0, t1;
             item_range(a, item, b, t0, t1);
             const uint32_t sb_ = b * CS + crank;     // this CTA's query block
@@ -764,22 +766,24 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
                 const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
                 const uint32_t r0 = t * TN;
-                // warp-uniform outcome: the tensor-memory loads below are .sync.aligned
-                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&acc_full[buf], aph, a.wait_ns))) { give_up(); ok = false; break; }
+                if (!mbar_wait(&acc_full[buf], aph, a.wait_ns)) { give_up(); ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
                 for (uint32_t cg = slice * (EPI2_COLS / 32); cg < (slice + 1) * (EPI2_COLS / 32); ++cg) {
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
+                    // x >> shift <= thr  <=>  x <= ((thr + 1) << shift) - 1; an empty
+                    // list (thr = ~0) admits every x
                     const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
+                    const uint32_t lim = ((thr + 1u) << a.shift) - 1u;
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
                         const uint32_t r = r0 + cg * 32 + e;
                         const int s = __float2int_rn(__uint_as_float(v[e]));
-                        const uint32_t d = (uint32_t)((int)a.bias - s) >> a.shift;
-                        if (r - lo < span && d <= thr) {
-                            const uint64_t key = ((uint64_t)d << 32) | __ldg(a.lib_orig + r);
+                        const uint32_t x = (uint32_t)((int)a.bias - s);
+                        if (r - lo < span && x <= lim) {
+                            const uint64_t key = ((uint64_t)(x >> a.shift) << 32) | __ldg(a.lib_orig + r);
                             if (key < best[K - 1]) topk_insert<K>(best, key);
                         }
                     }
