@@ -49,10 +49,10 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
     #     --form <form> --schedule <tile_group,super_group,cluster,cta_group>
-    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 239.35e9 + 0.01444e9, "sha256": "6f3db4798d42cca9"},
-    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 245.77e9 + 0.02128e9, "sha256": "6f3db4798d42cca9"},
-    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 463.04e9 + 0.04653e9, "sha256": "6f3db4798d42cca9"},
-    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 454.55e9 + 0.05802e9, "sha256": "6f3db4798d42cca9"},
+    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 240.14e9 + 0.01468e9, "sha256": "9c25f893e333d497"},
+    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 243.26e9 + 0.02170e9, "sha256": "9c25f893e333d497"},
+    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 458.49e9 + 0.04111e9, "sha256": "9c25f893e333d497"},
+    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 452.30e9 + 0.05556e9, "sha256": "9c25f893e333d497"},
 }
 
 
