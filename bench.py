@@ -51,6 +51,8 @@ TRAFFIC = {
     #     --form <form> --schedule <tile_group,super_group,cluster,cta_group>
     ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 240.14e9 + 0.01468e9, "sha256": "9c25f893e333d497"},
     ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 243.26e9 + 0.02170e9, "sha256": "9c25f893e333d497"},
+    ("k_search_mma2", "tc_fp4", 32, 2, 2, 2): {"bytes": 189.20e9 + 0.06860e9, "sha256": "9c25f893e333d497"},
+    ("k_search_mma2", "tc_fp4", 16, 2, 2, 2): {"bytes": 177.76e9 + 0.11686e9, "sha256": "9c25f893e333d497"},
     ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 458.49e9 + 0.04111e9, "sha256": "9c25f893e333d497"},
     ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 452.30e9 + 0.05556e9, "sha256": "9c25f893e333d497"},
 }

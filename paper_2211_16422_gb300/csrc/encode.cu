@@ -199,6 +199,131 @@ k_encode_mb(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__r
     if (bad) hd_flag(status, HD_DEV_BAD_INPUT);
 }
 
+// Multi-bit components of Eq. 1 from the bit-sliced counters of k_encode.
+// With c_d the count of 1-bits among the n bound bits, I_d = n - 2 c_d, so
+// |I| is largest at the smallest or the largest count: pass 1 finds both from
+// the planes (a descent over the planes, no per-bit count), pass 2 recounts
+// and maps each component's count through a per-spectrum table h(c), c = 0..n,
+// in shared memory.  Same result as k_encode_mb<false>.
+template <int WPL>
+__device__ __forceinline__ uint32_t sliced_count(const uint64_t *__restrict__ F, uint32_t n_bins,
+                                                 const uint64_t *__restrict__ L, uint32_t n_levels, uint32_t W,
+                                                 const uint32_t *__restrict__ bins,
+                                                 const uint8_t *__restrict__ levels, uint32_t beg, uint32_t end,
+                                                 uint32_t w0, uint32_t lane, uint64_t (&c)[WPL][ENC_PLANES],
+                                                 bool &bad)
+{
+#pragma unroll
+    for (int j = 0; j < WPL; ++j)
+#pragma unroll
+        for (int i = 0; i < ENC_PLANES; ++i) c[j][i] = 0;
+    uint32_t added = 0;
+    for (uint32_t p = beg; p < end; ++p) {
+        const uint32_t b = __ldg(bins + p), l = __ldg(levels + p);
+        if (b >= n_bins || l >= n_levels) {
+            bad = true;
+            continue;
+        }
+        const uint64_t *fr = F + (size_t)b * W, *lr = L + (size_t)l * W;
+        uint64_t x[WPL];
+#pragma unroll
+        for (int j = 0; j < WPL; ++j) {
+            const uint32_t w = w0 + lane + 32u * j;
+            x[j] = w < W ? (__ldg(fr + w) ^ __ldg(lr + w)) : 0ull;
+        }
+        ++added;
+        const int lim = 32 - __clz(added);
+#pragma unroll
+        for (int i = 0; i < ENC_PLANES; ++i) {
+            if (i < lim) {
+#pragma unroll
+                for (int j = 0; j < WPL; ++j) {
+                    const uint64_t t = c[j][i] & x[j];
+                    c[j][i] ^= x[j];
+                    x[j] = t;
+                }
+            }
+        }
+    }
+    return added;
+}
+
+template <int WPL>
+__global__ void __launch_bounds__(ENC_WARPS * 32)
+k_encode_mb_sliced(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__restrict__ L,
+                   uint32_t n_levels, uint32_t W, const uint32_t *__restrict__ off,
+                   const uint32_t *__restrict__ bins, const uint8_t *__restrict__ levels, uint32_t n_spec,
+                   uint32_t m, int8_t *__restrict__ out, uint32_t *status)
+{
+    __shared__ int8_t s_tab[ENC_WARPS][ENC_MAX_PEAKS + 1];   // component as a function of the count
+    const uint32_t wi = threadIdx.x >> 5;
+    const uint32_t sp = blockIdx.x * ENC_WARPS + wi;
+    const uint32_t lane = threadIdx.x & 31;
+    if (sp >= n_spec) return;
+    uint32_t beg = off[sp], end = off[sp + 1];
+    if (end < beg || end - beg > ENC_MAX_PEAKS) {
+        if (lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
+        end = beg;   // encode as an empty row
+    }
+    bool bad = false;
+    uint64_t c[WPL][ENC_PLANES];
+    uint32_t n = 0, cmin = 0xFFFFFFFFu, cmax = 0;
+    for (uint32_t w0 = 0; w0 < W; w0 += 32u * WPL) {
+        n = sliced_count<WPL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane, c, bad);
+#pragma unroll
+        for (int j = 0; j < WPL; ++j) {
+            if (w0 + lane + 32u * j >= W) continue;
+            // largest count among the 64 bits: keep the bits that are 1 in the highest plane possible
+            uint64_t hi_c = ~0ull, lo_c = ~0ull;
+            uint32_t mx = 0, mn = 0;
+#pragma unroll
+            for (int i = ENC_PLANES - 1; i >= 0; --i) {
+                const uint64_t t = hi_c & c[j][i];
+                if (t) { hi_c = t; mx |= 1u << i; }
+                const uint64_t u = lo_c & ~c[j][i];
+                if (u) lo_c = u; else mn |= 1u << i;
+            }
+            cmin = min(cmin, mn);
+            cmax = max(cmax, mx);
+        }
+    }
+    cmin = __reduce_min_sync(0xFFFFFFFFu, cmin);
+    cmax = __reduce_max_sync(0xFFFFFFFFu, cmax);
+    const int32_t a_lo = abs((int32_t)n - 2 * (int32_t)cmin), a_hi = abs(2 * (int32_t)cmax - (int32_t)n);
+    const uint32_t M = (uint32_t)max(a_lo, a_hi);
+    for (uint32_t cc = lane; cc <= n; cc += 32) {
+        const int32_t I = (int32_t)n - 2 * (int32_t)cc;
+        const uint32_t a = (uint32_t)abs(I);
+        const int32_t h = M ? (int32_t)((2u * m * a + M) / (2u * M)) : 0;
+        s_tab[wi][cc] = (int8_t)(I < 0 ? -h : h);
+    }
+    __syncwarp();
+    const int lim = 32 - __clz(n);   // planes that can be non-zero
+    for (uint32_t w0 = 0; w0 < W; w0 += 32u * WPL) {
+        if (W > 32u * WPL) sliced_count<WPL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane, c, bad);
+#pragma unroll
+        for (int j = 0; j < WPL; ++j) {
+            const uint32_t w = w0 + lane + 32u * j;
+            if (w >= W) continue;
+            uint32_t p[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) p[q] = 0;
+#pragma unroll
+            for (int b = 0; b < 64; ++b) {
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int i = 0; i < ENC_PLANES; ++i)
+                    if (i < lim) cnt |= (uint32_t)((c[j][i] >> b) & 1ull) << i;
+                p[b >> 2] |= (uint32_t)(uint8_t)s_tab[wi][cnt] << (8 * (b & 3));
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(out + (size_t)sp * W * 64 + (size_t)w * 64);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+        }
+    }
+    if (bad && lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
+}
+
 }  // namespace
 
 void hd_encode_mb_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins, const uint8_t *levels,
@@ -211,8 +336,14 @@ void hd_encode_mb_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t 
     if (ctx->p.encoder == HD_ENC_PROJECTION)
         hd_count_launches(1), k_encode_mb<true><<<grid, ENC_WARPS * 32, 0, s>>>(
             ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
+    else if (ctx->W >= 128)
+        hd_count_launches(1), k_encode_mb_sliced<4><<<grid, ENC_WARPS * 32, 0, s>>>(
+            ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
+    else if (ctx->W >= 64)
+        hd_count_launches(1), k_encode_mb_sliced<2><<<grid, ENC_WARPS * 32, 0, s>>>(
+            ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
     else
-        hd_count_launches(1), k_encode_mb<false><<<grid, ENC_WARPS * 32, 0, s>>>(
+        hd_count_launches(1), k_encode_mb_sliced<1><<<grid, ENC_WARPS * 32, 0, s>>>(
             ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
 }
 

@@ -45,7 +45,8 @@ def random_csr(rng, n, f, Q, lens):
 
 
 @pytest.mark.parametrize("D,Q,f,encoder", [(128, 4, 60, "id_level"), (2048, 16, 3000, "id_level"),
-                                           (8192, 32, synth.N_BINS, "id_level"), (1024, 64, 2000, "projection"),
+                                           (4096, 16, 3000, "id_level"), (8192, 32, synth.N_BINS, "id_level"),
+                                           (32768, 32, 3000, "id_level"), (1024, 64, 2000, "projection"),
                                            (4096, 256, 5000, "projection")])
 def test_encode_multibit_bit_exact(hd, D, Q, f, encoder):
     rng = np.random.default_rng(D + Q)
