@@ -254,6 +254,33 @@ __device__ __forceinline__ void item_range(const mma_args &a, uint32_t item, uin
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Bit e set for the columns e of a 32-column group starting at reference row
+// c0 that lie in the row window [lo, lo + span).
+__device__ __forceinline__ uint32_t window_bits(uint32_t lo, uint32_t span, uint32_t c0)
+{
+    const int64_t b0 = max((int64_t)0, min((int64_t)32, (int64_t)lo - (int64_t)c0));
+    const int64_t b1 = max((int64_t)0, min((int64_t)32, (int64_t)lo + (int64_t)span - (int64_t)c0));
+    if (b1 <= b0) return 0u;
+    const uint32_t hi = b1 == 32 ? 0xFFFFFFFFu : (1u << b1) - 1u;
+    return hi & ~((1u << b0) - 1u);
+}
+
+// v[e] for a run-time e in 0..31, by a tree of selects on the bits of e
+// (keeps v in registers).
+__device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], uint32_t e)
+{
+    uint32_t w16[16], w8[8], w4[4], w2[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) w16[i] = (e & 16u) ? v[i + 16] : v[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w8[i] = (e & 8u) ? w16[i + 8] : w16[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w4[i] = (e & 4u) ? w8[i + 4] : w8[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) w2[i] = (e & 2u) ? w4[i + 2] : w4[i];
+    return (e & 1u) ? w2[1] : w2[0];
+}
 __device__ __forceinline__ void epi_bar2() { asm volatile("bar.sync 1, %0;" ::"r"(EPI2_THREADS) : "memory"); }
 
 // CS > 1: clusters of CS CTAs take CS consecutive query blocks of one work
@@ -773,19 +800,28 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
-                    // x >> shift <= thr  <=>  x <= ((thr + 1) << shift) - 1; an empty
-                    // list (thr = ~0) admits every x
+                    const uint32_t c0 = r0 + cg * 32;   // reference row of column 0 of the group
+                    const uint32_t wm = window_bits(lo, span, c0);
+                    if (!wm) continue;
+                    // (bias - S) >> shift <= thr  <=>  S >= bias - (((thr + 1) << shift) - 1):
+                    // one float compare per column (S is an integer below 2^24); an
+                    // empty list (thr = ~0) admits every column
                     const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
-                    const uint32_t lim = ((thr + 1u) << a.shift) - 1u;
+                    const float smin = thr == 0xFFFFFFFFu
+                                           ? -INFINITY
+                                           : (float)((int)a.bias - (int)(((thr + 1u) << a.shift) - 1u));
+                    uint32_t cand = 0;
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const uint32_t r = r0 + cg * 32 + e;
-                        const int s = __float2int_rn(__uint_as_float(v[e]));
+                    for (int e = 0; e < 32; ++e) cand |= (uint32_t)(__uint_as_float(v[e]) >= smin) << e;
+                    cand &= wm;
+                    // the candidates, one at a time, in a loop that is not unrolled
+                    while (cand) {
+                        const int e = __ffs(cand) - 1;
+                        cand &= cand - 1u;
+                        const int s = __float2int_rn(__uint_as_float(pick32(v, (uint32_t)e)));
                         const uint32_t x = (uint32_t)((int)a.bias - s);
-                        if (r - lo < span && x <= lim) {
-                            const uint64_t key = ((uint64_t)(x >> a.shift) << 32) | __ldg(a.lib_orig + r);
-                            if (key < best[K - 1]) topk_insert<K>(best, key);
-                        }
+                        const uint64_t key = ((uint64_t)(x >> a.shift) << 32) | __ldg(a.lib_orig + c0 + e);
+                        if (key < best[K - 1]) topk_insert<K>(best, key);
                     }
                 }
                 tc_fence_before();
