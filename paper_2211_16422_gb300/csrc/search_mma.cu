@@ -281,6 +281,36 @@ __device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], uint32_t e)
     for (int i = 0; i < 2; ++i) w2[i] = (e & 2u) ? w4[i + 2] : w4[i];
     return (e & 1u) ? w2[1] : w2[0];
 }
+
+// Scores one 32-column group of a query row's accumulator (S in fp32, exact
+// integers) into its running top-k: key distance (bias - S) >> shift, window
+// [lo, lo + span) of library rows, column e = reference row c0 + e.  One
+// float compare per column builds the candidate mask, and the candidates go
+// through a loop that is not unrolled, which keeps the code small.
+template <int K>
+__device__ __forceinline__ void score_group(const uint32_t (&v)[32], uint32_t c0, uint32_t lo, uint32_t span,
+                                            uint32_t bias, uint32_t shift, const uint32_t *__restrict__ lib_orig,
+                                            uint64_t (&best)[K])
+{
+    const uint32_t wm = window_bits(lo, span, c0);
+    if (!wm) return;
+    // (bias - S) >> shift <= thr  <=>  S >= bias - (((thr + 1) << shift) - 1); an
+    // empty list (thr = ~0) admits every column
+    const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
+    const float smin = thr == 0xFFFFFFFFu ? -INFINITY : (float)((int)bias - (int)(((thr + 1u) << shift) - 1u));
+    uint32_t cand = 0;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) cand |= (uint32_t)(__uint_as_float(v[e]) >= smin) << e;
+    cand &= wm;
+    while (cand) {
+        const int e = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        const int sc = __float2int_rn(__uint_as_float(pick32(v, (uint32_t)e)));
+        const uint32_t x = (uint32_t)((int)bias - sc);
+        const uint64_t key = ((uint64_t)(x >> shift) << 32) | __ldg(lib_orig + c0 + e);
+        if (key < best[K - 1]) topk_insert<K>(best, key);
+    }
+}
 __device__ __forceinline__ void epi_bar2() { asm volatile("bar.sync 1, %0;" ::"r"(EPI2_THREADS) : "memory"); }
 
 // CS > 1: clusters of CS CTAs take CS consecutive query blocks of one work
@@ -425,20 +455,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
-                    // x >> shift <= thr  <=>  x <= ((thr + 1) << shift) - 1; an empty
-                    // list (thr = ~0) admits every x
-                    const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
-                    const uint32_t lim = ((thr + 1u) << a.shift) - 1u;
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const uint32_t r = r0 + cg * 32 + e;
-                        const int s = __float2int_rn(__uint_as_float(v[e]));
-                        const uint32_t x = (uint32_t)((int)a.bias - s);
-                        if (r - lo < span && x <= lim) {
-                            const uint64_t key = ((uint64_t)(x >> a.shift) << 32) | __ldg(a.lib_orig + r);
-                            if (key < best[K - 1]) topk_insert<K>(best, key);
-                        }
-                    }
+                    score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, best);
                 }
                 tc_fence_before();
                 mbar_arrive(&acc_empty[buf]);
@@ -800,29 +817,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
-                    const uint32_t c0 = r0 + cg * 32;   // reference row of column 0 of the group
-                    const uint32_t wm = window_bits(lo, span, c0);
-                    if (!wm) continue;
-                    // (bias - S) >> shift <= thr  <=>  S >= bias - (((thr + 1) << shift) - 1):
-                    // one float compare per column (S is an integer below 2^24); an
-                    // empty list (thr = ~0) admits every column
-                    const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
-                    const float smin = thr == 0xFFFFFFFFu
-                                           ? -INFINITY
-                                           : (float)((int)a.bias - (int)(((thr + 1u) << a.shift) - 1u));
-                    uint32_t cand = 0;
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) cand |= (uint32_t)(__uint_as_float(v[e]) >= smin) << e;
-                    cand &= wm;
-                    // the candidates, one at a time, in a loop that is not unrolled
-                    while (cand) {
-                        const int e = __ffs(cand) - 1;
-                        cand &= cand - 1u;
-                        const int s = __float2int_rn(__uint_as_float(pick32(v, (uint32_t)e)));
-                        const uint32_t x = (uint32_t)((int)a.bias - s);
-                        const uint64_t key = ((uint64_t)(x >> a.shift) << 32) | __ldg(a.lib_orig + c0 + e);
-                        if (key < best[K - 1]) topk_insert<K>(best, key);
-                    }
+                    score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, best);
                 }
                 tc_fence_before();
                 mbar_arrive_remote(acc_empty0 + buf * 8u);
