@@ -16,17 +16,19 @@
 //   warp 1      allocates 512 TMEM columns and issues tcgen05.mma (32
 //               components of K per instruction) into one of two accumulator
 //               buffers, committing stages and tiles to mbarriers;
-//   warps 2..    epilogue: tcgen05.ld of the finished accumulator, one query
-//               row per thread, window mask, top-k of (dist, input index) keys;
-//               the buffer is handed back while the next tile is accumulated
-//               in the other one.
+//   warps 2..5  epilogue: tcgen05.ld of the finished accumulator, one query
+//               row per thread; per 32 columns a candidate mask (window bits
+//               and one float compare per column against the row's current
+//               k-th score), then a rolled loop over the candidates into the
+//               top-k of (dist, input index) keys; the buffer is handed back
+//               while the next tile is accumulated in the other one.
 // k_search_mma: 192 threads (4 epilogue warps), M = 128, N = 256 per CTA, 4
 // stages of 48 KB; clusters of 1, 2 or 4 CTAs share each reference tile by
 // TMA multicast.
-// k_search_mma2 (default): 320 threads (8 epilogue warps, two per 32 query
-// rows, each on 128 of the 256 columns), SM pairs, tcgen05.mma.cta_group::2
-// with M = 256, N = 256 issued by the even CTA; each CTA stages its own query
-// block and half of the tile, 6 stages of 32 KB.
+// k_search_mma2 (default): 192 threads (HD_MMA2_EPI_WARPS = 8 splits each
+// quarter's columns over two warps), SM pairs, tcgen05.mma.cta_group::2 with
+// M = 256, N = 256 issued by the even CTA; each CTA stages its own query block
+// and half of the tile, 6 stages of 32 KB.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -73,10 +75,11 @@ constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* align */ + 256 /* barriers */;
 constexpr uint32_t TMEM_COLS = 2 * TN;
 // Epilogue warps of the pair kernel: EPI2_SPLIT per tensor-memory lane
-// quarter, each scoring 1/EPI2_SPLIT of the 256 columns of its 32 query rows,
-// so the scoring of a tile keeps up with its MMAs at D = 4096 as well.
+// quarter, each scoring 1/EPI2_SPLIT of the 256 columns of its 32 query rows.
+// With the compact group scoring one warp per quarter keeps up with the MMAs
+// at D = 4096 and leaves the issue slots to the producer and MMA warps.
 #ifndef HD_MMA2_EPI_WARPS
-#define HD_MMA2_EPI_WARPS 8
+#define HD_MMA2_EPI_WARPS 4
 #endif
 constexpr int EPI2_WARPS = HD_MMA2_EPI_WARPS;
 constexpr int EPI2_SPLIT = EPI2_WARPS / 4;
