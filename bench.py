@@ -49,12 +49,12 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
     #     --form <form> --schedule <tile_group,super_group,cluster,cta_group>
-    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 240.14e9 + 0.01468e9, "sha256": "9c25f893e333d497"},
-    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 243.26e9 + 0.02170e9, "sha256": "9c25f893e333d497"},
-    ("k_search_mma2", "tc_fp4", 32, 2, 2, 2): {"bytes": 189.20e9 + 0.06860e9, "sha256": "9c25f893e333d497"},
-    ("k_search_mma2", "tc_fp4", 16, 2, 2, 2): {"bytes": 177.76e9 + 0.11686e9, "sha256": "9c25f893e333d497"},
-    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 458.49e9 + 0.04111e9, "sha256": "9c25f893e333d497"},
-    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 452.30e9 + 0.05556e9, "sha256": "9c25f893e333d497"},
+    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 228.20e9 + 0.01504e9, "sha256": "ce686b086bb14c90"},
+    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 236.43e9 + 0.02175e9, "sha256": "ce686b086bb14c90"},
+    ("k_search_mma2", "tc_fp4", 32, 2, 2, 2): {"bytes": 182.10e9 + 0.07071e9, "sha256": "ce686b086bb14c90"},
+    ("k_search_mma2", "tc_fp4", 16, 2, 2, 2): {"bytes": 176.50e9 + 0.12780e9, "sha256": "ce686b086bb14c90"},
+    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 445.50e9 + 0.04100e9, "sha256": "ce686b086bb14c90"},
+    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 420.58e9 + 0.05932e9, "sha256": "ce686b086bb14c90"},
 }
 
 
