@@ -58,6 +58,11 @@ TRAFFIC = {
 }
 
 
+# The arithmetic type the search computes in: the tensor-core operand format
+# (products accumulated in fp32, exact), or 32-bit words for XOR + popcount.
+DTYPE_OF_FORM = {"tc_fp4": "e2m1", "tc_fp8": "e4m3", "tc_bf16": "bf16", "popc": "u32"}
+
+
 def kernel_source_hash():
     """sha256 of the kernel's code: its sources with C/C++ comments and blank
     lines removed, so that editing a comment keeps the captured figures."""
@@ -415,7 +420,8 @@ def run_ours(args, rank, world, local_rank):
                "seconds": tot_t}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded generator; stands in for the "
+            "vs_baseline": None, "dtype": DTYPE_OF_FORM.get(form, "u32"),
+            "data": "synthetic (seeded generator; stands in for the "
             "paper's MassIVE-KB/HEK293 and yeast/iPRG2012 sets)",
             "config": config_of(spec, world), "queries_per_s": qps,
             "comparisons_per_step": total_comparisons,
@@ -501,7 +507,7 @@ def run_batched(args):
         line = {"metric": "Hamming comparisons/s, batched uneven windows (200 batches, 20 ppm / 150 Da / 500 Da)",
                 "value": comparisons / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "vs_baseline": None, "dtype": DTYPE_OF_FORM.get(best["form"], "u32"), "data": "synthetic",
                 "config": {"workload": f"{n_r}-reference library x {len(sizes)} batches "
                                        f"({int(sizes.sum())} queries, sizes {int(sizes.min())}..{int(sizes.max())}), "
                                        f"D={D}, charge 1-5, windows round-robin", "dim": D,
@@ -608,7 +614,7 @@ def run_serving(args):
     best = max(l["queries_per_s"] for l in loads)
     line = {"metric": "serving: sustained queries/s and p50/p99 request latency under Poisson load, D=8192, +-500",
             "value": best, "unit": "queries/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "e2m1", "data": "synthetic",
             "config": {"workload": f"{n_r}-reference resident library, requests of {spec['req_lo']}..{hi_req} "
                                    "spectra (log-uniform), Poisson arrivals", "dim": D, "k": k,
                        "server": {"slots": 3, "max_batch_queries": 16384, "form": "tc_fp4"}},
@@ -670,7 +676,7 @@ def run_cascade(args):
     line = {"metric": "cascade search queries/s (20 ppm, then +-500 Da for the unidentified; 1% FDR per level), "
                       "D=8192",
             "value": nq / (ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e2m1",
             "data": "synthetic (seeded generator; decoys are targets with repositioned fragments)",
             "config": {"workload": f"{refs.n}-reference library (50% decoys) x {nq} queries, D={D}, Q={Q}, "
                                    "levels 20 ppm / +-500 Da, top-1, FDR 1%", "form": "tc_fp4",
@@ -765,7 +771,7 @@ def run_multibit(args):
     line = {"metric": f"in-window comparisons/s, dot-product search over {bits}-bit HV components (Section 4.3)",
             "value": comparisons / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "i8", "data": "synthetic (seeded generator)",
+            "vs_baseline": None, "dtype": DTYPE_OF_FORM.get(form, "e4m3"), "data": "synthetic (seeded generator)",
             "config": {"workload": f"{refs.n}-reference library x {nq} queries, D={D}, {bits}-bit components "
                                    f"(|h| <= {2 ** (bits - 1) - 1}), +-500 open window, top-5", "form": form,
                        "l2": "library and query set exceed L2: no flush needed"},
