@@ -573,6 +573,9 @@ def run_serving(args):
         s = min(s, hi_req, pool.n - 1)
         srv.wait(srv.submit(*make_request(s, wr), spec["tol"], spec["unit"]))
     loads = []
+    launches0 = hd.hd_launch_count()
+    clocks = ClockSampler(0)
+    clocks.__enter__()
     for lam in (50, 100, 200, 500, 1000, 2000):
         r = np.random.default_rng(100 + lam)
         n_req = int(min(2000, max(100, lam * 6 * min(1.0, args.scale * 10))))
@@ -610,6 +613,8 @@ def run_serving(args):
                       "queries_per_s": qn / (t_end - t0), "batches": st1["batches"] - st0["batches"],
                       "max_inflight_batches": st1["max_inflight"]})
         print(json.dumps({"load": loads[-1]}), file=sys.stderr, flush=True)
+    clocks.__exit__(None, None, None)
+    launches = hd.hd_launch_count() - launches0
     srv.close()
     best = max(l["queries_per_s"] for l in loads)
     line = {"metric": "serving: sustained queries/s and p50/p99 request latency under Poisson load, D=8192, +-500",
@@ -618,7 +623,7 @@ def run_serving(args):
             "config": {"workload": f"{n_r}-reference resident library, requests of {spec['req_lo']}..{hi_req} "
                                    "spectra (log-uniform), Poisson arrivals", "dim": D, "k": k,
                        "server": {"slots": 3, "max_batch_queries": 16384, "form": "tc_fp4"}},
-            "loads": loads}
+            "loads": loads, "gpu_launches": launches, "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
 
 
