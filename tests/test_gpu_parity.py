@@ -290,9 +290,11 @@ def test_invalid_arguments(hd):
 
 # ----------------------------------------------- full-size workload, sampled
 def test_full_size_sampled(hd):
-    """The 1,000,000 x 50,000, D=8192, Q=32, +-500, top-5 workload in the
-    benchmark's launch configuration; the oracle answers a seeded sample of
-    queries and encodes a sample of spectra."""
+    """The 1,000,000 x 50,000, D=8192, Q=32, +-500, top-5 workload: the
+    popcount form, then the benchmark's launch configurations (e2m1 SM pairs
+    at the schedules the autotuner picks, e4m3, the 1-SM form); the oracle
+    answers a seeded sample of queries and encodes a sample of spectra, and
+    every form must equal the popcount form on all 50,000 queries."""
     refs, qs, spec = synth.make_workload("full")
     D, Q, k = spec["dim"], spec["n_levels"], spec["k"]
     pp = pp_args(Q)
@@ -332,3 +334,17 @@ def test_full_size_sampled(hd):
     qq = np.nonzero(ok)[0]
     assert np.all(refs.charge[rows] == qs.charge[qq])
     assert np.all(np.abs(refs.precursor_mz[rows] - qs.precursor_mz[qq]) <= spec["tol"])
+    # the benchmark's form and schedules: e2m1 SM pairs at the autotuner's usual picks, e4m3, and
+    # the 1-SM form; each equal to the oracle on the sample and to the popcount form on every query
+    hd.hd_library_prepare(lib, "tc_fp4")
+    hd.hd_library_prepare(lib, "tc_fp8")
+    for form, sched in (("tc_fp4", (16, 16, 2, 2)), ("tc_fp4", (32, 16, 2, 2)), ("tc_fp4", (32, 2, 2, 2)),
+                        ("tc_fp8", (16, 16, 2, 2)), ("tc_fp4", (16, 16, 4, 1))):
+        hd.hd_library_set_schedule(lib, *sched)
+        ti, td = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), spec["tol"], spec["unit"], k,
+                                   form=form)
+        torch.cuda.synchronize()
+        lib.status()
+        ti, td = hd.as_u32(ti), hd.as_u16(td)
+        assert np.array_equal(ti[which], oi) and np.array_equal(td[which], od), (form, sched)
+        assert np.array_equal(ti, gi) and np.array_equal(td, gd), (form, sched)
