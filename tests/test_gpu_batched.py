@@ -174,3 +174,57 @@ def test_multi_window_mixed_units_exact(hd):
         lib.status()
         assert np.array_equal(hd.as_u32(i), oi), form
         assert np.array_equal(hd.as_u16(d), od), form
+
+
+def test_batched_full_size_sampled(hd):
+    """The benchmark's batched workload at full size (2,000,000 references, 200
+    batches, 445,653 queries, D=4096) through the CUDA-graph plan with e2m1 SM
+    pairs: every query equals the popcount form (an independent GPU path),
+    and a seeded sample of 20 ppm queries equals the oracle, which encodes
+    only those queries' candidate references."""
+    spec = synth.WORKLOADS["batched"]
+    rng = np.random.Generator(np.random.PCG64(spec["seed"]))
+    refs = synth.make_references(spec["n_refs"], spec["charges"], spec["weights"], rng,
+                                 decoy_fraction=spec["decoy_fraction"])
+    sizes = synth.batch_sizes(spec["n_batches"], spec["batch_lo"], spec["batch_hi"], rng)
+    qs = synth.make_queries(refs, int(sizes.sum()), rng)
+    windows = [(t, u) for t, u in spec["windows"]]
+    assert windows == WINDOWS
+    cls = np.repeat(np.arange(len(sizes)) % len(windows), sizes).astype(np.uint8)
+    D, Q, k = 4096, spec["n_levels"], spec["k"]
+    ctx, lib, r_hv, q_csr = _setup(hd, refs, qs, D, Q)
+    del r_hv
+    hd.hd_library_prepare(lib, "tc_fp4")
+    nnz = int(hd.as_u32(q_csr[0])[-1])
+    q_mz, q_z, q_cls = dev(qs.precursor_mz), dev(qs.charge), dev(cls)
+    plan = hd.Plan(ctx, lib, q_csr[0], q_csr[1][:nnz], q_csr[2][:nnz], q_mz, q_z, q_cls, windows, k=k,
+                   form="tc_fp4")
+    pi, pd = plan.launch()
+    torch.cuda.synchronize()
+    lib.status()
+    pi, pd = hd.as_u32(pi).copy(), hd.as_u16(pd).copy()
+    ci, cd = hd.hd_search_open_multi(lib, plan.q_hv, q_mz, q_z, q_cls, windows, k, form="popc")
+    torch.cuda.synchronize()
+    lib.status()
+    assert np.array_equal(pi, hd.as_u32(ci)) and np.array_equal(pd, hd.as_u16(cd))
+    # oracle on sampled 20 ppm queries: their candidates are few, so only those references are encoded
+    s_rng = np.random.default_rng(31)
+    which = np.sort(s_rng.choice(np.nonzero(cls == 0)[0], 300, replace=False))
+    tol_q = qs.precursor_mz[which] * (20.0 * 1e-6)
+    cand = set()
+    order = np.argsort(refs.precursor_mz, kind="stable")
+    mz_sorted = refs.precursor_mz[order]
+    for j, q in enumerate(which):
+        a = np.searchsorted(mz_sorted, qs.precursor_mz[q] - tol_q[j] - 1e-6, "left")
+        b = np.searchsorted(mz_sorted, qs.precursor_mz[q] + tol_q[j] + 1e-6, "right")
+        cand.update(order[a:b].tolist())
+    sub_idx = np.array(sorted(cand), dtype=np.int64)
+    sub = refs.subset(sub_idx)
+    r_np = oracle_side.hvs(sub, D, Q, 0)
+    q_sub = qs.subset(which)
+    q_np = oracle_side.hvs(q_sub, D, Q, 0)
+    oi, od = oracle.search(D, r_np, sub.precursor_mz, sub.charge, q_np, q_sub.precursor_mz, q_sub.charge,
+                           20.0, "ppm", k)
+    oi_g = np.where(oi == 0xFFFFFFFF, 0xFFFFFFFF, sub_idx[np.minimum(oi, sub_idx.size - 1)]).astype(np.uint32)
+    assert np.array_equal(pi[which], oi_g) and np.array_equal(pd[which], od)
+    assert np.mean(oi[:, 0] != 0xFFFFFFFF) > 0.5
