@@ -205,3 +205,46 @@ def test_multibit_argument_checks(hd):
     gi, gs = hd.hd_search_dot(empty, dev(R[:5]), dev(mz[:5]), dev(z[:5]), 1.0, "da", 3)
     torch.cuda.synchronize()
     assert np.all(u32(gi) == 0xFFFFFFFF) and np.all(gs.cpu().numpy() == np.iinfo(np.int32).min)
+
+
+def test_search_dot_full_size_sampled(hd):
+    """The multi-bit benchmark's shapes: the 1,000,000-reference "full" library
+    and 50,000 queries, D=8192, 3-bit components, +-500 Da, top-5, e2m1 SM
+    pairs.  e4m3 gives the same result on every query; the oracle encodes every
+    charge-4 reference and answers 16 sampled charge-4 queries by brute force;
+    a sample of spectra is encoded by both sides."""
+    refs, qs, spec = synth.make_workload("full")
+    D, Q, k, bits = spec["dim"], spec["n_levels"], spec["k"], 3
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, 0)
+    r_csr = hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp)
+    q_csr = hd.hd_preprocess(ctx, dev(qs.offsets), dev(qs.mz), dev(qs.intensity), **pp)
+    r_comp = hd.hd_encode_multibit(ctx, *r_csr, bits)
+    q_comp = hd.hd_encode_multibit(ctx, *q_csr, bits)
+    lib = hd.hd_build_library_multibit(ctx, r_comp, dev(refs.precursor_mz), dev(refs.charge), bits)
+    q_mz, q_z = dev(qs.precursor_mz), dev(qs.charge)
+    gi, gs = hd.hd_search_dot(lib, q_comp, q_mz, q_z, spec["tol"], spec["unit"], k, "tc_fp4")
+    torch.cuda.synchronize()
+    lib.status()
+    gi, gs = u32(gi), gs.cpu().numpy()
+    hd.hd_library_prepare(lib, "tc_fp8")
+    ei, es = hd.hd_search_dot(lib, q_comp, q_mz, q_z, spec["tol"], spec["unit"], k, "tc_fp8")
+    torch.cuda.synchronize()
+    assert np.array_equal(u32(ei), gi) and np.array_equal(es.cpu().numpy(), gs)
+    F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, 0)
+    rng = np.random.default_rng(8)
+    rs = np.sort(rng.choice(refs.n, 100, replace=False))
+    sub = refs.subset(rs)
+    want = oracle.encode_multibit(D, F, L, *oracle.preprocess(sub.offsets, sub.mz, sub.intensity, **pp), bits)
+    assert np.array_equal(r_comp[torch.from_numpy(rs).cuda()].cpu().numpy(), want)
+    z4 = np.nonzero(refs.charge == 4)[0]
+    r4 = refs.subset(z4)
+    R4 = oracle.encode_multibit(D, F, L, *oracle.preprocess(r4.offsets, r4.mz, r4.intensity, **pp), bits)
+    which = np.sort(rng.choice(np.nonzero(qs.charge == 4)[0], 16, replace=False))
+    q4 = qs.subset(which)
+    Q4 = oracle.encode_multibit(D, F, L, *oracle.preprocess(q4.offsets, q4.mz, q4.intensity, **pp), bits)
+    oi, osc = oracle.search_dot(R4, r4.precursor_mz, r4.charge, Q4, q4.precursor_mz, q4.charge, spec["tol"],
+                                spec["unit"], k)
+    oi_g = np.where(oi == 0xFFFFFFFF, 0xFFFFFFFF, z4[np.minimum(oi, z4.size - 1)]).astype(np.uint32)
+    assert np.array_equal(gi[which], oi_g) and np.array_equal(gs[which], osc)
