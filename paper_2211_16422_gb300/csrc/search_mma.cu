@@ -293,13 +293,16 @@ __device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], uint32_t e)
 template <int K>
 __device__ __forceinline__ void score_group(const uint32_t (&v)[32], uint32_t c0, uint32_t lo, uint32_t span,
                                             uint32_t bias, uint32_t shift, const uint32_t *__restrict__ lib_orig,
-                                            uint64_t (&best)[K])
+                                            uint64_t seed, uint64_t (&best)[K])
 {
     const uint32_t wm = window_bits(lo, span, c0);
     if (!wm) return;
+    // a key enters only below the list's last key and below `seed`, the last
+    // key of the query's running top-k when the work item started (that list
+    // only improves, so nothing at or above it can reach the result).
     // (bias - S) >> shift <= thr  <=>  S >= bias - (((thr + 1) << shift) - 1); an
     // empty list (thr = ~0) admits every column
-    const uint32_t thr = (uint32_t)(best[K - 1] >> 32);
+    const uint32_t thr = (uint32_t)(min(best[K - 1], seed) >> 32);
     const float smin = thr == 0xFFFFFFFFu ? -INFINITY : (float)((int)bias - (int)(((thr + 1u) << shift) - 1u));
     uint32_t cand = 0;
 #pragma unroll
@@ -311,7 +314,7 @@ __device__ __forceinline__ void score_group(const uint32_t (&v)[32], uint32_t c0
         const int sc = __float2int_rn(__uint_as_float(pick32(v, (uint32_t)e)));
         const uint32_t x = (uint32_t)((int)bias - sc);
         const uint64_t key = ((uint64_t)(x >> shift) << 32) | __ldg(lib_orig + c0 + e);
-        if (key < best[K - 1]) topk_insert<K>(best, key);
+        if (key < min(best[K - 1], seed)) topk_insert<K>(best, key);
     }
 }
 __device__ __forceinline__ void epi_bar2() { asm volatile("bar.sync 1, %0;" ::"r"(EPI2_THREADS) : "memory"); }
@@ -443,6 +446,10 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
             const uint32_t sb_ = b * CS + crank;     // this CTA's query block
             const uint32_t sq = sb_ * TM + row;
             const uint32_t lo = sq < a.n_q ? a.lo[sq] : 0u, hi = sq < a.n_q ? a.hi[sq] : 0u;
+            // last key of the query's running top-k (merged from its finished items)
+            const uint64_t seed = sq < a.n_q ? (uint64_t)__ldcg(reinterpret_cast<const unsigned long long *>(
+                                                   a.top + (size_t)sq * K + (K - 1)))
+                                             : KEY_NONE;
             const uint32_t span = hi > lo ? hi - lo : 0u;
             uint64_t best[K];
 #pragma unroll
@@ -458,7 +465,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
-                    score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, best);
+                    score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
                 }
                 tc_fence_before();
                 mbar_arrive(&acc_empty[buf]);
@@ -804,6 +811,10 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
             const uint32_t sb_ = b * CS + crank;     // this CTA's query block
             const uint32_t sq = sb_ * TM + row;
             const uint32_t lo = sq < a.n_q ? a.lo[sq] : 0u, hi = sq < a.n_q ? a.hi[sq] : 0u;
+            // last key of the query's running top-k (merged from its finished items)
+            const uint64_t seed = sq < a.n_q ? (uint64_t)__ldcg(reinterpret_cast<const unsigned long long *>(
+                                                   a.top + (size_t)sq * K + (K - 1)))
+                                             : KEY_NONE;
             const uint32_t span = hi > lo ? hi - lo : 0u;
             uint64_t best[K];
 #pragma unroll
@@ -820,7 +831,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                     uint32_t v[32];
                     tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
                     tmem_ld_wait();
-                    score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, best);
+                    score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
                 }
                 tc_fence_before();
                 mbar_arrive_remote(acc_empty0 + buf * 8u);
