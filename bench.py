@@ -49,18 +49,13 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
     #     --form <form> --schedule <tile_group,super_group,cluster,cta_group>
-    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 228.20e9 + 0.01504e9, "sha256": "ce686b086bb14c90"},
-    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 236.43e9 + 0.02175e9, "sha256": "ce686b086bb14c90"},
-    ("k_search_mma2", "tc_fp4", 32, 2, 2, 2): {"bytes": 182.10e9 + 0.07071e9, "sha256": "ce686b086bb14c90"},
-    ("k_search_mma2", "tc_fp4", 16, 2, 2, 2): {"bytes": 176.50e9 + 0.12780e9, "sha256": "ce686b086bb14c90"},
-    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 445.50e9 + 0.04100e9, "sha256": "ce686b086bb14c90"},
-    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 420.58e9 + 0.05932e9, "sha256": "ce686b086bb14c90"},
+    ("k_search_mma2", "tc_fp4", 32, 16, 2, 2): {"bytes": 236.92e9 + 0.01392e9, "sha256": "caa7df56edc7e93a"},
+    ("k_search_mma2", "tc_fp4", 16, 16, 2, 2): {"bytes": 237.71e9 + 0.02102e9, "sha256": "caa7df56edc7e93a"},
+    ("k_search_mma2", "tc_fp4", 32, 2, 2, 2): {"bytes": 183.91e9 + 0.06443e9, "sha256": "caa7df56edc7e93a"},
+    ("k_search_mma2", "tc_fp4", 16, 2, 2, 2): {"bytes": 171.92e9 + 0.11700e9, "sha256": "caa7df56edc7e93a"},
+    ("k_search_mma2", "tc_fp8", 32, 16, 2, 2): {"bytes": 443.87e9 + 0.04349e9, "sha256": "caa7df56edc7e93a"},
+    ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 413.00e9 + 0.04895e9, "sha256": "caa7df56edc7e93a"},
 }
-
-
-# The arithmetic type the search computes in: the tensor-core operand format
-# (products accumulated in fp32, exact), or 32-bit words for XOR + popcount.
-DTYPE_OF_FORM = {"tc_fp4": "e2m1", "tc_fp8": "e4m3", "tc_bf16": "bf16", "popc": "u32"}
 
 
 def kernel_source_hash():
