@@ -49,6 +49,15 @@ struct search_args {
     uint32_t stall;        // test hook: drop the first stage copies
 };
 
+// Carry-save step: ones + a + b = ones' + 2 * carry bitwise (a full adder per
+// bit position), and the carries are counted at once: acc += 2 * popc(carry).
+__device__ __forceinline__ void csa2(uint32_t &ones, uint32_t &acc, uint32_t a, uint32_t b)
+{
+    const uint32_t carry = (ones & a) | (ones & b) | (a & b);
+    ones ^= a ^ b;
+    acc += __popc(carry) << 1;
+}
+
 // ------------------------------------------------------------ search kernel
 template <int K>
 __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
@@ -110,11 +119,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int t = 0; t < K; ++t) best[i][t] = KEY_NONE;
-        uint32_t acc[4][4];
+        // distance of pair (i, j) = acc + popcount(ones): `ones` is a carry-save
+        // word (Harley and Seal's full adder) that absorbs two XOR words per
+        // step, so one popcount of the carries counts two words
+        uint32_t acc[4][4], ones[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+            for (int j = 0; j < 4; ++j) acc[i][j] = ones[i][j] = 0;
 
         // warp 0 stages step `st_step` (tile, chunk) into buffer st_step & 1
         auto issue = [&](uint32_t st_step) {
@@ -168,9 +180,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        acc[i][j] += __popc(qv[i].x ^ rv[j].x) + __popc(qv[i].y ^ rv[j].y) +
-                                     __popc(qv[i].z ^ rv[j].z) + __popc(qv[i].w ^ rv[j].w);
+                    for (int j = 0; j < 4; ++j) {
+                        csa2(ones[i][j], acc[i][j], qv[i].x ^ rv[j].x, qv[i].y ^ rv[j].y);
+                        csa2(ones[i][j], acc[i][j], qv[i].z ^ rv[j].z, qv[i].w ^ rv[j].w);
+                    }
             }
             if (ch == nchunks - 1) {
                 const uint32_t r0 = row_base + tile * BR;
@@ -180,6 +193,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
                     const uint32_t o = row < row_end ? __ldg(a.lib_orig + row) : 0u;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
+                        acc[i][j] += __popc(ones[i][j]);
+                        ones[i][j] = 0;
                         if (row >= qlo[i] && row < qhi[i]) {
                             const uint64_t key = ((uint64_t)acc[i][j] << 32) | o;
                             if (key < best[i][K - 1]) topk_insert<K>(best[i], key);
