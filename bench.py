@@ -57,6 +57,10 @@ TRAFFIC = {
     ("k_search_mma2", "tc_fp8", 16, 16, 2, 2): {"bytes": 413.00e9 + 0.04895e9, "sha256": "caa7df56edc7e93a"},
 }
 
+# The arithmetic type the search computes in: the tensor-core operand format
+# (products accumulated in fp32, exact), or 32-bit words for XOR + popcount.
+DTYPE_OF_FORM = {"tc_fp4": "e2m1", "tc_fp8": "e4m3", "tc_bf16": "bf16", "popc": "u32"}
+
 
 def kernel_source_hash():
     """sha256 of the kernel's code: its sources with C/C++ comments and blank
