@@ -508,6 +508,27 @@ def run_batched(args):
         hd.hd_profile_enable(False)
         search_ms, search_n = hd.hd_profile_collect(hd.HD_KERNEL_SEARCH)
         achieved = comparisons * 2.0 * D / (search_ms / max(1, search_n) / 1e3) / 1e12
+        # per-batch latency: each batch alone (encode + search with its window), CUDA events around it
+        starts = np.r_[0, np.cumsum(sizes)]
+        off_np = hd.as_u32(off)
+        batches = []
+        for b_ in range(len(sizes)):
+            a_, e_ = int(starts[b_]), int(starts[b_ + 1])
+            p0, p1 = int(off_np[a_]), int(off_np[e_])
+            batches.append((dev((off_np[a_:e_ + 1] - p0).astype(np.uint32)), bins[p0:p1].contiguous(),
+                            lv[p0:p1].contiguous(), q_mz[a_:e_].contiguous(), q_z[a_:e_].contiguous(),
+                            windows[b_ % len(windows)]))
+        lat = []
+        for off_b, bins_b, lv_b, mz_b, z_b, (tol_b, unit_b) in batches:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hv_b = hd.hd_encode(ctx, off_b, bins_b, lv_b)
+            hd.hd_search_open(lib, hv_b, mz_b, z_b, tol_b, unit_b, spec["k"], form=best["form"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lat.append(e0.elapsed_time(e1))
+        lib.status()
+        lat = np.asarray(lat)
         # the roofline comes from one eager launch timed alone: the burst bf16 figure (x2 for kind::f8f6f4)
         peak = measured_peaks().get("bf16_tflops", 1900.0) * (2.0 if best["form"] in ("tc_fp8", "tc_fp4") else 1.0)
         line = {"metric": "Hamming comparisons/s, batched uneven windows (200 batches, 20 ppm / 150 Da / 500 Da)",
@@ -519,7 +540,9 @@ def run_batched(args):
                                        f"D={D}, charge 1-5, windows round-robin", "dim": D,
                            "n_queries": int(qs.n), "n_batches": int(len(sizes))},
                 "queries_per_s": qs.n / (ms / 1e3), "comparisons_per_step": comparisons,
-                "batch_latency_ms": {"all_batches_one_graph": ms},
+                "batch_latency_ms": {"all_batches_one_graph": ms, "one_batch_alone_p50": float(np.percentile(lat, 50)),
+                                     "one_batch_alone_p99": float(np.percentile(lat, 99)),
+                                     "one_batch_alone_max": float(lat.max())},
                 "graph_kernel_nodes": plan.kernel_nodes, "gpu_launches": plan.kernel_nodes * args.steps,
                 "autotune": {"best": best, "candidates": len(table)},
                 "roofline": {"kernel": ("k_search_popc" if not best["form"].startswith("tc") else
