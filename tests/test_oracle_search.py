@@ -179,3 +179,36 @@ def test_mass_window_search_brute_force():
         got = [int(x) for x in idx[i] if x != 0xFFFFFFFF]
         assert got == best
         assert [int(dm[i, r]) for r in best] == [int(x) for x in dist[i][:len(best)]]
+
+
+def test_topk_prefix_and_reference_permutation():
+    """The k1 best are the first k1 of the k2 best (k1 < k2); relabelling the
+    references permutes indices but keeps every query's sorted distances."""
+    rng = np.random.default_rng(17)
+    n_ref, n_q = 400, 30
+    refs = _rand_hv(rng, n_ref)
+    refs[50] = refs[10]                       # ties
+    qs = _rand_hv(rng, n_q)
+    qs[0] = refs[10]
+    mz = rng.uniform(500, 503, n_ref)
+    z = rng.integers(2, 4, n_ref).astype(np.uint8)
+    mz[50], z[50] = mz[10], z[10]
+    q_mz = rng.uniform(500, 503, n_q)
+    q_z = rng.integers(2, 4, n_q).astype(np.uint8)
+    q_mz[0], q_z[0] = mz[10], z[10]
+    i16, d16 = oracle.search(D, refs, mz, z, qs, q_mz, q_z, 1.0, "da", k=16)
+    for k in (1, 3, 7):
+        ik, dk = oracle.search(D, refs, mz, z, qs, q_mz, q_z, 1.0, "da", k=k)
+        assert np.array_equal(ik, i16[:, :k]) and np.array_equal(dk, d16[:, :k])
+    assert i16[0, 0] == 10 and i16[0, 1] == 50 and d16[0, 0] == d16[0, 1] == 0
+    perm = rng.permutation(n_ref)
+    ip, dp = oracle.search(D, refs[perm], mz[perm], z[perm], qs, q_mz, q_z, 1.0, "da", k=16)
+    assert np.array_equal(dp, d16)
+    ok = ip != 0xFFFFFFFF
+    # the permuted run's rows map back to references with the same distances
+    back = np.where(ok, perm[np.minimum(ip, n_ref - 1)], 0xFFFFFFFF)
+    dist_of = lambda q, r: int(hamming_matrix(qs[q:q + 1], refs[r:r + 1])[0, 0])
+    for q in range(n_q):
+        for t in range(16):
+            if ok[q, t]:
+                assert dist_of(q, back[q, t]) == dp[q, t]
