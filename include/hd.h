@@ -57,7 +57,7 @@ typedef enum {
     HD_ERR_OOM = 2,           /* device allocation failed; nothing launched */
     HD_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has details) */
     HD_ERR_TIMEOUT = 4,       /* a bounded device wait expired; results are invalid */
-    HD_ERR_UNSUPPORTED = 5    /* valid request this build or GPU does not serve */
+    HD_ERR_UNSUPPORTED = 5    /* valid request that this library or GPU does not serve */
 } hd_status;
 
 /* Precursor tolerance units.  HD_TOL_DA and HD_TOL_PPM bound the precursor
