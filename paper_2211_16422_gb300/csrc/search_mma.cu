@@ -7,7 +7,9 @@
 // D - 2 dist(x, y) with fp32 accumulation in tensor memory.  Every product is
 // +-1 and every partial sum an integer of magnitude <= D <= 32768 < 2^24, so
 // the sum is exact and dist = (D - S) / 2 matches the popcount form bit for
-// bit.
+// bit.  Multi-bit components (integers in [-m, m], Section 4.3) use the same
+// kernels with the key distance D m^2 - S; their partial sums stay below
+// D m^2 < 2^24.
 //
 // Two kernels share the warp roles (one persistent CTA per SM):
 //   warp 0      TMA producer: 2-D tensor loads of 128-component K-slices of a
@@ -18,10 +20,12 @@
 //               buffers, committing stages and tiles to mbarriers;
 //   warps 2..5  epilogue: tcgen05.ld of the finished accumulator, one query
 //               row per thread; per 32 columns a candidate mask (window bits
-//               and one float compare per column against the row's current
-//               k-th score), then a rolled loop over the candidates into the
-//               top-k of (dist, input index) keys; the buffer is handed back
-//               while the next tile is accumulated in the other one.
+//               and one float compare per column against the score that could
+//               still enter the row's top-k, bounded by the query's running
+//               top-k at the work item's start), then a rolled loop over the
+//               candidates into the top-k of (dist, input index) keys; the
+//               buffer is handed back while the next tile is accumulated in
+//               the other one.
 // k_search_mma: 192 threads (4 epilogue warps), M = 128, N = 256 per CTA, 4
 // stages of 48 KB; clusters of 1, 2 or 4 CTAs share each reference tile by
 // TMA multicast.
