@@ -327,9 +327,9 @@ HD_API void hd_plan_destroy(hd_plan *plan);
  * is prepared for and, for the tensor-core forms, work-item shapes
  * tile_group x super_group x (cluster, cta_group) in {4, 16, 32} x {2, 16} x
  * {(1, 1), (2, 1), (4, 1), (2, 2)}, on the
- * given queries (a representative sample: whole batches rather than a random
- * subset of queries, whose sorted blocks would span wider m/z ranges than the
- * real batches' and can favour another schedule), and keeps the fastest as the library's
+ * given queries (the real query set, or one of the same density per window:
+ * a subset's sorted blocks span wider m/z ranges and can favour another
+ * schedule), and keeps the fastest as the library's
  * HD_FORM_AUTO form and schedule.  `all` (capacity `cap`) receives every
  * timing.  Synchronous; results never depend on the choice. */
 typedef struct {
