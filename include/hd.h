@@ -126,7 +126,10 @@ typedef enum {
                              (library: D/2 bytes/row; the TMA unpacks into shared memory) */
 } hd_search_form;
 
+/* Name of a status code ("HD_OK", ...); a static string, never NULL. */
 HD_API const char *hd_status_string(hd_status s);
+/* Message of the last failing call on the calling host thread (thread-local,
+ * valid until that thread's next failing call). */
 HD_API const char *hd_last_error_message(void);
 /* Library version as major*10000 + minor*100 + patch. */
 HD_API uint32_t hd_version(void);
