@@ -91,8 +91,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=("full", "batched", "serving", "cascade", "multibit"), default="full",
-                    help="full: the headline line; batched / serving / cascade / multibit: the extra workloads")
+    ap.add_argument("--popc-steps", type=int, default=3,
+                    help="timed steps of the popcount form beside the headline form (0: skip)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the instruction-rate microbenchmarks")
+    ap.add_argument("--workload", choices=("full", "batched", "serving", "cascade", "multibit", "peaks"),
+                    default="full",
+                    help="full: the headline line; batched / serving / cascade / multibit: the extra workloads; "
+                         "peaks: the instruction-rate microbenchmarks alone")
     ap.add_argument("--bits", type=int, default=3, help="component bits of --workload multibit (2..5)")
     return ap.parse_args()
 
@@ -111,6 +116,13 @@ def workload(scale: float, rank: int):
     queries = synth.make_queries(refs, n_q, qrng)
     spec.update(n_refs=n_r, n_queries=n_q)
     return refs, queries, spec
+
+
+def tuning_queries(refs, n_q, rank):
+    """A second query batch of the same recipe and size, drawn from its own seed:
+    the autotuner picks form and schedule on it, not on the batch it is timed on."""
+    spec = synth.WORKLOADS["full"]
+    return synth.make_queries(refs, n_q, np.random.Generator(np.random.PCG64([spec["seed"], 2000 + rank])))
 
 
 def pp_args(spec):
@@ -247,6 +259,76 @@ def reduce_over_ranks(seconds, units, device=None):
 
 
 # ---------------------------------------------------------------- our arm
+def measure_peaks(hd, kinds, launches=10, clock_index=0):
+    """The instruction-rate microbenchmarks (hd_measure_peak), with the SM clock
+    sampled while they run."""
+    with ClockSampler(clock_index) as clocks:
+        res = {k: hd.hd_measure_peak(k, launches) for k in kinds}
+    return res, clocks.summary()
+
+
+def tensor_roofline(form, comparisons, D, avg_search_ms, peaks, peak_clocks, sched):
+    """Roofline of a tensor-core search launch: 2*D flops per in-window comparison
+    (masked tile padding not counted) against the measured rate of the kernel's
+    own instruction and shape (hd_measure_peak), with the bf16-derived figure
+    beside it."""
+    achieved = comparisons * 2.0 * D / (avg_search_ms / 1e3) / 1e12
+    bf16 = measured_peaks().get("bf16_tflops", 1900.0)
+    eight_bit_kind = form in ("tc_fp8", "tc_fp4")   # kind::f8f6f4
+    derived = bf16 * (2.0 if eight_bit_kind else 1.0)
+    pair = sched.get("cta_group") == 2
+    kname = "k_search_mma2" if pair else "k_search_mma"
+    r = {"kernel": kname, "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
+         "schedule": {k_: sched.get(k_) for k_ in ("tile_group", "super_group", "cluster", "cta_group")},
+         "derived_peak": {"peak": derived, "frac": achieved / derived,
+                          "basis": "MEASURED_PEAKS burst cuBLAS bf16" + (" x 2 (nominal fp8/bf16 ratio 4.5/2.25)"
+                                                                          if eight_bit_kind else "")}}
+    p = (peaks or {}).get(form)
+    if p:
+        peak = p["best_per_s"] / 1e12
+        instr = ("tcgen05.mma.cta_group::2.kind::f8f6f4 (" + ("e2m1" if form == "tc_fp4" else "e4m3") + ")"
+                 if eight_bit_kind else "tcgen05.mma.cta_group::2.kind::f16 (bf16)")
+        r.update({"peak": peak, "frac": achieved / peak,
+                  "peak_basis": f"measured (own microbenchmark hd_measure_peak: {instr}, M=256 N=256, operands "
+                                f"resident in shared memory, {p['sms']} SMs, best of {p['launches']} launches, "
+                                f"SM clock median {(peak_clocks or {}).get('sm_mhz')} MHz)",
+                  "peak_median": p["median_per_s"] / 1e12})
+        if not pair:
+            r["peak_basis"] += "; the 1-SM kernel issues M=128 cta_group::1 at the same per-SM rate"
+    else:
+        r.update({"peak": derived, "frac": achieved / derived, "peak_basis": r["derived_peak"]["basis"]
+                  + " (of measured)"})
+    return r
+
+
+def popc_roofline(comparisons, D, avg_search_ms, n_sm, sm_mhz, peaks):
+    """Roofline of the popcount form: 32-bit words of XOR + popcount work.  The
+    paper's form counts one word per popcount (bound: the popcount unit's
+    measured rate); the carry-save kernel counts two words per popcount and
+    spends 2.5 integer-pipe operations per word (bound: the measured LOP3 rate
+    / 2.5)."""
+    words = comparisons * (D // 32)
+    achieved = words / (avg_search_ms / 1e3) / 1e12
+    pp, pl = (peaks or {}).get("popc"), (peaks or {}).get("lop3")
+    if pp and pl:
+        popc_bound = pp["best_per_s"] / 1e12
+        issue_bound = pl["best_per_s"] / 2.5 / 1e12
+        basis = "measured (own microbenchmarks hd_measure_peak 'lop3' / 2.5 and 'popc')"
+    else:
+        popc_bound = n_sm * 16 * sm_mhz * 1e6 / 1e12
+        issue_bound = n_sm * 64 / 2.5 * sm_mhz * 1e6 / 1e12
+        basis = f"{n_sm} SMs x (64 LOP3 / 2.5, 16 popc) per clk x {sm_mhz:.0f} MHz (nominal unit counts)"
+    return {"kernel": "k_search_popc", "bound": "alu", "unit": "Tword32/s", "achieved": achieved,
+            "peak": issue_bound, "frac": achieved / issue_bound,
+            "peak_basis": "integer-issue bound of the carry-save kernel: " + basis,
+            "popcount_unit_bound": {"peak": popc_bound, "frac": achieved / popc_bound,
+                                    "basis": "one popc32 per word (the paper's form): " + basis}}
+
+
+def pctl(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2211_16422_gb300 import build, hd
@@ -293,14 +375,18 @@ def run_ours(args, rank, world, local_rank):
         setup["schedule"] = {"tile_group": tg_, "super_group": sg_, "cluster": cs_, "cta_group": cg_}
     q_mz, q_z = dev(queries.precursor_mz), dev(queries.charge)
     if args.form == "auto":
-        # the library's autotuner picks form and schedule on this query batch (setup, not timed)
+        # the library's autotuner picks form and schedule on a second, separately seeded batch
+        # of the same size and recipe (setup, not timed)
         t = time.perf_counter()
-        q_hv_s = hd.hd_encode(ctx, *q_csr)
-        tuned, _ = hd.hd_library_autotune(lib, q_hv_s, q_mz, q_z, None, [(tol, unit)], k)
-        del q_hv_s
+        tq = tuning_queries(refs, queries.n, rank)
+        tq_hv = hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(tq.offsets), dev(tq.mz), dev(tq.intensity),
+                                                      **pp_args(spec)))
+        tuned, _ = hd.hd_library_autotune(lib, tq_hv, dev(tq.precursor_mz), dev(tq.charge), None, [(tol, unit)], k)
+        del tq_hv
         form = tuned["form"]
         setup["autotune_s"] = time.perf_counter() - t
         setup["autotune_choice"] = tuned
+        setup["autotune_batch"] = "separate seeded batch of the same recipe and size"
     lo, hi = hd.hd_query_windows(lib, q_mz, q_z, tol, unit)
     comparisons = int((hd.as_u32(hi).astype(np.int64) - hd.as_u32(lo).astype(np.int64)).sum())
     nq = queries.n
@@ -309,9 +395,16 @@ def run_ours(args, rank, world, local_rank):
     out_dist = torch.empty((nq, k), dtype=torch.int16, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
+    def step(f=None):
         hd.hd_encode(ctx, *q_csr, out=q_hv)
-        hd.hd_search_open(lib, q_hv, q_mz, q_z, tol, unit, k, form=form, out_idx=out_idx, out_dist=out_dist)
+        hd.hd_search_open(lib, q_hv, q_mz, q_z, tol, unit, k, form=f or form, out_idx=out_idx, out_dist=out_dist)
+
+    # instruction-rate microbenchmarks (the rooflines' denominators), outside the timed region
+    peaks, peak_clocks = None, None
+    if not args.no_peaks:
+        kinds = ((form,) if form.startswith("tc_") else ()) + (("popc", "lop3") if args.popc_steps > 0
+                                                                  or form == "popc" else ())
+        peaks, peak_clocks = measure_peaks(hd, kinds, clock_index=local_rank)
 
     for _ in range(args.warmup):
         step()
@@ -322,12 +415,12 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     hd.hd_profile_enable(True)
     launches0 = hd.hd_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local_rank) as clocks:
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for i in range(args.steps):
             step()
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize()
     barrier()
     launches = hd.hd_launch_count() - launches0
@@ -336,10 +429,48 @@ def run_ours(args, rank, world, local_rank):
     encode_ms, encode_n = hd.hd_profile_collect(hd.HD_KERNEL_ENCODE)
     ctx.status()
     lib.status()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    ms = evs[0].elapsed_time(evs[-1]) / args.steps
     ms, total_comparisons = reduce_over_ranks(ms, comparisons, device="cuda")
+    p50, _ = reduce_over_ranks(pctl(step_ms, 50), 0, device="cuda")
+    p99, _ = reduce_over_ranks(pctl(step_ms, 99), 0, device="cuda")
     value = total_comparisons / (ms / 1e3)
     qps = nq * world / (ms / 1e3)
+    ref_idx, ref_dist = out_idx.cpu().numpy(), out_dist.cpu().numpy()
+
+    # the paper's form (XOR + popcount) on the same batch: its own timed steps and
+    # its own roofline, and the same top-k as the headline form
+    forms = None
+    if args.popc_steps > 0 and form != "popc":
+        step("popc")
+        torch.cuda.synchronize()
+        lib.status()
+        assert np.array_equal(out_idx.cpu().numpy(), ref_idx) and np.array_equal(out_dist.cpu().numpy(), ref_dist), \
+            "popcount and tensor-core forms differ"
+        hd.hd_profile_enable(True)
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as pclocks:
+            pe0.record(stream)
+            for _ in range(args.popc_steps):
+                step("popc")
+            pe1.record(stream)
+            torch.cuda.synchronize()
+        hd.hd_profile_enable(False)
+        psearch_ms, psearch_n = hd.hd_profile_collect(hd.HD_KERNEL_SEARCH)
+        hd.hd_profile_collect(hd.HD_KERNEL_ENCODE)
+        lib.status()
+        pms = pe0.elapsed_time(pe1) / args.popc_steps
+        pms, _ = reduce_over_ranks(pms, 0, device="cuda")
+        popc_equal = bool(np.array_equal(out_idx.cpu().numpy(), ref_idx)
+                          and np.array_equal(out_dist.cpu().numpy(), ref_dist))
+        assert popc_equal, "popcount and tensor-core forms differ"
+        forms = {"popc": {"ms_per_step": pms, "search_ms": psearch_ms / max(1, psearch_n),
+                          "comparisons_per_s": total_comparisons / (pms / 1e3), "steps": args.popc_steps,
+                          "clocks": pclocks.summary()},
+                 form: {"ms_per_step": ms, "search_ms": search_ms / max(1, search_n),
+                        "comparisons_per_s": value, "steps": args.steps},
+                 "speedup": pms / ms, "speedup_of": f"{form} over popc, ms per step",
+                 "identical_topk": popc_equal}
 
     # end to end through hd_search_host: pinned host inputs, copies in the timed region
     e2e = None
@@ -354,16 +485,22 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(max(1, args.warmup // 2)):
             e2e_step()
         barrier()
+        walls = []
         t = time.perf_counter()
         for _ in range(args.steps):
+            t1 = time.perf_counter()
             e2e_step()
+            walls.append((time.perf_counter() - t1) * 1e3)
         e2e_s = (time.perf_counter() - t) / args.steps
         e2e_s, _ = reduce_over_ranks(e2e_s, 0, device="cuda")
+        e50, _ = reduce_over_ranks(pctl(walls, 50), 0, device="cuda")
+        e99, _ = reduce_over_ranks(pctl(walls, 99), 0, device="cuda")
         h2d = sum(t_.numel() * t_.element_size() for t_ in (h_off, h_bins, h_lv, h_mz, h_z))
         d2h = nq * k * (4 + 2)
         e2e = {"value": total_comparisons / e2e_s, "unit": UNIT, "queries_per_s": nq * world / e2e_s,
-               "ms_per_step": e2e_s * 1e3, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-        assert np.array_equal(h_idx.numpy(), out_idx.cpu().numpy()), "end-to-end results differ"
+               "ms_per_step": e2e_s * 1e3, "p50_ms": e50, "p99_ms": e99,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        assert np.array_equal(h_idx.numpy(), ref_idx), "end-to-end results differ"
 
     if rank != 0:
         return
@@ -373,38 +510,17 @@ def run_ours(args, rank, world, local_rank):
     sm_mhz = (cs or {}).get("sm_mhz") or 1455.0
     avg_search_ms = search_ms / max(1, search_n)
     if form.startswith("tc_"):
-        # dense +-1 contraction: 2*D flops per in-window comparison (masked tile
-        # padding is not counted)
-        # the search kernel is timed alone in a sub-second region at the full
-        # SM clock: the burst bf16 figure applies (x2 for e4m3, the nominal
-        # 4.5 / 2.25 PFLOP/s dense ratio)
-        peaks = measured_peaks()
-        bf16 = peaks.get("bf16_tflops", 1900.0)
-        eight_bit_kind = form in ("tc_fp8", "tc_fp4")   # kind::f8f6f4 runs e2m1 at the e4m3 rate
-        peak = bf16 * (2.0 if eight_bit_kind else 1.0)
-        achieved = comparisons * 2.0 * D / (avg_search_ms / 1e3) / 1e12
-        basis = ("measured burst cuBLAS bf16 x 2 (nominal fp8/bf16 ratio 4.5/2.25; tcgen05 kind::f8f6f4 runs "
-                 "e4m3 and e2m1 operands at the same rate)" if eight_bit_kind else "measured burst cuBLAS bf16")
         sched = (setup.get("autotune_choice") or setup.get("schedule")
                  or {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2})
-        kname = "k_search_mma2" if sched.get("cta_group") == 2 else "k_search_mma"
-        roofline = {"kernel": kname, "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
-                    "peak": peak, "frac": achieved / peak, "peak_basis": basis + " (of measured)",
-                    "schedule": {k_: sched.get(k_) for k_ in ("tile_group", "super_group", "cluster", "cta_group")}}
+        roofline = tensor_roofline(form, comparisons, D, avg_search_ms, peaks, peak_clocks, sched)
     else:
-        # 32-bit words of XOR + popcount work; the carry-save kernel spends
-        # 2.5 integer-pipe operations per word (XOR, and per two words a
-        # majority, a 3-input XOR and a shift-add of one popcount)
-        words = comparisons * (D // 32)
-        achieved = words / (avg_search_ms / 1e3) / 1e12
-        peak = n_sm * 64 / 2.5 * sm_mhz * 1e6 / 1e12
-        popc_bound = n_sm * 16 * sm_mhz * 1e6 / 1e12
-        roofline = {"kernel": "k_search_popc", "bound": "alu", "unit": "Tword32/s",
-                    "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                    "peak_basis": f"{n_sm} SMs x 64 integer ops/clk/SM / 2.5 ops per word x {sm_mhz:.0f} MHz "
-                                  "median SM clock sampled",
-                    "popcount_unit_bound": {"peak": popc_bound, "frac": achieved / popc_bound,
-                                            "basis": f"one popc32 per word at 16/clk/SM (the paper's form)"}}
+        roofline = popc_roofline(comparisons, D, avg_search_ms, n_sm, sm_mhz, peaks)
+    if forms:
+        pr = popc_roofline(comparisons, D, forms["popc"]["search_ms"], n_sm,
+                           (forms["popc"]["clocks"] or {}).get("sm_mhz") or sm_mhz, peaks)
+        forms["popc"].update({"frac_issue_bound": pr["frac"], "frac_popc_bound": pr["popcount_unit_bound"]["frac"],
+                              "roofline": pr})
+        forms[form].update({"frac": roofline["frac"], "peak_basis": roofline["peak_basis"]})
     traffic = None
     if form.startswith("tc_") and args.scale == 1.0:
         s_ = roofline["schedule"]
@@ -430,11 +546,31 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic (seeded generator; stands in for the "
             "paper's MassIVE-KB/HEK293 and yeast/iPRG2012 sets)",
             "config": config_of(spec, world), "queries_per_s": qps,
+            "latency_ms": {"p50": p50, "p99": p99, "of": "one step (encode + search of the query batch), "
+                                                         "CUDA events on the launching stream"},
             "comparisons_per_step": total_comparisons,
             "kernel_ms_per_step": {"search": search_ms / args.steps, "encode": encode_ms / args.steps},
-            "setup_s": setup, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "setup_s": setup, "roofline": roofline, "forms": forms, "peaks": peaks, "peak_clocks": peak_clocks,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": cs, "form": form, "device": props.name}
     print(json.dumps(line))
+
+
+def run_peaks(args):
+    """The instruction-rate microbenchmarks alone: one JSON line."""
+    import torch
+    from paper_2211_16422_gb300 import build, hd
+    build.build()
+    torch.cuda.set_device(0)
+    res, clocks = measure_peaks(hd, ("tc_fp4", "tc_fp8", "tc_bf16", "popc", "lop3"), launches=max(3, args.steps))
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    per_clk = {k: v["best_per_s"] / (n_sm * mhz * 1e6) for k, v in res.items()}
+    line = {"metric": "instruction-rate microbenchmarks (the search rooflines' denominators)",
+            "value": res["tc_fp4"]["best_per_s"] / 1e12, "unit": "TFLOP/s (tc_fp4)", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "peaks": res,
+            "per_clock_per_sm": per_clk, "clocks": clocks, "device": torch.cuda.get_device_properties(0).name}
+    print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------ batched uneven workload
@@ -508,7 +644,6 @@ def run_batched(args):
         torch.cuda.synchronize()
         hd.hd_profile_enable(False)
         search_ms, search_n = hd.hd_profile_collect(hd.HD_KERNEL_SEARCH)
-        achieved = comparisons * 2.0 * D / (search_ms / max(1, search_n) / 1e3) / 1e12
         # per-batch latency: each batch alone (encode + search with its window), CUDA events around it
         starts = np.r_[0, np.cumsum(sizes)]
         off_np = hd.as_u32(off)
@@ -530,8 +665,16 @@ def run_batched(args):
             lat.append(e0.elapsed_time(e1))
         lib.status()
         lat = np.asarray(lat)
-        # the roofline comes from one eager launch timed alone: the burst bf16 figure (x2 for kind::f8f6f4)
-        peak = measured_peaks().get("bf16_tflops", 1900.0) * (2.0 if best["form"] in ("tc_fp8", "tc_fp4") else 1.0)
+        # the roofline comes from one eager launch timed alone, against the measured rate of its instruction
+        if best["form"].startswith("tc_"):
+            pk, pclk = measure_peaks(hd, (best["form"],))
+            roof = tensor_roofline(best["form"], comparisons, D, search_ms / max(1, search_n), pk, pclk, best)
+        else:
+            pk, _ = measure_peaks(hd, ("popc", "lop3"))
+            roof = popc_roofline(comparisons, D, search_ms / max(1, search_n),
+                                 torch.cuda.get_device_properties(0).multi_processor_count,
+                                 (clocks.summary() or {}).get("sm_mhz") or 2070.0, pk)
+        roof.update({"avg_launch_ms": search_ms / max(1, search_n), "traffic": None})
         line = {"metric": "Hamming comparisons/s, batched uneven windows (200 batches, 20 ppm / 150 Da / 500 Da)",
                 "value": comparisons / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -546,12 +689,7 @@ def run_batched(args):
                                      "one_batch_alone_max": float(lat.max())},
                 "graph_kernel_nodes": plan.kernel_nodes, "gpu_launches": plan.kernel_nodes * args.steps,
                 "autotune": {"best": best, "candidates": len(table)},
-                "roofline": {"kernel": ("k_search_popc" if not best["form"].startswith("tc") else
-                                        "k_search_mma2" if best.get("cta_group") == 2 else "k_search_mma"),
-                             "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
-                             "frac": achieved / peak, "avg_launch_ms": search_ms / max(1, search_n),
-                             "peak_basis": "measured burst cuBLAS bf16 (x2 nominal fp8/bf16 ratio for kind::f8f6f4) "
-                                           "(of measured)", "traffic": None},
+                "roofline": roof,
                 "clocks": clocks.summary()}
         print(json.dumps(line), flush=True)
         plan.close()
@@ -785,15 +923,10 @@ def run_multibit(args):
     lib.status()
     ms = ev0.elapsed_time(ev1) / args.steps
     avg_search_ms = search_ms / max(1, search_n)
-    bf16 = measured_peaks().get("bf16_tflops", 1900.0)
-    peak = bf16 * (2.0 if form in ("tc_fp8", "tc_fp4") else 1.0)
-    achieved = comparisons * 2.0 * D / (avg_search_ms / 1e3) / 1e12
-    roofline = {"kernel": "k_search_mma2" if sched["cta_group"] == 2 else "k_search_mma", "bound": "tensor",
-                "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                "peak_basis": "measured burst cuBLAS bf16" + (" x 2 (kind::f8f6f4)" if peak > bf16 else "")
-                              + " (of measured)",
-                "schedule": sched, "traffic": None, "avg_launch_ms": avg_search_ms, "launches": search_n,
-                "step_share": search_ms / (ms * args.steps)}
+    pk, pclk = measure_peaks(hd, (form,))
+    roofline = tensor_roofline(form, comparisons, D, avg_search_ms, pk, pclk, sched)
+    roofline.update({"traffic": None, "avg_launch_ms": avg_search_ms, "launches": search_n,
+                     "step_share": search_ms / (ms * args.steps)})
     cpu = None
     if not args.no_cpu_baseline:
         per_step, threads, sample, cstep = cpu_oracle_rate(refs, queries, spec, args.cpu_seconds, bits=bits)
@@ -857,6 +990,8 @@ def main():
         run_cascade(args)
     elif args.workload == "multibit":
         run_multibit(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -30,7 +30,10 @@
  *    calling thread.
  *  - Thread safety: distinct objects are independent.  One hd_ctx or
  *    hd_library may serve concurrent read-only calls (hd_encode,
- *    hd_search_open*) from several host threads and streams.
+ *    hd_search_open, hd_search_open_ex, hd_search_open_multi, hd_search_dot)
+ *    from several host threads and streams.  hd_search_open_noalloc is the
+ *    exception: all its calls share one scratch buffer, so its calls that
+ *    overlap on the GPU race and must be serialised by the caller.
  */
 #ifndef HD_H
 #define HD_H
@@ -153,6 +156,16 @@ HD_API hd_status hd_ctx_item_memory(const hd_ctx *ctx, uint64_t *d_F, uint64_t *
                              uint32_t *d_rank_F, uint32_t *d_rank_L, hd_stream stream);
 /* Returns and clears the device status recorded by kernels of this ctx. */
 HD_API hd_status hd_ctx_status(hd_ctx *ctx);
+/* The random words behind the item memory (Section 3.3.1-3.3.2 draw the base
+ * HVs and flip positions at random; the generator is Philox4x32-10, Salmon et
+ * al., SC'11): d_out[i] = component i%4 of Philox4x32-10 applied to the
+ * counter (i/4, stream_id, 0, 0) under the key (seed low 32 bits, seed high
+ * 32 bits), for i < n.  Stream 0 holds the F_0 bits, 1 the position-
+ * permutation keys, 2 the L_0 bits, 3 the level-permutation keys, 4 the
+ * walk's flip draws, 5 the independent position HVs.  d_out [n] uint32
+ * device buffer owned by the caller; n <= 2^32 - 4.  Asynchronous. */
+HD_API hd_status hd_random_words(uint64_t seed, uint32_t stream_id, uint32_t n, uint32_t *d_out,
+                                 hd_stream stream);
 
 /* Preprocessing (Section 3.2, Table 1): raw peaks -> CSR spectrum vectors.
  * Per spectrum: drop peaks with non-finite values or intensity <= 0; drop
@@ -219,14 +232,15 @@ HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
  * rows form tiles of 256 on a grid fixed to row 0; one work item scores one
  * block of 128 sorted queries against `tile_group` consecutive tiles, and
  * items are ordered so that the CTAs running at once share `super_group`
- * consecutive groups of tiles through L2.  `cluster` (1, 2 or 4) CTAs of a
- * thread-block cluster take adjacent query blocks and share each reference
- * tile by TMA multicast.  `cta_group` 2 pairs the two CTAs of a cluster of
- * 2 on neighbouring SMs into one M = 256 tensor-core operation (each SM
- * stages half of every reference tile); it requires cluster 0 or 2.  0 keeps
- * the default (16, 16, 2, 2; cta_group 0 with cluster 1 or 4 means 1).
- * Results do not depend on the schedule.  Not to be changed while a search
- * on this library is in flight. */
+ * consecutive groups of tiles through L2.  (cluster, cta_group) = (2, 2)
+ * pairs two CTAs on neighbouring SMs into one M = 256 tensor-core operation
+ * (each SM stages its own query block and half of every reference tile);
+ * (1, 1) runs one CTA per SM at M = 128.  A 0 in either place takes the
+ * other's value; 0 everywhere keeps the default (16, 16, 2, 2).  Other
+ * combinations fail with HD_ERR_INVALID_ARG.  Every tensor load goes to the
+ * issuing CTA's own shared memory (no multicast).  Results do not depend on
+ * the schedule.  Not to be changed while a search on this library is in
+ * flight. */
 HD_API hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group,
                                          uint32_t cluster, uint32_t cta_group);
 
@@ -329,7 +343,7 @@ HD_API void hd_plan_destroy(hd_plan *plan);
 /* Autotuner (no counterpart in the paper): times each search form the library
  * is prepared for and, for the tensor-core forms, work-item shapes
  * tile_group x super_group x (cluster, cta_group) in {4, 16, 32} x {2, 16} x
- * {(1, 1), (2, 1), (4, 1), (2, 2)}, on the
+ * {(1, 1), (2, 2)}, on the
  * given queries (the real query set, or one of the same density per window:
  * a subset's sorted blocks span wider m/z ranges and can favour another
  * schedule), and keeps the fastest as the library's
@@ -382,6 +396,18 @@ HD_API hd_status hd_server_submit(hd_server *srv, const uint32_t *h_offsets, con
 /* Blocks until the request is done (HD_ERR_TIMEOUT after timeout_s > 0). */
 HD_API hd_status hd_server_wait(hd_server *srv, uint64_t request_id, double timeout_s, hd_request_info *info);
 HD_API hd_status hd_server_stats_get(hd_server *srv, hd_server_stats *out);
+/* Device-time record of finished batches (the last 4096), oldest first: two
+ * batches ran on the device at the same time when their [start, end)
+ * intervals intersect.  start: the batch's first host-to-device copy began;
+ * end: its last device-to-host copy finished; both in ms of device time
+ * since the server was created (CUDA events on the slot's stream). */
+typedef struct {
+    uint64_t batch;               /* launch order, from 0 */
+    uint32_t slot;                /* execution slot (stream) it ran on */
+    uint32_t n_queries, n_requests;
+    double device_start_ms, device_end_ms;
+} hd_batch_record;
+HD_API hd_status hd_server_batch_log(hd_server *srv, hd_batch_record *out, uint32_t cap, uint32_t *n);
 /* Drains every queued request, then stops the scheduler. */
 HD_API void hd_server_destroy(hd_server *srv);
 
@@ -402,8 +428,14 @@ HD_API hd_status hd_search_host(hd_ctx *ctx, const hd_library *lib, const uint32
  * held by every GPU that loads libhd until the process exits.  A request
  * that needs more scratch than that (on a 152-SM GPU: above about 140,000
  * queries at 9 <= k <= 16, more at smaller k) is rejected with
- * HD_ERR_INVALID_ARG before any launch.  The first call on a device looks up the buffer's device address
- * (make that first call before any stream capture).  All calls share the
+ * HD_ERR_INVALID_ARG before any launch.
+ * Set-up: the first call on a device (n_q = 0 is enough; it launches
+ * nothing) looks up the buffer's device address, and with lazy module
+ * loading (the CUDA default) that lookup is what loads the buffer, so its
+ * 32 MiB are reserved then.  Make that call once per device at start-up,
+ * before reserving the rest of the device memory and before any stream
+ * capture.  The address is kept for the life of the process: do not use this
+ * entry point on a device after cudaDeviceReset.  All calls share the
  * buffer: calls whose kernels overlap on the GPU (other streams, other host
  * threads) race and corrupt each other -- serialise them.  Asynchronous. */
 HD_API hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_t *d_q_hv,
@@ -470,6 +502,31 @@ HD_API hd_status hd_library_inject_stall(hd_library *lib, uint32_t n_searches);
  * and forgets them.  hd_launch_count() is the number of kernels libhd has
  * launched in this process. */
 typedef enum { HD_KERNEL_ENCODE = 0, HD_KERNEL_SEARCH = 1, HD_KERNEL_KINDS = 2 } hd_kernel_kind;
+
+/* Instruction-rate microbenchmarks (no counterpart in the paper; the rates
+ * the search kernels are held to).  Synchronous; each kind runs one warm-up
+ * launch and `launches` (1..1000) timed launches on a stream of its own, on
+ * the current device, and reports operations per second.
+ *  HD_PEAK_TC_FP4 / _FP8 / _BF16  tcgen05.mma.cta_group::2 with M = 256,
+ *      N = 256 and 32 bytes of K per instruction (kind::f8f6f4 with e2m1 or
+ *      e4m3 operands, kind::f16 with bf16), the pair search's instruction
+ *      and shape, on operands resident in shared memory, one CTA per SM, all
+ *      SM pairs; an operation is a flop (2 per multiply-add).
+ *  HD_PEAK_POPC  32-bit population counts (the popcount form's counting
+ *      instruction, Section 4.1); an operation is one popcount.
+ *  HD_PEAK_LOP3  three-input logic operations on 32-bit words (the carry-save
+ *      popcount form's adder); an operation is one LOP3. */
+typedef enum { HD_PEAK_TC_FP4 = 0, HD_PEAK_TC_FP8 = 1, HD_PEAK_TC_BF16 = 2, HD_PEAK_POPC = 3,
+               HD_PEAK_LOP3 = 4 } hd_peak_kind;
+typedef struct {
+    double best_per_s;        /* operations per second of the fastest timed launch */
+    double median_per_s;      /* ... of the median timed launch */
+    double ms_best;           /* duration of the fastest timed launch */
+    uint64_t ops_per_launch;
+    uint32_t sms;             /* SMs the launch covered */
+    uint32_t launches;        /* timed launches */
+} hd_peak_result;
+HD_API hd_status hd_measure_peak(hd_peak_kind kind, uint32_t launches, hd_peak_result *out);
 HD_API hd_status hd_profile_enable(int on);
 HD_API hd_status hd_profile_collect(hd_kernel_kind kind, double *total_ms, uint32_t *launches);
 HD_API uint64_t hd_launch_count(void);

@@ -48,6 +48,7 @@ def _load():
             P = C.c_void_p
             u32, u64, dbl, i32 = C.c_uint32, C.c_uint64, C.c_double, C.c_int
             lib.orc_philox4x32_10.argtypes = [P, P, P]
+            lib.orc_random_words.argtypes = [u64, u32, u32, P]
             lib.orc_item_memory.argtypes = [u32, u32, u32, u32, u64, u32, P, P, P, P]
             lib.orc_preprocess.argtypes = [u32, P, P, P, dbl, dbl, dbl, u32, u32, dbl, u32, P, P, P]
             lib.orc_preprocess.restype = C.c_longlong
@@ -74,6 +75,15 @@ def philox4x32_10(ctr, key):
     c, k = _c(ctr, np.uint32), _c(key, np.uint32)
     out = np.zeros(4, np.uint32)
     _load().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def random_words(seed, stream, n):
+    """Words 0..n-1 of Philox word stream `stream` under `seed`: word i is
+    component i%4 of the block at counter (i/4, stream, 0, 0), key (seed low,
+    seed high) -- the random words the item memory draws from."""
+    out = np.zeros(int(n), np.uint32)
+    _load().orc_random_words(int(seed), int(stream), int(n), _p(out))
     return out
 
 

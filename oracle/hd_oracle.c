@@ -64,6 +64,12 @@ static uint32_t stream_word(uint64_t seed, uint32_t stream, uint32_t i)
     return out[i & 3u];
 }
 
+/* Words 0..n-1 of one stream, word by word from the definition above. */
+void orc_random_words(uint64_t seed, uint32_t stream, uint32_t n, uint32_t *out)
+{
+    for (uint32_t i = 0; i < n; ++i) out[i] = stream_word(seed, stream, i);
+}
+
 static int get_bit(const uint64_t *hv, uint32_t d) { return (int)((hv[d >> 6] >> (d & 63u)) & 1u); }
 static void set_bit(uint64_t *hv, uint32_t d, int b)
 {

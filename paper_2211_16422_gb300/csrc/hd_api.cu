@@ -351,6 +351,30 @@ hd_status hd_ctx_item_memory(const hd_ctx *ctx, uint64_t *d_F, uint64_t *d_L, ui
     return HD_OK;
 }
 
+hd_status hd_random_words(uint64_t seed, uint32_t stream_id, uint32_t n, uint32_t *d_out, hd_stream stream)
+{
+    if (n == 0) return HD_OK;
+    HD_CHECK(d_out, "hd_random_words: null output");
+    HD_CHECK(n <= 0xFFFFFFFCu, "hd_random_words: n too large");
+    hd_random_words_launch(seed, stream_id, n, d_out, (cudaStream_t)stream);
+    HD_CUDA_TRY(cudaGetLastError());
+    return HD_OK;
+}
+
+hd_status hd_measure_peak(hd_peak_kind kind, uint32_t launches, hd_peak_result *out)
+{
+    HD_CHECK(out, "hd_measure_peak: null result");
+    HD_CHECK(launches >= 1 && launches <= 1000, "hd_measure_peak: launches must be in [1, 1000]");
+    switch (kind) {
+    case HD_PEAK_TC_FP4: return hd_peak_mma_run(HD_FORM_TC_FP4, launches, out);
+    case HD_PEAK_TC_FP8: return hd_peak_mma_run(HD_FORM_TC_FP8, launches, out);
+    case HD_PEAK_TC_BF16: return hd_peak_mma_run(HD_FORM_TC_BF16, launches, out);
+    case HD_PEAK_POPC: return hd_peak_alu_run(true, launches, out);
+    case HD_PEAK_LOP3: return hd_peak_alu_run(false, launches, out);
+    }
+    return hd_fail(HD_ERR_INVALID_ARG, "hd_measure_peak: unknown kind");
+}
+
 hd_status hd_ctx_status(hd_ctx *ctx)
 {
     HD_CHECK(ctx, "hd_ctx_status: null ctx");
@@ -703,15 +727,15 @@ hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t
 {
     HD_CHECK(lib, "hd_library_set_schedule: null library");
     HD_CHECK(tile_group <= 4096 && super_group <= 4096, "hd_library_set_schedule: values must be <= 4096");
-    HD_CHECK(cluster == 0 || cluster == 1 || cluster == 2 || cluster == 4,
-             "hd_library_set_schedule: cluster must be 0, 1, 2 or 4");
+    HD_CHECK(cluster <= 2, "hd_library_set_schedule: cluster must be 0, 1 or 2");
     HD_CHECK(cta_group <= 2, "hd_library_set_schedule: cta_group must be 0, 1 or 2");
-    HD_CHECK(cta_group != 2 || cluster == 0 || cluster == 2,
-             "hd_library_set_schedule: cta_group 2 needs a cluster of 2");
+    HD_CHECK(cluster == 0 || cta_group == 0 || cluster == cta_group,
+             "hd_library_set_schedule: the cluster is the SM pair (2, 2) or one SM (1, 1)");
+    const uint32_t cg = cta_group ? cta_group : (cluster == 1 ? 1u : 2u);
     lib->mma_tuning.tile_group = tile_group;
     lib->mma_tuning.super_group = super_group;
-    lib->mma_tuning.cluster = cta_group == 2 ? 2u : cluster;
-    lib->mma_tuning.cta_group = cta_group;
+    lib->mma_tuning.cluster = cg;
+    lib->mma_tuning.cta_group = cg;
     return HD_OK;
 }
 

@@ -59,7 +59,7 @@ struct hd_ctx {
 struct hd_mma_tuning {
     uint32_t tile_group = 0;
     uint32_t super_group = 0;
-    uint32_t cluster = 0;    // CTAs per cluster sharing reference tiles by multicast: 1, 2, 4
+    uint32_t cluster = 0;    // CTAs per cluster: 2 for the SM pair, 1 for one SM
     uint32_t cta_group = 0;  // 2: SM pairs issue M = 256 MMAs (cluster of 2); 0/1: one SM per MMA
 };
 
@@ -129,6 +129,7 @@ struct hd_arena {
 // Launchers implemented in the other translation units.
 // ---------------------------------------------------------------------------
 hd_status hd_item_memory_build(hd_ctx *ctx, cudaStream_t s);
+void hd_random_words_launch(uint64_t seed, uint32_t stream, uint32_t n, uint32_t *out, cudaStream_t s);
 
 hd_status hd_preprocess_launch(const hd_preprocess_params &pp, const uint32_t *raw_off,
                                const double *raw_mz, const double *raw_int, uint32_t n,
@@ -183,6 +184,8 @@ hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv
 
 // Tensor-core form: the bipolar copy of the library rows, and the search.
 hd_status hd_library_expand(hd_library *lib, hd_search_form form, cudaStream_t s);
+hd_status hd_peak_mma_run(hd_search_form form, uint32_t launches, hd_peak_result *out);
+hd_status hd_peak_alu_run(bool popc, uint32_t launches, hd_peak_result *out);
 hd_status hd_search_mma_run(const hd_library *lib, hd_search_form form, const uint64_t *q_hv, const double *q_mz,
                             const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
                             uint32_t *out_idx, uint16_t *out_dist, cudaStream_t s);

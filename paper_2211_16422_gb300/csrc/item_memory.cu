@@ -136,6 +136,12 @@ __global__ void k_random_table(uint64_t seed, uint32_t D, uint32_t rows, uint64_
 
 }  // namespace
 
+void hd_random_words_launch(uint64_t seed, uint32_t stream, uint32_t n, uint32_t *out, cudaStream_t s)
+{
+    const uint32_t blocks = hd_ceil_div(n, 4);
+    hd_count_launches(1), k_stream_words<<<hd_ceil_div(blocks, 256), 256, 0, s>>>(seed, stream, n, out);
+}
+
 hd_status hd_item_memory_build(hd_ctx *ctx, cudaStream_t s)
 {
     const uint32_t D = ctx->p.dim;
@@ -143,10 +149,7 @@ hd_status hd_item_memory_build(hd_ctx *ctx, cudaStream_t s)
     HD_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(uint32_t) * (size_t)(D / 32 + D) * 2, s));
     uint32_t *F0 = tmp, *keyF = F0 + D / 32, *L0 = keyF + D, *keyL = L0 + D / 32;
     const uint64_t seed = ctx->p.seed;
-    auto words = [&](uint32_t stream, uint32_t n, uint32_t *out) {
-        const uint32_t blocks = hd_ceil_div(n, 4);
-        hd_count_launches(1), k_stream_words<<<hd_ceil_div(blocks, 256), 256, 0, s>>>(seed, stream, n, out);
-    };
+    auto words = [&](uint32_t stream, uint32_t n, uint32_t *out) { hd_random_words_launch(seed, stream, n, out, s); };
     words(0, D / 32, F0);
     words(1, D, keyF);
     words(2, D / 32, L0);

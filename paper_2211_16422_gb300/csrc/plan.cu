@@ -142,7 +142,7 @@ hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const dou
     std::vector<hd_tune_result> cand;
     cand.push_back({HD_FORM_POPC, 0, 0, 0, 0, 0.0});
     const uint32_t tgs[3] = {4, 16, 32}, sgs[2] = {2, 16};
-    const uint32_t shapes[4][2] = {{1, 1}, {2, 1}, {4, 1}, {2, 2}};   // (cluster, cta_group)
+    const uint32_t shapes[2][2] = {{1, 1}, {2, 2}};   // (cluster, cta_group): one SM, or the SM pair
     for (hd_search_form f : {HD_FORM_TC_FP4, HD_FORM_TC_FP8, HD_FORM_TC_BF16}) {
         if ((f == HD_FORM_TC_FP8 && !lib->x_fp8) || (f == HD_FORM_TC_BF16 && !lib->x_bf16) ||
             (f == HD_FORM_TC_FP4 && !lib->x_fp4))

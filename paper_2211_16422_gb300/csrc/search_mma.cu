@@ -27,8 +27,8 @@
 //               buffer is handed back while the next tile is accumulated in
 //               the other one.
 // k_search_mma: 192 threads (4 epilogue warps), M = 128, N = 256 per CTA, 4
-// stages of 48 KB; clusters of 1, 2 or 4 CTAs share each reference tile by
-// TMA multicast.
+// stages of 48 KB, one CTA per SM with no cluster; every load goes to the
+// issuing CTA's own shared memory.
 // k_search_mma2 (default): 192 threads (HD_MMA2_EPI_WARPS = 8 splits each
 // quarter's columns over two warps), SM pairs, tcgen05.mma.cta_group::2 with
 // M = 256, N = 256 issued by the even CTA; each CTA stages its own query block
@@ -38,6 +38,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "hd_internal.cuh"
 #include "search_common.cuh"
@@ -167,28 +168,6 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
         "%3}], [%4];" ::"r"(smem_addr(dst)),
         "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// The same load delivered to the same shared-memory offset (and mbarrier) of
-// every CTA in `mask` of the cluster.
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int32_t x, int32_t y,
-                                               uint64_t *bar, uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
-        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar)), "h"(mask)
-        : "memory");
-}
-
-// tcgen05.commit arriving on the same-offset mbarrier of every CTA in `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_addr(bar)),
-        "h"(mask)
         : "memory");
 }
 
@@ -323,11 +302,9 @@ __device__ __forceinline__ void score_group(const uint32_t (&v)[32], uint32_t c0
 }
 __device__ __forceinline__ void epi_bar2() { asm volatile("bar.sync 1, %0;" ::"r"(EPI2_THREADS) : "memory"); }
 
-// CS > 1: clusters of CS CTAs take CS consecutive query blocks of one work
-// item and sweep the same reference tiles; each CTA loads 1/CS of every B
-// tile and multicasts it into all of them, so L2 serves each tile once per
-// cluster.  Stage-free barriers count the MMA commits of every CTA.
-template <int K, int FMT, int CS>
+// One CTA per SM: each CTA stages its own query block and whole reference
+// tiles, and its MMAs commit to its own barriers.
+template <int K, int FMT>
 __global__ void __launch_bounds__(THREADS, 1)
 k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
@@ -345,7 +322,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], CS);
+            mbar_init(&empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
@@ -361,13 +338,9 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     }
     tc_fence_before();
     __syncthreads();
-    if (CS > 1) cluster_sync();   // peers' barriers are initialised before any multicast
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t crank = CS > 1 ? cluster_rank() : 0u;
-    const uint32_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
-    constexpr uint16_t CMASK = (uint16_t)((1u << CS) - 1u);
-    constexpr uint32_t B_PART = B_BYTES / CS;
+    const uint32_t cid = blockIdx.x, ncl = gridDim.x;
 
     const uint32_t total = a.pair_start[a.n_pairs];
     const uint32_t nchunks = a.row_bytes / KB;
@@ -392,12 +365,8 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
                         uint8_t *sa = smem + s * STAGE_BYTES, *sb = sa + A_BYTES;
                         mbar_expect_tx(&full[s], tx_bytes(FMT, STAGE_BYTES));
                         if (a.stall && it == 0) continue;   // nothing ever completes this stage
-                        tma_load_2d(sa, &qmap, (int32_t)(c * KB), (int32_t)((b * CS + crank) * TM), &full[s]);
-                        if (CS == 1)
-                            tma_load_2d(sb, &lmap, (int32_t)(c * KB), r0, &full[s]);
-                        else
-                            tma_load_2d_mc(sb + crank * B_PART, &lmap, (int32_t)(c * KB),
-                                           r0 + (int32_t)(crank * (TN / CS)), &full[s], CMASK);
+                        tma_load_2d(sa, &qmap, (int32_t)(c * KB), (int32_t)(b * TM), &full[s]);
+                        tma_load_2d(sb, &lmap, (int32_t)(c * KB), r0, &full[s]);
                     }
                 }
             }
@@ -425,8 +394,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
 #pragma unroll
                         for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
                             mma_issue<FMT>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
-                        if (CS == 1) mma_commit(&empty[s]);
-                        else mma_commit_mc(&empty[s], CMASK);
+                        mma_commit(&empty[s]);
                     }
                     if (!ok) break;
                     mma_commit(&acc_full[buf]);
@@ -447,7 +415,7 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
         for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
             uint32_t b, t0, t1;
             item_range(a, item, b, t0, t1);
-            const uint32_t sb_ = b * CS + crank;     // this CTA's query block
+            const uint32_t sb_ = b;                  // this CTA's query block
             const uint32_t sq = sb_ * TM + row;
             const uint32_t lo = sq < a.n_q ? a.lo[sq] : 0u, hi = sq < a.n_q ? a.hi[sq] : 0u;
             // last key of the query's running top-k (merged from its finished items)
@@ -509,17 +477,13 @@ k_search_mma(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ C
     }
     tc_fence_before();
     __syncthreads();
-    if (CS > 1) {
-        cluster_sync();   // every peer has stopped issuing multicast loads
-        // After a give-up anywhere in the grid, loads that a peer issued before
-        // the barrier may still be landing in this CTA's shared memory: pause
-        // (bounded, 200 us) so that they complete before the CTA exits.
-        if (threadIdx.x == 0 && (*abort_flag || (a.status && (atomicOr_system(a.status, 0u) & HD_DEV_TIMEOUT) != 0u))) {
-            const uint64_t w0 = hd_globaltimer_ns();
-            while (hd_globaltimer_ns() - w0 < 200000ull) __nanosleep(1000);
-        }
-        __syncthreads();
+    // after a give-up, loads this CTA issued before it stopped may still be
+    // landing in its shared memory: a bounded pause (200 us) lets them complete
+    if (threadIdx.x == 0 && *abort_flag) {
+        const uint64_t w0 = hd_globaltimer_ns();
+        while (hd_globaltimer_ns() - w0 < 200000ull) __nanosleep(1000);
     }
+    __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
@@ -890,6 +854,80 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
     if (warp == 1) tmem_dealloc2(tmem, TMEM2_COLS);
 }
 
+// ------------------------------------------------- tensor-pipe microbenchmark
+// The pair form's tensor-core instruction alone, as the roofline of the
+// search: tcgen05.mma.cta_group::2 with M = 256, N = 256 and 32 bytes of K per
+// instruction (the search's shape, descriptors and instruction descriptor),
+// on +-1 operands already resident in shared memory (no global traffic),
+// issued back to back by rank 0 of every SM pair.  As in the search at
+// D = 8192, 256 instructions accumulate into one of two 256-column
+// accumulators before the other one is used.  160 KB of dynamic shared memory
+// keep one CTA per SM.
+constexpr uint32_t PEAK_SMEM_BYTES = 160u * 1024u;
+constexpr int PEAK_THREADS = 128;
+template <int FMT>
+__global__ void __launch_bounds__(PEAK_THREADS, 1) k_peak_mma2(uint32_t iters, uint64_t wait_ns, uint32_t *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *done = reinterpret_cast<uint64_t *>(smem + A_BYTES + B2_BYTES);
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t crank = cluster_rank();
+    // +-1 in the operand format: e4m3 0x38 / 0xB8, e2m1 codes 0x2 / 0xA, bf16 0x3F80 / 0xBF80
+    uint32_t *w = reinterpret_cast<uint32_t *>(smem);
+    for (uint32_t i = threadIdx.x; i < (A_BYTES + B2_BYTES) / 4; i += blockDim.x) {
+        const bool neg = ((i * 2654435761u) >> 31) != 0u;
+        w[i] = FMT == FMT_BF16 ? (neg ? 0xBF80BF80u : 0x3F803F80u)
+             : FMT == FMT_E4M3 ? (neg ? 0xB8B8B8B8u : 0x38383838u)
+                               : (neg ? 0x0A0A0A0Au : 0x02020202u);
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc2(&s_tmem, TMEM2_COLS);
+        tmem_relinquish2();
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands visible to the tensor core
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (threadIdx.x == 0 && ld_cluster_u32(cluster_addr(&s_tmem, crank ^ 1u)) != tmem) {
+        s_abort = 1;
+        hd_flag(status, HD_DEV_TMEM);
+    }
+    __syncthreads();
+    const bool run = s_abort == 0;
+    if (warp == 1 && lane == 0 && run) {
+        if (crank == 0) {
+            constexpr uint32_t idesc = instr_desc2<FMT>();
+            const uint32_t sa = smem_addr(smem), sb = sa + A_BYTES;
+            const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
+            for (uint32_t it = 0; it < iters; ++it) {
+                const uint32_t d_tmem = tmem + ((it >> 6) & 1u) * TN;
+#pragma unroll
+                for (uint32_t j = 0; j < KB / 32; ++j)
+                    mma_issue2<FMT>(d_tmem, da + 2 * j, db + 2 * j, idesc, ((it & 63u) | j) != 0);
+            }
+            mma_commit2_mc(done, 0x3);
+        }
+        // every MMA of the pair has finished before either CTA frees its tensor memory
+        if (!mbar_wait(done, 0, wait_ns)) hd_flag(status, HD_DEV_TIMEOUT);
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc2(tmem, TMEM2_COLS);
+}
+
 // Work list of the L2-blocked schedule (one CTA of 1024 threads): per query
 // block the absolute tile range covering the union of its windows, then the
 // item count of every (super-group, block) pair and its exclusive scan.
@@ -1155,15 +1193,14 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
                   cudaStream_t s, const hd_mma_tuning &tune, const dot_io *dot = nullptr)
 {
     const bool pair = tune.cta_group == 2;   // SM pairs, M = 256 (cluster of 2)
-    const uint32_t cs = pair ? 2u : tune.cluster;   // 1, 2 or 4 CTAs per cluster
+    const uint32_t cs = pair ? 2u : 1u;      // CTAs per cluster
     const uint32_t n_blocks = (n_q + TM * cs - 1) / (TM * cs);
     // shared-memory bytes of one operand row (the K extent the kernel walks) and HBM bytes
     const uint32_t row_bytes = lib->dim * (FMT == FMT_BF16 ? 2u : 1u);
     const uint32_t g_row_bytes = global_row_bytes<FMT>(lib->dim);
     const uint8_t *lib_x = FMT == FMT_BF16 ? lib->x_bf16 : (FMT == FMT_E4M3 ? lib->x_fp8 : lib->x_fp4);
     if (!lib_x) return hd_fail(HD_ERR_INVALID_ARG, "library not prepared for this tensor-core form");
-    auto kern = pair ? k_search_mma2<K, FMT>
-                     : (cs == 4 ? k_search_mma<K, FMT, 4> : (cs == 2 ? k_search_mma<K, FMT, 2> : k_search_mma<K, FMT, 1>));
+    auto kern = pair ? k_search_mma2<K, FMT> : k_search_mma<K, FMT>;
     const uint32_t smem_bytes = pair ? SMEM2_BYTES : SMEM_BYTES;
     const uint32_t threads = pair ? (uint32_t)THREADS2 : (uint32_t)THREADS;
     HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
@@ -1335,8 +1372,8 @@ hd_status hd_search_mma_run(const hd_library *lib, hd_search_form form, const ui
     hd_mma_tuning tu = lib->mma_tuning;
     if (tu.tile_group == 0) tu.tile_group = 16;
     if (tu.super_group == 0) tu.super_group = 16;
-    if (tu.cluster != 1 && tu.cluster != 2 && tu.cluster != 4) tu.cluster = 2;
-    if (tu.cta_group == 0) tu.cta_group = tu.cluster == 2 ? 2u : 1u;   // default: SM pairs
+    if (tu.cta_group != 1) tu.cta_group = 2;   // default: SM pairs
+    tu.cluster = tu.cta_group;
     const int fmt = form_fmt(form);
     if (fmt == FMT_E4M3) return run_fmt<FMT_E4M3>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
     if (fmt == FMT_BF16) return run_fmt<FMT_BF16>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
@@ -1356,11 +1393,81 @@ hd_status hd_search_mma_dot_run(const hd_library *lib, hd_search_form form, cons
     hd_mma_tuning tu = lib->mma_tuning;
     if (tu.tile_group == 0) tu.tile_group = 16;
     if (tu.super_group == 0) tu.super_group = 16;
-    if (tu.cluster != 1 && tu.cluster != 2 && tu.cluster != 4) tu.cluster = 2;
-    if (tu.cta_group == 0) tu.cta_group = tu.cluster == 2 ? 2u : 1u;
+    if (tu.cta_group != 1) tu.cta_group = 2;   // default: SM pairs
+    tu.cluster = tu.cta_group;
     const dot_io io{q_comp, out_score};
     const int fmt = form_fmt(form);
     if (fmt == FMT_E4M3) return run_fmt<FMT_E4M3>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
     if (fmt == FMT_BF16) return run_fmt<FMT_BF16>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
     return run_fmt<FMT_E2M1>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
+}
+
+hd_status hd_peak_mma_run(hd_search_form form, uint32_t launches, hd_peak_result *out)
+{
+    const int fmt = form_fmt(form);
+    auto kern = fmt == FMT_BF16 ? k_peak_mma2<FMT_BF16> : (fmt == FMT_E4M3 ? k_peak_mma2<FMT_E4M3> : k_peak_mma2<FMT_E2M1>);
+    int dev = 0, n_sms = 0;
+    HD_CUDA_TRY(cudaGetDevice(&dev));
+    HD_CUDA_TRY(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+    HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PEAK_SMEM_BYTES));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((uint32_t)n_sms / 2u * 2u);
+    cfg.blockDim = dim3(PEAK_THREADS);
+    cfg.dynamicSmemBytes = PEAK_SMEM_BYTES;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n_cl = 0;
+    HD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg));
+    if (n_cl < 1) return hd_fail(HD_ERR_UNSUPPORTED, "peak kernel: SM-pair cluster does not fit on this GPU");
+    cfg.gridDim = dim3(std::min((uint32_t)n_sms / 2u, (uint32_t)n_cl) * 2u);
+    const uint32_t iters = 16384;   // 65,536 instructions per SM pair
+    const uint32_t k_per_instr = fmt == FMT_BF16 ? 16u : 32u;
+    const uint64_t flops = (uint64_t)(cfg.gridDim.x / 2) * iters * (KB / 32) * 2ull * (2 * TM) * TN * k_per_instr;
+    uint32_t *status = nullptr;
+    HD_CUDA_TRY(cudaMalloc(&status, sizeof(uint32_t)));
+    HD_CUDA_TRY(cudaMemset(status, 0, sizeof(uint32_t)));
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cfg.stream = s;
+    std::vector<double> ms;
+    hd_status st = HD_OK;
+    for (uint32_t r = 0; r <= launches && st == HD_OK; ++r) {   // launch 0 warms up
+        cudaEventRecord(e0, s);
+        hd_count_launches(1);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, iters, (uint64_t)HD_WAIT_NS, status);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = hd_cuda_fail(e, "peak kernel launch");
+            break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0) ms.push_back(t);
+    }
+    uint32_t flags = 0;
+    if (st == HD_OK && cudaMemcpy(&flags, status, sizeof(flags), cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = hd_fail(HD_ERR_CUDA, "peak kernel: status read failed");
+    if (st == HD_OK && flags) st = hd_fail(flags & HD_DEV_TIMEOUT ? HD_ERR_TIMEOUT : HD_ERR_CUDA, "peak kernel: device wait failed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    cudaFree(status);
+    if (st != HD_OK) return st;
+    std::sort(ms.begin(), ms.end());
+    out->ops_per_launch = flops;
+    out->ms_best = ms.front();
+    out->best_per_s = (double)flops / (ms.front() * 1e-3);
+    out->median_per_s = (double)flops / (ms[ms.size() / 2] * 1e-3);
+    out->sms = cfg.gridDim.x;
+    out->launches = (uint32_t)ms.size();
+    return HD_OK;
 }

@@ -14,7 +14,12 @@
 // process exits.  In host code the array's name is only a host-side stand-in,
 // not a device address, so its device address is looked up with
 // cudaGetSymbolAddress -- once per device, with that device current, on the
-// first call made on that device -- and that address is what the kernels get.
+// first call made on that device, even one with no queries -- and that
+// address is what the kernels get.  With lazy module loading that lookup is
+// what loads this file's module and reserves the 32 MiB, so callers make a
+// first call at start-up, before the rest of their memory is reserved and
+// before any stream capture.  The cached address would be stale after
+// cudaDeviceReset, which callers of this entry point must not do.
 //
 // All calls share the one array and it keeps whatever the last call left in
 // it.  Every piece of it is written before it is read within a call (the work
@@ -67,17 +72,18 @@ extern "C" hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_
         return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: tol must be finite and >= 0");
     if (unit != HD_TOL_DA && unit != HD_TOL_PPM && unit != HD_TOL_MASS)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: bad unit");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != lib->device)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: library belongs to another device");
+    // set-up first, so that a call with no queries prepares the device
+    void *scratch = nullptr;
+    const hd_status st = scratch_address(dev, &scratch);
+    if (st != HD_OK) return st;
     if (n_q == 0) return HD_OK;
     if (!d_q_hv || !d_q_mz || !d_q_charge || !d_out_idx || !d_out_dist)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: null buffer");
     if (reinterpret_cast<uintptr_t>(d_q_hv) & 15u)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: d_q_hv must be 16-byte aligned");
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev != lib->device)
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_search_open_noalloc: library belongs to another device");
-    void *scratch = nullptr;
-    const hd_status st = scratch_address(dev, &scratch);
-    if (st != HD_OK) return st;
     return hd_search_popc_run_scratch(lib, d_q_hv, d_q_mz, d_q_charge, n_q,
                                       hd_single_window(tol, unit), k,
                                       d_out_idx, d_out_dist, (cudaStream_t)stream, scratch,

@@ -15,6 +15,8 @@
 //      a per-query top-k of (distance, input index) keys, merged across the
 //      warp with shuffles;
 //   5. merge the items of each block and scatter to the caller's order.
+#include <vector>
+#include <algorithm>
 #include "hd_internal.cuh"
 #include "search_common.cuh"
 
@@ -341,4 +343,94 @@ hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv
     if (k <= 8) return HD_RUN_K(8);
     return HD_RUN_K(16);
 #undef HD_RUN_K
+}
+
+// ----------------------------------------------- integer-pipe microbenchmarks
+// Sixteen independent chains per thread, 32 warps per SM.  k_peak_popc: one
+// population count of a 32-bit word per step (plus the XOR that makes the
+// word and the add that keeps the count, both on the ALU pipes, which issue
+// four times as many per clock): the popcount unit's rate.  k_peak_lop3: one
+// three-input LOP3 per step: the integer logic pipe's rate.
+namespace {
+constexpr uint32_t PEAK_ALU_THREADS = 256;
+__global__ void __launch_bounds__(PEAK_ALU_THREADS) k_peak_popc(uint32_t iters, uint32_t seed, uint32_t *sink)
+{
+    uint32_t v[16], acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = (seed + (blockIdx.x * blockDim.x + threadIdx.x) * 16u + (uint32_t)i) * 0x9E3779B9u;
+        acc[i] = 0u;
+    }
+#pragma unroll 4
+    for (uint32_t it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[i] += __popc(v[i] ^ it);
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t += acc[i];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+__global__ void __launch_bounds__(PEAK_ALU_THREADS) k_peak_lop3(uint32_t iters, uint32_t seed, uint32_t *sink)
+{
+    uint32_t v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = (seed + (blockIdx.x * blockDim.x + threadIdx.x) * 16u + (uint32_t)i) * 0x9E3779B9u;
+#pragma unroll 4
+    for (uint32_t it = 0; it < iters; ++it)
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(v[i]) : "r"(v[(i + 1) & 15]), "r"(v[(i + 5) & 15]));
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t ^= v[i];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+}  // namespace
+
+hd_status hd_peak_alu_run(bool popc, uint32_t launches, hd_peak_result *out)
+{
+    int dev = 0, n_sms = 0;
+    HD_CUDA_TRY(cudaGetDevice(&dev));
+    HD_CUDA_TRY(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
+    const uint32_t grid = (uint32_t)n_sms * 4u;   // 4 CTAs of 8 warps per SM
+    const uint32_t iters = popc ? 8192u : 16384u;
+    const uint64_t ops = (uint64_t)grid * PEAK_ALU_THREADS * iters * 16u;
+    uint32_t *sink = nullptr;
+    HD_CUDA_TRY(cudaMalloc(&sink, (size_t)grid * PEAK_ALU_THREADS * sizeof(uint32_t)));
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<double> ms;
+    hd_status st = HD_OK;
+    for (uint32_t r = 0; r <= launches; ++r) {   // launch 0 warms up
+        cudaEventRecord(e0, s);
+        hd_count_launches(1);
+        if (popc) k_peak_popc<<<grid, PEAK_ALU_THREADS, 0, s>>>(iters, r, sink);
+        else k_peak_lop3<<<grid, PEAK_ALU_THREADS, 0, s>>>(iters, r, sink);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = hd_cuda_fail(e, "integer peak kernel");
+            break;
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0) ms.push_back(t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    cudaFree(sink);
+    if (st != HD_OK) return st;
+    std::sort(ms.begin(), ms.end());
+    out->ops_per_launch = ops;
+    out->ms_best = ms.front();
+    out->best_per_s = (double)ops / (ms.front() * 1e-3);
+    out->median_per_s = (double)ops / (ms[ms.size() / 2] * 1e-3);
+    out->sms = (uint32_t)n_sms;
+    out->launches = (uint32_t)ms.size();
+    return HD_OK;
 }

@@ -12,6 +12,7 @@
 // that arrives while others run joins the next batch that starts.  Results
 // are exactly those of searching each request alone: the top-k of a query
 // depends only on that query.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -71,8 +72,11 @@ struct pinned {
 };
 
 struct slot {
+    uint32_t index = 0;
+    uint64_t batch = 0;               // number of the batch in flight
     cudaStream_t stream = nullptr;
-    cudaEvent_t done_ev = nullptr;
+    cudaEvent_t start_ev = nullptr;   // recorded before the batch's first copy
+    cudaEvent_t done_ev = nullptr;    // recorded after its last copy
     pinned<uint32_t> off, bins, out_idx;
     pinned<uint8_t> lv, z, cls;
     pinned<double> mz;
@@ -100,6 +104,9 @@ struct hd_server {
     uint64_t next_id = 1;
     hd_server_stats stats{};
     uint32_t busy_slots = 0;
+    cudaEvent_t ref_ev = nullptr;                 // device-time origin of the batch log
+    std::deque<hd_batch_record> log;              // the last HD_SERVER_LOG_CAP finished batches
+    static constexpr size_t HD_SERVER_LOG_CAP = 4096;
 
     // Launches the requests in `batch` on slot `s`.  Called with `mu` held.
     hd_status launch(slot &s, std::vector<req_ptr> &batch)
@@ -166,6 +173,7 @@ struct hd_server {
         carve(ar, &d_off, &d_bins, &d_lv, &d_mz, &d_z, &d_cls, &d_hv, &d_oi, &d_od);
         win.cls = wins.size() > 1 ? d_cls : nullptr;
         const auto H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+        cudaEventRecord(s.start_ev, s.stream);
         cudaError_t e = cudaMemcpyAsync(d_off, s.off.p, (size_t)(nq + 1) * 4, H2D, s.stream);
         if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_bins, s.bins.p, (size_t)nnz * 4, H2D, s.stream);
         if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_lv, s.lv.p, nnz, H2D, s.stream);
@@ -200,6 +208,16 @@ struct hd_server {
             const hd_status ls = hd_library_status(const_cast<hd_library *>(lib));
             const hd_status cs = hd_ctx_status(ctx);
             st = ls != HD_OK ? ls : cs;
+        }
+        if (st == HD_OK) {   // the batch's device-time interval, for the overlap record
+            float a = 0.f, b = 0.f;
+            if (cudaEventElapsedTime(&a, ref_ev, s.start_ev) == cudaSuccess &&
+                cudaEventElapsedTime(&b, ref_ev, s.done_ev) == cudaSuccess) {
+                uint32_t nq = 0;
+                for (auto &rp : s.reqs) nq += rp->n_q;
+                log.push_back(hd_batch_record{s.batch, s.index, nq, (uint32_t)s.reqs.size(), (double)a, (double)b});
+                if (log.size() > HD_SERVER_LOG_CAP) log.pop_front();
+            }
         }
         for (auto &rp : s.reqs) {
             auto &r = *rp;
@@ -262,6 +280,7 @@ struct hd_server {
                 }
                 sp->reqs = batch;
                 sp->bytes = bytes;
+                sp->batch = stats.batches;
                 sp->busy = true;
                 ++busy_slots;
                 inflight_bytes += bytes;
@@ -303,10 +322,15 @@ hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_p
     srv->budget = params->mem_budget_bytes ? (size_t)params->mem_budget_bytes : free_b / 2;
     for (uint32_t i = 0; i < params->slots; ++i) {
         auto sl = std::make_unique<slot>();
+        sl->index = i;
         HD_CUDA_TRY(cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking));
-        HD_CUDA_TRY(cudaEventCreateWithFlags(&sl->done_ev, cudaEventDisableTiming));
+        HD_CUDA_TRY(cudaEventCreate(&sl->start_ev));
+        HD_CUDA_TRY(cudaEventCreate(&sl->done_ev));
         srv->slots.push_back(std::move(sl));
     }
+    HD_CUDA_TRY(cudaEventCreate(&srv->ref_ev));
+    HD_CUDA_TRY(cudaEventRecord(srv->ref_ev, srv->slots[0]->stream));
+    HD_CUDA_TRY(cudaEventSynchronize(srv->ref_ev));
     hd_server *s = srv.release();
     s->th = std::thread([s] { s->loop(); });
     *out = s;
@@ -373,6 +397,16 @@ hd_status hd_server_wait(hd_server *s, uint64_t id, double timeout_s, hd_request
     return HD_OK;
 }
 
+hd_status hd_server_batch_log(hd_server *s, hd_batch_record *out, uint32_t cap, uint32_t *n)
+{
+    if (!s || !n || (cap && !out)) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_batch_log: null argument");
+    std::lock_guard<std::mutex> g(s->mu);
+    const uint32_t m = (uint32_t)std::min<size_t>(cap, s->log.size());
+    for (uint32_t i = 0; i < m; ++i) out[i] = s->log[s->log.size() - m + i];
+    *n = m;
+    return HD_OK;
+}
+
 hd_status hd_server_stats_get(hd_server *s, hd_server_stats *out)
 {
     if (!s || !out) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_stats_get: null argument");
@@ -395,8 +429,10 @@ void hd_server_destroy(hd_server *s)
             cudaStreamSynchronize(sl->stream);
             cudaStreamDestroy(sl->stream);
         }
+        if (sl->start_ev) cudaEventDestroy(sl->start_ev);
         if (sl->done_ev) cudaEventDestroy(sl->done_ev);
     }
+    if (s->ref_ev) cudaEventDestroy(s->ref_ev);
     delete s;
 }
 

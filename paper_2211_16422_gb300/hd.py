@@ -72,6 +72,7 @@ _SIGS = {
     "hd_ctx_destroy": ([P], None),
     "hd_ctx_item_memory": ([P, P, P, P, P, P], i32),
     "hd_ctx_status": ([P], i32),
+    "hd_random_words": ([u64, u32, u32, P, P], i32),
     "hd_preprocess": ([P, P, P, P, P, u32, P, P, P, P], i32),
     "hd_encode": ([P, P, P, P, u32, P, P], i32),
     "hd_build_library": ([P, P, P, P, u32, P], i32),
@@ -102,10 +103,12 @@ _SIGS = {
     "hd_server_submit": ([P, P, P, P, P, P, u32, dbl, i32, P, P, P], i32),
     "hd_server_wait": ([P, u64, dbl, P], i32),
     "hd_server_stats_get": ([P, P], i32),
+    "hd_server_batch_log": ([P, P, u32, P], i32),
     "hd_server_destroy": ([P], None),
     "hd_profile_enable": ([i32], i32),
     "hd_profile_collect": ([i32, P, P], i32),
     "hd_launch_count": ([], u64),
+    "hd_measure_peak": ([i32, u32, P], i32),
     "hd_encode_multibit": ([P, P, P, P, u32, u32, P, P], i32),
     "hd_build_library_multibit": ([P, P, P, P, u32, u32, P], i32),
     "hd_library_component_bits": ([P, P], i32),
@@ -162,6 +165,37 @@ def _dev(t, dtype, name):
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     return t.contiguous()
+
+
+def _out(t, dtype, n_elems, name):
+    """A caller's output tensor: written in place by the kernels, so it must be a
+    contiguous CUDA tensor of `dtype` with room for n_elems elements (a copy made
+    here would receive the results instead of the caller's tensor)."""
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < n_elems:
+        raise ValueError(f"{name} holds {t.numel()} elements, {n_elems} needed")
+    return t
+
+
+def _need(t, n_elems, name):
+    """An input tensor must hold at least n_elems elements (the kernels read that many)."""
+    if t.numel() < n_elems:
+        raise ValueError(f"{name} holds {t.numel()} elements, {n_elems} needed")
+    return t
+
+
+def _results(n, k, out_idx, out_dist, dist_dtype=torch.int16, dist_name="out_dist"):
+    """Output buffers of a top-k search: the caller's (checked) or new ones."""
+    if out_idx is None:
+        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    if out_dist is None:
+        out_dist = torch.empty((n, k), dtype=dist_dtype, device="cuda")
+    return _out(out_idx, torch.int32, n * k, "out_idx"), _out(out_dist, dist_dtype, n * k, dist_name)
 
 
 def _unit(unit) -> int:
@@ -239,6 +273,16 @@ def hd_ctx_item_memory(ctx: Ctx, stream=None):
     return F, L, rF, rL
 
 
+def hd_random_words(seed: int, stream_id: int, n: int, out=None, stream=None):
+    """Words 0..n-1 of Philox4x32-10 word stream `stream_id` under `seed` (int32 [n] holding
+    the uint32 words; read them with as_u32)."""
+    if out is None:
+        out = torch.empty(int(n), dtype=torch.int32, device="cuda")
+    _out(out, torch.int32, int(n), "out")
+    _check(load().hd_random_words(int(seed), int(stream_id), int(n), _ptr(out), _stream(stream)))
+    return out
+
+
 def hd_preprocess(ctx: Ctx, raw_off, raw_mz, raw_int, *, mz_min, mz_max, bin_width, n_bins, max_peaks,
                   n_levels, min_rel_intensity=0.01, stream=None):
     """Raw peak CSR on the device -> (offsets i32 [n+1], bins i32 [cap], levels u8 [cap]); the
@@ -264,6 +308,7 @@ def hd_encode(ctx: Ctx, offsets, bins, levels, out=None, stream=None):
     n = offsets.numel() - 1
     if out is None:
         out = torch.empty((n, ctx.dim // 64), dtype=torch.int64, device="cuda")
+    _out(out, torch.int64, n * (ctx.dim // 64), "out")
     _check(load().hd_encode(ctx.handle, _ptr(offsets), _ptr(bins), _ptr(levels), n, _ptr(out), _stream(stream)))
     return out
 
@@ -287,6 +332,7 @@ def hd_encode_multibit(ctx: Ctx, offsets, bins, levels, bits, out=None, stream=N
     n = offsets.numel() - 1
     if out is None:
         out = torch.empty((n, ctx.dim), dtype=torch.int8, device="cuda")
+    _out(out, torch.int8, n * ctx.dim, "out")
     _check(load().hd_encode_multibit(ctx.handle, _ptr(offsets), _ptr(bins), _ptr(levels), n, int(bits), _ptr(out),
                                      _stream(stream)))
     return out
@@ -319,10 +365,9 @@ def hd_search_dot(lib: Library, q_comp, q_mz, q_charge, tol, unit="da", k=1, for
     q_mz = _dev(q_mz, torch.float64, "q_mz")
     q_charge = _dev(q_charge, torch.uint8, "q_charge")
     n = q_mz.numel()
-    if out_idx is None:
-        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
-    if out_score is None:
-        out_score = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    _need(q_comp, n * lib.dim, "q_comp")
+    _need(q_charge, n, "q_charge")
+    out_idx, out_score = _results(n, k, out_idx, out_score, torch.int32, "out_score")
     _check(load().hd_search_dot(lib.handle, _ptr(q_comp), _ptr(q_mz), _ptr(q_charge), n, float(tol), _unit(unit),
                                 int(k), FORMS[form], _ptr(out_idx), _ptr(out_score), _stream(stream)))
     return out_idx, out_score
@@ -335,8 +380,8 @@ def hd_library_prepare(lib: Library, form: str):
 
 def hd_library_set_schedule(lib: Library, tile_group: int = 0, super_group: int = 0, cluster: int = 0,
                             cta_group: int = 0):
-    """Work-item shape, multicast cluster size and SM pairing (cta_group 2) of
-    the tensor-core forms (0 = default)."""
+    """Work-item shape and SM pairing of the tensor-core forms: (cluster,
+    cta_group) = (2, 2) for SM pairs or (1, 1) for one SM (0 = default)."""
     _check(load().hd_library_set_schedule(lib.handle, int(tile_group), int(super_group), int(cluster),
                                           int(cta_group)))
 
@@ -366,6 +411,7 @@ def hd_query_windows(lib: Library, q_mz, q_charge, tol, unit="da", stream=None):
     q_mz = _dev(q_mz, torch.float64, "q_mz")
     q_charge = _dev(q_charge, torch.uint8, "q_charge")
     n = q_mz.numel()
+    _need(q_charge, n, "q_charge")
     lo = torch.empty(n, dtype=torch.int32, device="cuda")
     hi = torch.empty(n, dtype=torch.int32, device="cuda")
     _check(load().hd_query_windows(lib.handle, _ptr(q_mz), _ptr(q_charge), n, float(tol), _unit(unit),
@@ -381,10 +427,9 @@ def hd_search_open(lib: Library, q_hv, q_mz, q_charge, tol, unit="da", k=1, form
     q_mz = _dev(q_mz, torch.float64, "q_mz")
     q_charge = _dev(q_charge, torch.uint8, "q_charge")
     n = q_mz.numel()
-    if out_idx is None:
-        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
-    if out_dist is None:
-        out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
+    _need(q_hv, n * (lib.dim // 64), "q_hv")
+    _need(q_charge, n, "q_charge")
+    out_idx, out_dist = _results(n, k, out_idx, out_dist)
     _check(load().hd_search_open_ex(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), n, float(tol),
                                     _unit(unit), int(k), FORMS[form], _ptr(out_idx), _ptr(out_dist),
                                     _stream(stream)))
@@ -394,16 +439,17 @@ def hd_search_open(lib: Library, q_hv, q_mz, q_charge, tol, unit="da", k=1, form
 def hd_search_open_noalloc(lib: Library, q_hv, q_mz, q_charge, tol, unit="da", k=1, out_idx=None,
                            out_dist=None, stream=None):
     """hd_search_open without device allocation inside libhd (scratch from its fixed
-    device buffer).  The outputs are the caller's: pass preallocated tensors to keep the
-    whole call allocation-free."""
+    device buffer).  The outputs are the caller's: pass preallocated contiguous tensors
+    (int32 / int16, at least n_q * k elements each) to keep the whole call
+    allocation-free.  Calls that overlap on the GPU share the buffer and must be
+    serialised by the caller."""
     q_hv = _dev(q_hv, torch.int64, "q_hv")
     q_mz = _dev(q_mz, torch.float64, "q_mz")
     q_charge = _dev(q_charge, torch.uint8, "q_charge")
     n = q_mz.numel()
-    if out_idx is None:
-        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
-    if out_dist is None:
-        out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
+    _need(q_hv, n * (lib.dim // 64), "q_hv")
+    _need(q_charge, n, "q_charge")
+    out_idx, out_dist = _results(n, k, out_idx, out_dist)
     _check(load().hd_search_open_noalloc(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), n, float(tol),
                                          _unit(unit), int(k), _ptr(out_idx), _ptr(out_dist), _stream(stream)))
     return out_idx, out_dist
@@ -416,13 +462,12 @@ def hd_search_open_multi(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k
     q_hv = _dev(q_hv, torch.int64, "q_hv")
     q_mz = _dev(q_mz, torch.float64, "q_mz")
     q_charge = _dev(q_charge, torch.uint8, "q_charge")
-    if q_class is not None:
-        q_class = _dev(q_class, torch.uint8, "q_class")
     n = q_mz.numel()
-    if out_idx is None:
-        out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
-    if out_dist is None:
-        out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
+    if q_class is not None:
+        q_class = _need(_dev(q_class, torch.uint8, "q_class"), n, "q_class")
+    _need(q_hv, n * (lib.dim // 64), "q_hv")
+    _need(q_charge, n, "q_charge")
+    out_idx, out_dist = _results(n, k, out_idx, out_dist)
     w = _windows(windows)
     _check(load().hd_search_open_multi(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), _ptr(q_class), n, w,
                                        len(windows), int(k), FORMS[form], _ptr(out_idx), _ptr(out_dist),
@@ -458,6 +503,8 @@ def hd_cascade_search(lib: Library, q_hv, q_mz, q_charge, levels, fdr=0.01, form
     q_mz = _dev(q_mz, torch.float64, "q_mz")
     q_charge = _dev(q_charge, torch.uint8, "q_charge")
     n = q_mz.numel()
+    _need(q_hv, n * (lib.dim // 64), "q_hv")
+    _need(q_charge, n, "q_charge")
     idx = torch.empty(n, dtype=torch.int32, device="cuda")
     dist = torch.empty(n, dtype=torch.int16, device="cuda")
     q = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -516,8 +563,11 @@ def hd_library_autotune(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=
     q_hv = _dev(q_hv, torch.int64, "q_hv")
     q_mz = _dev(q_mz, torch.float64, "q_mz")
     q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    n = q_mz.numel()
+    _need(q_hv, n * (lib.dim // 64), "q_hv")
+    _need(q_charge, n, "q_charge")
     if q_class is not None:
-        q_class = _dev(q_class, torch.uint8, "q_class")
+        q_class = _need(_dev(q_class, torch.uint8, "q_class"), n, "q_class")
     torch.cuda.current_stream().synchronize()
     best = _TuneResult()
     allr = (_TuneResult * 64)()
@@ -530,6 +580,22 @@ def hd_library_autotune(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=
     conv = lambda r: {"form": names[r.form], "tile_group": r.tile_group, "super_group": r.super_group,
                       "cluster": r.cluster, "cta_group": r.cta_group, "ms": r.ms}
     return conv(best), [conv(allr[i]) for i in range(min(64, n_all.value))]
+
+
+class _PeakResult(C.Structure):
+    _fields_ = [("best_per_s", C.c_double), ("median_per_s", C.c_double), ("ms_best", C.c_double),
+                ("ops_per_launch", C.c_uint64), ("sms", C.c_uint32), ("launches", C.c_uint32)]
+
+
+PEAK_KINDS = {"tc_fp4": 0, "tc_fp8": 1, "tc_bf16": 2, "popc": 3, "lop3": 4}
+
+
+def hd_measure_peak(kind: str, launches: int = 10):
+    """Instruction-rate microbenchmark (hd_measure_peak): 'tc_fp4' / 'tc_fp8' / 'tc_bf16'
+    (flops/s of the SM-pair tensor-core instruction), 'popc' (popcounts/s) or 'lop3'."""
+    r = _PeakResult()
+    _check(load().hd_measure_peak(PEAK_KINDS[kind], int(launches), C.byref(r)))
+    return {f: getattr(r, f) for f, _ in _PeakResult._fields_}
 
 
 class _ServerParams(C.Structure):
@@ -545,6 +611,11 @@ class _RequestInfo(C.Structure):
 class _ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("queries", C.c_uint64),
                 ("batches", C.c_uint64), ("max_inflight", C.c_uint32)]
+
+
+class _BatchRecord(C.Structure):
+    _fields_ = [("batch", C.c_uint64), ("slot", C.c_uint32), ("n_queries", C.c_uint32), ("n_requests", C.c_uint32),
+                ("device_start_ms", C.c_double), ("device_end_ms", C.c_double)]
 
 
 class Server:
@@ -589,6 +660,13 @@ class Server:
         st = _ServerStats()
         _check(load().hd_server_stats_get(self._h, C.byref(st)))
         return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+    def batch_log(self, cap=4096):
+        """Device-time intervals of the finished batches (oldest first), as dicts."""
+        arr = (_BatchRecord * cap)()
+        n = C.c_uint32()
+        _check(load().hd_server_batch_log(self._h, arr, cap, C.byref(n)))
+        return [{f: getattr(arr[i], f) for f, _ in _BatchRecord._fields_} for i in range(n.value)]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -24,8 +24,8 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("form,cluster,cta_group", [("popc", 0, 0), ("tc_fp8", 4, 1), ("tc_fp8", 2, 2),
-                                                    ("tc_fp4", 2, 2)])
+@pytest.mark.parametrize("form,cluster,cta_group", [("popc", 0, 0), ("tc_fp8", 1, 1), ("tc_fp8", 2, 2),
+                                                    ("tc_fp4", 1, 1), ("tc_fp4", 2, 2)])
 def test_stalled_wait_times_out_then_recovers(hd, form, cluster, cta_group):
     rng = np.random.default_rng(12)
     D, W, n = 2048, 32, 3000

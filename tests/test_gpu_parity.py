@@ -69,6 +69,19 @@ def test_item_memory_bit_exact(hd, D, Q, f, alpha, seed):
     assert np.array_equal(hd.as_u64(L), oL)
 
 
+@pytest.mark.parametrize("seed,stream,n", [(0, 0, 4_000_000), (0x0123456789ABCDEF, 3, 4_000_000),
+                                           (2**64 - 1, 5, 1_000_003), (7, 1, 1)])
+def test_philox_word_stream_bit_exact(hd, seed, stream, n):
+    """The GPU's Philox4x32-10 word stream (the item memory's random words)
+    equals the oracle's, written independently, on 10^6 counters; the first
+    block of stream 0 under seed 0 is the first Random123 known-answer vector."""
+    got = hd.as_u32(hd.hd_random_words(seed, stream, n))
+    want = oracle.random_words(seed, stream, n)
+    assert np.array_equal(got, want)
+    if seed == 0 and stream == 0:
+        assert [int(x) for x in got[:4]] == [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]
+
+
 # ---------------------------------------------------------- preprocessing
 @pytest.mark.parametrize("n_levels,bin_width,max_peaks", [(16, 0.05, 50), (32, 0.04, 50), (256, 0.05, 3),
                                                           (2, 0.05, 1023)])
@@ -339,7 +352,7 @@ def test_full_size_sampled(hd):
     hd.hd_library_prepare(lib, "tc_fp4")
     hd.hd_library_prepare(lib, "tc_fp8")
     for form, sched in (("tc_fp4", (16, 16, 2, 2)), ("tc_fp4", (32, 16, 2, 2)), ("tc_fp4", (32, 2, 2, 2)),
-                        ("tc_fp8", (16, 16, 2, 2)), ("tc_fp4", (16, 16, 4, 1))):
+                        ("tc_fp4", (16, 2, 2, 2)), ("tc_fp8", (16, 16, 2, 2)), ("tc_fp4", (16, 16, 1, 1))):
         hd.hd_library_set_schedule(lib, *sched)
         ti, td = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), spec["tol"], spec["unit"], k,
                                    form=form)

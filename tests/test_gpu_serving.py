@@ -93,6 +93,47 @@ def test_server_results_equal_alone(hd, world):
         assert info["n_queries"] == len(req[3]) and info["latency_s"] >= info["queue_s"] >= 0
 
 
+def _overlapping_pairs(log):
+    return [(a["batch"], b["batch"]) for i, a in enumerate(log) for b in log[i + 1:]
+            if a["slot"] != b["slot"] and a["device_start_ms"] < b["device_end_ms"]
+            and b["device_start_ms"] < a["device_end_ms"]]
+
+
+@pytest.mark.parametrize("slots", [3, 1])
+def test_server_batches_overlap_on_the_device(hd, world, slots):
+    """Requests that arrive while others run go to free slots, and their batches
+    run on the device at the same time: with three slots some pair of batches on
+    different streams has intersecting device-time intervals (CUDA events around
+    each batch's copies, encode and search), and each result still equals the
+    request searched alone.  One slot serialises the batches: no overlap."""
+    ctx, lib, refs, pool, csr, r_hv = world
+    off, bins, lv = csr
+    n_req, size = 6, 5000
+    rng = np.random.default_rng(21)
+    reqs = []
+    for j in range(n_req):
+        a = int(rng.integers(0, pool.n - size))
+        b = a + size
+        reqs.append((off[a:b + 1] - off[a], bins[off[a]:off[b]], lv[off[a]:off[b]], pool.precursor_mz[a:b],
+                     pool.charge[a:b], (500.0, "da")))
+    # the popcount form keeps each batch on the device for a while
+    srv = hd.Server(ctx, lib, k=K, slots=slots, max_batch_queries=size, form="popc")
+    ids = [srv.submit(*r[:5], *r[5]) for r in reqs]
+    got = [srv.wait(r) for r in ids]
+    st, log = srv.stats(), srv.batch_log()
+    srv.close()
+    assert st["completed"] == n_req and len(log) == st["batches"] == n_req
+    assert all(r["device_end_ms"] > r["device_start_ms"] >= 0 for r in log)
+    pairs = _overlapping_pairs(log)
+    if slots == 1:
+        assert st["max_inflight"] == 1 and not pairs
+    else:
+        assert st["max_inflight"] >= 2 and pairs, log
+    for req, (i, d, _) in zip(reqs, got):
+        ai, ad = _alone(hd, ctx, lib, req)
+        assert np.array_equal(i, ai) and np.array_equal(d, ad)
+
+
 def test_server_matches_oracle_sample(hd, world):
     ctx, lib, refs, pool, csr, r_hv = world
     req = _requests(pool, csr, 1, np.random.default_rng(5), 200, 200)[0]

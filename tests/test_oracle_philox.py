@@ -1,8 +1,11 @@
 """Pins of the oracle's Philox4x32-10 (Salmon et al., SC'11).
 
 The paper draws its position and level HVs at random (Section 3.3.1-3.3.2)
-without naming a generator; Philox4x32-10 is the reading.  No known-answer
-vector is available here, so the generator is pinned by properties a correct
+without naming a generator; Philox4x32-10 is the reading.  The generator is
+pinned by the published known-answer vectors of the Random123 distribution
+(its kat_vectors file, "philox4x32 10" lines: counter words, key words,
+expected output words), which fix the round function, the key schedule, the
+round count and the order of the output words; and by properties a correct
 Philox has and a broken one (a dropped key word, too few rounds, a lost
 counter word) loses: bit balance, distinct outputs for distinct counters,
 and avalanche in every counter and key word."""
@@ -12,6 +15,34 @@ import pytest
 import oracle
 
 pytestmark = pytest.mark.filterwarnings("ignore")
+
+# Random123 known-answer vectors for philox4x32_10: (ctr[4], key[2], out[4])
+KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,want", KAT)
+def test_known_answer_vectors(ctr, key, want):
+    assert [int(x) for x in oracle.philox4x32_10(ctr, key)] == list(want)
+
+
+def test_word_stream_layout():
+    """Word i of stream s under seed is component i%4 of the block at counter
+    (i/4, s, 0, 0) with key (seed low, seed high); counter 0 of stream 0 under
+    seed 0 is the first known-answer vector."""
+    assert [int(x) for x in oracle.random_words(0, 0, 4)] == list(KAT[0][2])
+    seed, stream = 0x0123456789ABCDEF, 3
+    w = oracle.random_words(seed, stream, 4 * 37 + 3)
+    for c in (0, 1, 17, 36, 37):
+        blk = oracle.philox4x32_10([c, stream, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        n = min(4, w.size - 4 * c)
+        assert np.array_equal(w[4 * c:4 * c + n], blk[:n])
 
 
 def _block(c, k):
