@@ -140,7 +140,9 @@ def test_autotune_keeps_results(hd):
     args = (lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
     i0, d0 = hd.hd_search_open_multi(*args, 5, form="popc")
     best, allr = hd.hd_library_autotune(*args, 5)
-    assert best["ms"] > 0 and len(allr) == 1 + 24
+    # popc, then 3 tile groups x 2 super groups x {(1, 1), (2, 2)} for the prepared e4m3 copy
+    assert best["ms"] > 0 and len(allr) == 1 + 12
+    assert {(r["cluster"], r["cta_group"]) for r in allr[1:]} == {(1, 1), (2, 2)}
     assert best["ms"] == min(r["ms"] for r in allr)
     i1, d1 = hd.hd_search_open_multi(*args, 5, form="auto")
     torch.cuda.synchronize()
