@@ -209,10 +209,13 @@ HD_API hd_status hd_library_info(const hd_library *lib, uint32_t *n_refs, uint32
  * 8-byte magic "HDLIB001"; u32 dim, n_levels, n_bins, alpha, u64 seed and u32
  * position_mode, encoder of the context that encoded the rows; u32 n, u32
  * flags (bit 0: decoy flags
- * follow); then hv [n][D/64] u64 in sorted row order, mz [n] f64, charge [n]
- * u8, orig [n] u32, decoy [n] u8 (input order, if flagged); then a u64
- * FNV-1a hash of every preceding byte.  Tensor-core copies are not stored
- * (hd_library_prepare rebuilds them).  Load requires a context with the same
+ * follow; bits 8..15: component bits of a multi-bit library, 0 for binary
+ * HVs); then the rows in sorted order, hv [n][D/64] u64 (binary) or
+ * components [n][D] int8 (multi-bit), mz [n] f64, charge [n] u8, orig [n]
+ * u32, decoy [n] u8 (input order, if flagged); then a u64 FNV-1a hash of
+ * every preceding byte.  Tensor-core copies are not stored (load rebuilds a
+ * multi-bit library's default copy, as hd_build_library_multibit does;
+ * hd_library_prepare adds others).  Load requires a context with the same
  * parameters, checks the hash and the row order (charge, then m/z,
  * ascending, m/z finite), and fails with HD_ERR_INVALID_ARG otherwise.  Both
  * calls are synchronous. */
@@ -365,7 +368,11 @@ HD_API hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, co
  * and coalesces the pending requests into batches whenever one of `slots`
  * execution slots (each its own stream) is free and the device-memory budget
  * allows; batches in different slots overlap on the device.  Each request's
- * results equal those of searching it alone. */
+ * results equal those of searching it alone.  A multi-bit library (Section
+ * 4.3) is served too: its requests are encoded into components
+ * (hd_encode_multibit with the library's bits), scored by the dot-product
+ * search (hd_search_dot; `form` AUTO or a tensor-core form the library holds)
+ * and submitted with hd_server_submit_dot. */
 typedef struct hd_server hd_server;
 typedef struct {
     uint32_t slots;               /* batches in flight at once, 1..64 */
@@ -393,6 +400,14 @@ HD_API hd_status hd_server_submit(hd_server *srv, const uint32_t *h_offsets, con
                                   const uint8_t *h_levels, const double *h_q_mz, const uint8_t *h_q_charge,
                                   uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *h_out_idx,
                                   uint16_t *h_out_dist, uint64_t *request_id);
+/* hd_server_submit for a server on a multi-bit library: h_out_score
+ * [n_q][k] receives the dot-product scores (padding INT32_MIN, as
+ * hd_search_dot).  Each submit call fails with HD_ERR_INVALID_ARG on the
+ * other kind of library. */
+HD_API hd_status hd_server_submit_dot(hd_server *srv, const uint32_t *h_offsets, const uint32_t *h_bins,
+                                      const uint8_t *h_levels, const double *h_q_mz, const uint8_t *h_q_charge,
+                                      uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *h_out_idx,
+                                      int32_t *h_out_score, uint64_t *request_id);
 /* Blocks until the request is done (HD_ERR_TIMEOUT after timeout_s > 0). */
 HD_API hd_status hd_server_wait(hd_server *srv, uint64_t request_id, double timeout_s, hd_request_info *info);
 HD_API hd_status hd_server_stats_get(hd_server *srv, hd_server_stats *out);
@@ -465,8 +480,9 @@ HD_API hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_t *d
  * HD_FORM_TC_FP4 for bits <= 3).  Every partial sum is an integer of size at
  * most D m^2 < 2^24, so the fp32 accumulation is exact.  Such a library is
  * searched only with hd_search_dot; the binary entry points (hd_search_*,
- * cascade, plan, server, autotune, save, export) reject it with
- * HD_ERR_INVALID_ARG, and HD_FORM_POPC does not apply.
+ * cascade, plan, autotune, export) reject it with HD_ERR_INVALID_ARG, and
+ * HD_FORM_POPC does not apply; hd_library_save / hd_library_load keep it and
+ * the server serves it (hd_server_submit_dot).
  * hd_search_dot: windows as hd_search_open (Section 3.4); per query the k
  * best candidates by S, higher first, the lower input index on a tie; d_q_comp
  * [n_q][D] int8 (16-byte aligned, components in [-m, m]; others flag

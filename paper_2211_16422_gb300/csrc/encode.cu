@@ -8,9 +8,10 @@
 //
 // One warp per spectrum; each lane owns WPL 64-bit words of a 32*WPL-word
 // slice of the HV and keeps, per word, a bit-sliced counter: plane i holds
-// bit i of the 64 per-bit counts.  Adding a bound word is a ripple-carry add
-// across the planes that can be non-zero so far.  The majority test compares
-// the planes with ceil(n/2) from the top bit down.
+// bit i of the 64 per-bit counts.  Bound words are added four at a time by a
+// carry-save adder (full adders into planes 0 and 1, the one remaining carry
+// rippled from plane 2 across the planes that can be non-zero so far).  The
+// majority test compares the planes with ceil(n/2) from the top bit down.
 #include "hd_internal.cuh"
 
 namespace {
@@ -18,6 +19,120 @@ namespace {
 constexpr int ENC_PLANES = 10;          // counts up to 1023 peaks
 constexpr uint32_t ENC_MAX_PEAKS = (1u << ENC_PLANES) - 1u;
 constexpr int ENC_WARPS = 8;
+// Widest per-lane word slice of the binary encoder.  At D = 8192, two passes
+// over the peaks with 2 words per lane (96 registers, two CTAs per SM) took
+// 2.05 ms for 200,000 spectra against 2.47 ms for one pass with 4 words (165
+// registers, one CTA per SM); the ripple-carry encoder before the carry-save
+// groups took 3.09 ms.
+#ifndef HD_ENC_WPL_MAX
+#define HD_ENC_WPL_MAX 2
+#endif
+
+__device__ __forceinline__ uint64_t maj3(uint64_t a, uint64_t b, uint64_t c) { return (a & b) | (a & c) | (b & c); }
+
+// Bound words F_bin XOR L_level of one peak, for the lane's WPL words of the
+// slice starting at word w0 (0 beyond the row).
+template <int WPL>
+__device__ __forceinline__ void bound_words(const uint64_t *__restrict__ F, const uint64_t *__restrict__ L,
+                                            uint32_t W, uint32_t b, uint32_t l, uint32_t w0, uint32_t lane,
+                                            uint64_t (&x)[WPL])
+{
+    const uint64_t *fr = F + (size_t)b * W, *lr = L + (size_t)l * W;
+#pragma unroll
+    for (int j = 0; j < WPL; ++j) {
+        const uint32_t w = w0 + lane + 32u * j;
+        x[j] = w < W ? (__ldg(fr + w) ^ __ldg(lr + w)) : 0ull;
+    }
+}
+
+// Bit-sliced counts of the bound words of peaks [beg, end): c[j][i] holds bit
+// i of the 64 per-bit counts of the lane's word j.  Four peaks at a time go
+// through a carry-save adder: two full adders (sum a^b^c, carry maj(a, b, c))
+// add them to plane 0 and emit two carries of weight 2, a third adds those to
+// plane 1 and emits one carry of weight 4, which ripples from plane 2 through
+// the planes that can be non-zero.  The last peaks, and a group holding a peak
+// out of range (flagged in `bad` and skipped), ripple one by one from plane 0.
+// Returns the number of peaks added.
+template <int WPL>
+__device__ __forceinline__ uint32_t sliced_count(const uint64_t *__restrict__ F, uint32_t n_bins,
+                                                 const uint64_t *__restrict__ L, uint32_t n_levels, uint32_t W,
+                                                 const uint32_t *__restrict__ bins,
+                                                 const uint8_t *__restrict__ levels, uint32_t beg, uint32_t end,
+                                                 uint32_t w0, uint32_t lane, uint64_t (&c)[WPL][ENC_PLANES],
+                                                 bool &bad)
+{
+#pragma unroll
+    for (int j = 0; j < WPL; ++j)
+#pragma unroll
+        for (int i = 0; i < ENC_PLANES; ++i) c[j][i] = 0;
+    uint32_t added = 0;
+    auto add_one = [&](uint32_t b, uint32_t l) {
+        uint64_t x[WPL];
+        bound_words<WPL>(F, L, W, b, l, w0, lane, x);
+        ++added;
+        const int lim = 32 - __clz(added);   // planes that can be non-zero
+#pragma unroll
+        for (int i = 0; i < ENC_PLANES; ++i) {
+            if (i < lim) {
+#pragma unroll
+                for (int j = 0; j < WPL; ++j) {
+                    const uint64_t t = c[j][i] & x[j];
+                    c[j][i] ^= x[j];
+                    x[j] = t;
+                }
+            }
+        }
+    };
+    uint32_t p = beg;
+    for (; p + 4 <= end; p += 4) {
+        uint32_t bq[4], lq[4];
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            bq[q] = __ldg(bins + p + q);
+            lq[q] = __ldg(levels + p + q);
+            ok = ok && bq[q] < n_bins && lq[q] < n_levels;
+        }
+        if (!ok) {
+            for (int q = 0; q < 4; ++q) {
+                if (bq[q] >= n_bins || lq[q] >= n_levels) bad = true;
+                else add_one(bq[q], lq[q]);
+            }
+            continue;
+        }
+        uint64_t x0[WPL], x1[WPL], x2[WPL], x3[WPL];
+        bound_words<WPL>(F, L, W, bq[0], lq[0], w0, lane, x0);
+        bound_words<WPL>(F, L, W, bq[1], lq[1], w0, lane, x1);
+        bound_words<WPL>(F, L, W, bq[2], lq[2], w0, lane, x2);
+        bound_words<WPL>(F, L, W, bq[3], lq[3], w0, lane, x3);
+        added += 4;
+        const int lim = 32 - __clz(added);
+#pragma unroll
+        for (int j = 0; j < WPL; ++j) {
+            const uint64_t a = c[j][0];
+            const uint64_t s1 = a ^ x0[j] ^ x1[j], k1 = maj3(a, x0[j], x1[j]);
+            const uint64_t k2 = maj3(s1, x2[j], x3[j]);
+            c[j][0] = s1 ^ x2[j] ^ x3[j];
+            const uint64_t b1 = c[j][1];
+            c[j][1] = b1 ^ k1 ^ k2;
+            uint64_t carry = maj3(b1, k1, k2);
+#pragma unroll
+            for (int i = 2; i < ENC_PLANES; ++i) {
+                if (i < lim) {
+                    const uint64_t t = c[j][i] & carry;
+                    c[j][i] ^= carry;
+                    carry = t;
+                }
+            }
+        }
+    }
+    for (; p < end; ++p) {
+        const uint32_t b = __ldg(bins + p), l = __ldg(levels + p);
+        if (b >= n_bins || l >= n_levels) bad = true;
+        else add_one(b, l);
+    }
+    return added;
+}
 
 template <int WPL>
 __global__ void __launch_bounds__(ENC_WARPS * 32)
@@ -34,42 +149,11 @@ k_encode(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__rest
         if (lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
         end = beg;   // encode as an empty row
     }
+    bool any_bad = false;
     for (uint32_t w0 = 0; w0 < W; w0 += 32u * WPL) {
         uint64_t c[WPL][ENC_PLANES];
-#pragma unroll
-        for (int j = 0; j < WPL; ++j)
-#pragma unroll
-            for (int i = 0; i < ENC_PLANES; ++i) c[j][i] = 0;
-        bool any_bad = false;
-        uint32_t added = 0;
-        for (uint32_t p = beg; p < end; ++p) {
-            const uint32_t b = __ldg(bins + p), l = __ldg(levels + p);
-            if (b >= n_bins || l >= n_levels) {
-                any_bad = true;
-                continue;
-            }
-            const uint64_t *fr = F + (size_t)b * W, *lr = L + (size_t)l * W;
-            uint64_t x[WPL];
-#pragma unroll
-            for (int j = 0; j < WPL; ++j) {
-                const uint32_t w = w0 + lane + 32u * j;
-                x[j] = w < W ? (__ldg(fr + w) ^ __ldg(lr + w)) : 0ull;
-            }
-            ++added;
-            const int lim = 32 - __clz(added);   // planes that can be non-zero
-#pragma unroll
-            for (int i = 0; i < ENC_PLANES; ++i) {
-                if (i < lim) {
-#pragma unroll
-                    for (int j = 0; j < WPL; ++j) {
-                        const uint64_t t = c[j][i] & x[j];
-                        c[j][i] ^= x[j];
-                        x[j] = t;
-                    }
-                }
-            }
-        }
-        if (any_bad && lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
+        const uint32_t added = sliced_count<WPL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane, c,
+                                                 any_bad);
         const uint32_t thresh = (added + 1) >> 1;   // c >= ceil(n/2)  <=>  2c >= n
 #pragma unroll
         for (int j = 0; j < WPL; ++j) {
@@ -83,6 +167,7 @@ k_encode(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__rest
             if (w < W) out[(size_t)sp * W + w] = gt | eq;
         }
     }
+    if (any_bad && lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
 }
 
 // Random-projection encoder (the LSH baseline of Section 4.2): out_d = [I_d <= 0]
@@ -206,49 +291,6 @@ k_encode_mb(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__r
 // and maps each component's count through a per-spectrum table h(c), c = 0..n,
 // in shared memory.  Same result as k_encode_mb<false>.
 template <int WPL>
-__device__ __forceinline__ uint32_t sliced_count(const uint64_t *__restrict__ F, uint32_t n_bins,
-                                                 const uint64_t *__restrict__ L, uint32_t n_levels, uint32_t W,
-                                                 const uint32_t *__restrict__ bins,
-                                                 const uint8_t *__restrict__ levels, uint32_t beg, uint32_t end,
-                                                 uint32_t w0, uint32_t lane, uint64_t (&c)[WPL][ENC_PLANES],
-                                                 bool &bad)
-{
-#pragma unroll
-    for (int j = 0; j < WPL; ++j)
-#pragma unroll
-        for (int i = 0; i < ENC_PLANES; ++i) c[j][i] = 0;
-    uint32_t added = 0;
-    for (uint32_t p = beg; p < end; ++p) {
-        const uint32_t b = __ldg(bins + p), l = __ldg(levels + p);
-        if (b >= n_bins || l >= n_levels) {
-            bad = true;
-            continue;
-        }
-        const uint64_t *fr = F + (size_t)b * W, *lr = L + (size_t)l * W;
-        uint64_t x[WPL];
-#pragma unroll
-        for (int j = 0; j < WPL; ++j) {
-            const uint32_t w = w0 + lane + 32u * j;
-            x[j] = w < W ? (__ldg(fr + w) ^ __ldg(lr + w)) : 0ull;
-        }
-        ++added;
-        const int lim = 32 - __clz(added);
-#pragma unroll
-        for (int i = 0; i < ENC_PLANES; ++i) {
-            if (i < lim) {
-#pragma unroll
-                for (int j = 0; j < WPL; ++j) {
-                    const uint64_t t = c[j][i] & x[j];
-                    c[j][i] ^= x[j];
-                    x[j] = t;
-                }
-            }
-        }
-    }
-    return added;
-}
-
-template <int WPL>
 __global__ void __launch_bounds__(ENC_WARPS * 32)
 k_encode_mb_sliced(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__restrict__ L,
                    uint32_t n_levels, uint32_t W, const uint32_t *__restrict__ off,
@@ -358,7 +400,7 @@ void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bi
         hd_count_launches(1), k_encode_projection<<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins,
                                                                               ctx->p.n_levels, W, off, bins,
                                                                               levels, n, out, (uint32_t *)st);
-    else if (W >= 128)
+    else if (W >= 128 && HD_ENC_WPL_MAX >= 4)
         hd_count_launches(1), k_encode<4><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
                                                     W, off, bins, levels, n, out, (uint32_t *)st);
     else if (W >= 64)

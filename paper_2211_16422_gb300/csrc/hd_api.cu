@@ -552,17 +552,18 @@ struct file_closer {
 hd_status hd_library_save(const hd_library *lib, const hd_ctx *ctx, const char *path)
 {
     HD_CHECK(lib && ctx && path, "hd_library_save: null argument");
-    HD_CHECK(hd_lib_binary(lib), "hd_library_save: multi-bit library (binary HVs only)");
     HD_CHECK(ctx->p.dim == lib->dim, "hd_library_save: ctx and library dims differ");
     hd_status st = check_device(lib->device);
     if (st != HD_OK) return st;
-    const size_t n = lib->n, W = lib->W;
+    // binary rows: D/64 words; multi-bit rows: D int8 components (D/8 words)
+    const size_t n = lib->n, W = hd_lib_binary(lib) ? lib->W : lib->dim / 8;
     std::vector<uint64_t> hv(n * W);
     std::vector<double> mz(n);
     std::vector<uint8_t> z(n), dec(lib->decoy ? n : 0);
     std::vector<uint32_t> orig(n);
     if (n) {
-        HD_CUDA_TRY(cudaMemcpy(hv.data(), lib->hv, n * W * 8, cudaMemcpyDeviceToHost));
+        HD_CUDA_TRY(cudaMemcpy(hv.data(), hd_lib_binary(lib) ? (const void *)lib->hv : (const void *)lib->comp, n * W * 8,
+                               cudaMemcpyDeviceToHost));
         HD_CUDA_TRY(cudaMemcpy(mz.data(), lib->mz, n * 8, cudaMemcpyDeviceToHost));
         HD_CUDA_TRY(cudaMemcpy(z.data(), lib->charge, n, cudaMemcpyDeviceToHost));
         HD_CUDA_TRY(cudaMemcpy(orig.data(), lib->orig, n * 4, cudaMemcpyDeviceToHost));
@@ -578,7 +579,7 @@ hd_status hd_library_save(const hd_library *lib, const hd_ctx *ctx, const char *
     h.position_mode = ctx->p.position_mode;
     h.encoder = ctx->p.encoder;
     h.n = lib->n;
-    h.flags = lib->decoy ? 1u : 0u;
+    h.flags = (lib->decoy ? 1u : 0u) | (hd_lib_binary(lib) ? 0u : (lib->bits << 8));
     file_closer fc;
     fc.f = std::fopen(path, "wb");
     if (!fc.f) return hd_fail(HD_ERR_INVALID_ARG, std::string("hd_library_save: cannot open ") + path);
@@ -627,7 +628,10 @@ hd_status hd_library_load(hd_ctx *ctx, const char *path, hd_library **out)
         h.alpha != ctx->p.alpha || h.seed != ctx->p.seed || h.position_mode != ctx->p.position_mode ||
         h.encoder != ctx->p.encoder)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_library_load: the file was encoded with other item-memory parameters");
-    const size_t n = h.n, W = ctx->W;
+    const uint32_t bits = (h.flags >> 8) & 0xFFu;   // 0: binary rows
+    if ((h.flags & ~0xFF01u) != 0 || bits == 1 || bits > 5)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_library_load: unknown flags");
+    const size_t n = h.n, W = bits ? ctx->p.dim / 8 : ctx->W;
     std::vector<uint64_t> hv(n * W);
     std::vector<double> mz(n);
     std::vector<uint8_t> z(n), dec((h.flags & 1u) ? n : 0);
@@ -651,6 +655,7 @@ hd_status hd_library_load(hd_ctx *ctx, const char *path, hd_library **out)
     lib->n = h.n;
     lib->dim = ctx->p.dim;
     lib->W = ctx->W;
+    lib->bits = bits ? bits : 1u;
     lib->device = ctx->device;
     lib->num_sms = ctx->num_sms;
     auto fail = [&](hd_status s) {
@@ -658,7 +663,12 @@ hd_status hd_library_load(hd_ctx *ctx, const char *path, hd_library **out)
         return s;
     };
     const size_t n1 = n ? n : 1;
-    if (cudaMalloc(&lib->hv, n1 * W * 8) != cudaSuccess || cudaMalloc(&lib->mz, n1 * 8) != cudaSuccess ||
+    uint64_t *rows = nullptr;
+    if (cudaMalloc(&rows, n1 * W * 8) == cudaSuccess) {
+        if (bits) lib->comp = reinterpret_cast<int8_t *>(rows);
+        else lib->hv = rows;
+    }
+    if (!rows || cudaMalloc(&lib->mz, n1 * 8) != cudaSuccess ||
         cudaMalloc(&lib->charge, n1) != cudaSuccess || cudaMalloc(&lib->orig, n1 * 4) != cudaSuccess ||
         cudaMalloc(&lib->charge_start, 257 * 4) != cudaSuccess ||
         (!dec.empty() && cudaMalloc(&lib->decoy, n) != cudaSuccess)) {
@@ -669,7 +679,7 @@ hd_status hd_library_load(hd_ctx *ctx, const char *path, hd_library **out)
     if (st != HD_OK) return fail(st);
     cudaError_t e = cudaSuccess;
     if (n) {
-        e = cudaMemcpy(lib->hv, hv.data(), n * W * 8, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(rows, hv.data(), n * W * 8, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(lib->mz, mz.data(), n * 8, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(lib->charge, z.data(), n, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(lib->orig, orig.data(), n * 4, cudaMemcpyHostToDevice);
@@ -680,6 +690,14 @@ hd_status hd_library_load(hd_ctx *ctx, const char *path, hd_library **out)
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(lib->charge_start_h, lib->charge_start, 257 * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(hd_cuda_fail(e, "hd_library_load"));
+    if (bits) {   // multi-bit rows: the default tensor-core copy, which also checks the component range
+        st = hd_library_expand(lib, bits <= 3 ? HD_FORM_TC_FP4 : HD_FORM_TC_FP8, nullptr);
+        if (st != HD_OK) return fail(st);
+        e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) return fail(hd_cuda_fail(e, "hd_library_load"));
+        st = status_take(lib->status, "hd_library_load");
+        if (st != HD_OK) return fail(hd_fail(st, "hd_library_load: components must lie in [-m, m]"));
+    }
     *out = lib;
     return HD_OK;
 }

@@ -11,7 +11,9 @@
 // top-k back.  Batches in different slots overlap on the device; a request
 // that arrives while others run joins the next batch that starts.  Results
 // are exactly those of searching each request alone: the top-k of a query
-// depends only on that query.
+// depends only on that query.  On a multi-bit library (Section 4.3) the
+// batch is encoded into components and scored by the dot-product search, and
+// requests come through hd_server_submit_dot with score outputs.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -42,7 +44,8 @@ struct request {
     uint32_t n_q = 0;
     hd_window win{};
     uint32_t *out_idx = nullptr;
-    uint16_t *out_dist = nullptr;
+    uint16_t *out_dist = nullptr;   // binary library
+    int32_t *out_score = nullptr;   // multi-bit library
     double t_submit = 0, t_start = 0, t_done = 0;
     uint32_t batch_queries = 0;
     bool done = false;
@@ -81,6 +84,7 @@ struct slot {
     pinned<uint8_t> lv, z, cls;
     pinned<double> mz;
     pinned<uint16_t> out_dist;
+    pinned<int32_t> out_score;
     std::vector<req_ptr> reqs;
     size_t bytes = 0;
     bool busy = false;
@@ -94,6 +98,8 @@ struct hd_server {
     const hd_library *lib = nullptr;
     hd_server_params p{};
     size_t budget = 0, inflight_bytes = 0, per_query_bytes = 0;
+    bool multibit = false;            // lib->bits > 1: components, dot-product scores
+    hd_search_form form = HD_FORM_AUTO;
     std::thread th;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -125,7 +131,7 @@ struct hd_server {
         }
         if (!s.off.reserve(nq + 1) || !s.bins.reserve(nnz + 1) || !s.lv.reserve(nnz + 1) || !s.mz.reserve(nq) ||
             !s.z.reserve(nq) || !s.cls.reserve(nq) || !s.out_idx.reserve((size_t)nq * p.k) ||
-            !s.out_dist.reserve((size_t)nq * p.k))
+            (multibit ? !s.out_score.reserve((size_t)nq * p.k) : !s.out_dist.reserve((size_t)nq * p.k)))
             return hd_fail(HD_ERR_OOM, "hd_server: page-locked staging allocation failed");
         uint32_t q0 = 0, p0 = 0;
         s.off.p[0] = 0;
@@ -147,30 +153,34 @@ struct hd_server {
         hd_status st = hd_make_qwin(nullptr, wins.data(), (uint32_t)wins.size(), &win);
         if (st != HD_OK) return st;
         hd_arena plan;
+        // query rows: W words of HV bits, or D int8 components (D/8 words) on a multi-bit library
+        const size_t row_words = multibit ? lib->dim / 8 : ctx->W;
         auto carve = [&](hd_arena &ar, uint32_t **off, uint32_t **bins, uint8_t **lv, double **mz, uint8_t **z,
-                         uint8_t **cls, uint64_t **hv, uint32_t **oi, uint16_t **od) {
+                         uint8_t **cls, uint64_t **hv, uint32_t **oi, uint16_t **od, int32_t **os) {
             *off = ar.take<uint32_t>(nq + 1);
             *bins = ar.take<uint32_t>(nnz ? nnz : 1);
             *lv = ar.take<uint8_t>(nnz ? nnz : 1);
             *mz = ar.take<double>(nq);
             *z = ar.take<uint8_t>(nq);
             *cls = ar.take<uint8_t>(nq);
-            *hv = ar.take<uint64_t>((size_t)nq * ctx->W);
+            *hv = ar.take<uint64_t>((size_t)nq * row_words);
             *oi = ar.take<uint32_t>((size_t)nq * p.k);
-            *od = ar.take<uint16_t>((size_t)nq * p.k);
+            *od = multibit ? nullptr : ar.take<uint16_t>((size_t)nq * p.k);
+            *os = multibit ? ar.take<int32_t>((size_t)nq * p.k) : nullptr;
         };
         uint32_t *d_off, *d_bins, *d_oi;
         uint8_t *d_lv, *d_z, *d_cls;
         double *d_mz;
         uint64_t *d_hv;
         uint16_t *d_od;
-        carve(plan, &d_off, &d_bins, &d_lv, &d_mz, &d_z, &d_cls, &d_hv, &d_oi, &d_od);
+        int32_t *d_os;
+        carve(plan, &d_off, &d_bins, &d_lv, &d_mz, &d_z, &d_cls, &d_hv, &d_oi, &d_od, &d_os);
         hd_arena ar;
         if (cudaMallocAsync((void **)&ar.base, plan.used, s.stream) != cudaSuccess) {
             cudaGetLastError();
             return hd_fail(HD_ERR_OOM, "hd_server: device allocation failed");
         }
-        carve(ar, &d_off, &d_bins, &d_lv, &d_mz, &d_z, &d_cls, &d_hv, &d_oi, &d_od);
+        carve(ar, &d_off, &d_bins, &d_lv, &d_mz, &d_z, &d_cls, &d_hv, &d_oi, &d_od, &d_os);
         win.cls = wins.size() > 1 ? d_cls : nullptr;
         const auto H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
         cudaEventRecord(s.start_ev, s.stream);
@@ -181,15 +191,23 @@ struct hd_server {
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_z, s.z.p, nq, H2D, s.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_cls, s.cls.p, nq, H2D, s.stream);
         if (e == cudaSuccess) {
-            hd_encode_launch(ctx, d_off, d_bins, d_lv, nq, d_hv, s.stream);
+            if (multibit)
+                hd_encode_mb_launch(ctx, d_off, d_bins, d_lv, nq, lib->bits, reinterpret_cast<int8_t *>(d_hv), s.stream);
+            else
+                hd_encode_launch(ctx, d_off, d_bins, d_lv, nq, d_hv, s.stream);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
-            st = hd_search_dispatch(lib, d_hv, d_mz, d_z, nq, win, p.k, p.form, d_oi, d_od, s.stream);
+            st = multibit ? hd_search_mma_dot_run(lib, form, reinterpret_cast<const int8_t *>(d_hv), d_mz, d_z, nq, win,
+                                                  p.k, d_oi, d_os, s.stream)
+                          : hd_search_dispatch(lib, d_hv, d_mz, d_z, nq, win, p.k, p.form, d_oi, d_od, s.stream);
             if (st != HD_OK) e = cudaErrorUnknown;
         }
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.out_idx.p, d_oi, (size_t)nq * p.k * 4, D2H, s.stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(s.out_dist.p, d_od, (size_t)nq * p.k * 2, D2H, s.stream);
+        if (e == cudaSuccess && multibit)
+            e = cudaMemcpyAsync(s.out_score.p, d_os, (size_t)nq * p.k * 4, D2H, s.stream);
+        if (e == cudaSuccess && !multibit)
+            e = cudaMemcpyAsync(s.out_dist.p, d_od, (size_t)nq * p.k * 2, D2H, s.stream);
         cudaFreeAsync(ar.base, s.stream);
         cudaEventRecord(s.done_ev, s.stream);
         if (st != HD_OK) return st;
@@ -223,7 +241,8 @@ struct hd_server {
             auto &r = *rp;
             if (st == HD_OK) {
                 std::memcpy(r.out_idx, s.out_idx.p + (size_t)q0 * p.k, (size_t)r.n_q * p.k * 4);
-                std::memcpy(r.out_dist, s.out_dist.p + (size_t)q0 * p.k, (size_t)r.n_q * p.k * 2);
+                if (multibit) std::memcpy(r.out_score, s.out_score.p + (size_t)q0 * p.k, (size_t)r.n_q * p.k * 4);
+                else std::memcpy(r.out_dist, s.out_dist.p + (size_t)q0 * p.k, (size_t)r.n_q * p.k * 2);
             }
             q0 += r.n_q;
             r.status = st;
@@ -295,6 +314,54 @@ struct hd_server {
     }
 };
 
+namespace {
+
+hd_status submit(hd_server *s, const uint32_t *h_offsets, const uint32_t *h_bins, const uint8_t *h_levels,
+                 const double *h_q_mz, const uint8_t *h_q_charge, uint32_t n_q, double tol, hd_tol_unit unit,
+                 uint32_t *h_out_idx, uint16_t *h_out_dist, int32_t *h_out_score, uint64_t *request_id,
+                 const char *fn)
+{
+    const std::string f(fn);
+    if (!s || !request_id) return hd_fail(HD_ERR_INVALID_ARG, f + ": null argument");
+    if (n_q == 0 || !h_offsets || !h_q_mz || !h_q_charge || !h_out_idx || (!h_out_dist && !h_out_score))
+        return hd_fail(HD_ERR_INVALID_ARG, f + ": empty request or null buffer");
+    if (s->multibit != (h_out_score != nullptr))
+        return hd_fail(HD_ERR_INVALID_ARG, s->multibit ? f + ": multi-bit library: use hd_server_submit_dot"
+                                                       : f + ": binary library: use hd_server_submit");
+    if (!(tol >= 0.0) || tol > 1.7976931348623157e308 || (unit != HD_TOL_DA && unit != HD_TOL_PPM && unit != HD_TOL_MASS))
+        return hd_fail(HD_ERR_INVALID_ARG, f + ": bad window");
+    const uint32_t nnz = h_offsets[n_q] - h_offsets[0];
+    if (nnz && (!h_bins || !h_levels)) return hd_fail(HD_ERR_INVALID_ARG, f + ": null CSR buffer");
+    for (uint32_t q = 0; q < n_q; ++q)
+        if (h_offsets[q + 1] < h_offsets[q]) return hd_fail(HD_ERR_INVALID_ARG, f + ": bad offsets");
+    auto r = std::make_shared<request>();
+    r->n_q = n_q;
+    r->off.resize(n_q + 1);
+    for (uint32_t q = 0; q <= n_q; ++q) r->off[q] = h_offsets[q] - h_offsets[0];
+    r->bins.assign(h_bins ? h_bins + h_offsets[0] : nullptr, h_bins ? h_bins + h_offsets[n_q] : nullptr);
+    r->lv.assign(h_levels ? h_levels + h_offsets[0] : nullptr, h_levels ? h_levels + h_offsets[n_q] : nullptr);
+    r->mz.assign(h_q_mz, h_q_mz + n_q);
+    r->z.assign(h_q_charge, h_q_charge + n_q);
+    r->win = hd_window{tol, unit};
+    r->out_idx = h_out_idx;
+    r->out_dist = h_out_dist;
+    r->out_score = h_out_score;
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->stop) return hd_fail(HD_ERR_INVALID_ARG, f + ": server is stopping");
+        r->id = s->next_id++;
+        s->reqs[r->id] = r;
+        s->pending.push_back(r);
+        s->stats.submitted += 1;
+    }
+    s->cv_work.notify_one();
+    *request_id = r->id;
+    return HD_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_params *params, hd_server **out)
@@ -302,7 +369,6 @@ hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_p
     if (!out) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: null output");
     *out = nullptr;
     if (!ctx || !lib || !params) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: null argument");
-    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: multi-bit library (binary HVs only)");
     if (ctx->p.dim != lib->dim) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: ctx and library dims differ");
     if (params->k < 1 || params->k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: k must be in [1, 16]");
     if (params->slots < 1 || params->slots > 64)
@@ -315,8 +381,20 @@ hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_p
     srv->ctx = ctx;
     srv->lib = lib;
     srv->p = *params;
+    srv->multibit = !hd_lib_binary(lib);
+    srv->form = params->form;
+    if (srv->multibit) {   // the dot-product search runs on a tensor-core copy the library holds
+        if (srv->form == HD_FORM_AUTO)
+            srv->form = lib->x_fp4 ? HD_FORM_TC_FP4 : (lib->x_fp8 ? HD_FORM_TC_FP8 : HD_FORM_TC_BF16);
+        const uint8_t *copy = srv->form == HD_FORM_TC_FP4 ? lib->x_fp4
+                            : srv->form == HD_FORM_TC_FP8 ? lib->x_fp8
+                            : srv->form == HD_FORM_TC_BF16 ? lib->x_bf16 : nullptr;
+        if (!copy && lib->n)
+            return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: multi-bit library needs a prepared tensor-core form");
+    }
     const size_t row_tc = (size_t)lib->dim * 2;
-    srv->per_query_bytes = (size_t)lib->dim / 8 + row_tc + 1024 + (size_t)params->k * 32;
+    srv->per_query_bytes = (srv->multibit ? (size_t)lib->dim : (size_t)lib->dim / 8) + row_tc + 1024 +
+                           (size_t)params->k * 32;
     size_t free_b = 0, total_b = 0;
     HD_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     srv->budget = params->mem_budget_bytes ? (size_t)params->mem_budget_bytes : free_b / 2;
@@ -341,38 +419,19 @@ hd_status hd_server_submit(hd_server *s, const uint32_t *h_offsets, const uint32
                            const double *h_q_mz, const uint8_t *h_q_charge, uint32_t n_q, double tol,
                            hd_tol_unit unit, uint32_t *h_out_idx, uint16_t *h_out_dist, uint64_t *request_id)
 {
-    if (!s || !request_id) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: null argument");
-    if (n_q == 0 || !h_offsets || !h_q_mz || !h_q_charge || !h_out_idx || !h_out_dist)
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: empty request or null buffer");
-    if (!(tol >= 0.0) || tol > 1.7976931348623157e308 || (unit != HD_TOL_DA && unit != HD_TOL_PPM && unit != HD_TOL_MASS))
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: bad window");
-    const uint32_t nnz = h_offsets[n_q] - h_offsets[0];
-    if (nnz && (!h_bins || !h_levels)) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: null CSR buffer");
-    for (uint32_t q = 0; q < n_q; ++q)
-        if (h_offsets[q + 1] < h_offsets[q]) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: bad offsets");
-    auto r = std::make_shared<request>();
-    r->n_q = n_q;
-    r->off.resize(n_q + 1);
-    for (uint32_t q = 0; q <= n_q; ++q) r->off[q] = h_offsets[q] - h_offsets[0];
-    r->bins.assign(h_bins ? h_bins + h_offsets[0] : nullptr, h_bins ? h_bins + h_offsets[n_q] : nullptr);
-    r->lv.assign(h_levels ? h_levels + h_offsets[0] : nullptr, h_levels ? h_levels + h_offsets[n_q] : nullptr);
-    r->mz.assign(h_q_mz, h_q_mz + n_q);
-    r->z.assign(h_q_charge, h_q_charge + n_q);
-    r->win = hd_window{tol, unit};
-    r->out_idx = h_out_idx;
-    r->out_dist = h_out_dist;
-    r->t_submit = now_s();
-    {
-        std::lock_guard<std::mutex> g(s->mu);
-        if (s->stop) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: server is stopping");
-        r->id = s->next_id++;
-        s->reqs[r->id] = r;
-        s->pending.push_back(r);
-        s->stats.submitted += 1;
-    }
-    s->cv_work.notify_one();
-    *request_id = r->id;
-    return HD_OK;
+    if (!h_out_dist) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit: null buffer");
+    return submit(s, h_offsets, h_bins, h_levels, h_q_mz, h_q_charge, n_q, tol, unit, h_out_idx, h_out_dist, nullptr,
+                  request_id, "hd_server_submit");
+}
+
+hd_status hd_server_submit_dot(hd_server *s, const uint32_t *h_offsets, const uint32_t *h_bins,
+                               const uint8_t *h_levels, const double *h_q_mz, const uint8_t *h_q_charge, uint32_t n_q,
+                               double tol, hd_tol_unit unit, uint32_t *h_out_idx, int32_t *h_out_score,
+                               uint64_t *request_id)
+{
+    if (!h_out_score) return hd_fail(HD_ERR_INVALID_ARG, "hd_server_submit_dot: null buffer");
+    return submit(s, h_offsets, h_bins, h_levels, h_q_mz, h_q_charge, n_q, tol, unit, h_out_idx, nullptr, h_out_score,
+                  request_id, "hd_server_submit_dot");
 }
 
 hd_status hd_server_wait(hd_server *s, uint64_t id, double timeout_s, hd_request_info *info)

@@ -101,6 +101,7 @@ _SIGS = {
     "hd_library_autotune": ([P, P, P, P, P, u32, P, u32, u32, P, P, u32, P], i32),
     "hd_server_create": ([P, P, P, P], i32),
     "hd_server_submit": ([P, P, P, P, P, P, u32, dbl, i32, P, P, P], i32),
+    "hd_server_submit_dot": ([P, P, P, P, P, P, u32, dbl, i32, P, P, P], i32),
     "hd_server_wait": ([P, u64, dbl, P], i32),
     "hd_server_stats_get": ([P, P], i32),
     "hd_server_batch_log": ([P, P, u32, P], i32),
@@ -626,13 +627,15 @@ class Server:
         self.k = int(k)
         self._keep = (ctx, lib)
         self._pending = {}
+        self.multibit = hd_library_component_bits(lib) > 1
         p = _ServerParams(int(slots), int(max_batch_queries), int(mem_budget_bytes), self.k, FORMS[form])
         h = C.c_void_p()
         _check(load().hd_server_create(ctx.handle, lib.handle, C.byref(p), C.byref(h)))
         self._h = h
 
     def submit(self, offsets, bins, levels, q_mz, q_charge, tol, unit="da"):
-        """Queue one request (host arrays); returns its id."""
+        """Queue one request (host arrays); returns its id.  On a multi-bit library the
+        request is scored by the dot product (wait() returns int32 scores)."""
         off = np.ascontiguousarray(offsets, np.uint32)
         b = np.ascontiguousarray(bins, np.uint32)
         lv = np.ascontiguousarray(levels, np.uint8)
@@ -640,15 +643,17 @@ class Server:
         z = np.ascontiguousarray(q_charge, np.uint8)
         n = mz.size
         oi = np.empty((n, self.k), np.uint32)
-        od = np.empty((n, self.k), np.uint16)
+        od = np.empty((n, self.k), np.int32 if self.multibit else np.uint16)
         rid = C.c_uint64()
-        _check(load().hd_server_submit(self._h, _ptr(off), _ptr(b), _ptr(lv), _ptr(mz), _ptr(z), n, float(tol),
-                                       _unit(unit), _ptr(oi), _ptr(od), C.byref(rid)))
+        fn = load().hd_server_submit_dot if self.multibit else load().hd_server_submit
+        _check(fn(self._h, _ptr(off), _ptr(b), _ptr(lv), _ptr(mz), _ptr(z), n, float(tol), _unit(unit), _ptr(oi),
+                  _ptr(od), C.byref(rid)))
         self._pending[rid.value] = (oi, od)
         return rid.value
 
     def wait(self, rid, timeout_s=120.0):
-        """(idx [n, k] u32, dist [n, k] u16, info dict) once the request is done."""
+        """(idx [n, k] u32, dist [n, k] u16 -- or score [n, k] int32 on a multi-bit
+        library --, info dict) once the request is done."""
         info = _RequestInfo()
         oi, od = self._pending[rid]
         _check(load().hd_server_wait(self._h, C.c_uint64(rid), float(timeout_s), C.byref(info)))

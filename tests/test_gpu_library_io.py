@@ -109,3 +109,51 @@ def test_empty_library_round_trip(hd, tmp_path):
     torch.cuda.synchronize()
     assert np.all(hd.as_u32(i) == 0xFFFFFFFF)
     assert os.path.getsize(path) > 0
+
+
+@pytest.mark.parametrize("bits", [3, 4])
+def test_multibit_round_trip(hd, tmp_path, bits):
+    """A multi-bit library (Section 4.3 components) is saved with its component
+    bits and loaded back row for row: the dot-product search on the loaded
+    library equals the saved one's and the oracle's, the default tensor-core
+    copy is rebuilt on load, and a file whose components were edited out of
+    range (hash recomputed) is refused."""
+    import oracle
+    D, m = 512, 2 ** (bits - 1) - 1
+    rng = np.random.default_rng(60 + bits)
+    n, n_q = 3000, 200
+    R = rng.integers(-m, m + 1, (n, D)).astype(np.int8)
+    mz = rng.uniform(400.0, 420.0, n)
+    z = rng.integers(2, 4, n).astype(np.uint8)
+    Qv = rng.integers(-m, m + 1, (n_q, D)).astype(np.int8)
+    q_mz, q_z = rng.uniform(400.0, 420.0, n_q), rng.integers(2, 4, n_q).astype(np.uint8)
+    ctx = hd.Ctx(D, 8, 100, D // 2, 2)
+    lib = hd.hd_build_library_multibit(ctx, dev(R), dev(mz), dev(z), bits)
+    path = str(tmp_path / f"mb{bits}.hdl")
+    hd.hd_library_save(lib, ctx, path)
+    lib2 = hd.hd_library_load(ctx, path)
+    assert lib2.n == n and hd.hd_library_component_bits(lib2) == bits
+    form = "tc_fp4" if bits <= 3 else "tc_fp8"
+    a = hd.hd_search_dot(lib, dev(Qv), dev(q_mz), dev(q_z), 2.0, "da", 5, form)
+    b = hd.hd_search_dot(lib2, dev(Qv), dev(q_mz), dev(q_z), 2.0, "da", 5, "auto")
+    torch.cuda.synchronize()
+    lib2.status()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    oi, osc = oracle.search_dot(R, mz, z, Qv, q_mz, q_z, 2.0, "da", 5)
+    assert np.array_equal(b[0].cpu().numpy().view(np.uint32), oi) and np.array_equal(b[1].cpu().numpy(), osc)
+    with pytest.raises(hd.HDError):                   # still refused by the binary entry points
+        hd.hd_search_open(lib2, torch.zeros((4, D // 64), dtype=torch.int64, device="cuda"), dev(q_mz[:4]),
+                          dev(q_z[:4]), 1.0, "da", 1)
+    # component out of range, with a valid hash: the load's range check refuses it
+    blob = bytearray(open(path, "rb").read())
+    head = 8 + 4 * 4 + 8 + 4 * 4                      # magic, dim..alpha, seed, mode, encoder, n, flags
+    blob[head + 7] = (m + 1) & 0xFF
+    h = 1469598103934665603
+    for byte in bytes(blob[:-8]):
+        h = ((h ^ byte) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    blob[-8:] = h.to_bytes(8, "little")
+    p2 = str(tmp_path / "bad.hdl")
+    open(p2, "wb").write(bytes(blob))
+    with pytest.raises(hd.HDError) as e:
+        hd.hd_library_load(ctx, p2)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG

@@ -162,3 +162,47 @@ def test_server_small_memory_budget(hd, world):
     for req, (i, d, info) in zip(reqs, got):
         ai, ad = _alone(hd, ctx, lib, req)
         assert np.array_equal(i, ai) and np.array_equal(d, ad)
+
+
+def test_server_multibit_library(hd, world):
+    """A server on a multi-bit library (Section 4.3 components, 3 bits):
+    requests are encoded into components and scored by the dot-product
+    search; every result equals hd_search_dot of the request alone, one
+    request equals the oracle, and the binary submit call is refused."""
+    import ctypes
+    ctx, lib, refs, pool, csr, r_hv = world
+    bits = 3
+    pp = oracle_side.pp_args(Q)
+    r_csr = hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp)
+    mlib = hd.hd_build_library_multibit(ctx, hd.hd_encode_multibit(ctx, *r_csr, bits), dev(refs.precursor_mz),
+                                        dev(refs.charge), bits)
+    reqs = _requests(pool, csr, 12, np.random.default_rng(33), 1, 300)
+    srv = hd.Server(ctx, mlib, k=K, slots=3, max_batch_queries=1000)
+    ids = [srv.submit(*r[:5], *r[5]) for r in reqs]
+    got = [srv.wait(r) for r in ids]
+    # the binary submit call on a multi-bit server is refused before anything is queued
+    o, b, lv, mz, z, (tol, unit) = reqs[0]
+    oi = np.empty((len(mz), K), np.uint32)
+    od = np.empty((len(mz), K), np.uint16)
+    rid = ctypes.c_uint64()
+    st = hd.load().hd_server_submit(srv._h, hd._ptr(np.ascontiguousarray(o, np.uint32)),
+                                    hd._ptr(np.ascontiguousarray(b, np.uint32)), hd._ptr(np.ascontiguousarray(lv)),
+                                    hd._ptr(np.ascontiguousarray(mz)), hd._ptr(np.ascontiguousarray(z)), len(mz),
+                                    float(tol), hd._unit(unit), hd._ptr(oi), hd._ptr(od), ctypes.byref(rid))
+    assert st == hd.HD_ERR_INVALID_ARG
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(reqs)
+    for req, (i, sc, info) in zip(reqs, got):
+        o, b, lv, mz, z, (tol, unit) = req
+        q = hd.hd_encode_multibit(ctx, dev(o), dev(b), dev(lv), bits)
+        ai, asc = hd.hd_search_dot(mlib, q, dev(mz), dev(z), tol, unit, K)
+        torch.cuda.synchronize()
+        assert sc.dtype == np.int32
+        assert np.array_equal(i, hd.as_u32(ai)) and np.array_equal(sc, asc.cpu().numpy())
+    o, b, lv, mz, z, (tol, unit) = reqs[1]
+    F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, 0)
+    R = oracle.encode_multibit(D, F, L, *oracle.preprocess(refs.offsets, refs.mz, refs.intensity, **pp), bits)
+    oi, osc = oracle.search_dot(R, refs.precursor_mz, refs.charge, oracle.encode_multibit(D, F, L, o, b, lv, bits),
+                                mz, z, tol, unit, K)
+    assert np.array_equal(got[1][0], oi) and np.array_equal(got[1][1], osc)
