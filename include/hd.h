@@ -119,14 +119,20 @@ typedef struct hd_library hd_library;
 
 /* Scoring forms; all give identical results.  The tensor-core forms score
  * bipolar copies (bit 0 -> +1, bit 1 -> -1) of the HVs by matrix multiply,
- * S = sum_d x_d y_d = D - 2*dist, accumulated exactly in fp32. */
+ * S = sum_d x_d y_d = D - 2*dist, accumulated exactly in fp32.  HD_FORM_AUTO
+ * takes the autotuner's choice, else the fastest prepared tensor-core form
+ * (kind::mxf4 when the e2m1 copy exists and D is a multiple of 256), else
+ * popc. */
 typedef enum {
     HD_FORM_AUTO = 0,     /* fastest form the library was prepared for */
     HD_FORM_POPC = 1,     /* XOR + population count on the integer pipes */
     HD_FORM_TC_FP8 = 2,   /* tcgen05 kind::f8f6f4, +-1 as e4m3 (library: D bytes/row) */
     HD_FORM_TC_BF16 = 3,  /* tcgen05 kind::f16, +-1 as bf16 (library: 2D bytes/row) */
-    HD_FORM_TC_FP4 = 4    /* tcgen05 kind::f8f6f4, +-1 as e2m1 packed two per byte
+    HD_FORM_TC_FP4 = 4,   /* tcgen05 kind::f8f6f4, +-1 as e2m1 packed two per byte
                              (library: D/2 bytes/row; the TMA unpacks into shared memory) */
+    HD_FORM_TC_MXF4 = 5   /* tcgen05 kind::mxf4 (block-scaled, unit ue8m0 scales) on the same
+                             packed e2m1 rows, kept packed in shared memory; SM pairs, N = 224
+                             per MMA; D a multiple of 256 (else HD_ERR_UNSUPPORTED) */
 } hd_search_form;
 
 /* Name of a status code ("HD_OK", ...); a static string, never NULL. */
@@ -344,9 +350,10 @@ HD_API hd_status hd_plan_info(const hd_plan *plan, uint32_t *kernel_nodes);
 HD_API void hd_plan_destroy(hd_plan *plan);
 
 /* Autotuner (no counterpart in the paper): times each search form the library
- * is prepared for and, for the tensor-core forms, work-item shapes
+ * is prepared for (HD_FORM_TC_MXF4 too when the e2m1 copy exists and D is a
+ * multiple of 256) and, for the tensor-core forms, work-item shapes
  * tile_group x super_group x (cluster, cta_group) in {4, 16, 32} x {2, 16} x
- * {(1, 1), (2, 2)}, on the
+ * {(1, 1), (2, 2)} ((2, 2) only for kind::mxf4), on the
  * given queries (the real query set, or one of the same density per window:
  * a subset's sorted blocks span wider m/z ranges and can favour another
  * schedule), and keeps the fastest as the library's
@@ -528,12 +535,16 @@ typedef enum { HD_KERNEL_ENCODE = 0, HD_KERNEL_SEARCH = 1, HD_KERNEL_KINDS = 2 }
  *      e4m3 operands, kind::f16 with bf16), the pair search's instruction
  *      and shape, on operands resident in shared memory, one CTA per SM, all
  *      SM pairs; an operation is a flop (2 per multiply-add).
+ *  HD_PEAK_TC_MXF4  tcgen05.mma.cta_group::2.kind::mxf4.block_scale with
+ *      M = 256, N = 224, K = 64 packed e2m1 components and unit ue8m0 scale
+ *      factors; its warm-up launch runs on all-(+1) operands and checks that
+ *      every accumulator holds the exact sum (HD_ERR_CUDA otherwise).
  *  HD_PEAK_POPC  32-bit population counts (the popcount form's counting
  *      instruction, Section 4.1); an operation is one popcount.
  *  HD_PEAK_LOP3  three-input logic operations on 32-bit words (the carry-save
  *      popcount form's adder); an operation is one LOP3. */
 typedef enum { HD_PEAK_TC_FP4 = 0, HD_PEAK_TC_FP8 = 1, HD_PEAK_TC_BF16 = 2, HD_PEAK_POPC = 3,
-               HD_PEAK_LOP3 = 4 } hd_peak_kind;
+               HD_PEAK_LOP3 = 4, HD_PEAK_TC_MXF4 = 5 } hd_peak_kind;
 typedef struct {
     double best_per_s;        /* operations per second of the fastest timed launch */
     double median_per_s;      /* ... of the median timed launch */

@@ -188,8 +188,7 @@ hd_status hd_cascade_search(const hd_library *lib, const uint64_t *d_q_hv, const
     if (!levels || n_levels < 1 || n_levels > HD_MAX_WINDOWS)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_cascade_search: 1 <= n_levels <= 16");
     if (std::isnan(fdr)) return hd_fail(HD_ERR_INVALID_ARG, "hd_cascade_search: fdr is NaN");
-    if (form != HD_FORM_AUTO && form != HD_FORM_POPC && form != HD_FORM_TC_FP8 && form != HD_FORM_TC_BF16 &&
-        form != HD_FORM_TC_FP4)
+    if (form != HD_FORM_AUTO && form != HD_FORM_POPC && !hd_is_tc_form(form))
         return hd_fail(HD_ERR_INVALID_ARG, "hd_cascade_search: unknown form");
     for (uint32_t l = 0; l < n_levels; ++l) {
         hd_qwin w;

@@ -69,7 +69,7 @@ hd_status check_device(int want)
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 bool form_ok(hd_search_form f)
 {
-    return f == HD_FORM_AUTO || f == HD_FORM_POPC || f == HD_FORM_TC_FP8 || f == HD_FORM_TC_BF16 || f == HD_FORM_TC_FP4;
+    return f == HD_FORM_AUTO || f == HD_FORM_POPC || hd_is_tc_form(f);
 }
 bool unit_ok(hd_tol_unit u) { return u == HD_TOL_DA || u == HD_TOL_PPM || u == HD_TOL_MASS; }
 
@@ -170,18 +170,19 @@ hd_status hd_search_dispatch(const hd_library *lib, const uint64_t *q_hv, const 
                              uint16_t *out_dist, cudaStream_t s)
 {
     if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "multi-bit library: search it with hd_search_dot");
-    auto copy_of = [&](hd_search_form f) -> const uint8_t * {
-        return f == HD_FORM_TC_FP8 ? lib->x_fp8 : (f == HD_FORM_TC_BF16 ? lib->x_bf16 : lib->x_fp4);
-    };
     if (form == HD_FORM_AUTO) {
         form = lib->auto_form;
-        const bool ok = form == HD_FORM_POPC || (form != HD_FORM_AUTO && copy_of(form));
-        if (!ok)
-            form = lib->x_fp4 ? HD_FORM_TC_FP4
-                              : (lib->x_fp8 ? HD_FORM_TC_FP8 : (lib->x_bf16 ? HD_FORM_TC_BF16 : HD_FORM_POPC));
+        const bool ok = form == HD_FORM_POPC || (form != HD_FORM_AUTO && hd_tc_copy(lib, form));
+        if (!ok) {
+            form = hd_fastest_tc_form(lib);
+            if (form == HD_FORM_AUTO) form = HD_FORM_POPC;
+        }
     }
-    if (form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16 || form == HD_FORM_TC_FP4) {
-        HD_CHECK(copy_of(form) != nullptr || lib->n == 0, "hd_search_open: call hd_library_prepare for this form first");
+    if (hd_is_tc_form(form)) {
+        HD_CHECK(hd_tc_copy(lib, form) != nullptr || lib->n == 0,
+                 "hd_search_open: call hd_library_prepare for this form first");
+        HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
+                 "hd_search_open: the kind::mxf4 form needs D to be a multiple of 256");
         return hd_search_mma_run(lib, form, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
     }
     return hd_search_popc_run(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s);
@@ -371,6 +372,7 @@ hd_status hd_measure_peak(hd_peak_kind kind, uint32_t launches, hd_peak_result *
     case HD_PEAK_TC_BF16: return hd_peak_mma_run(HD_FORM_TC_BF16, launches, out);
     case HD_PEAK_POPC: return hd_peak_alu_run(true, launches, out);
     case HD_PEAK_LOP3: return hd_peak_alu_run(false, launches, out);
+    case HD_PEAK_TC_MXF4: return hd_peak_mma_run(HD_FORM_TC_MXF4, launches, out);
     }
     return hd_fail(HD_ERR_INVALID_ARG, "hd_measure_peak: unknown kind");
 }
@@ -476,12 +478,14 @@ hd_status hd_search_dot(const hd_library *lib, const int8_t *d_q_comp, const dou
     HD_CHECK(k >= 1 && k <= 16, "hd_search_dot: k must be in [1, 16]");
     HD_CHECK(tol_ok(tol), "hd_search_dot: tol must be finite and >= 0");
     HD_CHECK(unit_ok(unit), "hd_search_dot: bad unit");
-    HD_CHECK(form == HD_FORM_AUTO || form == HD_FORM_TC_FP4 || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16,
-             "hd_search_dot: form must be AUTO or a tensor-core form");
-    if (form == HD_FORM_AUTO)
-        form = lib->x_fp4 ? HD_FORM_TC_FP4 : (lib->x_fp8 ? HD_FORM_TC_FP8 : HD_FORM_TC_BF16);
-    const uint8_t *copy = form == HD_FORM_TC_FP8 ? lib->x_fp8 : (form == HD_FORM_TC_BF16 ? lib->x_bf16 : lib->x_fp4);
-    HD_CHECK(copy || lib->n == 0, "hd_search_dot: call hd_library_prepare for this form first");
+    HD_CHECK(form == HD_FORM_AUTO || hd_is_tc_form(form), "hd_search_dot: form must be AUTO or a tensor-core form");
+    if (form == HD_FORM_AUTO) {
+        form = hd_fastest_tc_form(lib);
+        if (form == HD_FORM_AUTO) form = HD_FORM_TC_BF16;
+    }
+    HD_CHECK(hd_tc_copy(lib, form) || lib->n == 0, "hd_search_dot: call hd_library_prepare for this form first");
+    HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
+             "hd_search_dot: the kind::mxf4 form needs D to be a multiple of 256");
     if (n_q == 0) return HD_OK;
     HD_CHECK(d_q_comp && d_q_mz && d_q_charge && d_out_idx && d_out_score, "hd_search_dot: null buffer");
     HD_CHECK(aligned16(d_q_comp), "hd_search_dot: d_q_comp must be 16-byte aligned");
@@ -711,8 +715,9 @@ hd_status hd_library_status(hd_library *lib)
 hd_status hd_library_prepare(hd_library *lib, hd_search_form form)
 {
     HD_CHECK(lib, "hd_library_prepare: null library");
-    HD_CHECK(form == HD_FORM_POPC || form == HD_FORM_TC_FP8 || form == HD_FORM_TC_BF16 || form == HD_FORM_TC_FP4,
-             "hd_library_prepare: unknown form");
+    HD_CHECK(form == HD_FORM_POPC || hd_is_tc_form(form), "hd_library_prepare: unknown form");
+    HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
+             "hd_library_prepare: the kind::mxf4 form needs D to be a multiple of 256");
     HD_CHECK(form != HD_FORM_POPC || hd_lib_binary(lib), "hd_library_prepare: popc scores binary HVs only");
     hd_status st = check_device(lib->device);
     if (st != HD_OK || form == HD_FORM_POPC) return st;

@@ -198,6 +198,26 @@ hd_status hd_search_mma_dot_run(const hd_library *lib, hd_search_form form, cons
                                 const double *q_mz, const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win,
                                 uint32_t k, uint32_t *out_idx, int32_t *out_score, cudaStream_t s);
 inline uint32_t hd_comp_max(uint32_t bits) { return (1u << (bits - 1)) - 1u; }
+// The tensor-core copy a form scores (kind::mxf4 shares the e2m1 rows), and
+// the fastest tensor-core form the library is prepared for (HD_FORM_AUTO when
+// none): kind::mxf4 needs D to be a multiple of 256.
+inline const uint8_t *hd_tc_copy(const hd_library *lib, hd_search_form f)
+{
+    return f == HD_FORM_TC_FP8 ? lib->x_fp8
+         : f == HD_FORM_TC_BF16 ? lib->x_bf16
+         : (f == HD_FORM_TC_FP4 || f == HD_FORM_TC_MXF4) ? lib->x_fp4 : nullptr;
+}
+inline bool hd_is_tc_form(hd_search_form f)
+{
+    return f == HD_FORM_TC_FP8 || f == HD_FORM_TC_BF16 || f == HD_FORM_TC_FP4 || f == HD_FORM_TC_MXF4;
+}
+inline hd_search_form hd_fastest_tc_form(const hd_library *lib)
+{
+    if (lib->x_fp4) return lib->dim % 256 == 0 ? HD_FORM_TC_MXF4 : HD_FORM_TC_FP4;
+    if (lib->x_fp8) return HD_FORM_TC_FP8;
+    if (lib->x_bf16) return HD_FORM_TC_BF16;
+    return HD_FORM_AUTO;
+}
 // Entry points that score binary HVs refuse a multi-bit library.
 inline bool hd_lib_binary(const hd_library *lib) { return lib->bits == 1; }
 

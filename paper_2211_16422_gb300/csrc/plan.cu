@@ -143,13 +143,12 @@ hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const dou
     cand.push_back({HD_FORM_POPC, 0, 0, 0, 0, 0.0});
     const uint32_t tgs[3] = {4, 16, 32}, sgs[2] = {2, 16};
     const uint32_t shapes[2][2] = {{1, 1}, {2, 2}};   // (cluster, cta_group): one SM, or the SM pair
-    for (hd_search_form f : {HD_FORM_TC_FP4, HD_FORM_TC_FP8, HD_FORM_TC_BF16}) {
-        if ((f == HD_FORM_TC_FP8 && !lib->x_fp8) || (f == HD_FORM_TC_BF16 && !lib->x_bf16) ||
-            (f == HD_FORM_TC_FP4 && !lib->x_fp4))
-            continue;
+    for (hd_search_form f : {HD_FORM_TC_MXF4, HD_FORM_TC_FP4, HD_FORM_TC_FP8, HD_FORM_TC_BF16}) {
+        if (!hd_tc_copy(lib, f) || (f == HD_FORM_TC_MXF4 && lib->dim % 256 != 0)) continue;
         for (uint32_t tg : tgs)
             for (uint32_t sg : sgs)
-                for (const auto &sh : shapes) cand.push_back({f, tg, sg, sh[0], sh[1], 0.0});
+                for (const auto &sh : shapes)   // kind::mxf4 runs on SM pairs only
+                    if (f != HD_FORM_TC_MXF4 || sh[1] == 2) cand.push_back({f, tg, sg, sh[0], sh[1], 0.0});
     }
     scoped_stream ss;
     HD_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));

@@ -60,7 +60,9 @@ using namespace hd_search;
 // 1 byte), FMT_E2M1 (kind::f8f6f4, 4 bits packed in HBM and unpacked by the TMA
 // into 16-byte shared-memory containers of 16 values, so the shared-memory
 // image of a K-chunk is that of e4m3 while HBM and L2 carry half the bytes).
-constexpr int FMT_BF16 = 0, FMT_E4M3 = 1, FMT_E2M1 = 2;
+// FMT_MXF4: the e2m1 rows of FMT_E2M1, kept packed in shared memory and
+// scored by the block-scaled kind::mxf4 (SM-pair form only).
+constexpr int FMT_BF16 = 0, FMT_E4M3 = 1, FMT_E2M1 = 2, FMT_MXF4 = 3;
 // instruction-descriptor A/B format code of each operand format
 __host__ __device__ constexpr uint32_t fmt_code(int fmt) { return fmt == FMT_BF16 ? 1u : (fmt == FMT_E4M3 ? 0u : 5u); }
 // Transaction bytes a load of `smem_bytes` of operand counts on its mbarrier:
@@ -88,7 +90,6 @@ constexpr uint32_t TMEM_COLS = 2 * TN;
 #endif
 constexpr int EPI2_WARPS = HD_MMA2_EPI_WARPS;
 constexpr int EPI2_SPLIT = EPI2_WARPS / 4;
-constexpr int EPI2_COLS = TN / EPI2_SPLIT;   // accumulator columns per epilogue warp
 static_assert(EPI2_WARPS % 4 == 0 && (TN / 32) % EPI2_SPLIT == 0, "epilogue split");
 constexpr int THREADS2 = 64 + 32 * EPI2_WARPS;
 constexpr uint32_t EPI2_THREADS = 32 * EPI2_WARPS;
@@ -641,6 +642,69 @@ __host__ __device__ constexpr uint32_t instr_desc2()
            ((uint32_t)((2 * TM) >> 4) << 24);
 }
 
+// ------------------------------------------------ block-scaled fp4 (kind::mxf4)
+// e2m1 operands packed two per byte in shared memory as in HBM, scored by the
+// block-scaled tcgen05.mma kind::mxf4: 64 components of K per instruction and
+// one ue8m0 scale factor per 32 components of a row, every one 1.0 (0x7F), so
+// S = sum_d x_d y_d as before.  N = 224 lets two accumulators and the two
+// scale-factor regions share the 512 tensor-memory columns:
+//   [0, 224) accumulator 0, [224, 256) A scale factors,
+//   [256, 480) accumulator 1, [480, 512) B scale factors.
+constexpr int TN_MX = 224;
+constexpr uint32_t MX_SFA_COL = 224, MX_BUF1_COL = 256, MX_SFB_COL = 480;
+constexpr uint32_t B2MX_BYTES = (TN_MX / 2) * KB;   // 112 reference rows of 128 bytes (256 components)
+
+// Block-scaled instruction descriptor: B scale-factor id 0 (bits 4-5), A and
+// B e2m1 (code 1 of kind::mxf4, bits 7 and 10), both K-major, N >> 3 at bit
+// 17, ue8m0 scale factors (bit 23), M >> 4 at bit 24, A scale-factor id 0
+// (bits 29-30), dense K = 64 (bit 31 clear).
+__host__ __device__ constexpr uint32_t instr_desc_mxf4()
+{
+    return (1u << 7) | (1u << 10) | ((uint32_t)(TN_MX >> 3) << 17) | (1u << 23) | ((uint32_t)((2 * TM) >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_issue2_mxf4(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                                uint32_t sfa, uint32_t sfb, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 32 consecutive columns of this warp's lane quarter, all set to v.
+__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Every scale factor 1.0: the warp fills its lane quarter of both regions.
+__device__ __forceinline__ void mxf4_unit_scales(uint32_t tmem, uint32_t quarter)
+{
+    const uint32_t lanes = (quarter * 32u) << 16;
+    tmem_fill32(tmem + lanes + MX_SFA_COL, 0x7F7F7F7Fu);
+    tmem_fill32(tmem + lanes + MX_SFB_COL, 0x7F7F7F7Fu);
+    tmem_st_wait();
+}
+
+// Per-format shape of the pair kernel: reference rows per tile (the MMA's N),
+// bytes of one stage, shared memory, and the tensor-memory column of each
+// accumulator.
+template <int FMT> __host__ __device__ constexpr uint32_t pair_tn() { return FMT == FMT_MXF4 ? (uint32_t)TN_MX : (uint32_t)TN; }
+template <int FMT> __host__ __device__ constexpr uint32_t pair_stage_bytes() { return A_BYTES + (pair_tn<FMT>() / 2) * KB; }
+template <int FMT> __host__ __device__ constexpr uint32_t pair_smem_bytes()
+{
+    return STAGES2 * pair_stage_bytes<FMT>() + PAD2_BYTES + 1024 + 256;
+}
+template <int FMT> __device__ __forceinline__ uint32_t pair_acc_col(uint32_t buf)
+{
+    return FMT == FMT_MXF4 ? (buf ? MX_BUF1_COL : 0u) : buf * TN;
+}
+static_assert(pair_smem_bytes<FMT_MXF4>() <= 232448 && (TN_MX / 32) % EPI2_SPLIT == 0, "mxf4 pair shape");
+
 // A cluster of two CTAs on an SM pair (cluster ranks 0 and 1; rank 0 issues
 // the pair's MMAs).  Each CTA holds its own block of 128 queries (A) and its
 // half of the pair's reference tile (B); all loads complete on rank 0's stage
@@ -650,9 +714,12 @@ __global__ void __launch_bounds__(THREADS2, 1)
 k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
     constexpr uint32_t CS = 2;
+    constexpr uint32_t TNF = pair_tn<FMT>();                // reference rows per tile
+    constexpr uint32_t STAGE2F = pair_stage_bytes<FMT>();   // A block slice + this CTA's half of the tile
+    constexpr uint32_t EPI2_COLS_F = TNF / EPI2_SPLIT;      // accumulator columns per epilogue warp
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES2 * STAGE2_BYTES + PAD2_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES2 * STAGE2F + PAD2_BYTES);
     uint64_t *empty = full + STAGES2;
     uint64_t *acc_full = empty + STAGES2;
     uint64_t *acc_empty = acc_full + 2;
@@ -694,6 +761,13 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         *abort_flag = 1;
         hd_flag(a.status, HD_DEV_TMEM);
     }
+    if (FMT == FMT_MXF4) {   // unit scale factors in both CTAs before the first MMA
+        if (warp >= 2) mxf4_unit_scales(tmem, (uint32_t)warp & 3u);
+        tc_fence_before();
+        __syncthreads();
+        cluster_sync();
+        tc_fence_after();
+    }
     __syncthreads();
     const uint32_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
     const uint32_t total = a.pair_start[a.n_pairs];
@@ -710,13 +784,13 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 item_range(a, item, b, t0, t1);
                 const int32_t ya = (int32_t)((b * CS + crank) * TM);
                 for (uint32_t t = t0; t < t1 && !*abort_flag; ++t) {
-                    const int32_t rb = (int32_t)(t * TN + crank * (TN / 2));
+                    const int32_t rb = (int32_t)(t * TNF + crank * (TNF / 2));
                     for (uint32_t c = 0; c < nchunks; ++c, ++it) {
                         const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
                         if (!mbar_wait(&empty[s], ph ^ 1u, a.wait_ns)) { give_up(); break; }
-                        if (crank == 0) mbar_expect_tx(&full[s], tx_bytes(FMT, 2 * STAGE2_BYTES));
+                        if (crank == 0) mbar_expect_tx(&full[s], tx_bytes(FMT, 2 * STAGE2F));
                         if (a.stall && it == 0) continue;   // nothing ever completes this stage
-                        uint8_t *sa = smem + s * STAGE2_BYTES, *sb = sa + A_BYTES;
+                        uint8_t *sa = smem + s * STAGE2F, *sb = sa + A_BYTES;
                         const uint32_t bar = full0 + s * 8u;
                         const int32_t x = (int32_t)(c * KB);
                         if (HD_MMA2_HINT_A) tma_load_2d_pair_hint(sa, &qmap, x, ya, bar, pol_a);
@@ -731,7 +805,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         if (crank == 0) {
             // ------------------------------------------- MMA issuer (rank 0)
             if (lane == 0) {
-                constexpr uint32_t idesc = instr_desc2<FMT>();
+                constexpr uint32_t idesc = FMT == FMT_MXF4 ? instr_desc_mxf4() : instr_desc2<FMT>();
                 uint32_t it = 0, acc_it = 0;
                 for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
                     uint32_t b, t0, t1;
@@ -741,17 +815,22 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                         const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
                         if (!mbar_wait(&acc_empty[buf], aph ^ 1u, a.wait_ns)) { give_up(); break; }
                         tc_fence_after();
-                        const uint32_t d_tmem = tmem + buf * TN;
+                        const uint32_t d_tmem = tmem + pair_acc_col<FMT>(buf);
                         bool ok = true;
                         for (uint32_t c = 0; c < nchunks; ++c, ++it) {
                             const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
                             if (!mbar_wait(&full[s], ph, a.wait_ns)) { give_up(); ok = false; break; }
                             tc_fence_after();
-                            const uint32_t sa = smem_addr(smem + s * STAGE2_BYTES), sb = sa + A_BYTES;
+                            const uint32_t sa = smem_addr(smem + s * STAGE2F), sb = sa + A_BYTES;
                             const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
 #pragma unroll
-                            for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes of K per instruction
-                                mma_issue2<FMT>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
+                            for (uint32_t j = 0; j < KB / 32; ++j) {   // 32 bytes of K per instruction
+                                if (FMT == FMT_MXF4)
+                                    mma_issue2_mxf4(d_tmem, da + 2 * j, db + 2 * j, idesc, tmem + MX_SFA_COL,
+                                                    tmem + MX_SFB_COL, (c | j) != 0);
+                                else
+                                    mma_issue2<FMT>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
+                            }
                             mma_commit2_mc(&empty[s], 0x3);
                         }
                         if (!ok) break;
@@ -791,13 +870,13 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
             for (uint32_t t = t0; t < t1; ++t, ++acc_it) {
                 const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
                 const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
-                const uint32_t r0 = t * TN;
+                const uint32_t r0 = t * TNF;
                 if (!mbar_wait(&acc_full[buf], aph, a.wait_ns)) { give_up(); ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
-                for (uint32_t cg = slice * (EPI2_COLS / 32); cg < (slice + 1) * (EPI2_COLS / 32); ++cg) {
+                for (uint32_t cg = slice * (EPI2_COLS_F / 32); cg < (slice + 1) * (EPI2_COLS_F / 32); ++cg) {
                     uint32_t v[32];
-                    tmem_ld32(tmem + lane_addr + buf * TN + cg * 32, v);
+                    tmem_ld32(tmem + lane_addr + pair_acc_col<FMT>(buf) + cg * 32, v);
                     tmem_ld_wait();
                     score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
                 }
@@ -928,13 +1007,107 @@ __global__ void __launch_bounds__(PEAK_THREADS, 1) k_peak_mma2(uint32_t iters, u
     if (warp == 1) tmem_dealloc2(tmem, TMEM2_COLS);
 }
 
+// The kind::mxf4 instruction alone (the mxf4 search's roofline), as
+// k_peak_mma2 for the other kinds.  With `check`, every operand is +1 and
+// the accumulators start cleared: the last accumulator then holds 64
+// instructions-groups x 4 x 64 products = 16384 in every element, which the
+// kernel verifies (HD_DEV_BAD_INPUT in the status word otherwise).
+__global__ void __launch_bounds__(PEAK_THREADS, 1)
+k_peak_mxf4(uint32_t iters, uint32_t check, uint64_t wait_ns, uint32_t *status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *done = reinterpret_cast<uint64_t *>(smem + A_BYTES + B2MX_BYTES);
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t crank = cluster_rank();
+    uint32_t *w = reinterpret_cast<uint32_t *>(smem);
+    for (uint32_t i = threadIdx.x; i < (A_BYTES + B2MX_BYTES) / 4; i += blockDim.x) {
+        const bool neg = !check && ((i * 2654435761u) >> 31) != 0u;
+        w[i] = neg ? 0xAAAAAAAAu : 0x22222222u;   // e2m1 -1 / +1 in both nibbles
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc2(&s_tmem, TMEM2_COLS);
+        tmem_relinquish2();
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    if (threadIdx.x == 0 && ld_cluster_u32(cluster_addr(&s_tmem, crank ^ 1u)) != tmem) {
+        s_abort = 1;
+        hd_flag(status, HD_DEV_TMEM);
+    }
+    const uint32_t quarter = (uint32_t)warp & 3u, lanes = (quarter * 32u) << 16;
+    mxf4_unit_scales(tmem, quarter);
+    if (check) {
+        for (uint32_t c = 0; c < (uint32_t)TN_MX; c += 32) {
+            tmem_fill32(tmem + lanes + c, 0u);
+            tmem_fill32(tmem + lanes + MX_BUF1_COL + c, 0u);
+        }
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    const bool run = s_abort == 0;
+    if (warp == 1 && lane == 0 && run) {
+        if (crank == 0) {
+            constexpr uint32_t idesc = instr_desc_mxf4();
+            const uint32_t sa = smem_addr(smem), sb = sa + A_BYTES;
+            const uint64_t da = sw128_desc(sa), db = sw128_desc(sb);
+            for (uint32_t it = 0; it < iters; ++it) {
+                const uint32_t d_tmem = tmem + (((it >> 6) & 1u) ? MX_BUF1_COL : 0u);
+#pragma unroll
+                for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes = 64 components of K per instruction
+                    mma_issue2_mxf4(d_tmem, da + 2 * j, db + 2 * j, idesc, tmem + MX_SFA_COL, tmem + MX_SFB_COL,
+                                    ((it & 63u) | j) != 0);
+            }
+            mma_commit2_mc(done, 0x3);
+        }
+        if (!mbar_wait(done, 0, wait_ns)) hd_flag(status, HD_DEV_TIMEOUT);
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    if (check && run && iters >= 64) {
+        const uint32_t col0 = ((iters - 1) >> 6) & 1u ? MX_BUF1_COL : 0u;
+        bool bad = false;
+#pragma unroll 1
+        for (uint32_t cg = 0; cg < (uint32_t)TN_MX / 32; ++cg) {
+            uint32_t v[32];
+            tmem_ld32(tmem + lanes + col0 + cg * 32, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 32; ++e) bad |= __uint_as_float(v[e]) != 16384.0f;
+        }
+        if (bad) hd_flag(status, HD_DEV_BAD_INPUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc2(tmem, TMEM2_COLS);
+}
+
 // Work list of the L2-blocked schedule (one CTA of 1024 threads): per query
 // block the absolute tile range covering the union of its windows, then the
 // item count of every (super-group, block) pair and its exclusive scan.
 __global__ void __launch_bounds__(1024)
 k_worklist_l2(const uint32_t *__restrict__ lo, const uint32_t *__restrict__ hi, uint32_t n_q, uint32_t bq,
-              uint32_t n_blocks, uint32_t tg, uint32_t sg, uint32_t n_super, uint32_t *__restrict__ blk_t0,
-              uint32_t *__restrict__ blk_t1, uint32_t *__restrict__ pair_start)
+              uint32_t tn, uint32_t n_blocks, uint32_t tg, uint32_t sg, uint32_t n_super,
+              uint32_t *__restrict__ blk_t0, uint32_t *__restrict__ blk_t1, uint32_t *__restrict__ pair_start)
 {
     __shared__ uint32_t sh[33];
     for (uint32_t b = threadIdx.x; b < n_blocks; b += blockDim.x) {
@@ -945,8 +1118,8 @@ k_worklist_l2(const uint32_t *__restrict__ lo, const uint32_t *__restrict__ hi, 
                 l = min(l, lo[s]);
                 h = max(h, hi[s]);
             }
-        blk_t0[b] = h > l ? l / TN : 0u;
-        blk_t1[b] = h > l ? (h + TN - 1) / TN : 0u;
+        blk_t0[b] = h > l ? l / tn : 0u;
+        blk_t1[b] = h > l ? (h + tn - 1) / tn : 0u;
     }
     __syncthreads();
     const uint32_t n_pairs = n_super * n_blocks;
@@ -1192,16 +1365,23 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
                   uint32_t n_q, const hd_qwin &win, uint32_t k, uint32_t *out_idx, uint16_t *out_dist,
                   cudaStream_t s, const hd_mma_tuning &tune, const dot_io *dot = nullptr)
 {
-    const bool pair = tune.cta_group == 2;   // SM pairs, M = 256 (cluster of 2)
+    constexpr int XF = FMT == FMT_MXF4 ? FMT_E2M1 : FMT;   // format of the rows in HBM
+    const bool pair = FMT == FMT_MXF4 || tune.cta_group == 2;   // SM pairs, M = 256 (cluster of 2)
     const uint32_t cs = pair ? 2u : 1u;      // CTAs per cluster
     const uint32_t n_blocks = (n_q + TM * cs - 1) / (TM * cs);
     // shared-memory bytes of one operand row (the K extent the kernel walks) and HBM bytes
-    const uint32_t row_bytes = lib->dim * (FMT == FMT_BF16 ? 2u : 1u);
-    const uint32_t g_row_bytes = global_row_bytes<FMT>(lib->dim);
-    const uint8_t *lib_x = FMT == FMT_BF16 ? lib->x_bf16 : (FMT == FMT_E4M3 ? lib->x_fp8 : lib->x_fp4);
+    const uint32_t row_bytes = FMT == FMT_MXF4 ? lib->dim / 2 : lib->dim * (FMT == FMT_BF16 ? 2u : 1u);
+    const uint32_t g_row_bytes = global_row_bytes<XF>(lib->dim);
+    if (FMT == FMT_MXF4 && lib->dim % 256 != 0)
+        return hd_fail(HD_ERR_UNSUPPORTED, "kind::mxf4 form needs D to be a multiple of 256");
+    const uint8_t *lib_x = XF == FMT_BF16 ? lib->x_bf16 : (XF == FMT_E4M3 ? lib->x_fp8 : lib->x_fp4);
     if (!lib_x) return hd_fail(HD_ERR_INVALID_ARG, "library not prepared for this tensor-core form");
-    auto kern = pair ? k_search_mma2<K, FMT> : k_search_mma<K, FMT>;
-    const uint32_t smem_bytes = pair ? SMEM2_BYTES : SMEM_BYTES;
+    auto kern = [&]() {
+        if constexpr (FMT == FMT_MXF4) return k_search_mma2<K, FMT>;
+        else return pair ? k_search_mma2<K, FMT> : k_search_mma<K, FMT>;
+    }();
+    const uint32_t tn = pair ? pair_tn<FMT>() : (uint32_t)TN;   // reference rows per tile
+    const uint32_t smem_bytes = pair ? pair_smem_bytes<FMT>() : SMEM_BYTES;
     const uint32_t threads = pair ? (uint32_t)THREADS2 : (uint32_t)THREADS;
     HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
     if (cs > 1) HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
@@ -1224,7 +1404,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
         grid = std::min(grid, (uint32_t)n_cl * cs);
     }
     const uint32_t tg = tune.tile_group, sg = tune.super_group;
-    const uint32_t n_tiles = (lib->n + TN - 1) / TN;
+    const uint32_t n_tiles = (lib->n + tn - 1) / tn;
     const uint32_t n_super = (n_tiles + tg * sg - 1) / (tg * sg);
     const size_t n_pairs = (size_t)n_super * n_blocks;
     if (n_pairs >= 0xFFFFFFFFull) return hd_fail(HD_ERR_UNSUPPORTED, "work list too large");
@@ -1254,11 +1434,12 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     }
     carve(ar, &perm, &lo, &hi, &bt0, &bt1, &pst, &top, &locks, &qx);
     CUtensorMap qmap, lmap;
+    // e2m1 for kind::f8f6f4 is unpacked by the TMA; every other form copies its bytes as they are
     hd_status st = FMT == FMT_E2M1 ? make_map_e2m1(&qmap, qx, n_q, lib->dim, TM)
                                    : make_map(&qmap, qx, n_q, row_bytes, TM);
     if (st == HD_OK)
-        st = FMT == FMT_E2M1 ? make_map_e2m1(&lmap, lib_x, lib->n, lib->dim, TN / cs)
-                             : make_map(&lmap, lib_x, lib->n, row_bytes, TN / cs);
+        st = FMT == FMT_E2M1 ? make_map_e2m1(&lmap, lib_x, lib->n, lib->dim, tn / cs)
+                             : make_map(&lmap, lib_x, lib->n, row_bytes, tn / cs);
     if (st != HD_OK) {
         cudaFreeAsync(ar.base, s);
         return st;
@@ -1267,15 +1448,15 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     HD_CUDA_TRY(cudaMemsetAsync(locks, 0, (size_t)n_blocks * cs * sizeof(uint32_t), s));
     hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, perm, ar, s);
     if (dot)
-        hd_count_launches(1), k_expand_comp<FMT><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(
+        hd_count_launches(1), k_expand_comp<XF><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(
             dot->q_comp, perm, n_q, lib->dim, (int)hd_comp_max(lib->bits), qx, lib->status.dev);
     else
-        hd_count_launches(1), k_expand<FMT><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
+        hd_count_launches(1), k_expand<XF><<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_hv, perm, n_q, lib->W, qx);
     const uint32_t mq = hd_comp_max(lib->bits);
     const uint32_t bias = dot ? lib->dim * mq * mq : lib->dim, shift = dot ? 0u : 1u;
     hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z,
                                                                           perm, n_q, win, lo, hi);
-    hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, TM * cs, n_blocks, tg, sg, n_super, bt0, bt1, pst);
+    hd_count_launches(1), k_worklist_l2<<<1, 1024, 0, s>>>(lo, hi, n_q, TM * cs, tn, n_blocks, tg, sg, n_super, bt0, bt1, pst);
     mma_args ma{lib->orig, lo, hi, bt0, bt1, pst, top, locks, lib->status.dev, n_q, n_blocks, (uint32_t)n_pairs,
                 tg, sg, lib->dim, row_bytes, hd_wait_limit(lib), hd_take_injected_stall(lib) ? 1u : 0u,
                 bias, shift};
@@ -1321,6 +1502,7 @@ hd_status run_fmt(const hd_library *lib, const uint64_t *q_hv, const double *q_m
 }  // namespace
 
 namespace {
+// Operand format of a tensor-core form (kind::mxf4 keeps the e2m1 rows of HD_FORM_TC_FP4).
 int form_fmt(hd_search_form form)
 {
     return form == HD_FORM_TC_BF16 ? FMT_BF16 : (form == HD_FORM_TC_FP8 ? FMT_E4M3 : FMT_E2M1);
@@ -1374,6 +1556,8 @@ hd_status hd_search_mma_run(const hd_library *lib, hd_search_form form, const ui
     if (tu.super_group == 0) tu.super_group = 16;
     if (tu.cta_group != 1) tu.cta_group = 2;   // default: SM pairs
     tu.cluster = tu.cta_group;
+    if (form == HD_FORM_TC_MXF4)
+        return run_fmt<FMT_MXF4>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
     const int fmt = form_fmt(form);
     if (fmt == FMT_E4M3) return run_fmt<FMT_E4M3>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
     if (fmt == FMT_BF16) return run_fmt<FMT_BF16>(lib, q_hv, q_mz, q_charge, n_q, win, k, out_idx, out_dist, s, tu);
@@ -1396,6 +1580,8 @@ hd_status hd_search_mma_dot_run(const hd_library *lib, hd_search_form form, cons
     if (tu.cta_group != 1) tu.cta_group = 2;   // default: SM pairs
     tu.cluster = tu.cta_group;
     const dot_io io{q_comp, out_score};
+    if (form == HD_FORM_TC_MXF4)
+        return run_fmt<FMT_MXF4>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
     const int fmt = form_fmt(form);
     if (fmt == FMT_E4M3) return run_fmt<FMT_E4M3>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
     if (fmt == FMT_BF16) return run_fmt<FMT_BF16>(lib, nullptr, q_mz, q_charge, n_q, win, k, out_idx, nullptr, s, tu, &io);
@@ -1404,12 +1590,16 @@ hd_status hd_search_mma_dot_run(const hd_library *lib, hd_search_form form, cons
 
 hd_status hd_peak_mma_run(hd_search_form form, uint32_t launches, hd_peak_result *out)
 {
+    const bool mx = form == HD_FORM_TC_MXF4;
     const int fmt = form_fmt(form);
-    auto kern = fmt == FMT_BF16 ? k_peak_mma2<FMT_BF16> : (fmt == FMT_E4M3 ? k_peak_mma2<FMT_E4M3> : k_peak_mma2<FMT_E2M1>);
+    using peak_fn = void (*)(uint32_t, uint64_t, uint32_t *);
+    const peak_fn kern = fmt == FMT_BF16 ? k_peak_mma2<FMT_BF16>
+                       : (fmt == FMT_E4M3 ? k_peak_mma2<FMT_E4M3> : k_peak_mma2<FMT_E2M1>);
+    const void *fn = mx ? (const void *)k_peak_mxf4 : (const void *)kern;
     int dev = 0, n_sms = 0;
     HD_CUDA_TRY(cudaGetDevice(&dev));
     HD_CUDA_TRY(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
-    HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PEAK_SMEM_BYTES));
+    HD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PEAK_SMEM_BYTES));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((uint32_t)n_sms / 2u * 2u);
     cfg.blockDim = dim3(PEAK_THREADS);
@@ -1422,12 +1612,15 @@ hd_status hd_peak_mma_run(hd_search_form form, uint32_t launches, hd_peak_result
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n_cl = 0;
-    HD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n_cl, kern, &cfg));
+    HD_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n_cl, fn, &cfg));
     if (n_cl < 1) return hd_fail(HD_ERR_UNSUPPORTED, "peak kernel: SM-pair cluster does not fit on this GPU");
     cfg.gridDim = dim3(std::min((uint32_t)n_sms / 2u, (uint32_t)n_cl) * 2u);
     const uint32_t iters = 16384;   // 65,536 instructions per SM pair
-    const uint32_t k_per_instr = fmt == FMT_BF16 ? 16u : 32u;
-    const uint64_t flops = (uint64_t)(cfg.gridDim.x / 2) * iters * (KB / 32) * 2ull * (2 * TM) * TN * k_per_instr;
+    // components of K per instruction: 32 bytes of bf16, e4m3 / e2m1 containers, or packed e2m1
+    const uint32_t k_per_instr = mx ? 64u : (fmt == FMT_BF16 ? 16u : 32u);
+    const uint32_t n_per_instr = mx ? (uint32_t)TN_MX : (uint32_t)TN;
+    const uint64_t flops =
+        (uint64_t)(cfg.gridDim.x / 2) * iters * (KB / 32) * 2ull * (2 * TM) * n_per_instr * k_per_instr;
     uint32_t *status = nullptr;
     HD_CUDA_TRY(cudaMalloc(&status, sizeof(uint32_t)));
     HD_CUDA_TRY(cudaMemset(status, 0, sizeof(uint32_t)));
@@ -1439,10 +1632,11 @@ hd_status hd_peak_mma_run(hd_search_form form, uint32_t launches, hd_peak_result
     cfg.stream = s;
     std::vector<double> ms;
     hd_status st = HD_OK;
-    for (uint32_t r = 0; r <= launches && st == HD_OK; ++r) {   // launch 0 warms up
+    for (uint32_t r = 0; r <= launches && st == HD_OK; ++r) {   // launch 0 warms up (and checks mxf4 sums)
         cudaEventRecord(e0, s);
         hd_count_launches(1);
-        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, iters, (uint64_t)HD_WAIT_NS, status);
+        cudaError_t e = mx ? cudaLaunchKernelEx(&cfg, k_peak_mxf4, iters, r == 0 ? 1u : 0u, (uint64_t)HD_WAIT_NS, status)
+                           : cudaLaunchKernelEx(&cfg, kern, iters, (uint64_t)HD_WAIT_NS, status);
         cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
@@ -1456,7 +1650,10 @@ hd_status hd_peak_mma_run(hd_search_form form, uint32_t launches, hd_peak_result
     uint32_t flags = 0;
     if (st == HD_OK && cudaMemcpy(&flags, status, sizeof(flags), cudaMemcpyDeviceToHost) != cudaSuccess)
         st = hd_fail(HD_ERR_CUDA, "peak kernel: status read failed");
-    if (st == HD_OK && flags) st = hd_fail(flags & HD_DEV_TIMEOUT ? HD_ERR_TIMEOUT : HD_ERR_CUDA, "peak kernel: device wait failed");
+    if (st == HD_OK && (flags & HD_DEV_BAD_INPUT))
+        st = hd_fail(HD_ERR_CUDA, "peak kernel: kind::mxf4 sums differ from the exact value");
+    else if (st == HD_OK && flags)
+        st = hd_fail(flags & HD_DEV_TIMEOUT ? HD_ERR_TIMEOUT : HD_ERR_CUDA, "peak kernel: device wait failed");
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);

@@ -384,12 +384,9 @@ hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_p
     srv->multibit = !hd_lib_binary(lib);
     srv->form = params->form;
     if (srv->multibit) {   // the dot-product search runs on a tensor-core copy the library holds
-        if (srv->form == HD_FORM_AUTO)
-            srv->form = lib->x_fp4 ? HD_FORM_TC_FP4 : (lib->x_fp8 ? HD_FORM_TC_FP8 : HD_FORM_TC_BF16);
-        const uint8_t *copy = srv->form == HD_FORM_TC_FP4 ? lib->x_fp4
-                            : srv->form == HD_FORM_TC_FP8 ? lib->x_fp8
-                            : srv->form == HD_FORM_TC_BF16 ? lib->x_bf16 : nullptr;
-        if (!copy && lib->n)
+        if (srv->form == HD_FORM_AUTO) srv->form = hd_fastest_tc_form(lib);
+        if (!hd_is_tc_form(srv->form) || (!hd_tc_copy(lib, srv->form) && lib->n) ||
+            (srv->form == HD_FORM_TC_MXF4 && lib->dim % 256 != 0))
             return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: multi-bit library needs a prepared tensor-core form");
     }
     const size_t row_tc = (size_t)lib->dim * 2;

@@ -19,9 +19,9 @@ from . import build as _build
 
 HD_OK, HD_ERR_INVALID_ARG, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_TIMEOUT, HD_ERR_UNSUPPORTED = range(6)
 HD_TOL_DA, HD_TOL_PPM, HD_TOL_MASS = 0, 1, 2
-HD_FORM_AUTO, HD_FORM_POPC, HD_FORM_TC_FP8, HD_FORM_TC_BF16, HD_FORM_TC_FP4 = 0, 1, 2, 3, 4
+HD_FORM_AUTO, HD_FORM_POPC, HD_FORM_TC_FP8, HD_FORM_TC_BF16, HD_FORM_TC_FP4, HD_FORM_TC_MXF4 = 0, 1, 2, 3, 4, 5
 FORMS = {"auto": HD_FORM_AUTO, "popc": HD_FORM_POPC, "tc_fp8": HD_FORM_TC_FP8, "tc_bf16": HD_FORM_TC_BF16,
-         "tc_fp4": HD_FORM_TC_FP4}
+         "tc_fp4": HD_FORM_TC_FP4, "tc_mxf4": HD_FORM_TC_MXF4}
 NO_IDX, NO_DIST = 0xFFFFFFFF, 0xFFFF
 
 
@@ -375,7 +375,8 @@ def hd_search_dot(lib: Library, q_comp, q_mz, q_charge, tol, unit="da", k=1, for
 
 
 def hd_library_prepare(lib: Library, form: str):
-    """Build the library's copy for a tensor-core form ('tc_fp8' or 'tc_bf16')."""
+    """Build the library's copy for a tensor-core form ('tc_fp4' / 'tc_mxf4' share the e2m1
+    copy; 'tc_fp8', 'tc_bf16')."""
     _check(load().hd_library_prepare(lib.handle, FORMS[form]))
 
 
@@ -588,7 +589,7 @@ class _PeakResult(C.Structure):
                 ("ops_per_launch", C.c_uint64), ("sms", C.c_uint32), ("launches", C.c_uint32)]
 
 
-PEAK_KINDS = {"tc_fp4": 0, "tc_fp8": 1, "tc_bf16": 2, "popc": 3, "lop3": 4}
+PEAK_KINDS = {"tc_fp4": 0, "tc_fp8": 1, "tc_bf16": 2, "popc": 3, "lop3": 4, "tc_mxf4": 5}
 
 
 def hd_measure_peak(kind: str, launches: int = 10):

@@ -79,7 +79,7 @@ def test_multi_window_all_forms_exact(hd, D):
     for f in ("tc_fp8", "tc_bf16", "tc_fp4"):
         hd.hd_library_prepare(lib, f)
     oi, od = _oracle_by_class(D, oracle_side.hvs(refs, D, 32, 0), refs, oracle_side.hvs(qs, D, 32, 0), qs, cls, 5)
-    for form in ("popc", "tc_fp8", "tc_bf16", "tc_fp4"):
+    for form in ("popc", "tc_fp8", "tc_bf16", "tc_fp4", "tc_mxf4"):
         i, d = hd.hd_search_open_multi(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, 5,
                                        form=form)
         torch.cuda.synchronize()
@@ -209,6 +209,10 @@ def test_batched_full_size_sampled(hd):
     torch.cuda.synchronize()
     lib.status()
     assert np.array_equal(pi, hd.as_u32(ci)) and np.array_equal(pd, hd.as_u16(cd))
+    mi, md = hd.hd_search_open_multi(lib, plan.q_hv, q_mz, q_z, q_cls, windows, k, form="tc_mxf4")
+    torch.cuda.synchronize()
+    lib.status()
+    assert np.array_equal(pi, hd.as_u32(mi)) and np.array_equal(pd, hd.as_u16(md))
     # oracle on sampled 20 ppm queries: their candidates are few, so only those references are encoded
     s_rng = np.random.default_rng(31)
     which = np.sort(s_rng.choice(np.nonzero(cls == 0)[0], 300, replace=False))

@@ -84,7 +84,7 @@ def _hv_workload(seed, D, n_t, n_q):
     return hv, mz, z, dec, q_hv, q_mz, q_z
 
 
-@pytest.mark.parametrize("form", ["popc", "tc_fp8", "tc_bf16", "tc_fp4"])
+@pytest.mark.parametrize("form", ["popc", "tc_fp8", "tc_bf16", "tc_fp4", "tc_mxf4"])
 @pytest.mark.parametrize("levels,fdr", [(LEVELS2, 0.01), (LEVELS3, 0.05)])
 def test_cascade_matches_oracle(hd, form, levels, fdr):
     D = 2048

@@ -25,7 +25,7 @@ def dev(a):
 
 
 @pytest.mark.parametrize("form,cluster,cta_group", [("popc", 0, 0), ("tc_fp8", 1, 1), ("tc_fp8", 2, 2),
-                                                    ("tc_fp4", 1, 1), ("tc_fp4", 2, 2)])
+                                                    ("tc_fp4", 1, 1), ("tc_fp4", 2, 2), ("tc_mxf4", 2, 2)])
 def test_stalled_wait_times_out_then_recovers(hd, form, cluster, cta_group):
     rng = np.random.default_rng(12)
     D, W, n = 2048, 32, 3000
@@ -34,7 +34,7 @@ def test_stalled_wait_times_out_then_recovers(hd, form, cluster, cta_group):
     z = np.full(n, 2, np.uint8)
     ctx = hd.Ctx(D, 4, 10, D // 2, 0)
     lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
-    hd.hd_library_prepare(lib, "tc_fp4" if form == "tc_fp4" else "tc_fp8")
+    hd.hd_library_prepare(lib, form if form in ("tc_fp4", "tc_mxf4") else "tc_fp8")
     hd.hd_library_set_schedule(lib, 0, 0, cluster, cta_group)
     q, qm, qz = dev(refs[:300]), dev(mz[:300]), dev(z[:300])
     hd.hd_library_set_wait_limit(lib, 0.05)

@@ -14,7 +14,12 @@ from paper_2211_16422_gb300 import synth
 from tests import oracle_side
 
 pytestmark = pytest.mark.gpu
-FORMS = ("tc_fp8", "tc_bf16", "tc_fp4")
+FORMS = ("tc_fp8", "tc_bf16", "tc_fp4", "tc_mxf4")
+
+
+def forms_for(D):
+    """The tensor-core forms that serve dimension D (kind::mxf4 needs D % 256 == 0)."""
+    return tuple(f for f in FORMS if f != "tc_mxf4" or D % 256 == 0)
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +46,7 @@ def _rand_hv(rng, n, W):
 
 def _search_all(hd, lib, q, qmz, qz, tol, unit, k):
     out = {}
-    for form in ("popc",) + FORMS:
+    for form in ("popc",) + forms_for(lib.dim):
         i, d = hd.hd_search_open(lib, dev(q), dev(qmz), dev(qz), tol, unit, k, form=form)
         torch.cuda.synchronize()
         lib.status()
@@ -67,8 +72,12 @@ def test_tc_forms_small_exact(hd, D):
     qz = rng.integers(1, 4, len(q)).astype(np.uint8)
     ctx = hd.Ctx(D, 4, 10, D // 2, 0)
     lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
-    for f in FORMS:
+    for f in forms_for(D):
         hd.hd_library_prepare(lib, f)
+    if D % 256:   # kind::mxf4 reads K in 256-component stages: refused before anything runs
+        with pytest.raises(hd.HDError) as e:
+            hd.hd_search_open(lib, dev(q), dev(qmz), dev(qz), 500.0, "da", 5, form="tc_mxf4")
+        assert e.value.status == hd.HD_ERR_INVALID_ARG
     for k, tol, unit in ((5, 500.0, "da"), (1, 60.0, "da"), (16, 2e5, "ppm")):
         res = _search_all(hd, lib, q, qmz, qz, tol, unit, k)
         oi, od = oracle.search(D, refs, mz, z, q, qmz, qz, tol, unit, k)
@@ -89,7 +98,7 @@ def test_tc_forms_all_distances_exact(hd):
     mz, z = np.full(n, 500.0), np.full(n, 2, np.uint8)
     ctx = hd.Ctx(D, 4, 10, D // 2, 0)
     lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
-    for f in FORMS:
+    for f in forms_for(D):
         hd.hd_library_prepare(lib, f)
     # k is at most 16; sweep windows that each hold 16 references at a time
     for start in range(0, n, 16):
@@ -97,7 +106,7 @@ def test_tc_forms_all_distances_exact(hd):
         sub_mz[:] = 1000.0
         sub_mz[start:start + 16] = 500.0
         lib2 = hd.hd_build_library(ctx, dev(refs), dev(sub_mz), dev(z))
-        for f in FORMS:
+        for f in forms_for(D):
             hd.hd_library_prepare(lib2, f)
         res = _search_all(hd, lib2, q, np.full(16, 500.0), np.full(16, 2, np.uint8), 0.5, "da", 16)
         oi, od = oracle.search(D, refs, sub_mz, z, q, np.full(16, 500.0), np.full(16, 2, np.uint8), 0.5, "da", 16)
@@ -121,11 +130,11 @@ def test_tc_forms_workload_exact(hd, D, k):
 
     r_hv, q_hv = enc(refs), enc(qs)
     lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
-    for f in FORMS:
+    for f in forms_for(D):
         hd.hd_library_prepare(lib, f)
     for tol, unit in ((500.0, "da"), (20.0, "ppm")):
         res = {}
-        for form in ("popc",) + FORMS:
+        for form in ("popc",) + forms_for(D):
             i, d = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), tol, unit, k, form=form)
             torch.cuda.synchronize()
             res[form] = (hd.as_u32(i), hd.as_u16(d))
@@ -234,10 +243,15 @@ def test_schedule_arguments_checked(hd):
     hd.hd_library_set_schedule(lib, 0, 0, 0, 0)
 
 
-@pytest.mark.parametrize("tg,sg,cs,cg", [(1, 1, 1, 1), (8, 4, 1, 1), (3, 5, 2, 2), (16, 16, 2, 2)])
-def test_e2m1_schedules_exact(hd, tg, sg, cs, cg):
-    """The e2m1 form (4-bit operands in HBM, unpacked by the TMA) under the
-    1-SM and the SM-pair schedules."""
+@pytest.mark.parametrize("form,tg,sg,cs,cg", [("tc_fp4", 1, 1, 1, 1), ("tc_fp4", 8, 4, 1, 1), ("tc_fp4", 3, 5, 2, 2),
+                                              ("tc_fp4", 16, 16, 2, 2), ("tc_mxf4", 1, 1, 2, 2),
+                                              ("tc_mxf4", 3, 5, 2, 2), ("tc_mxf4", 16, 2, 2, 2),
+                                              ("tc_mxf4", 64, 64, 2, 2), ("tc_mxf4", 8, 4, 1, 1)])
+def test_e2m1_schedules_exact(hd, form, tg, sg, cs, cg):
+    """The e2m1 rows (4-bit operands in HBM) under kind::f8f6f4 (unpacked by
+    the TMA) with the 1-SM and the SM-pair schedules, and under the
+    block-scaled kind::mxf4 (kept packed; 224-row tiles, SM pairs whatever
+    the schedule asks)."""
     rng = np.random.default_rng(90 + tg)
     D, n, m = 2048, 5000, 333
     refs = _rand_hv(rng, n, D // 64)
@@ -246,9 +260,9 @@ def test_e2m1_schedules_exact(hd, tg, sg, cs, cg):
     q = refs[:m] ^ (_rand_hv(rng, m, D // 64) & np.uint64(0x0000FFFF0000FFFF))
     ctx = hd.Ctx(D, 4, 10, D // 2, 0)
     lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
-    hd.hd_library_prepare(lib, "tc_fp4")
+    hd.hd_library_prepare(lib, form)
     hd.hd_library_set_schedule(lib, tg, sg, cs, cg)
-    i, d = hd.hd_search_open(lib, dev(q), dev(mz[:m]), dev(z[:m]), 100.0, "da", 4, form="tc_fp4")
+    i, d = hd.hd_search_open(lib, dev(q), dev(mz[:m]), dev(z[:m]), 100.0, "da", 4, form=form)
     torch.cuda.synchronize()
     lib.status()
     oi, od = oracle.search(D, refs, mz, z, q, mz[:m], z[:m], 100.0, "da", 4)

@@ -101,19 +101,19 @@ def test_search_dot_encoded_spectra(hd, bits):
     ref_mz, ref_z, q_mz, q_z = windowed(rng, n_ref, n_q)
     lib = hd.hd_build_library_multibit(ctx, r_gpu, dev(ref_mz), dev(ref_z), bits)
     assert hd.hd_library_component_bits(lib) == bits
-    forms = ["tc_fp8", "tc_bf16"] + (["tc_fp4"] if bits <= 3 else [])
+    forms = ["tc_fp8", "tc_bf16"] + (["tc_fp4", "tc_mxf4"] if bits <= 3 else [])
     for form in forms:
         hd.hd_library_prepare(lib, form)
     for form in forms:
         for unit, tol, k in (("da", 6.0, 5), ("ppm", 9000.0, 1), ("mass", 15.0, 16)):
             check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, tol, unit, k, form)
-    # 'auto' takes e2m1 when the library holds it, else e4m3
+    # 'auto' takes e2m1 (kind::mxf4) when the library holds it, else e4m3
     oi = check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, 6.0, "da", 5, "auto")
     assert np.mean(oi[:, 0] != 0xFFFFFFFF) > 0.9
 
 
 @pytest.mark.parametrize("cluster,cta_group", [(2, 2), (1, 1)])
-@pytest.mark.parametrize("form,bits", [("tc_fp4", 3), ("tc_fp8", 4)])
+@pytest.mark.parametrize("form,bits", [("tc_fp4", 3), ("tc_fp8", 4), ("tc_mxf4", 3)])
 def test_search_dot_random_components_schedules(hd, form, bits, cluster, cta_group):
     """Random components in [-m, m], duplicate rows (ties go to the lower input
     index) and rows of all +m / all -m (scores D m^2 and -D m^2, the ends of
@@ -229,9 +229,10 @@ def test_search_dot_full_size_sampled(hd):
     lib.status()
     gi, gs = u32(gi), gs.cpu().numpy()
     hd.hd_library_prepare(lib, "tc_fp8")
-    ei, es = hd.hd_search_dot(lib, q_comp, q_mz, q_z, spec["tol"], spec["unit"], k, "tc_fp8")
-    torch.cuda.synchronize()
-    assert np.array_equal(u32(ei), gi) and np.array_equal(es.cpu().numpy(), gs)
+    for form in ("tc_fp8", "tc_mxf4"):
+        ei, es = hd.hd_search_dot(lib, q_comp, q_mz, q_z, spec["tol"], spec["unit"], k, form)
+        torch.cuda.synchronize()
+        assert np.array_equal(u32(ei), gi) and np.array_equal(es.cpu().numpy(), gs), form
     F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, 0)
     rng = np.random.default_rng(8)
     rs = np.sort(rng.choice(refs.n, 100, replace=False))

@@ -352,7 +352,9 @@ def test_full_size_sampled(hd):
     hd.hd_library_prepare(lib, "tc_fp4")
     hd.hd_library_prepare(lib, "tc_fp8")
     for form, sched in (("tc_fp4", (16, 16, 2, 2)), ("tc_fp4", (32, 16, 2, 2)), ("tc_fp4", (32, 2, 2, 2)),
-                        ("tc_fp4", (16, 2, 2, 2)), ("tc_fp8", (16, 16, 2, 2)), ("tc_fp4", (16, 16, 1, 1))):
+                        ("tc_fp4", (16, 2, 2, 2)), ("tc_fp8", (16, 16, 2, 2)), ("tc_fp4", (16, 16, 1, 1)),
+                        ("tc_mxf4", (16, 2, 2, 2)), ("tc_mxf4", (32, 2, 2, 2)), ("tc_mxf4", (16, 16, 2, 2)),
+                        ("tc_mxf4", (4, 2, 2, 2))):
         hd.hd_library_set_schedule(lib, *sched)
         ti, td = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), spec["tol"], spec["unit"], k,
                                    form=form)
