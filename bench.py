@@ -56,7 +56,7 @@ TRAFFIC = {
 
 # The arithmetic type the search computes in: the tensor-core operand format
 # (products accumulated in fp32, exact), or 32-bit words for XOR + popcount.
-DTYPE_OF_FORM = {"tc_fp4": "e2m1", "tc_fp8": "e4m3", "tc_bf16": "bf16", "popc": "u32"}
+DTYPE_OF_FORM = {"tc_mxf4": "e2m1", "tc_fp4": "e2m1", "tc_fp8": "e4m3", "tc_bf16": "bf16", "popc": "u32"}
 
 
 def kernel_source_hash():
@@ -272,21 +272,26 @@ def tensor_roofline(form, comparisons, D, avg_search_ms, peaks, peak_clocks, sch
     achieved = comparisons * 2.0 * D / (avg_search_ms / 1e3) / 1e12
     bf16 = measured_peaks().get("bf16_tflops", 1900.0)
     eight_bit_kind = form in ("tc_fp8", "tc_fp4")   # kind::f8f6f4
-    derived = bf16 * (2.0 if eight_bit_kind else 1.0)
+    # the recipe's nominal dense ratios to bf16: fp8 4.5 / 2.25, fp4 13.5 / 2.25
+    ratio = 2.0 if eight_bit_kind else (6.0 if form == "tc_mxf4" else 1.0)
+    derived = bf16 * ratio
     pair = sched.get("cta_group") == 2
     kname = "k_search_mma2" if pair else "k_search_mma"
     r = {"kernel": kname, "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
          "schedule": {k_: sched.get(k_) for k_ in ("tile_group", "super_group", "cluster", "cta_group")},
          "derived_peak": {"peak": derived, "frac": achieved / derived,
-                          "basis": "MEASURED_PEAKS burst cuBLAS bf16" + (" x 2 (nominal fp8/bf16 ratio 4.5/2.25)"
-                                                                          if eight_bit_kind else "")}}
+                          "basis": "MEASURED_PEAKS burst cuBLAS bf16" + (
+                              " x 2 (nominal fp8/bf16 ratio 4.5/2.25)" if eight_bit_kind else
+                              " x 6 (nominal fp4/bf16 ratio 13.5/2.25)" if form == "tc_mxf4" else "")}}
     p = (peaks or {}).get(form)
     if p:
         peak = p["best_per_s"] / 1e12
-        instr = ("tcgen05.mma.cta_group::2.kind::f8f6f4 (" + ("e2m1" if form == "tc_fp4" else "e4m3") + ")"
-                 if eight_bit_kind else "tcgen05.mma.cta_group::2.kind::f16 (bf16)")
+        instr = ("tcgen05.mma.cta_group::2.kind::f8f6f4 (" + ("e2m1" if form == "tc_fp4" else "e4m3") + "), M=256 N=256"
+                 if eight_bit_kind else
+                 "tcgen05.mma.cta_group::2.kind::mxf4.block_scale (packed e2m1, unit ue8m0 scales), M=256 N=224"
+                 if form == "tc_mxf4" else "tcgen05.mma.cta_group::2.kind::f16 (bf16), M=256 N=256")
         r.update({"peak": peak, "frac": achieved / peak,
-                  "peak_basis": f"measured (own microbenchmark hd_measure_peak: {instr}, M=256 N=256, operands "
+                  "peak_basis": f"measured (own microbenchmark hd_measure_peak: {instr}, operands "
                                 f"resident in shared memory, {p['sms']} SMs, best of {p['launches']} launches, "
                                 f"SM clock median {(peak_clocks or {}).get('sm_mhz')} MHz)",
                   "peak_median": p["median_per_s"] / 1e12})
