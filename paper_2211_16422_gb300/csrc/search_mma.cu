@@ -253,13 +253,14 @@ __device__ __forceinline__ uint32_t window_bits(uint32_t lo, uint32_t span, uint
     return hi & ~((1u << b0) - 1u);
 }
 
-// v[e] for a run-time e in 0..31, by a tree of selects on the bits of e
-// (keeps v in registers).
-__device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], uint32_t e)
+// v[e] for a run-time e in 0..G-1 (G = 32 or 16), by a tree of selects on
+// the bits of e (keeps v in registers).
+template <int G>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&v)[G], uint32_t e)
 {
     uint32_t w16[16], w8[8], w4[4], w2[2];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) w16[i] = (e & 16u) ? v[i + 16] : v[i];
+    for (int i = 0; i < 16; ++i) w16[i] = G == 32 ? ((e & 16u) ? v[(i + 16) % G] : v[i]) : v[i % G];
 #pragma unroll
     for (int i = 0; i < 8; ++i) w8[i] = (e & 8u) ? w16[i + 8] : w16[i];
 #pragma unroll
@@ -269,17 +270,18 @@ __device__ __forceinline__ uint32_t pick32(const uint32_t (&v)[32], uint32_t e)
     return (e & 1u) ? w2[1] : w2[0];
 }
 
-// Scores one 32-column group of a query row's accumulator (S in fp32, exact
-// integers) into its running top-k: key distance (bias - S) >> shift, window
-// [lo, lo + span) of library rows, column e = reference row c0 + e.  One
-// float compare per column builds the candidate mask, and the candidates go
-// through a loop that is not unrolled, which keeps the code small.
-template <int K>
-__device__ __forceinline__ void score_group(const uint32_t (&v)[32], uint32_t c0, uint32_t lo, uint32_t span,
+// Scores one group of G (32, or 16 for the last columns of a 240-column
+// tile) columns of a query row's accumulator (S in fp32, exact integers)
+// into its running top-k: key distance (bias - S) >> shift, window [lo, lo +
+// span) of library rows, column e = reference row c0 + e.  One float compare
+// per column builds the candidate mask, and the candidates go through a loop
+// that is not unrolled, which keeps the code small.
+template <int K, int G = 32>
+__device__ __forceinline__ void score_group(const uint32_t (&v)[G], uint32_t c0, uint32_t lo, uint32_t span,
                                             uint32_t bias, uint32_t shift, const uint32_t *__restrict__ lib_orig,
                                             uint64_t seed, uint64_t (&best)[K])
 {
-    const uint32_t wm = window_bits(lo, span, c0);
+    const uint32_t wm = window_bits(lo, span, c0) & (G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u));
     if (!wm) return;
     // a key enters only below the list's last key and below `seed`, the last
     // key of the query's running top-k when the work item started (that list
@@ -290,12 +292,12 @@ __device__ __forceinline__ void score_group(const uint32_t (&v)[32], uint32_t c0
     const float smin = thr == 0xFFFFFFFFu ? -INFINITY : (float)((int)bias - (int)(((thr + 1u) << shift) - 1u));
     uint32_t cand = 0;
 #pragma unroll
-    for (int e = 0; e < 32; ++e) cand |= (uint32_t)(__uint_as_float(v[e]) >= smin) << e;
+    for (int e = 0; e < G; ++e) cand |= (uint32_t)(__uint_as_float(v[e]) >= smin) << e;
     cand &= wm;
     while (cand) {
         const int e = __ffs(cand) - 1;
         cand &= cand - 1u;
-        const int sc = __float2int_rn(__uint_as_float(pick32(v, (uint32_t)e)));
+        const int sc = __float2int_rn(__uint_as_float(pick<G>(v, (uint32_t)e)));
         const uint32_t x = (uint32_t)((int)bias - sc);
         const uint64_t key = ((uint64_t)(x >> shift) << 32) | __ldg(lib_orig + c0 + e);
         if (key < min(best[K - 1], seed)) topk_insert<K>(best, key);
@@ -646,13 +648,15 @@ __host__ __device__ constexpr uint32_t instr_desc2()
 // e2m1 operands packed two per byte in shared memory as in HBM, scored by the
 // block-scaled tcgen05.mma kind::mxf4: 64 components of K per instruction and
 // one ue8m0 scale factor per 32 components of a row, every one 1.0 (0x7F), so
-// S = sum_d x_d y_d as before.  N = 224 lets two accumulators and the two
-// scale-factor regions share the 512 tensor-memory columns:
-//   [0, 224) accumulator 0, [224, 256) A scale factors,
-//   [256, 480) accumulator 1, [480, 512) B scale factors.
-constexpr int TN_MX = 224;
-constexpr uint32_t MX_SFA_COL = 224, MX_BUF1_COL = 256, MX_SFB_COL = 480;
-constexpr uint32_t B2MX_BYTES = (TN_MX / 2) * KB;   // 112 reference rows of 128 bytes (256 components)
+// S = sum_d x_d y_d as before.  N = 240 lets two accumulators and the
+// scale factors share the 512 tensor-memory columns:
+//   [0, 240) accumulator 0, [240, 256) the scale factors of A and B (every
+//   one 1.0, so both operands read the same columns),
+//   [256, 496) accumulator 1, [496, 512) unused (also filled with 1.0).
+// Accumulators and tensor-memory loads stay on 32-column boundaries.
+constexpr int TN_MX = 240;
+constexpr uint32_t MX_SF_COL = 240, MX_BUF1_COL = 256, MX_SPARE_COL = 496;
+constexpr uint32_t B2MX_BYTES = (TN_MX / 2) * KB;   // 120 reference rows of 128 bytes (256 components)
 
 // Block-scaled instruction descriptor: B scale-factor id 0 (bits 4-5), A and
 // B e2m1 (code 1 of kind::mxf4, bits 7 and 10), both K-major, N >> 3 at bit
@@ -674,6 +678,22 @@ __device__ __forceinline__ void mma_issue2_mxf4(uint32_t d_tmem, uint64_t a_desc
         : "memory");
 }
 
+// 32 lanes x 16 consecutive columns of this warp's lane quarter, all set to v.
+__device__ __forceinline__ void tmem_fill16(uint32_t taddr, uint32_t v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr), "r"(v) : "memory");
+}
+// 32 lanes x 16 consecutive fp32 columns of this warp's lane quarter.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+}
 // 32 lanes x 32 consecutive columns of this warp's lane quarter, all set to v.
 __device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v)
 {
@@ -681,12 +701,13 @@ __device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v)
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Every scale factor 1.0: the warp fills its lane quarter of both regions.
+// Every scale factor 1.0: the warp fills its lane quarter of the scale
+// columns (and of the spare columns).
 __device__ __forceinline__ void mxf4_unit_scales(uint32_t tmem, uint32_t quarter)
 {
     const uint32_t lanes = (quarter * 32u) << 16;
-    tmem_fill32(tmem + lanes + MX_SFA_COL, 0x7F7F7F7Fu);
-    tmem_fill32(tmem + lanes + MX_SFB_COL, 0x7F7F7F7Fu);
+    tmem_fill16(tmem + lanes + MX_SF_COL, 0x7F7F7F7Fu);
+    tmem_fill16(tmem + lanes + MX_SPARE_COL, 0x7F7F7F7Fu);
     tmem_st_wait();
 }
 
@@ -703,7 +724,8 @@ template <int FMT> __device__ __forceinline__ uint32_t pair_acc_col(uint32_t buf
 {
     return FMT == FMT_MXF4 ? (buf ? MX_BUF1_COL : 0u) : buf * TN;
 }
-static_assert(pair_smem_bytes<FMT_MXF4>() <= 232448 && (TN_MX / 32) % EPI2_SPLIT == 0, "mxf4 pair shape");
+static_assert(pair_smem_bytes<FMT_MXF4>() <= 232448 && (EPI2_SPLIT == 1 || TN_MX % (32 * EPI2_SPLIT) == 0),
+              "mxf4 pair shape");
 
 // A cluster of two CTAs on an SM pair (cluster ranks 0 and 1; rank 0 issues
 // the pair's MMAs).  Each CTA holds its own block of 128 queries (A) and its
@@ -826,8 +848,8 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
 #pragma unroll
                             for (uint32_t j = 0; j < KB / 32; ++j) {   // 32 bytes of K per instruction
                                 if (FMT == FMT_MXF4)
-                                    mma_issue2_mxf4(d_tmem, da + 2 * j, db + 2 * j, idesc, tmem + MX_SFA_COL,
-                                                    tmem + MX_SFB_COL, (c | j) != 0);
+                                    mma_issue2_mxf4(d_tmem, da + 2 * j, db + 2 * j, idesc, tmem + MX_SF_COL,
+                                                    tmem + MX_SF_COL, (c | j) != 0);
                                 else
                                     mma_issue2<FMT>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
                             }
@@ -879,6 +901,13 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                     tmem_ld32(tmem + lane_addr + pair_acc_col<FMT>(buf) + cg * 32, v);
                     tmem_ld_wait();
                     score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
+                }
+                if (TNF % 32 != 0) {   // the last 16 columns of a 240-column tile (one epilogue warp per quarter)
+                    constexpr uint32_t c16 = TNF / 32 * 32;
+                    uint32_t v[16];
+                    tmem_ld16(tmem + lane_addr + pair_acc_col<FMT>(buf) + c16, v);
+                    tmem_ld_wait();
+                    score_group<K, 16>(v, r0 + c16, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
                 }
                 tc_fence_before();
                 mbar_arrive_remote(acc_empty0 + buf * 8u);
@@ -1049,9 +1078,13 @@ k_peak_mxf4(uint32_t iters, uint32_t check, uint64_t wait_ns, uint32_t *status)
     const uint32_t quarter = (uint32_t)warp & 3u, lanes = (quarter * 32u) << 16;
     mxf4_unit_scales(tmem, quarter);
     if (check) {
-        for (uint32_t c = 0; c < (uint32_t)TN_MX; c += 32) {
+        for (uint32_t c = 0; c + 32 <= (uint32_t)TN_MX; c += 32) {
             tmem_fill32(tmem + lanes + c, 0u);
             tmem_fill32(tmem + lanes + MX_BUF1_COL + c, 0u);
+        }
+        if (TN_MX % 32) {
+            tmem_fill16(tmem + lanes + TN_MX / 32 * 32, 0u);
+            tmem_fill16(tmem + lanes + MX_BUF1_COL + TN_MX / 32 * 32, 0u);
         }
         tmem_st_wait();
     }
@@ -1069,7 +1102,7 @@ k_peak_mxf4(uint32_t iters, uint32_t check, uint64_t wait_ns, uint32_t *status)
                 const uint32_t d_tmem = tmem + (((it >> 6) & 1u) ? MX_BUF1_COL : 0u);
 #pragma unroll
                 for (uint32_t j = 0; j < KB / 32; ++j)   // 32 bytes = 64 components of K per instruction
-                    mma_issue2_mxf4(d_tmem, da + 2 * j, db + 2 * j, idesc, tmem + MX_SFA_COL, tmem + MX_SFB_COL,
+                    mma_issue2_mxf4(d_tmem, da + 2 * j, db + 2 * j, idesc, tmem + MX_SF_COL, tmem + MX_SF_COL,
                                     ((it & 63u) | j) != 0);
             }
             mma_commit2_mc(done, 0x3);
@@ -1091,6 +1124,13 @@ k_peak_mxf4(uint32_t iters, uint32_t check, uint64_t wait_ns, uint32_t *status)
             tmem_ld_wait();
 #pragma unroll
             for (int e = 0; e < 32; ++e) bad |= __uint_as_float(v[e]) != 16384.0f;
+        }
+        if (TN_MX % 32) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lanes + col0 + TN_MX / 32 * 32, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) bad |= __uint_as_float(v[e]) != 16384.0f;
         }
         if (bad) hd_flag(status, HD_DEV_BAD_INPUT);
     }
