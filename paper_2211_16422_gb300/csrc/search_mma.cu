@@ -290,6 +290,12 @@ __device__ __forceinline__ void score_group(const uint32_t (&v)[G], uint32_t c0,
     // empty list (thr = ~0) admits every column
     const uint32_t thr = (uint32_t)(min(best[K - 1], seed) >> 32);
     const float smin = thr == 0xFFFFFFFFu ? -INFINITY : (float)((int)bias - (int)(((thr + 1u) << shift) - 1u));
+    // once the list is seeded almost no group holds a candidate: one maximum over
+    // the group decides before any per-column mask is built
+    float mx = __uint_as_float(v[0]);
+#pragma unroll
+    for (int e = 1; e < G; ++e) mx = fmaxf(mx, __uint_as_float(v[e]));
+    if (mx < smin) return;
     uint32_t cand = 0;
 #pragma unroll
     for (int e = 0; e < G; ++e) cand |= (uint32_t)(__uint_as_float(v[e]) >= smin) << e;
