@@ -48,7 +48,9 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
     #     --popc-steps 0 --no-peaks --form <form> --schedule <tile_group,super_group,cluster,cta_group>
-    ("k_search_mma2", "tc_mxf4", 16, 2, 2, 2): {"bytes": 179.470e9 + 0.13093e9, "sha256": "30c4ad6949a7bdd9"},
+    ("k_search_mma2", "tc_mxf4", 16, 2, 2, 2): {"bytes": 175.169e9 + 0.13250e9, "sha256": "fd03760f22912b03"},
+    ("k_search_mma2", "tc_mxf4", 32, 2, 2, 2): {"bytes": 183.691e9 + 0.08475e9, "sha256": "fd03760f22912b03"},
+    ("k_search_mma2", "tc_mxf4", 16, 16, 2, 2): {"bytes": 219.509e9 + 0.02162e9, "sha256": "fd03760f22912b03"},
 }
 
 # The arithmetic type the search computes in: the tensor-core operand format
