@@ -287,7 +287,7 @@ def tensor_roofline(form, comparisons, D, avg_search_ms, peaks, peak_clocks, sch
         peak = p["best_per_s"] / 1e12
         instr = ("tcgen05.mma.cta_group::2.kind::f8f6f4 (" + ("e2m1" if form == "tc_fp4" else "e4m3") + "), M=256 N=256"
                  if eight_bit_kind else
-                 "tcgen05.mma.cta_group::2.kind::mxf4.block_scale (packed e2m1, unit ue8m0 scales), M=256 N=224"
+                 "tcgen05.mma.cta_group::2.kind::mxf4.block_scale (packed e2m1, unit ue8m0 scales), M=256 N=240"
                  if form == "tc_mxf4" else "tcgen05.mma.cta_group::2.kind::f16 (bf16), M=256 N=256")
         r.update({"peak": peak, "frac": achieved / peak,
                   "peak_basis": f"measured (own microbenchmark hd_measure_peak: {instr}, operands "

@@ -131,7 +131,7 @@ typedef enum {
     HD_FORM_TC_FP4 = 4,   /* tcgen05 kind::f8f6f4, +-1 as e2m1 packed two per byte
                              (library: D/2 bytes/row; the TMA unpacks into shared memory) */
     HD_FORM_TC_MXF4 = 5   /* tcgen05 kind::mxf4 (block-scaled, unit ue8m0 scales) on the same
-                             packed e2m1 rows, kept packed in shared memory; SM pairs, N = 224
+                             packed e2m1 rows, kept packed in shared memory; SM pairs, N = 240
                              per MMA; D a multiple of 256 (else HD_ERR_UNSUPPORTED) */
 } hd_search_form;
 
@@ -536,7 +536,7 @@ typedef enum { HD_KERNEL_ENCODE = 0, HD_KERNEL_SEARCH = 1, HD_KERNEL_KINDS = 2 }
  *      and shape, on operands resident in shared memory, one CTA per SM, all
  *      SM pairs; an operation is a flop (2 per multiply-add).
  *  HD_PEAK_TC_MXF4  tcgen05.mma.cta_group::2.kind::mxf4.block_scale with
- *      M = 256, N = 224, K = 64 packed e2m1 components and unit ue8m0 scale
+ *      M = 256, N = 240, K = 64 packed e2m1 components and unit ue8m0 scale
  *      factors; its warm-up launch runs on all-(+1) operands and checks that
  *      every accumulator holds the exact sum (HD_ERR_CUDA otherwise).
  *  HD_PEAK_POPC  32-bit population counts (the popcount form's counting

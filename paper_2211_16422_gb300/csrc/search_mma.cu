@@ -760,7 +760,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES2; ++i) {
             mbar_init(&full[i], 1);    // rank 0's producer arms it for both CTAs' bytes
-            mbar_init(&empty[i], 1);   // one multicast commit per use
+            mbar_init(&empty[i], 1);   // one commit arrive (sent to both CTAs) per use
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);

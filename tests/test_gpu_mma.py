@@ -250,7 +250,7 @@ def test_schedule_arguments_checked(hd):
 def test_e2m1_schedules_exact(hd, form, tg, sg, cs, cg):
     """The e2m1 rows (4-bit operands in HBM) under kind::f8f6f4 (unpacked by
     the TMA) with the 1-SM and the SM-pair schedules, and under the
-    block-scaled kind::mxf4 (kept packed; 224-row tiles, SM pairs whatever
+    block-scaled kind::mxf4 (kept packed; 240-row tiles, SM pairs whatever
     the schedule asks)."""
     rng = np.random.default_rng(90 + tg)
     D, n, m = 2048, 5000, 333
