@@ -54,7 +54,7 @@ def _search_all(hd, lib, q, qmz, qz, tol, unit, k):
     return out
 
 
-@pytest.mark.parametrize("D", [128, 2048, 8192, 16384, 32768])
+@pytest.mark.parametrize("D", [128, 256, 384, 768, 2048, 8192, 16384, 32768])
 def test_tc_forms_small_exact(hd, D):
     rng = np.random.default_rng(D)
     W = D // 64
