@@ -8,10 +8,14 @@
 //
 // One warp per spectrum; each lane owns WPL 64-bit words of a 32*WPL-word
 // slice of the HV and keeps, per word, a bit-sliced counter: plane i holds
-// bit i of the 64 per-bit counts.  Bound words are added four at a time by a
-// carry-save adder (full adders into planes 0 and 1, the one remaining carry
-// rippled from plane 2 across the planes that can be non-zero so far).  The
-// majority test compares the planes with ceil(n/2) from the top bit down.
+// bit i of the 64 per-bit counts.  The warp reads its peaks 32 at a time
+// (one per lane), drops the invalid ones and packs the rest into a per-warp
+// list in shared memory.  Bound words then enter the counter sixteen at a
+// time through a Harley-Seal tree of full adders, which keeps planes 0..3
+// exact and emits one carry of weight 16 (rippled from plane 4); the rest of
+// a chunk goes four at a time (full adders into planes 0 and 1) and then one
+// at a time.  The majority test compares the planes with ceil(n/2) from the
+// top bit down.
 #include "hd_internal.cuh"
 
 namespace {
@@ -19,129 +23,164 @@ namespace {
 constexpr int ENC_PLANES = 10;          // counts up to 1023 peaks
 constexpr uint32_t ENC_MAX_PEAKS = (1u << ENC_PLANES) - 1u;
 constexpr int ENC_WARPS = 8;
-// Widest per-lane word slice of the binary encoder.  At D = 8192, two passes
-// over the peaks with 2 words per lane (96 registers, two CTAs per SM) took
-// 2.05 ms for 200,000 spectra against 2.47 ms for one pass with 4 words (165
-// registers, one CTA per SM); the ripple-carry encoder before the carry-save
-// groups took 3.09 ms.
+// Widest per-lane word slice of the binary encoder.  Timed at D = 8192 for
+// 200,000 spectra of 50 peaks: 2 words per lane with two CTAs per SM
+// (128 registers) 1.13 ms; 200 registers and one CTA per SM 1.58 ms; 80
+// registers (three CTAs, spills) 1.17 ms; 1 word per lane 1.33 ms; 4 words
+// 1.35 ms; the four-at-a-time adder without the tree 2.03 ms.
 #ifndef HD_ENC_WPL_MAX
 #define HD_ENC_WPL_MAX 2
 #endif
 
 __device__ __forceinline__ uint64_t maj3(uint64_t a, uint64_t b, uint64_t c) { return (a & b) | (a & c) | (b & c); }
 
-// Bound words F_bin XOR L_level of one peak, for the lane's WPL words of the
-// slice starting at word w0 (0 beyond the row).
-template <int WPL>
+// Bound words F_bin XOR L_level of one peak (pk = (bin, level)) for the
+// lane's WPL words wl, wl + 32, ...; 0 beyond the row unless FULL (W a
+// multiple of 32 * WPL, every word in range).
+template <int WPL, bool FULL>
 __device__ __forceinline__ void bound_words(const uint64_t *__restrict__ F, const uint64_t *__restrict__ L,
-                                            uint32_t W, uint32_t b, uint32_t l, uint32_t w0, uint32_t lane,
-                                            uint64_t (&x)[WPL])
+                                            uint32_t W, uint2 pk, uint32_t wl, uint64_t (&x)[WPL])
 {
-    const uint64_t *fr = F + (size_t)b * W, *lr = L + (size_t)l * W;
+    const uint64_t *fr = F + (size_t)pk.x * W + wl, *lr = L + (size_t)pk.y * W + wl;
+#pragma unroll
+    for (int j = 0; j < WPL; ++j)
+        x[j] = (FULL || wl + 32u * j < W) ? (__ldg(fr + 32 * j) ^ __ldg(lr + 32 * j)) : 0ull;
+}
+
+// Full adder of plane `plane` with inputs a, b: the plane takes the sum bit,
+// `carry` the carry bit (weight of the next plane).
+template <int WPL>
+__device__ __forceinline__ void full_add(uint64_t (&c)[WPL][ENC_PLANES], int plane, const uint64_t (&a)[WPL],
+                                         const uint64_t (&b)[WPL], uint64_t (&carry)[WPL])
+{
 #pragma unroll
     for (int j = 0; j < WPL; ++j) {
-        const uint32_t w = w0 + lane + 32u * j;
-        x[j] = w < W ? (__ldg(fr + w) ^ __ldg(lr + w)) : 0ull;
+        const uint64_t u = c[j][plane];
+        carry[j] = maj3(u, a[j], b[j]);
+        c[j][plane] = u ^ a[j] ^ b[j];
     }
 }
 
-// Bit-sliced counts of the bound words of peaks [beg, end): c[j][i] holds bit
-// i of the 64 per-bit counts of the lane's word j.  Four peaks at a time go
-// through a carry-save adder: two full adders (sum a^b^c, carry maj(a, b, c))
-// add them to plane 0 and emit two carries of weight 2, a third adds those to
-// plane 1 and emits one carry of weight 4, which ripples from plane 2 through
-// the planes that can be non-zero.  The last peaks, and a group holding a peak
-// out of range (flagged in `bad` and skipped), ripple one by one from plane 0.
-// Returns the number of peaks added.
-template <int WPL>
+// Adds carry words of weight 2^P into planes P..Q-1.
+template <int P, int Q, int WPL>
+__device__ __forceinline__ void ripple(uint64_t (&c)[WPL][ENC_PLANES], const uint64_t (&k)[WPL])
+{
+#pragma unroll
+    for (int j = 0; j < WPL; ++j) {
+        uint64_t carry = k[j];
+#pragma unroll
+        for (int i = P; i < Q; ++i) {
+            const uint64_t t = c[j][i] & carry;
+            c[j][i] ^= carry;
+            carry = t;
+        }
+    }
+}
+
+// The same, over the planes that can be non-zero once the count reaches
+// `added` (a warp-uniform branch: planes up to 6 hold counts below 128).
+template <int P, int WPL>
+__device__ __forceinline__ void ripple_to(uint64_t (&c)[WPL][ENC_PLANES], const uint64_t (&k)[WPL], uint32_t added)
+{
+    if (added < 128u) ripple<P, 7, WPL>(c, k);
+    else ripple<P, ENC_PLANES, WPL>(c, k);
+}
+
+// Bit-sliced counts of the bound words of the valid peaks of [beg, end):
+// c[j][i] holds bit i of the 64 per-bit counts of the lane's word j (words
+// w0 + lane + 32 j).  A peak with bin >= n_bins or level >= n_levels is
+// skipped and sets `bad` in every lane.  Called by all 32 lanes of a warp with the same
+// row; `pk` is the warp's 32-entry list in shared memory.  Returns the
+// number of peaks counted.
+template <int WPL, bool FULL>
 __device__ __forceinline__ uint32_t sliced_count(const uint64_t *__restrict__ F, uint32_t n_bins,
                                                  const uint64_t *__restrict__ L, uint32_t n_levels, uint32_t W,
                                                  const uint32_t *__restrict__ bins,
                                                  const uint8_t *__restrict__ levels, uint32_t beg, uint32_t end,
                                                  uint32_t w0, uint32_t lane, uint64_t (&c)[WPL][ENC_PLANES],
-                                                 bool &bad)
+                                                 bool &bad, uint2 *pk)
 {
 #pragma unroll
     for (int j = 0; j < WPL; ++j)
 #pragma unroll
         for (int i = 0; i < ENC_PLANES; ++i) c[j][i] = 0;
+    const uint32_t wl = w0 + lane;
     uint32_t added = 0;
-    auto add_one = [&](uint32_t b, uint32_t l) {
-        uint64_t x[WPL];
-        bound_words<WPL>(F, L, W, b, l, w0, lane, x);
-        ++added;
-        const int lim = 32 - __clz(added);   // planes that can be non-zero
-#pragma unroll
-        for (int i = 0; i < ENC_PLANES; ++i) {
-            if (i < lim) {
-#pragma unroll
-                for (int j = 0; j < WPL; ++j) {
-                    const uint64_t t = c[j][i] & x[j];
-                    c[j][i] ^= x[j];
-                    x[j] = t;
-                }
-            }
+    for (uint32_t p0 = beg; p0 < end; p0 += 32) {
+        const uint32_t p = p0 + lane;
+        bool ok = false;
+        uint32_t b = 0, l = 0;
+        if (p < end) {
+            b = __ldg(bins + p);
+            l = __ldg(levels + p);
+            ok = b < n_bins && l < n_levels;
         }
-    };
-    uint32_t p = beg;
-    for (; p + 4 <= end; p += 4) {
-        uint32_t bq[4], lq[4];
-        bool ok = true;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            bq[q] = __ldg(bins + p + q);
-            lq[q] = __ldg(levels + p + q);
-            ok = ok && bq[q] < n_bins && lq[q] < n_levels;
+        if (__ballot_sync(0xFFFFFFFFu, p < end && !ok)) bad = true;   // every lane learns of a bad peak
+        const uint32_t valid = __ballot_sync(0xFFFFFFFFu, ok);
+        const uint32_t nv = __popc(valid);
+        __syncwarp();   // the previous chunk's reads of pk are done
+        if (ok) pk[__popc(valid & ((1u << lane) - 1u))] = make_uint2(b, l);
+        __syncwarp();
+        uint32_t t = 0;
+        for (; t + 16 <= nv; t += 16) {
+            // Harley-Seal: pairs into plane 0 give weight-2 carries, pairs of
+            // those into plane 1 weight 4, then plane 2 weight 8, plane 3 weight 16.
+            uint64_t xa[WPL], xb[WPL], k2a[WPL], k2b[WPL], k4a[WPL], k4b[WPL], k8a[WPL], k8b[WPL], k16[WPL];
+            auto pair = [&](uint32_t i, uint64_t(&k2)[WPL]) {
+                bound_words<WPL, FULL>(F, L, W, pk[t + i], wl, xa);
+                bound_words<WPL, FULL>(F, L, W, pk[t + i + 1], wl, xb);
+                full_add<WPL>(c, 0, xa, xb, k2);
+            };
+            pair(0, k2a);
+            pair(2, k2b);
+            full_add<WPL>(c, 1, k2a, k2b, k4a);
+            pair(4, k2a);
+            pair(6, k2b);
+            full_add<WPL>(c, 1, k2a, k2b, k4b);
+            full_add<WPL>(c, 2, k4a, k4b, k8a);
+            pair(8, k2a);
+            pair(10, k2b);
+            full_add<WPL>(c, 1, k2a, k2b, k4a);
+            pair(12, k2a);
+            pair(14, k2b);
+            full_add<WPL>(c, 1, k2a, k2b, k4b);
+            full_add<WPL>(c, 2, k4a, k4b, k8b);
+            full_add<WPL>(c, 3, k8a, k8b, k16);
+            added += 16;
+            ripple_to<4, WPL>(c, k16, added);
         }
-        if (!ok) {
-            for (int q = 0; q < 4; ++q) {
-                if (bq[q] >= n_bins || lq[q] >= n_levels) bad = true;
-                else add_one(bq[q], lq[q]);
-            }
-            continue;
+        for (; t + 4 <= nv; t += 4) {
+            uint64_t xa[WPL], xb[WPL], k2a[WPL], k2b[WPL], k4[WPL];
+            bound_words<WPL, FULL>(F, L, W, pk[t], wl, xa);
+            bound_words<WPL, FULL>(F, L, W, pk[t + 1], wl, xb);
+            full_add<WPL>(c, 0, xa, xb, k2a);
+            bound_words<WPL, FULL>(F, L, W, pk[t + 2], wl, xa);
+            bound_words<WPL, FULL>(F, L, W, pk[t + 3], wl, xb);
+            full_add<WPL>(c, 0, xa, xb, k2b);
+            full_add<WPL>(c, 1, k2a, k2b, k4);
+            added += 4;
+            ripple_to<2, WPL>(c, k4, added);
         }
-        uint64_t x0[WPL], x1[WPL], x2[WPL], x3[WPL];
-        bound_words<WPL>(F, L, W, bq[0], lq[0], w0, lane, x0);
-        bound_words<WPL>(F, L, W, bq[1], lq[1], w0, lane, x1);
-        bound_words<WPL>(F, L, W, bq[2], lq[2], w0, lane, x2);
-        bound_words<WPL>(F, L, W, bq[3], lq[3], w0, lane, x3);
-        added += 4;
-        const int lim = 32 - __clz(added);
-#pragma unroll
-        for (int j = 0; j < WPL; ++j) {
-            const uint64_t a = c[j][0];
-            const uint64_t s1 = a ^ x0[j] ^ x1[j], k1 = maj3(a, x0[j], x1[j]);
-            const uint64_t k2 = maj3(s1, x2[j], x3[j]);
-            c[j][0] = s1 ^ x2[j] ^ x3[j];
-            const uint64_t b1 = c[j][1];
-            c[j][1] = b1 ^ k1 ^ k2;
-            uint64_t carry = maj3(b1, k1, k2);
-#pragma unroll
-            for (int i = 2; i < ENC_PLANES; ++i) {
-                if (i < lim) {
-                    const uint64_t t = c[j][i] & carry;
-                    c[j][i] ^= carry;
-                    carry = t;
-                }
-            }
+        for (; t < nv; ++t) {
+            uint64_t x[WPL];
+            bound_words<WPL, FULL>(F, L, W, pk[t], wl, x);
+            ++added;
+            ripple_to<0, WPL>(c, x, added);
         }
-    }
-    for (; p < end; ++p) {
-        const uint32_t b = __ldg(bins + p), l = __ldg(levels + p);
-        if (b >= n_bins || l >= n_levels) bad = true;
-        else add_one(b, l);
     }
     return added;
 }
 
-template <int WPL>
-__global__ void __launch_bounds__(ENC_WARPS * 32)
+template <int WPL, bool FULL>
+__global__ void __launch_bounds__(ENC_WARPS * 32, WPL == 2 ? 2 : 1)
 k_encode(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__restrict__ L,
          uint32_t n_levels, uint32_t W, const uint32_t *__restrict__ off,
          const uint32_t *__restrict__ bins, const uint8_t *__restrict__ levels, uint32_t n_spec,
          uint64_t *__restrict__ out, uint32_t *status)
 {
-    const uint32_t sp = blockIdx.x * ENC_WARPS + (threadIdx.x >> 5);
+    __shared__ uint2 s_pk[ENC_WARPS][32];
+    const uint32_t wi = threadIdx.x >> 5;
+    const uint32_t sp = blockIdx.x * ENC_WARPS + wi;
     const uint32_t lane = threadIdx.x & 31;
     if (sp >= n_spec) return;
     uint32_t beg = off[sp], end = off[sp + 1];
@@ -152,8 +191,8 @@ k_encode(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__rest
     bool any_bad = false;
     for (uint32_t w0 = 0; w0 < W; w0 += 32u * WPL) {
         uint64_t c[WPL][ENC_PLANES];
-        const uint32_t added = sliced_count<WPL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane, c,
-                                                 any_bad);
+        const uint32_t added = sliced_count<WPL, FULL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane,
+                                                       c, any_bad, s_pk[wi]);
         const uint32_t thresh = (added + 1) >> 1;   // c >= ceil(n/2)  <=>  2c >= n
 #pragma unroll
         for (int j = 0; j < WPL; ++j) {
@@ -164,7 +203,7 @@ k_encode(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__rest
                 if ((thresh >> i) & 1u) eq &= c[j][i];
                 else gt |= eq & c[j][i];
             }
-            if (w < W) out[(size_t)sp * W + w] = gt | eq;
+            if (FULL || w < W) out[(size_t)sp * W + w] = gt | eq;
         }
     }
     if (any_bad && lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
@@ -290,7 +329,7 @@ k_encode_mb(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__r
 // the planes (a descent over the planes, no per-bit count), pass 2 recounts
 // and maps each component's count through a per-spectrum table h(c), c = 0..n,
 // in shared memory.  Same result as k_encode_mb<false>.
-template <int WPL>
+template <int WPL, bool FULL>
 __global__ void __launch_bounds__(ENC_WARPS * 32)
 k_encode_mb_sliced(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64_t *__restrict__ L,
                    uint32_t n_levels, uint32_t W, const uint32_t *__restrict__ off,
@@ -298,6 +337,7 @@ k_encode_mb_sliced(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64
                    uint32_t m, int8_t *__restrict__ out, uint32_t *status)
 {
     __shared__ int8_t s_tab[ENC_WARPS][ENC_MAX_PEAKS + 1];   // component as a function of the count
+    __shared__ uint2 s_pk[ENC_WARPS][32];
     const uint32_t wi = threadIdx.x >> 5;
     const uint32_t sp = blockIdx.x * ENC_WARPS + wi;
     const uint32_t lane = threadIdx.x & 31;
@@ -311,7 +351,8 @@ k_encode_mb_sliced(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64
     uint64_t c[WPL][ENC_PLANES];
     uint32_t n = 0, cmin = 0xFFFFFFFFu, cmax = 0;
     for (uint32_t w0 = 0; w0 < W; w0 += 32u * WPL) {
-        n = sliced_count<WPL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane, c, bad);
+        n = sliced_count<WPL, FULL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane, c, bad,
+                                    s_pk[wi]);
 #pragma unroll
         for (int j = 0; j < WPL; ++j) {
             if (w0 + lane + 32u * j >= W) continue;
@@ -342,7 +383,8 @@ k_encode_mb_sliced(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64
     __syncwarp();
     const int lim = 32 - __clz(n);   // planes that can be non-zero
     for (uint32_t w0 = 0; w0 < W; w0 += 32u * WPL) {
-        if (W > 32u * WPL) sliced_count<WPL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane, c, bad);
+        if (W > 32u * WPL)
+            sliced_count<WPL, FULL>(F, n_bins, L, n_levels, W, bins, levels, beg, end, w0, lane, c, bad, s_pk[wi]);
 #pragma unroll
         for (int j = 0; j < WPL; ++j) {
             const uint32_t w = w0 + lane + 32u * j;
@@ -366,6 +408,34 @@ k_encode_mb_sliced(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64
     if (bad && lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
 }
 
+// Launchers choosing the form without per-word range checks when every
+// slice of 32 * WPL words lies inside the row.
+template <int WPL>
+void mb_sliced(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins, const uint8_t *levels, uint32_t n,
+               uint32_t m, int8_t *out, uint32_t *st, unsigned grid, cudaStream_t s)
+{
+    hd_count_launches(1);
+    if (ctx->W % (32u * WPL) == 0)
+        k_encode_mb_sliced<WPL, true><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
+                                                                     ctx->W, off, bins, levels, n, m, out, st);
+    else
+        k_encode_mb_sliced<WPL, false><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
+                                                                      ctx->W, off, bins, levels, n, m, out, st);
+}
+
+template <int WPL>
+void binary(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins, const uint8_t *levels, uint32_t n,
+            uint64_t *out, uint32_t *st, unsigned grid, cudaStream_t s)
+{
+    hd_count_launches(1);
+    if (ctx->W % (32u * WPL) == 0)
+        k_encode<WPL, true><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W,
+                                                           off, bins, levels, n, out, st);
+    else
+        k_encode<WPL, false><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W,
+                                                            off, bins, levels, n, out, st);
+}
+
 }  // namespace
 
 void hd_encode_mb_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins, const uint8_t *levels,
@@ -379,14 +449,11 @@ void hd_encode_mb_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t 
         hd_count_launches(1), k_encode_mb<true><<<grid, ENC_WARPS * 32, 0, s>>>(
             ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
     else if (ctx->W >= 128)
-        hd_count_launches(1), k_encode_mb_sliced<4><<<grid, ENC_WARPS * 32, 0, s>>>(
-            ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
+        mb_sliced<4>(ctx, off, bins, levels, n, m, out, st, grid, s);
     else if (ctx->W >= 64)
-        hd_count_launches(1), k_encode_mb_sliced<2><<<grid, ENC_WARPS * 32, 0, s>>>(
-            ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
+        mb_sliced<2>(ctx, off, bins, levels, n, m, out, st, grid, s);
     else
-        hd_count_launches(1), k_encode_mb_sliced<1><<<grid, ENC_WARPS * 32, 0, s>>>(
-            ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels, ctx->W, off, bins, levels, n, m, out, st);
+        mb_sliced<1>(ctx, off, bins, levels, n, m, out, st, grid, s);
 }
 
 void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bins,
@@ -394,19 +461,18 @@ void hd_encode_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t *bi
 {
     const uint32_t W = ctx->W;
     const unsigned grid = hd_ceil_div(n, ENC_WARPS);
-    const uint32_t *st = ctx->status.dev;
+    uint32_t *st = ctx->status.dev;
     hd_prof_scope timed(HD_KERNEL_ENCODE, s);
     if (ctx->p.encoder == HD_ENC_PROJECTION)
         hd_count_launches(1), k_encode_projection<<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins,
                                                                               ctx->p.n_levels, W, off, bins,
-                                                                              levels, n, out, (uint32_t *)st);
-    else if (W >= 128 && HD_ENC_WPL_MAX >= 4)
-        hd_count_launches(1), k_encode<4><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
-                                                    W, off, bins, levels, n, out, (uint32_t *)st);
+                                                                              levels, n, out, st);
+#if HD_ENC_WPL_MAX >= 4
+    else if (W >= 128)
+        binary<4>(ctx, off, bins, levels, n, out, st, grid, s);
+#endif
     else if (W >= 64)
-        hd_count_launches(1), k_encode<2><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
-                                                    W, off, bins, levels, n, out, (uint32_t *)st);
+        binary<2>(ctx, off, bins, levels, n, out, st, grid, s);
     else
-        hd_count_launches(1), k_encode<1><<<grid, ENC_WARPS * 32, 0, s>>>(ctx->F, ctx->p.n_bins, ctx->L, ctx->p.n_levels,
-                                                    W, off, bins, levels, n, out, (uint32_t *)st);
+        binary<1>(ctx, off, bins, levels, n, out, st, grid, s);
 }

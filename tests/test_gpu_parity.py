@@ -125,6 +125,58 @@ def test_encode_bit_exact(hd, D, f, Q):
     assert np.array_equal(hd.as_u64(got), oracle.encode(D, F, L, off, b, lv))
 
 
+def _drop_peaks(off, b, lv, keep):
+    """CSR rows without the peaks where keep is False."""
+    n = len(off) - 1
+    row = np.repeat(np.arange(n), np.diff(off.astype(np.int64)))
+    cnt = np.bincount(row[keep], minlength=n)
+    o = np.zeros(len(off), np.uint32)
+    o[1:] = np.cumsum(cnt)
+    return o, b[keep], lv[keep]
+
+
+@pytest.mark.parametrize("D,f,Q", [(128, 50, 4), (2048, 3000, 16), (8192, 3000, 32), (12288, 700, 16)])
+def test_encode_skips_bad_peaks(hd, D, f, Q):
+    """A peak whose bin or level is out of range is left out of its row's
+    bundle (Eq. 1 over the remaining peaks) and flags the status; a row over
+    1023 peaks encodes as an empty row.  Bad peaks sit at chunk starts and
+    ends and inside full 16-peak groups."""
+    rng = np.random.default_rng(D + 7)
+    lens = [1, 2, 16, 17, 31, 32, 33, 48, 50, 64, 65, 100, 1023, 1024] + list(rng.integers(0, 130, 60))
+    off, b, lv = _random_csr(rng, len(lens), f, Q, lens)
+    nnz = len(b)
+    bad_b = np.zeros(nnz, bool)
+    bad_l = np.zeros(nnz, bool)
+    bad_b[rng.choice(nnz, nnz // 40, replace=False)] = True
+    bad_l[rng.choice(nnz, nnz // 40, replace=False)] = True
+    starts = off[:-1][np.diff(off) > 0].astype(np.int64)
+    bad_b[starts[::3]] = True                      # first peak of some rows
+    bad_l[(off[1:][np.diff(off) > 0] - 1)[::4].astype(np.int64)] = True   # last peak of others
+    b = np.where(bad_b, f + rng.integers(0, 4, nnz), b).astype(np.uint32)
+    lv = np.where(bad_l, Q + rng.integers(0, 2, nnz), lv).astype(np.uint8) if Q < 255 else lv
+    keep = ~(bad_b | (lv >= Q))
+    row_len = np.diff(off.astype(np.int64))
+    too_long = np.repeat(row_len > 1023, row_len)
+    keep &= ~too_long                              # an over-long row encodes as empty
+    want_off, want_b, want_lv = _drop_peaks(off, b, lv, keep)
+    F, L, _, _ = oracle.item_memory(D, Q, f, D // 2, 5)
+    ctx = hd.Ctx(D, Q, f, D // 2, 5)
+    got = hd.hd_encode(ctx, dev(off), dev(b), dev(lv))
+    torch.cuda.synchronize()
+    with pytest.raises(hd.HDError) as e:
+        ctx.status()
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    assert np.array_equal(hd.as_u64(got), oracle.encode(D, F, L, want_off, want_b, want_lv))
+    for bits in (2, 3):
+        got = hd.hd_encode_multibit(ctx, dev(off), dev(b), dev(lv), bits)
+        torch.cuda.synchronize()
+        with pytest.raises(hd.HDError):
+            ctx.status()
+        want = oracle.encode_multibit(D, F, L, want_off, want_b, want_lv, bits)
+        assert np.array_equal(got.cpu().numpy(), want), bits
+    ctx.status()   # cleared
+
+
 # --------------------------------------------------------------- library
 def _refs_with_ties(rng, n):
     mz = np.round(rng.uniform(400, 420, n), 1)
