@@ -279,3 +279,42 @@ def cascade(dim, ref_hv, ref_mz, ref_z, ref_decoy, q_hv, q_mz, q_z, levels, fdr,
         level[hit] = li
         active = np.setdiff1d(active, hit).astype(np.uint32)
     return idx, dist, level, q
+
+
+def cascade_dot(ref_comp, ref_mz, ref_z, ref_decoy, q_comp, q_mz, q_z, levels, fdr, n_threads=None):
+    """Cascade search of multi-bit components (Section 3.4's cascade with the
+    target-decoy FDR of Section 2.1, scored by the dot product of Section
+    4.3's higher-precision components).  The same steps as ``cascade``: at
+    each level the queries not identified so far are searched top-1 (as
+    ``search_dot``), the level's SSMs get q-values among themselves
+    (``fdr_qvalues`` on the score S), and a target SSM with q <= fdr
+    identifies its query at that level.
+
+    Returns (idx u32 [n], score i32 [n], level u8 [n], q f64 [n]): the SSM of
+    the last level each query was searched at (idx 0xFFFFFFFF, score
+    INT32_MIN, q NaN when that level had no candidate), and the level that
+    identified it (0xFF: none).
+    """
+    dec_flags = np.asarray(ref_decoy).astype(bool)
+    n = int(np.asarray(q_mz).size)
+    idx = np.full(n, 0xFFFFFFFF, np.uint32)
+    score = np.full(n, np.iinfo(np.int32).min, np.int32)
+    level = np.full(n, 0xFF, np.uint8)
+    q = np.full(n, np.nan, np.float64)
+    active = np.arange(n, dtype=np.uint32)
+    for li, (tol, unit) in enumerate(levels):
+        if active.size == 0:
+            break
+        i1, s1 = search_dot(ref_comp, ref_mz, ref_z, q_comp, q_mz, q_z, tol, unit, k=1, which=active,
+                            n_threads=n_threads)
+        i1, s1 = i1[:, 0], s1[:, 0]
+        idx[active], score[active], q[active] = i1, s1, np.nan
+        has = i1 != 0xFFFFFFFF
+        ssm = active[has]
+        is_dec = dec_flags[i1[has]]
+        qv = fdr_qvalues(s1[has].astype(np.int64), is_dec)
+        q[ssm] = qv
+        hit = ssm[(~is_dec) & (qv <= fdr)]
+        level[hit] = li
+        active = np.setdiff1d(active, hit).astype(np.uint32)
+    return idx, score, level, q

@@ -153,3 +153,100 @@ def test_cascade_fdr_extremes():
     assert np.all(level0 == 0xFF)
     assert np.array_equal(idx0, idx) and np.array_equal(dist0, dist)
     assert np.array_equal(q0, q, equal_nan=True)
+
+
+# ------------------------------------------------ multi-bit components (Section 4.3)
+def _pm1(hv, D):
+    """+-1 components of binary HVs (bit b -> 1 - 2b)."""
+    bits = np.unpackbits(hv.view(np.uint8), bitorder="little").reshape(hv.shape[0], D)
+    return (1 - 2 * bits.astype(np.int16)).astype(np.int8)
+
+
+def test_cascade_dot_pm1_equals_binary_cascade():
+    """For +-1 components S = D - 2 dist, a strictly increasing map of the
+    Hamming similarity D - dist: the same SSMs, the same q-values, the same
+    levels as the binary cascade."""
+    rng = np.random.default_rng(21)
+    D, n_t, n_q = 256, 300, 150
+    hv, mz, z, dec = _lib(rng, n_t, D)
+    src = rng.integers(0, n_t, n_q)
+    shift = np.where(rng.random(n_q) < 0.4, 0.0, rng.uniform(-80, 80, n_q))
+    q_mz, q_z = mz[src] + shift / z[src], z[src]
+    q_hv = _noisy(rng, hv[src], rng.integers(10, 110, n_q), D)
+    levels = [(20.0, "ppm"), (100.0, "da"), (5.0, "mass")]
+    i1, d1, l1, q1 = oracle.cascade(D, hv, mz, z, dec, q_hv, q_mz, q_z, levels, 0.01)
+    i2, s2, l2, q2 = oracle.cascade_dot(_pm1(hv, D), mz, z, dec, _pm1(q_hv, D), q_mz, q_z, levels, 0.01)
+    assert np.array_equal(i1, i2) and np.array_equal(l1, l2)
+    assert np.array_equal(q1, q2, equal_nan=True)
+    ok = i1 != 0xFFFFFFFF
+    assert np.array_equal(s2[ok], D - 2 * d1[ok].astype(np.int32))
+    assert np.all(s2[~ok] == np.iinfo(np.int32).min)
+    assert (l1 == 0).any() and (l1 == 1).any()
+
+
+def _comp_lib(rng, n_t, D, m):
+    t = rng.integers(-m, m + 1, (n_t, D)).astype(np.int8)
+    d = rng.integers(-m, m + 1, (n_t, D)).astype(np.int8)
+    mz = rng.uniform(400, 1500, n_t)
+    z = rng.integers(2, 4, n_t).astype(np.uint8)
+    return np.concatenate([t, d]), np.r_[mz, mz], np.r_[z, z], np.r_[np.zeros(n_t, np.uint8), np.ones(n_t, np.uint8)]
+
+
+def _noisy_comp(rng, c, frac, m):
+    out = c.copy()
+    for r in range(c.shape[0]):
+        sel = rng.random(c.shape[1]) < frac[r]
+        out[r, sel] = rng.integers(-m, m + 1, int(sel.sum()))
+    return out
+
+
+@pytest.mark.parametrize("m", [1, 3, 15])
+def test_cascade_dot_levels_match_brute_force(m):
+    """Each level's SSMs against an int64 matrix product with (score
+    descending, index ascending) top-1 on the queries still active; each
+    level's identifications recomputed from its SSMs."""
+    rng = np.random.default_rng(30 + m)
+    D, n_t, n_q = 128, 250, 120
+    R, mz, z, dec = _comp_lib(rng, n_t, D, m)
+    src = rng.integers(0, n_t, n_q)
+    shift = np.where(rng.random(n_q) < 0.4, 0.0, rng.uniform(-80, 80, n_q))
+    q_mz, q_z = mz[src] + shift / z[src], z[src]
+    Qc = _noisy_comp(rng, R[src], rng.uniform(0.2, 0.95, n_q), m)
+    levels = [(20.0, "ppm"), (100.0, "da")]
+    idx, score, level, q = oracle.cascade_dot(R, mz, z, dec, Qc, q_mz, q_z, levels, 0.01)
+    S = Qc.astype(np.int64) @ R.astype(np.int64).T
+    n_r = R.shape[0]
+    active = np.ones(n_q, bool)
+    for li, (tol, unit) in enumerate(levels):
+        tq = np.full(n_q, tol) if unit == "da" else q_mz * (tol * 1e-6)
+        cand = (z[None, :] == q_z[:, None]) & (np.abs(mz[None, :] - q_mz[:, None]) <= tq[:, None])
+        key = np.where(cand, -S * (2 * n_r) + np.arange(n_r)[None, :], np.iinfo(np.int64).max)
+        best = key.argmin(axis=1)
+        has = cand.any(axis=1)
+        sel = active & has
+        here = sel & ((level == li) | ((level == 0xFF) & (li == len(levels) - 1)))
+        assert here.any()
+        assert np.array_equal(idx[here], best[here].astype(np.uint32))
+        assert np.array_equal(score[here], S[here, best[here]].astype(np.int32))
+        qv = oracle.fdr_qvalues(S[sel, best[sel]], dec[best[sel]])
+        ident = np.zeros(n_q, bool)
+        ident[np.nonzero(sel)[0]] = (dec[best[sel]] == 0) & (qv <= 0.01)
+        assert np.array_equal(level == li, ident)
+        active &= ~ident
+    assert np.all(level[active] == 0xFF)
+    assert (level == 0).sum() > 0 and (level == 1).sum() > 0
+
+
+def test_cascade_dot_fdr_extremes():
+    rng = np.random.default_rng(41)
+    D, n_t, n_q, m = 128, 100, 60, 3
+    R, mz, z, dec = _comp_lib(rng, n_t, D, m)
+    src = rng.integers(0, n_t, n_q)
+    Qc = _noisy_comp(rng, R[src], rng.uniform(0.0, 0.9, n_q), m)
+    args = (R, mz, z, dec, Qc, mz[src], z[src], [(10.0, "da")])
+    idx, score, level, q = oracle.cascade_dot(*args, 1e9)
+    assert np.array_equal(level == 0, (idx != 0xFFFFFFFF) & (dec[np.minimum(idx, 2 * n_t - 1)] == 0))
+    idx0, score0, level0, q0 = oracle.cascade_dot(*args, -1.0)
+    assert np.all(level0 == 0xFF)
+    assert np.array_equal(idx0, idx) and np.array_equal(score0, score)
+    assert np.array_equal(q0, q, equal_nan=True)
