@@ -329,6 +329,19 @@ HD_API hd_status hd_cascade_search(const hd_library *lib, const uint64_t *d_q_hv
                                    uint32_t n_levels, double fdr, hd_search_form form, uint32_t *d_out_idx,
                                    uint16_t *d_out_dist, double *d_out_q, uint8_t *d_out_level,
                                    hd_stream stream);
+/* hd_cascade_search for a multi-bit library (Section 4.3 components scored
+ * by the dot product): each level searches the unidentified queries' rows
+ * d_q_comp [n_q][D] int8 (16-byte aligned) with k = 1 as hd_search_dot with
+ * `form` (AUTO or a tensor-core form the library holds), and the SSMs are
+ * ranked by their score S.  Thresholds, q-values and identification as
+ * hd_cascade_search.  d_out_score [n_q] receives S (INT32_MIN without a
+ * candidate).  HD_ERR_INVALID_ARG on a binary library (and
+ * hd_cascade_search refuses a multi-bit one). */
+HD_API hd_status hd_cascade_search_dot(const hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
+                                       const uint8_t *d_q_charge, uint32_t n_q, const hd_window *levels,
+                                       uint32_t n_levels, double fdr, hd_search_form form, uint32_t *d_out_idx,
+                                       int32_t *d_out_score, double *d_out_q, uint8_t *d_out_level,
+                                       hd_stream stream);
 
 /* Batched plan (no counterpart in the paper, which batches to fill memory,
  * Section 4.1): encoding (Eq. 1) of a fixed set of query batches plus the
@@ -344,6 +357,18 @@ HD_API hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32
                                 const hd_window *windows, uint32_t n_windows, uint32_t k, hd_search_form form,
                                 uint64_t *d_q_hv_work, uint32_t *d_out_idx, uint16_t *d_out_dist,
                                 hd_plan **out);
+/* The plan for a multi-bit library (Section 4.3): multi-bit encoding
+ * (hd_encode_multibit with the library's bits) into d_q_comp_work [n_q][D]
+ * int8 (16-byte aligned) plus hd_search_dot_multi with `form` (AUTO or a
+ * tensor-core form the library holds); d_out_score [n_q][k] receives the
+ * scores.  hd_plan_create refuses a multi-bit library and this call a
+ * binary one (HD_ERR_INVALID_ARG). */
+HD_API hd_status hd_plan_create_dot(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_offsets,
+                                    const uint32_t *d_bins, const uint8_t *d_levels, const double *d_q_mz,
+                                    const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                                    const hd_window *windows, uint32_t n_windows, uint32_t k, hd_search_form form,
+                                    int8_t *d_q_comp_work, uint32_t *d_out_idx, int32_t *d_out_score,
+                                    hd_plan **out);
 HD_API hd_status hd_plan_launch(hd_plan *plan, hd_stream stream);
 /* Kernel nodes in the plan's graph (the launches one hd_plan_launch makes). */
 HD_API hd_status hd_plan_info(const hd_plan *plan, uint32_t *kernel_nodes);
@@ -506,6 +531,13 @@ HD_API hd_status hd_library_component_bits(const hd_library *lib, uint32_t *bits
 HD_API hd_status hd_search_dot(const hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
                                const uint8_t *d_q_charge, uint32_t n_q, double tol, hd_tol_unit unit, uint32_t k,
                                hd_search_form form, uint32_t *d_out_idx, int32_t *d_out_score, hd_stream stream);
+/* hd_search_dot with a window per query, as hd_search_open_multi: query q
+ * uses windows[d_q_class[q]] (windows[0] for every query when d_q_class is
+ * NULL), in one persistent search launch. */
+HD_API hd_status hd_search_dot_multi(const hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
+                                     const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                                     const hd_window *windows, uint32_t n_windows, uint32_t k, hd_search_form form,
+                                     uint32_t *d_out_idx, int32_t *d_out_score, hd_stream stream);
 
 /* Failure-detection hooks (no counterpart in the paper).  Every device wait
  * of a search (stage loads, tensor-core commits, merge locks) gives up after

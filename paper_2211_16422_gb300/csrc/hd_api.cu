@@ -495,6 +495,35 @@ hd_status hd_search_dot(const hd_library *lib, const int8_t *d_q_comp, const dou
                                  d_out_idx, d_out_score, (cudaStream_t)stream);
 }
 
+hd_status hd_search_dot_multi(const hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
+                              const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                              const hd_window *windows, uint32_t n_windows, uint32_t k, hd_search_form form,
+                              uint32_t *d_out_idx, int32_t *d_out_score, hd_stream stream)
+{
+    HD_CHECK(lib, "hd_search_dot_multi: null library");
+    HD_CHECK(lib->bits > 1, "hd_search_dot_multi: binary library (use hd_search_open_multi)");
+    HD_CHECK(k >= 1 && k <= 16, "hd_search_dot_multi: k must be in [1, 16]");
+    HD_CHECK(form == HD_FORM_AUTO || hd_is_tc_form(form),
+             "hd_search_dot_multi: form must be AUTO or a tensor-core form");
+    hd_qwin win;
+    hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
+    if (st != HD_OK) return st;
+    if (form == HD_FORM_AUTO) {
+        form = hd_fastest_tc_form(lib);
+        if (form == HD_FORM_AUTO) form = HD_FORM_TC_BF16;
+    }
+    HD_CHECK(hd_tc_copy(lib, form) || lib->n == 0, "hd_search_dot_multi: call hd_library_prepare for this form first");
+    HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
+             "hd_search_dot_multi: the kind::mxf4 form needs D to be a multiple of 256");
+    if (n_q == 0) return HD_OK;
+    HD_CHECK(d_q_comp && d_q_mz && d_q_charge && d_out_idx && d_out_score, "hd_search_dot_multi: null buffer");
+    HD_CHECK(aligned16(d_q_comp), "hd_search_dot_multi: d_q_comp must be 16-byte aligned");
+    st = check_device(lib->device);
+    if (st != HD_OK) return st;
+    return hd_search_mma_dot_run(lib, form, d_q_comp, d_q_mz, d_q_charge, n_q, win, k, d_out_idx, d_out_score,
+                                 (cudaStream_t)stream);
+}
+
 void hd_library_free(hd_library *lib) { lib_release(lib); }
 
 hd_status hd_library_info(const hd_library *lib, uint32_t *n_refs, uint32_t *dim)

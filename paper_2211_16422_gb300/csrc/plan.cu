@@ -3,6 +3,7 @@
 // computation is one of libhd's kernels.
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <vector>
 
 #include "hd_internal.cuh"
@@ -32,44 +33,13 @@ void plan_release(hd_plan *p)
     delete p;
 }
 
-}  // namespace
-
-extern "C" {
-
-hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_offsets, const uint32_t *d_bins,
-                         const uint8_t *d_levels, const double *d_q_mz, const uint8_t *d_q_charge,
-                         const uint8_t *d_q_class, uint32_t n_q, const hd_window *windows, uint32_t n_windows,
-                         uint32_t k, hd_search_form form, uint64_t *d_q_hv_work, uint32_t *d_out_idx,
-                         uint16_t *d_out_dist, hd_plan **out)
+// One eager run of `body` on a private stream (kernel attributes and lazy
+// module loading happen outside capture), then its capture into a graph.
+hd_status plan_capture(int dev, const std::function<hd_status(cudaStream_t)> &body, hd_plan **out)
 {
-    if (!out) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null output");
-    *out = nullptr;
-    if (!ctx || !lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null ctx or library");
-    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: multi-bit library (binary HVs only)");
-    if (ctx->p.dim != lib->dim) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: ctx and library dims differ");
-    if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: k must be in [1, 16]");
-    if (n_q == 0) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: empty query set");
-    if (!d_offsets || !d_bins || !d_levels || !d_q_mz || !d_q_charge || !d_q_hv_work || !d_out_idx || !d_out_dist)
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null buffer");
-    if (reinterpret_cast<uintptr_t>(d_q_hv_work) & 15u)
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: d_q_hv_work must be 16-byte aligned");
-    hd_qwin win;
-    hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
-    if (st != HD_OK) return st;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev != lib->device || dev != ctx->device)
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: objects belong to another device");
-
     scoped_stream ss;
     HD_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
-    auto body = [&]() -> hd_status {
-        hd_encode_launch(ctx, d_offsets, d_bins, d_levels, n_q, d_q_hv_work, ss.s);
-        HD_CUDA_TRY(cudaGetLastError());
-        return hd_search_dispatch(lib, d_q_hv_work, d_q_mz, d_q_charge, n_q, win, k, form, d_out_idx, d_out_dist,
-                                  ss.s);
-    };
-    // one eager run: kernel attributes and lazy module loading happen outside capture
-    st = body();
+    hd_status st = body(ss.s);
     if (st != HD_OK) return st;
     HD_CUDA_TRY(cudaStreamSynchronize(ss.s));
 
@@ -80,7 +50,7 @@ hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_o
         plan_release(p);
         return hd_cuda_fail(e, "hd_plan_create: begin capture");
     }
-    st = body();
+    st = body(ss.s);
     e = cudaStreamEndCapture(ss.s, &p->graph);
     if (st != HD_OK || e != cudaSuccess) {
         plan_release(p);
@@ -101,6 +71,82 @@ hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_o
     }
     *out = p;
     return HD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_offsets, const uint32_t *d_bins,
+                         const uint8_t *d_levels, const double *d_q_mz, const uint8_t *d_q_charge,
+                         const uint8_t *d_q_class, uint32_t n_q, const hd_window *windows, uint32_t n_windows,
+                         uint32_t k, hd_search_form form, uint64_t *d_q_hv_work, uint32_t *d_out_idx,
+                         uint16_t *d_out_dist, hd_plan **out)
+{
+    if (!out) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null output");
+    *out = nullptr;
+    if (!ctx || !lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null ctx or library");
+    if (!hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: multi-bit library (use hd_plan_create_dot)");
+    if (ctx->p.dim != lib->dim) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: ctx and library dims differ");
+    if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: k must be in [1, 16]");
+    if (n_q == 0) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: empty query set");
+    if (!d_offsets || !d_bins || !d_levels || !d_q_mz || !d_q_charge || !d_q_hv_work || !d_out_idx || !d_out_dist)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: null buffer");
+    if (reinterpret_cast<uintptr_t>(d_q_hv_work) & 15u)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: d_q_hv_work must be 16-byte aligned");
+    hd_qwin win;
+    hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
+    if (st != HD_OK) return st;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != lib->device || dev != ctx->device)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create: objects belong to another device");
+    return plan_capture(dev, [&](cudaStream_t s) -> hd_status {
+        hd_encode_launch(ctx, d_offsets, d_bins, d_levels, n_q, d_q_hv_work, s);
+        HD_CUDA_TRY(cudaGetLastError());
+        return hd_search_dispatch(lib, d_q_hv_work, d_q_mz, d_q_charge, n_q, win, k, form, d_out_idx, d_out_dist, s);
+    }, out);
+}
+
+hd_status hd_plan_create_dot(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_offsets, const uint32_t *d_bins,
+                             const uint8_t *d_levels, const double *d_q_mz, const uint8_t *d_q_charge,
+                             const uint8_t *d_q_class, uint32_t n_q, const hd_window *windows, uint32_t n_windows,
+                             uint32_t k, hd_search_form form, int8_t *d_q_comp_work, uint32_t *d_out_idx,
+                             int32_t *d_out_score, hd_plan **out)
+{
+    if (!out) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: null output");
+    *out = nullptr;
+    if (!ctx || !lib) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: null ctx or library");
+    if (hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: binary library (use hd_plan_create)");
+    if (ctx->p.dim != lib->dim) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: ctx and library dims differ");
+    if (k < 1 || k > 16) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: k must be in [1, 16]");
+    if (n_q == 0) return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: empty query set");
+    if (!d_offsets || !d_bins || !d_levels || !d_q_mz || !d_q_charge || !d_q_comp_work || !d_out_idx || !d_out_score)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: null buffer");
+    if (reinterpret_cast<uintptr_t>(d_q_comp_work) & 15u)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: d_q_comp_work must be 16-byte aligned");
+    if (form != HD_FORM_AUTO && !hd_is_tc_form(form))
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: form must be AUTO or a tensor-core form");
+    if (form == HD_FORM_AUTO) {
+        form = hd_fastest_tc_form(lib);
+        if (form == HD_FORM_AUTO) form = HD_FORM_TC_BF16;
+    }
+    if (!hd_tc_copy(lib, form) && lib->n > 0)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: call hd_library_prepare for this form first");
+    if (form == HD_FORM_TC_MXF4 && lib->dim % 256 != 0)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: the kind::mxf4 form needs D to be a multiple of 256");
+    hd_qwin win;
+    hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
+    if (st != HD_OK) return st;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != lib->device || dev != ctx->device)
+        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: objects belong to another device");
+    const uint32_t bits = lib->bits;
+    return plan_capture(dev, [&](cudaStream_t s) -> hd_status {
+        hd_encode_mb_launch(ctx, d_offsets, d_bins, d_levels, n_q, bits, d_q_comp_work, s);
+        HD_CUDA_TRY(cudaGetLastError());
+        return hd_search_mma_dot_run(lib, form, d_q_comp_work, d_q_mz, d_q_charge, n_q, win, k, d_out_idx,
+                                     d_out_score, s);
+    }, out);
 }
 
 hd_status hd_plan_launch(hd_plan *plan, hd_stream stream)

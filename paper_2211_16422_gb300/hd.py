@@ -94,7 +94,9 @@ _SIGS = {
     "hd_library_save": ([P, P, C.c_char_p], i32),
     "hd_library_load": ([P, C.c_char_p, P], i32),
     "hd_cascade_search": ([P, P, P, P, u32, P, u32, dbl, i32, P, P, P, P, P], i32),
+    "hd_cascade_search_dot": ([P, P, P, P, u32, P, u32, dbl, i32, P, P, P, P, P], i32),
     "hd_plan_create": ([P, P, P, P, P, P, P, P, u32, P, u32, u32, i32, P, P, P, P], i32),
+    "hd_plan_create_dot": ([P, P, P, P, P, P, P, P, u32, P, u32, u32, i32, P, P, P, P], i32),
     "hd_plan_launch": ([P, P], i32),
     "hd_plan_info": ([P, P], i32),
     "hd_plan_destroy": ([P], None),
@@ -114,6 +116,7 @@ _SIGS = {
     "hd_build_library_multibit": ([P, P, P, P, u32, u32, P], i32),
     "hd_library_component_bits": ([P, P], i32),
     "hd_search_dot": ([P, P, P, P, u32, dbl, i32, u32, i32, P, P, P], i32),
+    "hd_search_dot_multi": ([P, P, P, P, P, u32, P, u32, u32, i32, P, P, P], i32),
 }
 HD_KERNEL_ENCODE, HD_KERNEL_SEARCH = 0, 1
 
@@ -374,6 +377,24 @@ def hd_search_dot(lib: Library, q_comp, q_mz, q_charge, tol, unit="da", k=1, for
     return out_idx, out_score
 
 
+def hd_search_dot_multi(lib: Library, q_comp, q_mz, q_charge, q_class, windows, k=1, form="auto",
+                        out_idx=None, out_score=None, stream=None):
+    """hd_search_dot with a window per query (query q uses windows[q_class[q]])."""
+    q_comp = _dev(q_comp, torch.int8, "q_comp")
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    n = q_mz.numel()
+    if q_class is not None:
+        q_class = _need(_dev(q_class, torch.uint8, "q_class"), n, "q_class")
+    _need(q_comp, n * lib.dim, "q_comp")
+    _need(q_charge, n, "q_charge")
+    out_idx, out_score = _results(n, k, out_idx, out_score, torch.int32, "out_score")
+    w = _windows(windows)
+    _check(load().hd_search_dot_multi(lib.handle, _ptr(q_comp), _ptr(q_mz), _ptr(q_charge), _ptr(q_class), n, w,
+                                      len(windows), int(k), FORMS[form], _ptr(out_idx), _ptr(out_score),
+                                      _stream(stream)))
+    return out_idx, out_score
+
 def hd_library_prepare(lib: Library, form: str):
     """Build the library's copy for a tensor-core form ('tc_fp4' / 'tc_mxf4' share the e2m1
     copy; 'tc_fp8', 'tc_bf16')."""
@@ -518,12 +539,35 @@ def hd_cascade_search(lib: Library, q_hv, q_mz, q_charge, levels, fdr=0.01, form
     return idx, dist, q, level
 
 
+def hd_cascade_search_dot(lib: Library, q_comp, q_mz, q_charge, levels, fdr=0.01, form="auto", stream=None):
+    """Cascade search of a multi-bit library: q_comp int8 [n, D] components.  Returns
+    (idx int32 [n], score int32 [n], q float64 [n], level uint8 [n]); score INT32_MIN without a
+    candidate, level 255 = not identified."""
+    q_comp = _dev(q_comp, torch.int8, "q_comp")
+    q_mz = _dev(q_mz, torch.float64, "q_mz")
+    q_charge = _dev(q_charge, torch.uint8, "q_charge")
+    n = q_mz.numel()
+    _need(q_comp, n * lib.dim, "q_comp")
+    _need(q_charge, n, "q_charge")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    score = torch.empty(n, dtype=torch.int32, device="cuda")
+    q = torch.empty(n, dtype=torch.float64, device="cuda")
+    level = torch.empty(n, dtype=torch.uint8, device="cuda")
+    w = _windows(levels)
+    _check(load().hd_cascade_search_dot(lib.handle, _ptr(q_comp), _ptr(q_mz), _ptr(q_charge), n, w, len(levels),
+                                        float(fdr), FORMS[form], _ptr(idx), _ptr(score), _ptr(q), _ptr(level),
+                                        _stream(stream)))
+    return idx, score, q, level
+
+
 class Plan:
     """Encode + multi-window search of a fixed query set, captured as one CUDA graph.
     Keeps references to every bound buffer; refill them in place and call launch()."""
 
     def __init__(self, ctx: Ctx, lib: Library, offsets, bins, levels, q_mz, q_charge, q_class, windows, k=1,
                  form="auto"):
+        """On a multi-bit library the plan encodes components and runs the dot-product search:
+        launch() then returns (idx, score int32)."""
         self.offsets = _dev(offsets, torch.int32, "offsets")
         self.bins = _dev(bins, torch.int32, "bins")
         self.levels = _dev(levels, torch.uint8, "levels")
@@ -531,17 +575,27 @@ class Plan:
         self.q_charge = _dev(q_charge, torch.uint8, "q_charge")
         self.q_class = None if q_class is None else _dev(q_class, torch.uint8, "q_class")
         n = self.q_mz.numel()
-        self.q_hv = torch.empty((n, ctx.dim // 64), dtype=torch.int64, device="cuda")
+        self.multibit = hd_library_component_bits(lib) > 1
         self.out_idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
-        self.out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
         self._keep = (ctx, lib)
         w = _windows(windows)
         h = C.c_void_p()
         torch.cuda.current_stream().synchronize()
-        _check(load().hd_plan_create(ctx.handle, lib.handle, _ptr(self.offsets), _ptr(self.bins),
-                                     _ptr(self.levels), _ptr(self.q_mz), _ptr(self.q_charge), _ptr(self.q_class),
-                                     n, w, len(windows), int(k), FORMS[form], _ptr(self.q_hv),
-                                     _ptr(self.out_idx), _ptr(self.out_dist), C.byref(h)))
+        if self.multibit:
+            self.q_comp = torch.empty((n, ctx.dim), dtype=torch.int8, device="cuda")
+            self.out_score = torch.empty((n, k), dtype=torch.int32, device="cuda")
+            _check(load().hd_plan_create_dot(ctx.handle, lib.handle, _ptr(self.offsets), _ptr(self.bins),
+                                             _ptr(self.levels), _ptr(self.q_mz), _ptr(self.q_charge),
+                                             _ptr(self.q_class), n, w, len(windows), int(k), FORMS[form],
+                                             _ptr(self.q_comp), _ptr(self.out_idx), _ptr(self.out_score),
+                                             C.byref(h)))
+        else:
+            self.q_hv = torch.empty((n, ctx.dim // 64), dtype=torch.int64, device="cuda")
+            self.out_dist = torch.empty((n, k), dtype=torch.int16, device="cuda")
+            _check(load().hd_plan_create(ctx.handle, lib.handle, _ptr(self.offsets), _ptr(self.bins),
+                                         _ptr(self.levels), _ptr(self.q_mz), _ptr(self.q_charge),
+                                         _ptr(self.q_class), n, w, len(windows), int(k), FORMS[form],
+                                         _ptr(self.q_hv), _ptr(self.out_idx), _ptr(self.out_dist), C.byref(h)))
         self._h = h
         nodes = C.c_uint32()
         _check(load().hd_plan_info(h, C.byref(nodes)))
@@ -549,7 +603,7 @@ class Plan:
 
     def launch(self, stream=None):
         _check(load().hd_plan_launch(self._h, _stream(stream)))
-        return self.out_idx, self.out_dist
+        return (self.out_idx, self.out_score) if self.multibit else (self.out_idx, self.out_dist)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -234,3 +234,107 @@ def test_batched_full_size_sampled(hd):
     oi_g = np.where(oi == 0xFFFFFFFF, 0xFFFFFFFF, sub_idx[np.minimum(oi, sub_idx.size - 1)]).astype(np.uint32)
     assert np.array_equal(pi[which], oi_g) and np.array_equal(pd[which], od)
     assert np.mean(oi[:, 0] != 0xFFFFFFFF) > 0.5
+
+
+# ------------------------------------------------ multi-bit components (Section 4.3)
+def _oracle_dot_by_class(r_comp, refs, q_comp, qs, cls, k):
+    n = qs.n
+    oi = np.full((n, k), 0xFFFFFFFF, np.uint32)
+    osc = np.full((n, k), np.iinfo(np.int32).min, np.int32)
+    for c, (tol, unit) in enumerate(WINDOWS):
+        idx = np.nonzero(cls == c)[0]
+        if idx.size == 0:
+            continue
+        i, s = oracle.search_dot(r_comp, refs.precursor_mz, refs.charge, q_comp, qs.precursor_mz, qs.charge, tol,
+                                 unit, k, which=idx.astype(np.uint32))
+        oi[idx], osc[idx] = i, s
+    return oi, osc
+
+
+def _setup_mb(hd, refs, qs, D, Q, bits, seed=0):
+    pp = dict(mz_min=synth.MZ_MIN, mz_max=synth.MZ_MAX, bin_width=synth.BIN_WIDTH, n_bins=synth.N_BINS,
+              max_peaks=synth.MAX_PEAKS, n_levels=Q)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, seed)
+    r_csr = hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp)
+    q_csr = hd.hd_preprocess(ctx, dev(qs.offsets), dev(qs.mz), dev(qs.intensity), **pp)
+    lib = hd.hd_build_library_multibit(ctx, hd.hd_encode_multibit(ctx, *r_csr, bits), dev(refs.precursor_mz),
+                                       dev(refs.charge), bits)
+    F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, seed)
+    o_r = oracle.encode_multibit(D, F, L, *oracle.preprocess(refs.offsets, refs.mz, refs.intensity, **pp), bits)
+    o_q = oracle.encode_multibit(D, F, L, *oracle.preprocess(qs.offsets, qs.mz, qs.intensity, **pp), bits)
+    return ctx, lib, q_csr, o_r, o_q, pp
+
+
+@pytest.mark.parametrize("bits,forms", [(3, ("tc_mxf4", "tc_fp4", "tc_bf16")), (4, ("tc_fp8",))])
+def test_multi_window_dot_exact(hd, bits, forms):
+    D, Q = 2048, 32
+    refs, qs, cls, _ = _batched_workload(11 + bits, 5000, 24, 10, 300)
+    ctx, lib, q_csr, o_r, o_q, _ = _setup_mb(hd, refs, qs, D, Q, bits)
+    q_comp = hd.hd_encode_multibit(ctx, *q_csr, bits)
+    want = _oracle_dot_by_class(o_r, refs, o_q, qs, cls, 5)
+    for form in forms:
+        if form == "tc_bf16":
+            hd.hd_library_prepare(lib, form)
+        i, s = hd.hd_search_dot_multi(lib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, k=5,
+                                      form=form)
+        torch.cuda.synchronize()
+        lib.status()
+        assert np.array_equal(hd.as_u32(i), want[0]), form
+        assert np.array_equal(s.cpu().numpy(), want[1]), form
+    # without classes every query takes windows[0]
+    i, s = hd.hd_search_dot_multi(lib, q_comp, dev(qs.precursor_mz), dev(qs.charge), None, [(150.0, "da")], k=2)
+    torch.cuda.synchronize()
+    oi, osc = oracle.search_dot(o_r, refs.precursor_mz, refs.charge, o_q, qs.precursor_mz, qs.charge, 150.0, "da", 2)
+    assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(s.cpu().numpy(), osc)
+
+
+def test_plan_dot_matches_oracle_and_refills(hd):
+    D, Q, bits = 4096, 32, 3
+    refs, qs, cls, _ = _batched_workload(17, 6000, 20, 10, 300)
+    ctx, lib, q_csr, o_r, o_q, pp = _setup_mb(hd, refs, qs, D, Q, bits)
+    off, b, lv = q_csr       # bins / levels hold n * max_peaks entries: room for any refill
+    plan = hd.Plan(ctx, lib, off, b, lv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, k=5)
+    assert plan.multibit and plan.kernel_nodes > 5
+    want = _oracle_dot_by_class(o_r, refs, o_q, qs, cls, 5)
+    for _ in range(2):
+        i, s = plan.launch()
+        torch.cuda.synchronize()
+        lib.status()
+        assert np.array_equal(hd.as_u32(i), want[0]) and np.array_equal(s.cpu().numpy(), want[1])
+    assert np.array_equal(plan.q_comp.cpu().numpy(), o_q)     # the plan's own multi-bit encode
+    rng = np.random.Generator(np.random.PCG64(98))
+    qs2 = synth.make_queries(refs, qs.n, rng)
+    off2, bins2, lv2 = oracle.preprocess(qs2.offsets, qs2.mz, qs2.intensity, **pp)
+    nnz2 = int(off2[-1])
+    plan.offsets.copy_(dev(off2))
+    plan.bins[:nnz2].copy_(dev(bins2))
+    plan.levels[:nnz2].copy_(dev(lv2))
+    plan.q_mz.copy_(dev(qs2.precursor_mz))
+    plan.q_charge.copy_(dev(qs2.charge))
+    i, s = plan.launch()
+    torch.cuda.synchronize()
+    F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, 0)
+    o_q2 = oracle.encode_multibit(D, F, L, off2, bins2, lv2, bits)
+    want2 = _oracle_dot_by_class(o_r, refs, o_q2, qs2, cls, 5)
+    assert np.array_equal(hd.as_u32(i), want2[0]) and np.array_equal(s.cpu().numpy(), want2[1])
+
+
+def test_multibit_batched_argument_errors(hd):
+    D, Q = 1024, 8
+    refs, qs, cls, _ = _batched_workload(23, 600, 4, 5, 20)
+    ctx, lib, q_csr, o_r, o_q, _ = _setup_mb(hd, refs, qs, D, Q, 3)
+    off, b, lv = q_csr
+    q_hv = dev(np.zeros((qs.n, D // 64), np.uint64))
+    with pytest.raises(hd.HDError) as e:       # the binary multi-window search refuses a multi-bit library
+        hd.hd_search_open_multi(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    q_comp = hd.hd_encode_multibit(ctx, *q_csr, 3)
+    for kw in (dict(form="popc"), dict(form="tc_bf16"), dict(k=0), dict(k=17)):
+        with pytest.raises(hd.HDError) as e:
+            hd.hd_search_dot_multi(lib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, **kw)
+        assert e.value.status == hd.HD_ERR_INVALID_ARG
+    blib = hd.hd_build_library(ctx, dev(np.zeros((refs.n, D // 64), np.uint64)), dev(refs.precursor_mz),
+                               dev(refs.charge))
+    with pytest.raises(hd.HDError) as e:       # the dot search refuses a binary library
+        hd.hd_search_dot_multi(blib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG

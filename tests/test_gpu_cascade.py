@@ -199,3 +199,126 @@ def test_cascade_full_size_one_level(hd):
     oi, od = oracle.search(D, r_np, refs.precursor_mz, refs.charge, q_np, sub.precursor_mz, sub.charge, 500.0,
                            "da", 1)
     assert np.array_equal(gi[which], oi[:, 0]) and np.array_equal(gd[which], od[:, 0])
+
+
+# ------------------------------------------------ multi-bit components (Section 4.3)
+def _comp_workload(seed, D, n_t, n_q, m):
+    """Seeded random component rows in [-m, m] (targets, then as many decoys
+    with the same precursors) and queries that are copies of targets with 5-60%
+    of their components redrawn, 40% at the target's precursor and the rest
+    shifted."""
+    rng = np.random.default_rng(seed)
+    comp = rng.integers(-m, m + 1, (2 * n_t, D)).astype(np.int8)
+    mz_t = rng.uniform(400, 1500, n_t)
+    z_t = rng.integers(2, 5, n_t).astype(np.uint8)
+    mz, z = np.r_[mz_t, mz_t], np.r_[z_t, z_t]
+    dec = np.r_[np.zeros(n_t, np.uint8), np.ones(n_t, np.uint8)]
+    src = rng.integers(0, n_t, n_q)
+    shift = np.where(rng.random(n_q) < 0.4, 0.0, rng.uniform(-900, 900, n_q))
+    q_mz, q_z = mz[src] + shift / z[src], z[src]
+    q = comp[src].copy()
+    redraw = rng.random((n_q, D)) < rng.uniform(0.05, 0.6, (n_q, 1))
+    q[redraw] = rng.integers(-m, m + 1, int(redraw.sum()))
+    return comp, mz, z, dec, q, q_mz, q_z
+
+
+def _check_dot(hd, got, want):
+    gi, gs, gq, gl = got
+    oi, os_, ol, oq = want
+    assert np.array_equal(hd.as_u32(gi), oi)
+    assert np.array_equal(gs.cpu().numpy(), os_)
+    assert np.array_equal(gl.cpu().numpy(), ol)
+    assert np.array_equal(gq.cpu().numpy(), oq, equal_nan=True)
+
+
+@pytest.mark.parametrize("bits,form", [(2, "tc_mxf4"), (3, "tc_mxf4"), (3, "tc_fp4"), (4, "tc_fp8"),
+                                       (5, "tc_bf16"), (3, "auto")])
+@pytest.mark.parametrize("levels,fdr", [(LEVELS2, 0.01), (LEVELS3, 0.05)])
+def test_cascade_dot_matches_oracle(hd, bits, form, levels, fdr):
+    D, m = 2048, (1 << (bits - 1)) - 1
+    comp, mz, z, dec, q, q_mz, q_z = _comp_workload(40 + bits, D, 6000, 2000, m)
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library_multibit(ctx, dev(comp), dev(mz), dev(z), bits)
+    hd.hd_library_set_decoys(lib, dev(dec))
+    if form == "tc_bf16":   # bits <= 3 come with the e2m1 copy, bits 4..5 with e4m3
+        hd.hd_library_prepare(lib, form)
+    got = hd.hd_cascade_search_dot(lib, dev(q), dev(q_mz), dev(q_z), levels, fdr, form=form)
+    torch.cuda.synchronize()
+    lib.status()
+    want = oracle.cascade_dot(comp, mz, z, dec, q, q_mz, q_z, levels, fdr)
+    _check_dot(hd, got, want)
+    lv = want[2]
+    assert (lv == 0).sum() > 0 and (lv == len(levels) - 1).sum() > 0
+
+
+def test_cascade_dot_encoded_spectra_and_edges(hd):
+    """Multi-bit encode of synthetic spectra on each side, a charge with no
+    candidates, the FDR extremes and one query."""
+    D, Q, seed, bits = 1024, 8, 5, 3
+    rng = np.random.Generator(np.random.PCG64(seed))
+    refs = synth.make_references(3000, (2, 3), (0.5, 0.5), rng, decoy_fraction=0.5)
+    qs = synth.make_queries(refs, 400, rng)
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, seed)
+    pp = oracle_side.pp_args(Q)
+
+    def enc(sp):
+        return hd.hd_encode_multibit(ctx, *hd.hd_preprocess(ctx, dev(sp.offsets), dev(sp.mz), dev(sp.intensity),
+                                                            **pp), bits)
+
+    lib = hd.hd_build_library_multibit(ctx, enc(refs), dev(refs.precursor_mz), dev(refs.charge), bits)
+    hd.hd_library_set_decoys(lib, dev(refs.decoy))
+    q_comp = enc(qs)
+    F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, seed)
+    o_r = oracle.encode_multibit(D, F, L, *oracle.preprocess(refs.offsets, refs.mz, refs.intensity, **pp), bits)
+    o_q = oracle.encode_multibit(D, F, L, *oracle.preprocess(qs.offsets, qs.mz, qs.intensity, **pp), bits)
+    z = qs.charge.copy()
+    z[::7] = 5
+    for fdr in (-1.0, 0.0, 0.02, 1e9):
+        got = hd.hd_cascade_search_dot(lib, q_comp, dev(qs.precursor_mz), dev(z), LEVELS2, fdr)
+        torch.cuda.synchronize()
+        lib.status()
+        want = oracle.cascade_dot(o_r, refs.precursor_mz, refs.charge, refs.decoy, o_q, qs.precursor_mz, z,
+                                  LEVELS2, fdr)
+        _check_dot(hd, got, want)
+        assert np.all(got[3].cpu().numpy()[::7] == 255)
+        assert np.all(got[1].cpu().numpy()[::7] == np.iinfo(np.int32).min)
+    got = hd.hd_cascade_search_dot(lib, q_comp[:1], dev(qs.precursor_mz[:1]), dev(qs.charge[:1]),
+                                   [(500.0, "da")], 0.01)
+    torch.cuda.synchronize()
+    want = oracle.cascade_dot(o_r, refs.precursor_mz, refs.charge, refs.decoy, o_q[:1], qs.precursor_mz[:1],
+                              qs.charge[:1], [(500.0, "da")], 0.01)
+    _check_dot(hd, got, want)
+
+
+def test_cascade_dot_argument_errors(hd):
+    D = 1024
+    comp, mz, z, dec, q, q_mz, q_z = _comp_workload(9, D, 200, 8, 3)
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library_multibit(ctx, dev(comp), dev(mz), dev(z), 3)
+    args = (dev(q), dev(q_mz), dev(q_z), LEVELS2, 0.01)
+    with pytest.raises(hd.HDError) as e:            # no decoy flags yet
+        hd.hd_cascade_search_dot(lib, *args)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    hd.hd_library_set_decoys(lib, dev(dec))
+    for form in ("popc", "tc_bf16"):                # not a tensor-core form / not prepared
+        with pytest.raises(hd.HDError) as e:
+            hd.hd_cascade_search_dot(lib, *args, form=form)
+        assert e.value.status == hd.HD_ERR_INVALID_ARG
+    hv = dev(np.zeros((8, D // 64), np.uint64))
+    with pytest.raises(hd.HDError) as e:            # the binary entry point refuses a multi-bit library
+        hd.hd_cascade_search(lib, hv, dev(q_mz), dev(q_z), LEVELS2, 0.01)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    blib = hd.hd_build_library(ctx, dev(np.zeros((400, D // 64), np.uint64)), dev(mz), dev(z))
+    hd.hd_library_set_decoys(blib, dev(dec))
+    with pytest.raises(hd.HDError) as e:            # and the dot entry point a binary one
+        hd.hd_cascade_search_dot(blib, *args)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    lib384 = hd.hd_build_library_multibit(hd.Ctx(384, 4, 10, 192, 0), dev(comp[:, :384]), dev(mz), dev(z), 3)
+    hd.hd_library_set_decoys(lib384, dev(dec))
+    with pytest.raises(hd.HDError) as e:            # kind::mxf4 needs D % 256 == 0
+        hd.hd_cascade_search_dot(lib384, dev(q[:, :384]), dev(q_mz), dev(q_z), LEVELS2, 0.01, form="tc_mxf4")
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    got = hd.hd_cascade_search_dot(lib, *args, form="tc_fp4")
+    torch.cuda.synchronize()
+    lib.status()
+    _check_dot(hd, got, oracle.cascade_dot(comp, mz, z, dec, q, q_mz, q_z, LEVELS2, 0.01))
