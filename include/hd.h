@@ -394,6 +394,18 @@ HD_API hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, co
                                      const hd_window *windows, uint32_t n_windows, uint32_t k,
                                      hd_tune_result *best, hd_tune_result *all, uint32_t cap,
                                      uint32_t *n_all);
+/* The autotuner for a multi-bit library (Section 4.3): times the
+ * dot-product search (hd_search_dot_multi) over the same tensor-core forms
+ * and schedules on the queries' components d_q_comp [n_q][D] int8 (16-byte
+ * aligned; no popc candidate) and keeps the fastest as the library's
+ * HD_FORM_AUTO, which every dot-product call then takes.  HD_ERR_INVALID_ARG
+ * on a binary library or one without a tensor-core copy (and
+ * hd_library_autotune refuses a multi-bit library). */
+HD_API hd_status hd_library_autotune_dot(hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
+                                         const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
+                                         const hd_window *windows, uint32_t n_windows, uint32_t k,
+                                         hd_tune_result *best, hd_tune_result *all, uint32_t cap,
+                                         uint32_t *n_all);
 
 /* Continuous-batching server (no counterpart in the paper, which batches to
  * fill memory, Section 4.1).  A scheduler thread keeps the library resident

@@ -357,10 +357,7 @@ hd_status hd_cascade_search_dot(const hd_library *lib, const int8_t *d_q_comp, c
     if (hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, name + ": binary library (use hd_cascade_search)");
     if (form != HD_FORM_AUTO && !hd_is_tc_form(form))
         return hd_fail(HD_ERR_INVALID_ARG, name + ": form must be AUTO or a tensor-core form");
-    if (form == HD_FORM_AUTO) {
-        form = hd_fastest_tc_form(lib);
-        if (form == HD_FORM_AUTO) form = HD_FORM_TC_BF16;
-    }
+    form = hd_dot_form(lib, form);
     if (!hd_tc_copy(lib, form) && lib->n > 0)
         return hd_fail(HD_ERR_INVALID_ARG, name + ": call hd_library_prepare for this form first");
     if (form == HD_FORM_TC_MXF4 && lib->dim % 256 != 0)

@@ -479,10 +479,7 @@ hd_status hd_search_dot(const hd_library *lib, const int8_t *d_q_comp, const dou
     HD_CHECK(tol_ok(tol), "hd_search_dot: tol must be finite and >= 0");
     HD_CHECK(unit_ok(unit), "hd_search_dot: bad unit");
     HD_CHECK(form == HD_FORM_AUTO || hd_is_tc_form(form), "hd_search_dot: form must be AUTO or a tensor-core form");
-    if (form == HD_FORM_AUTO) {
-        form = hd_fastest_tc_form(lib);
-        if (form == HD_FORM_AUTO) form = HD_FORM_TC_BF16;
-    }
+    form = hd_dot_form(lib, form);
     HD_CHECK(hd_tc_copy(lib, form) || lib->n == 0, "hd_search_dot: call hd_library_prepare for this form first");
     HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
              "hd_search_dot: the kind::mxf4 form needs D to be a multiple of 256");
@@ -508,10 +505,7 @@ hd_status hd_search_dot_multi(const hd_library *lib, const int8_t *d_q_comp, con
     hd_qwin win;
     hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
     if (st != HD_OK) return st;
-    if (form == HD_FORM_AUTO) {
-        form = hd_fastest_tc_form(lib);
-        if (form == HD_FORM_AUTO) form = HD_FORM_TC_BF16;
-    }
+    form = hd_dot_form(lib, form);
     HD_CHECK(hd_tc_copy(lib, form) || lib->n == 0, "hd_search_dot_multi: call hd_library_prepare for this form first");
     HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
              "hd_search_dot_multi: the kind::mxf4 form needs D to be a multiple of 256");

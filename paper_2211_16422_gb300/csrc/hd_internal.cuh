@@ -218,6 +218,17 @@ inline hd_search_form hd_fastest_tc_form(const hd_library *lib)
     if (lib->x_bf16) return HD_FORM_TC_BF16;
     return HD_FORM_AUTO;
 }
+// Form of a dot-product search (multi-bit library): AUTO takes the
+// autotuner's choice when the library holds its copy, else the fastest
+// prepared tensor-core form, else bf16 (which the caller then finds
+// unprepared).
+inline hd_search_form hd_dot_form(const hd_library *lib, hd_search_form f)
+{
+    if (f != HD_FORM_AUTO) return f;
+    if (hd_is_tc_form(lib->auto_form) && hd_tc_copy(lib, lib->auto_form)) return lib->auto_form;
+    const hd_search_form g = hd_fastest_tc_form(lib);
+    return g == HD_FORM_AUTO ? HD_FORM_TC_BF16 : g;
+}
 // Entry points that score binary HVs refuse a multi-bit library.
 inline bool hd_lib_binary(const hd_library *lib) { return lib->bits == 1; }
 

@@ -384,7 +384,7 @@ hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_p
     srv->multibit = !hd_lib_binary(lib);
     srv->form = params->form;
     if (srv->multibit) {   // the dot-product search runs on a tensor-core copy the library holds
-        if (srv->form == HD_FORM_AUTO) srv->form = hd_fastest_tc_form(lib);
+        srv->form = hd_dot_form(lib, srv->form);
         if (!hd_is_tc_form(srv->form) || (!hd_tc_copy(lib, srv->form) && lib->n) ||
             (srv->form == HD_FORM_TC_MXF4 && lib->dim % 256 != 0))
             return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: multi-bit library needs a prepared tensor-core form");

@@ -101,6 +101,7 @@ _SIGS = {
     "hd_plan_info": ([P, P], i32),
     "hd_plan_destroy": ([P], None),
     "hd_library_autotune": ([P, P, P, P, P, u32, P, u32, u32, P, P, u32, P], i32),
+    "hd_library_autotune_dot": ([P, P, P, P, P, u32, P, u32, u32, P, P, u32, P], i32),
     "hd_server_create": ([P, P, P, P], i32),
     "hd_server_submit": ([P, P, P, P, P, P, u32, dbl, i32, P, P, P], i32),
     "hd_server_submit_dot": ([P, P, P, P, P, P, u32, dbl, i32, P, P, P], i32),
@@ -615,12 +616,17 @@ class Plan:
 
 def hd_library_autotune(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=1):
     """Times every prepared form and schedule; keeps the fastest as the library's 'auto'.
-    Returns (best, all) as dicts."""
-    q_hv = _dev(q_hv, torch.int64, "q_hv")
+    Returns (best, all) as dicts.  On a multi-bit library q_hv holds the queries' int8
+    components [n, D] and the dot-product search is tuned (hd_library_autotune_dot)."""
+    multibit = hd_library_component_bits(lib) > 1
+    if multibit:
+        q = _dev(q_hv, torch.int8, "q_comp")
+    else:
+        q = _dev(q_hv, torch.int64, "q_hv")
     q_mz = _dev(q_mz, torch.float64, "q_mz")
     q_charge = _dev(q_charge, torch.uint8, "q_charge")
     n = q_mz.numel()
-    _need(q_hv, n * (lib.dim // 64), "q_hv")
+    _need(q, n * (lib.dim if multibit else lib.dim // 64), "q_comp" if multibit else "q_hv")
     _need(q_charge, n, "q_charge")
     if q_class is not None:
         q_class = _need(_dev(q_class, torch.uint8, "q_class"), n, "q_class")
@@ -629,9 +635,9 @@ def hd_library_autotune(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=
     allr = (_TuneResult * 64)()
     n_all = C.c_uint32()
     w = _windows(windows)
-    _check(load().hd_library_autotune(lib.handle, _ptr(q_hv), _ptr(q_mz), _ptr(q_charge), _ptr(q_class),
-                                      q_mz.numel(), w, len(windows), int(k), C.byref(best), allr, 64,
-                                      C.byref(n_all)))
+    fn = load().hd_library_autotune_dot if multibit else load().hd_library_autotune
+    _check(fn(lib.handle, _ptr(q), _ptr(q_mz), _ptr(q_charge), _ptr(q_class), q_mz.numel(), w, len(windows),
+              int(k), C.byref(best), allr, 64, C.byref(n_all)))
     names = {v: k_ for k_, v in FORMS.items()}
     conv = lambda r: {"form": names[r.form], "tile_group": r.tile_group, "super_group": r.super_group,
                       "cluster": r.cluster, "cta_group": r.cta_group, "ms": r.ms}

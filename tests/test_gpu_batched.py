@@ -338,3 +338,37 @@ def test_multibit_batched_argument_errors(hd):
     with pytest.raises(hd.HDError) as e:       # the dot search refuses a binary library
         hd.hd_search_dot_multi(blib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
     assert e.value.status == hd.HD_ERR_INVALID_ARG
+
+
+def test_autotune_dot_keeps_results(hd):
+    """The multi-bit autotuner: mxf4 pairs (6 schedules) and e2m1 (12) for a
+    3-bit library; the chosen form and schedule serve AUTO in the dot search
+    and in a multi-bit plan, with the oracle's results."""
+    D, Q, bits = 2048, 32, 3
+    refs, qs, cls, _ = _batched_workload(29, 8000, 9, 50, 400)
+    ctx, lib, q_csr, o_r, o_q, _ = _setup_mb(hd, refs, qs, D, Q, bits)
+    q_comp = hd.hd_encode_multibit(ctx, *q_csr, bits)
+    args = (lib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
+    best, allr = hd.hd_library_autotune(*args, 5)
+    forms = [r["form"] for r in allr]
+    assert forms.count("tc_mxf4") == 6 and forms.count("tc_fp4") == 12 and len(allr) == 18
+    assert all((r["cluster"], r["cta_group"]) == (2, 2) for r in allr if r["form"] == "tc_mxf4")
+    assert best["ms"] == min(r["ms"] for r in allr) and best["form"] in ("tc_mxf4", "tc_fp4")
+    want = _oracle_dot_by_class(o_r, refs, o_q, qs, cls, 5)
+    i, s = hd.hd_search_dot_multi(*args, 5, form="auto")
+    torch.cuda.synchronize()
+    assert np.array_equal(hd.as_u32(i), want[0]) and np.array_equal(s.cpu().numpy(), want[1])
+    off, b, lv = q_csr
+    plan = hd.Plan(ctx, lib, off, b, lv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, k=5)
+    i, s = plan.launch()
+    torch.cuda.synchronize()
+    lib.status()
+    assert np.array_equal(hd.as_u32(i), want[0]) and np.array_equal(s.cpu().numpy(), want[1])
+    blib = hd.hd_build_library(ctx, dev(np.zeros((refs.n, D // 64), np.uint64)), dev(refs.precursor_mz),
+                               dev(refs.charge))
+    q_hv = dev(np.zeros((qs.n, D // 64), np.uint64))
+    with pytest.raises(hd.HDError) as e:       # a binary library without a tensor-core copy is tuned as binary
+        hd.hd_search_dot_multi(blib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    best_b, allr_b = hd.hd_library_autotune(blib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, 5)
+    assert [r["form"] for r in allr_b] == ["popc"]
