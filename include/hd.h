@@ -30,7 +30,8 @@
  *    calling thread.
  *  - Thread safety: distinct objects are independent.  One hd_ctx or
  *    hd_library may serve concurrent read-only calls (hd_encode,
- *    hd_search_open, hd_search_open_ex, hd_search_open_multi, hd_search_dot)
+ *    hd_search_open, hd_search_open_ex, hd_search_open_multi, hd_search_dot,
+ *    hd_search_dot_multi)
  *    from several host threads and streams.  hd_search_open_noalloc is the
  *    exception: all its calls share one scratch buffer, so its calls that
  *    overlap on the GPU race and must be serialised by the caller.
