@@ -94,7 +94,9 @@ def parse():
                     default="full",
                     help="full: the headline line; batched / serving / cascade / multibit: the extra workloads; "
                          "peaks: the instruction-rate microbenchmarks alone")
-    ap.add_argument("--bits", type=int, default=3, help="component bits of --workload multibit (2..5)")
+    ap.add_argument("--bits", type=int, default=None,
+                    help="component bits (2..5) of --workload multibit (default 3), or of --workload cascade "
+                         "(default: binary HVs)")
     return ap.parse_args()
 
 
@@ -819,21 +821,36 @@ def run_cascade(args):
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32
                                      else np.ascontiguousarray(a)).cuda()
     ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, seed=0)
-    r_hv = hd.hd_encode(ctx, *hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity),
-                                                **pp_args(spec)))
-    lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
-    del r_hv
+    bits = args.bits
+    r_csr = hd.hd_preprocess(ctx, dev(refs.offsets), dev(refs.mz), dev(refs.intensity), **pp_args(spec))
+    if bits:   # multi-bit components (Section 4.3), SSMs ranked by the dot product
+        r_comp = hd.hd_encode_multibit(ctx, *r_csr, bits)
+        lib = hd.hd_build_library_multibit(ctx, r_comp, dev(refs.precursor_mz), dev(refs.charge), bits)
+        del r_comp
+        cform = ("tc_mxf4" if D % 256 == 0 else "tc_fp4") if bits <= 3 else "tc_fp8"
+    else:
+        r_hv = hd.hd_encode(ctx, *r_csr)
+        lib = hd.hd_build_library(ctx, r_hv, dev(refs.precursor_mz), dev(refs.charge))
+        del r_hv
+        hd.hd_library_prepare(lib, "tc_fp4")
+        cform = "tc_mxf4" if D % 256 == 0 else "tc_fp4"   # kind::mxf4 on the e2m1 rows
+    del r_csr
     hd.hd_library_set_decoys(lib, dev(refs.decoy))
-    hd.hd_library_prepare(lib, "tc_fp4")
-    cform = "tc_mxf4" if D % 256 == 0 else "tc_fp4"   # kind::mxf4 on the e2m1 rows
     q_csr = hd.hd_preprocess(ctx, dev(queries.offsets), dev(queries.mz), dev(queries.intensity), **pp_args(spec))
     q_mz, q_z = dev(queries.precursor_mz), dev(queries.charge)
     nq = queries.n
-    q_hv = torch.empty((nq, D // 64), dtype=torch.int64, device="cuda")
+    if bits:
+        q_comp = torch.empty((nq, D), dtype=torch.int8, device="cuda")
 
-    def step():
-        hd.hd_encode(ctx, *q_csr, out=q_hv)
-        return hd.hd_cascade_search(lib, q_hv, q_mz, q_z, levels, fdr, form=cform)
+        def step():
+            hd.hd_encode_multibit(ctx, *q_csr, bits, out=q_comp)
+            return hd.hd_cascade_search_dot(lib, q_comp, q_mz, q_z, levels, fdr, form=cform)
+    else:
+        q_hv = torch.empty((nq, D // 64), dtype=torch.int64, device="cuda")
+
+        def step():
+            hd.hd_encode(ctx, *q_csr, out=q_hv)
+            return hd.hd_cascade_search(lib, q_hv, q_mz, q_z, levels, fdr, form=cform)
 
     for _ in range(args.warmup):
         out = step()
@@ -855,13 +872,15 @@ def run_cascade(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     level = out[3].cpu().numpy()
     ident = [int((level == i).sum()) for i in range(len(levels))]
+    kind = f", {bits}-bit components scored by the dot product" if bits else ""
     line = {"metric": "cascade search queries/s (20 ppm, then +-500 Da for the unidentified; 1% FDR per level), "
-                      "D=8192",
+                      "D=8192" + kind,
             "value": nq / (ms / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e2m1",
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE_OF_FORM.get(cform, "e2m1"),
             "data": "synthetic (seeded generator; decoys are targets with repositioned fragments)",
             "config": {"workload": f"{refs.n}-reference library (50% decoys) x {nq} queries, D={D}, Q={Q}, "
-                                   "levels 20 ppm / +-500 Da, top-1, FDR 1%", "form": cform,
+                                   "levels 20 ppm / +-500 Da, top-1, FDR 1%" + kind, "form": cform,
                        "l2": "library and query set exceed L2: no flush needed"},
             "identified_per_level": ident, "identified_fraction": sum(ident) / nq,
             "search_ms_per_step": search_ms / args.steps, "search_launches_per_step": search_n / args.steps,
@@ -879,7 +898,7 @@ def run_multibit(args):
     import torch
     from paper_2211_16422_gb300 import build, hd
     build.build()
-    bits = args.bits
+    bits = args.bits or 3
     refs, queries, spec = workload(args.scale, 0)
     D, Q, k, tol, unit = spec["dim"], spec["n_levels"], spec["k"], spec["tol"], spec["unit"]
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32
@@ -889,15 +908,26 @@ def run_multibit(args):
     r_comp = hd.hd_encode_multibit(ctx, *r_csr, bits)
     lib = hd.hd_build_library_multibit(ctx, r_comp, dev(refs.precursor_mz), dev(refs.charge), bits)
     del r_comp
-    form = args.form if args.form != "auto" else ("tc_mxf4" if bits <= 3 else "tc_fp8")
-    hd.hd_library_prepare(lib, form)
-    sched = {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2}
-    if args.schedule:
-        tg_, sg_, cs_, cg_ = (int(x) for x in args.schedule.split(","))
-        sched = {"tile_group": tg_, "super_group": sg_, "cluster": cs_, "cta_group": cg_}
+    q_csr = hd.hd_preprocess(ctx, dev(queries.offsets), dev(queries.mz), dev(queries.intensity), **pp_args(spec))
+    tuned = None
+    if args.form == "auto" and not args.schedule:
+        # the autotuner picks form and schedule on a second batch of the same recipe
+        tq = tuning_queries(refs, queries.n, 0)
+        tq_comp = hd.hd_encode_multibit(ctx, *hd.hd_preprocess(ctx, dev(tq.offsets), dev(tq.mz), dev(tq.intensity),
+                                                               **pp_args(spec)), bits)
+        tuned, _ = hd.hd_library_autotune(lib, tq_comp, dev(tq.precursor_mz), dev(tq.charge), None, [(tol, unit)], k)
+        del tq_comp
+        form = tuned["form"]
+        sched = {key: tuned[key] for key in ("tile_group", "super_group", "cluster", "cta_group")}
+    else:
+        form = args.form if args.form != "auto" else ("tc_mxf4" if bits <= 3 else "tc_fp8")
+        hd.hd_library_prepare(lib, form)
+        sched = {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2}
+        if args.schedule:
+            tg_, sg_, cs_, cg_ = (int(x) for x in args.schedule.split(","))
+            sched = {"tile_group": tg_, "super_group": sg_, "cluster": cs_, "cta_group": cg_}
     hd.hd_library_set_schedule(lib, sched["tile_group"], sched["super_group"], sched["cluster"],
                                sched["cta_group"])
-    q_csr = hd.hd_preprocess(ctx, dev(queries.offsets), dev(queries.mz), dev(queries.intensity), **pp_args(spec))
     q_mz, q_z = dev(queries.precursor_mz), dev(queries.charge)
     lo, hi = hd.hd_query_windows(lib, q_mz, q_z, tol, unit)
     comparisons = int((hd.as_u32(hi).astype(np.int64) - hd.as_u32(lo).astype(np.int64)).sum())
@@ -951,6 +981,7 @@ def run_multibit(args):
             "vs_baseline": None, "dtype": DTYPE_OF_FORM.get(form, "e4m3"), "data": "synthetic (seeded generator)",
             "config": {"workload": f"{refs.n}-reference library x {nq} queries, D={D}, {bits}-bit components "
                                    f"(|h| <= {2 ** (bits - 1) - 1}), +-500 open window, top-5", "form": form,
+                       "schedule": sched, "autotuned_on": "a second seeded query batch" if tuned else None,
                        "l2": "library and query set exceed L2: no flush needed"},
             "queries_per_s": nq / (ms / 1e3), "comparisons_per_step": comparisons,
             "kernel_ms_per_step": {"search": search_ms / args.steps, "encode": encode_ms / args.steps},
