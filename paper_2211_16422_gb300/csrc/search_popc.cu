@@ -34,7 +34,16 @@ constexpr uint32_t CHUNK_W32 = 128;     // 4096 bits of a row staged per step
 constexpr uint32_t PITCH32 = CHUNK_W32 + 4;   // padded row pitch (conflict-free LDS.128)
 constexpr uint32_t PITCH_B = PITCH32 * 4;
 constexpr uint32_t STAGE_B = (BQ + BR) * PITCH_B;
-constexpr uint32_t SMEM_B = 2 * STAGE_B + 64;
+// Stage ring: the loads of step s + NST - 1 are issued at the start of step
+// s, once the CTA barrier that opens the step has shown every warp done with
+// step s - 1, so each step needs one barrier.  At "full": 3 stages 831 ms
+// against 943 ms for 2 stages with a second barrier at the end of each step.
+#ifndef HD_POPC_STAGES
+#define HD_POPC_STAGES 3
+#endif
+constexpr uint32_t NST = HD_POPC_STAGES;
+static_assert(NST >= 2 && NST <= 3, "two or three stages fit in shared memory");
+constexpr uint32_t SMEM_B = NST * STAGE_B + 64;
 
 struct search_args {
     const uint64_t *lib_hv;
@@ -65,7 +74,7 @@ template <int K>
 __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE_B);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + NST * STAGE_B);
     __shared__ uint32_t s_item;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -75,8 +84,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
     const uint32_t nchunks = (W32 + CHUNK_W32 - 1) / CHUNK_W32;
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (uint32_t i = 0; i < NST; ++i) mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -130,35 +138,34 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = ones[i][j] = 0;
 
-        // warp 0 stages step `st_step` (tile, chunk) into buffer st_step & 1
+        // warp 0 stages step `st_step` (tile, chunk) into buffer st_step % NST
         auto issue = [&](uint32_t st_step) {
             const uint32_t tile = t0 + st_step / nchunks, ch = st_step % nchunks;
             const uint32_t cw = min(CHUNK_W32, W32 - ch * CHUNK_W32);
             const uint32_t rb = cw * 4;
             const uint32_t r0 = row_base + tile * BR;
             const uint32_t nr = min((uint32_t)BR, row_end - r0);
-            uint8_t *stage = smem + (st_step & 1) * STAGE_B;
-            if (lane == 0) mbar_expect_tx(&bar[st_step & 1], (nq + nr) * rb);
+            const uint32_t sb = st_step % NST;
+            uint8_t *stage = smem + sb * STAGE_B;
+            if (lane == 0) mbar_expect_tx(&bar[sb], (nq + nr) * rb);
             __syncwarp();
             if (a.stall && first_item && st_step == 0) return;   // nothing completes this stage
             for (uint32_t x = lane; x < nq; x += 32)
                 bulk_load(stage + x * PITCH_B,
                           a.q_hv + (size_t)a.perm[q0 + x] * a.W64 + ch * (CHUNK_W32 / 2), rb,
-                          &bar[st_step & 1]);
+                          &bar[sb]);
             for (uint32_t x = lane; x < nr; x += 32)
                 bulk_load(stage + (BQ + x) * PITCH_B,
                           a.lib_hv + (size_t)(r0 + x) * a.W64 + ch * (CHUNK_W32 / 2), rb,
-                          &bar[st_step & 1]);
+                          &bar[sb]);
         };
 
-        if (warp == 0 && steps > 0) {
-            issue(0);
-            if (steps > 1) issue(1);
-        }
+        if (warp == 0)
+            for (uint32_t p = 0; p + 1 < NST && p < steps; ++p) issue(p);
         uint32_t waited = 0;
         bool aborted = false;
         for (uint32_t s = 0; s < steps; ++s) {
-            const uint32_t st = s & 1;
+            const uint32_t st = s % NST;
             const bool ok = mbar_wait(&bar[st], (parity >> st) & 1u, a.wait_ns);
             parity ^= 1u << st;
             ++waited;
@@ -166,6 +173,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
                 aborted = true;
                 break;
             }
+            // every warp is done with step s - 1: its buffer takes step s + NST - 1
+            if (warp == 0 && s + NST - 1 < steps) issue(s + NST - 1);
             const uint32_t tile = t0 + s / nchunks, ch = s % nchunks;
             const uint32_t cw = min(CHUNK_W32, W32 - ch * CHUNK_W32);
             const uint32_t *qs = reinterpret_cast<const uint32_t *>(smem + st * STAGE_B);
@@ -205,16 +214,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc(search_args a)
                     }
                 }
             }
-            __syncthreads();
-            if (warp == 0 && s + 2 < steps) issue(s + 2);
         }
         if (aborted) {
             if (tid == 0) hd_flag(a.status, HD_DEV_TIMEOUT);
             // let copies still in flight land before the CTA's memory is released
-            const uint32_t issued = min(steps, waited + 1);
+            const uint32_t issued = min(steps, waited + NST - 2);
             for (uint32_t s = waited; s < issued; ++s) {
-                mbar_wait(&bar[s & 1], (parity >> (s & 1)) & 1u, a.wait_ns);
-                parity ^= 1u << (s & 1);
+                mbar_wait(&bar[s % NST], (parity >> (s % NST)) & 1u, a.wait_ns);
+                parity ^= 1u << (s % NST);
             }
             return;
         }
