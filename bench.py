@@ -44,6 +44,7 @@ L2_BYTES = 129 * 2**20
 # captured value and the launch uses the captured form and schedule;
 # otherwise `traffic` is null.
 KERNEL_SOURCES = ("paper_2211_16422_gb300/csrc/search_mma.cu", "paper_2211_16422_gb300/csrc/search_common.cuh")
+POPC_SOURCES = ("paper_2211_16422_gb300/csrc/search_popc.cu", "paper_2211_16422_gb300/csrc/search_common.cuh")
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
@@ -58,13 +59,13 @@ TRAFFIC = {
 DTYPE_OF_FORM = {"tc_mxf4": "e2m1", "tc_fp4": "e2m1", "tc_fp8": "e4m3", "tc_bf16": "bf16", "popc": "u32"}
 
 
-def kernel_source_hash():
+def kernel_source_hash(sources=KERNEL_SOURCES):
     """sha256 of the kernel's code: its sources with C/C++ comments and blank
     lines removed, so that editing a comment keeps the captured figures."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
             t = fh.read()
         t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
@@ -539,7 +540,8 @@ def run_ours(args, rank, world, local_rank):
             traffic = t_["bytes"]
     roofline.update({"traffic": traffic, "traffic_unit": "bytes per launch", "avg_launch_ms": avg_search_ms,
                      "launches": search_n, "step_share": search_ms / (ms * args.steps),
-                     "kernel_source_sha256": kernel_source_hash()})
+                     "kernel_source_sha256": kernel_source_hash(POPC_SOURCES if roofline["kernel"] == "k_search_popc"
+                                                                 else KERNEL_SOURCES)})
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         per_step, threads, sample, cstep = cpu_oracle_rate(refs, queries, spec, args.cpu_seconds)
