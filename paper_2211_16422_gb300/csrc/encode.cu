@@ -34,6 +34,20 @@ constexpr int ENC_WARPS = 8;
 
 __device__ __forceinline__ uint64_t maj3(uint64_t a, uint64_t b, uint64_t c) { return (a & b) | (a & c) | (b & c); }
 
+// Transpose of an 8 x 8 bit matrix held as 8 bytes (row r = byte r, column
+// c = bit c): three rounds of masked exchanges of the off-diagonal 1 x 1,
+// 2 x 2 and 4 x 4 blocks (H. S. Warren, Hacker's Delight, section 7-3).
+__device__ __forceinline__ uint64_t transpose8x8(uint64_t x)
+{
+    uint64_t t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+    x ^= t ^ (t << 7);
+    t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+    x ^= t ^ (t << 14);
+    t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+    x ^= t ^ (t << 28);
+    return x;
+}
+
 // Bound words F_bin XOR L_level of one peak (pk = (bin, level)) for the
 // lane's WPL words wl, wl + 32, ...; 0 beyond the row unless FULL (W a
 // multiple of 32 * WPL, every word in range).
@@ -392,13 +406,28 @@ k_encode_mb_sliced(const uint64_t *__restrict__ F, uint32_t n_bins, const uint64
             uint32_t p[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) p[q] = 0;
+            if (lim <= 8) {
+                // counts below 256: the eight planes' byte g, transposed as an 8 x 8
+                // bit matrix, give the counts of components 8g..8g+7 as bytes
 #pragma unroll
-            for (int b = 0; b < 64; ++b) {
-                uint32_t cnt = 0;
+                for (int g = 0; g < 8; ++g) {
+                    uint64_t x = 0;
 #pragma unroll
-                for (int i = 0; i < ENC_PLANES; ++i)
-                    if (i < lim) cnt |= (uint32_t)((c[j][i] >> b) & 1ull) << i;
-                p[b >> 2] |= (uint32_t)(uint8_t)s_tab[wi][cnt] << (8 * (b & 3));
+                    for (int i = 0; i < 8; ++i) x |= ((c[j][i] >> (8 * g)) & 0xFFull) << (8 * i);
+                    x = transpose8x8(x);
+#pragma unroll
+                    for (int b = 0; b < 8; ++b)
+                        p[2 * g + (b >> 2)] |= (uint32_t)(uint8_t)s_tab[wi][(x >> (8 * b)) & 0xFF] << (8 * (b & 3));
+                }
+            } else {
+#pragma unroll
+                for (int b = 0; b < 64; ++b) {
+                    uint32_t cnt = 0;
+#pragma unroll
+                    for (int i = 0; i < ENC_PLANES; ++i)
+                        if (i < lim) cnt |= (uint32_t)((c[j][i] >> b) & 1ull) << i;
+                    p[b >> 2] |= (uint32_t)(uint8_t)s_tab[wi][cnt] << (8 * (b & 3));
+                }
             }
             uint4 *o = reinterpret_cast<uint4 *>(out + (size_t)sp * W * 64 + (size_t)w * 64);
 #pragma unroll
