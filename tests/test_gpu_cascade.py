@@ -322,3 +322,70 @@ def test_cascade_dot_argument_errors(hd):
     torch.cuda.synchronize()
     lib.status()
     _check_dot(hd, got, oracle.cascade_dot(comp, mz, z, dec, q, q_mz, q_z, LEVELS2, 0.01))
+
+
+def test_cascade_dot_full_size_one_level(hd):
+    """1,000,000 references x 50,000 queries, D=8192, 3-bit components, one
+    +-500 level under kind::mxf4: every query's SSM equals the dot-product
+    search's top-1, the q-values are recomputed by the oracle from the GPU's
+    own SSM scores and decoy flags (bit for bit), and 16 sampled charge-4
+    SSMs are checked against the oracle encoding and searching every charge-4
+    reference."""
+    refs, qs, spec = synth.make_workload("full")
+    D, Q, bits = spec["dim"], spec["n_levels"], 3
+    ctx = hd.Ctx(D, Q, synth.N_BINS, D // 2, 0)
+    pp = oracle_side.pp_args(Q)
+
+    def enc(sp):
+        return hd.hd_encode_multibit(ctx, *hd.hd_preprocess(ctx, dev(sp.offsets), dev(sp.mz), dev(sp.intensity),
+                                                            **pp), bits)
+
+    lib = hd.hd_build_library_multibit(ctx, enc(refs), dev(refs.precursor_mz), dev(refs.charge), bits)
+    hd.hd_library_set_decoys(lib, dev(refs.decoy))
+    q_comp = enc(qs)
+    q_mz, q_z = dev(qs.precursor_mz), dev(qs.charge)
+    gi, gs, gq, gl = hd.hd_cascade_search_dot(lib, q_comp, q_mz, q_z, [(500.0, "da")], 0.01, form="tc_mxf4")
+    si, ss = hd.hd_search_dot(lib, q_comp, q_mz, q_z, 500.0, "da", 1, "tc_mxf4")
+    torch.cuda.synchronize()
+    lib.status()
+    gi, gs, gq, gl = hd.as_u32(gi), gs.cpu().numpy(), gq.cpu().numpy(), gl.cpu().numpy()
+    assert np.array_equal(gi, hd.as_u32(si)[:, 0]) and np.array_equal(gs, ss.cpu().numpy()[:, 0])
+    has = gi != 0xFFFFFFFF
+    qv = oracle.fdr_qvalues(gs[has].astype(np.int64), refs.decoy[gi[has]])
+    assert np.array_equal(gq[has], qv) and np.all(np.isnan(gq[~has]))
+    ident = np.zeros(qs.n, bool)
+    ident[np.nonzero(has)[0]] = (refs.decoy[gi[has]] == 0) & (qv <= 0.01)
+    assert np.array_equal(gl == 0, ident) and np.all(gl[~ident] == 255)
+    F, L, _, _ = oracle.item_memory(D, Q, synth.N_BINS, D // 2, 0)
+    z4 = np.nonzero(refs.charge == 4)[0]
+    r4 = refs.subset(z4)
+    R4 = oracle.encode_multibit(D, F, L, *oracle.preprocess(r4.offsets, r4.mz, r4.intensity, **pp), bits)
+    rng = np.random.default_rng(78)
+    which = np.sort(rng.choice(np.nonzero(qs.charge == 4)[0], 16, replace=False))
+    q4 = qs.subset(which)
+    Q4 = oracle.encode_multibit(D, F, L, *oracle.preprocess(q4.offsets, q4.mz, q4.intensity, **pp), bits)
+    oi, osc = oracle.search_dot(R4, r4.precursor_mz, r4.charge, Q4, q4.precursor_mz, q4.charge, 500.0, "da", 1)
+    oi_g = np.where(oi[:, 0] == 0xFFFFFFFF, 0xFFFFFFFF, z4[np.minimum(oi[:, 0], z4.size - 1)]).astype(np.uint32)
+    assert np.array_equal(gi[which], oi_g) and np.array_equal(gs[which], osc[:, 0])
+
+
+def test_cascade_dot_empty_library_and_queries(hd):
+    D = 1024
+    comp, mz, z, dec, q, q_mz, q_z = _comp_workload(12, D, 50, 20, 3)
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    empty = hd.hd_build_library_multibit(ctx, dev(np.zeros((0, D), np.int8)), dev(np.zeros(0)),
+                                         dev(np.zeros(0, np.uint8)), 3)
+    # an empty library needs no decoy flags
+    gi, gs, gq, gl = hd.hd_cascade_search_dot(empty, dev(q), dev(q_mz), dev(q_z), LEVELS2, 0.01)
+    torch.cuda.synchronize()
+    empty.status()
+    assert np.all(hd.as_u32(gi) == 0xFFFFFFFF) and np.all(gs.cpu().numpy() == np.iinfo(np.int32).min)
+    assert np.all(gl.cpu().numpy() == 255) and np.all(np.isnan(gq.cpu().numpy()))
+    _check_dot(hd, (gi, gs, gq, gl),
+               oracle.cascade_dot(np.zeros((0, D), np.int8), np.zeros(0), np.zeros(0, np.uint8),
+                                  np.zeros(0, np.uint8), q, q_mz, q_z, LEVELS2, 0.01))
+    lib = hd.hd_build_library_multibit(ctx, dev(comp), dev(mz), dev(z), 3)
+    hd.hd_library_set_decoys(lib, dev(dec))
+    gi, gs, gq, gl = hd.hd_cascade_search_dot(lib, dev(q[:0]), dev(q_mz[:0]), dev(q_z[:0]), LEVELS2, 0.01)
+    torch.cuda.synchronize()
+    assert gi.numel() == 0 and gs.numel() == 0 and gq.numel() == 0 and gl.numel() == 0
