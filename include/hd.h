@@ -236,7 +236,9 @@ HD_API hd_status hd_library_status(hd_library *lib);
 /* Builds the bipolar copy of the library a tensor-core form scores
  * (HD_FORM_TC_FP8: n*D bytes; HD_FORM_TC_BF16: n*2D bytes; HD_FORM_TC_FP4:
  * n*D/2 bytes of device memory, owned by the library).  HD_FORM_POPC needs
- * nothing.  Synchronous; idempotent. */
+ * nothing on binary HVs; on a multi-bit library it builds the bit planes of
+ * the popcount dot product (n*bits*D/8 + 4n bytes).  Synchronous;
+ * idempotent. */
 HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
 /* Schedule of the tensor-core forms (no counterpart in the paper).  Reference
  * rows form tiles of 256 on a grid fixed to row 0; one work item scores one
@@ -523,11 +525,17 @@ HD_API hd_status hd_search_open_noalloc(const hd_library *lib, const uint64_t *d
  * HD_FORM_TC_FP8 (e4m3 holds the integers up to 16 exactly);
  * hd_library_prepare adds HD_FORM_TC_FP8 or HD_FORM_TC_BF16 (and
  * HD_FORM_TC_FP4 for bits <= 3).  Every partial sum is an integer of size at
- * most D m^2 < 2^24, so the fp32 accumulation is exact.  Such a library is
- * searched only with hd_search_dot; the binary entry points (hd_search_*,
- * cascade, plan, autotune, export) reject it with HD_ERR_INVALID_ARG, and
- * HD_FORM_POPC does not apply; hd_library_save / hd_library_load keep it and
- * the server serves it (hd_server_submit_dot).
+ * most D m^2 < 2^24, so the fp32 accumulation is exact.  HD_FORM_POPC
+ * scores the same S on the integer pipes once hd_library_prepare built the
+ * bit planes: with u = h + m in `bits` planes Q_i, R_i and U the row sums of
+ * u, S = sum over plane pairs of 2^(i+j) popc(Q_i & R_j) - m (U_q + U_r) +
+ * D m^2 (exact integer arithmetic).  Such a library is searched only with
+ * the dot-product calls (hd_search_dot, hd_search_dot_multi,
+ * hd_cascade_search_dot, hd_plan_create_dot, hd_library_autotune_dot); the
+ * binary entry points (hd_search_*, cascade, plan, autotune, export) reject
+ * it with HD_ERR_INVALID_ARG; hd_library_save / hd_library_load keep it and
+ * the server serves it (hd_server_submit_dot).  `form` of the dot-product
+ * calls: AUTO, HD_FORM_POPC or a tensor-core form the library holds.
  * hd_search_dot: windows as hd_search_open (Section 3.4); per query the k
  * best candidates by S, higher first, the lower input index on a tie; d_q_comp
  * [n_q][D] int8 (16-byte aligned, components in [-m, m]; others flag

@@ -186,7 +186,7 @@ hd_status level_search(const hd_library *lib, const uint8_t *q, const double *qm
 hd_status level_search(const hd_library *lib, const uint8_t *q, const double *qm, const uint8_t *qz, uint32_t n,
                        const hd_qwin &win, hd_search_form form, uint32_t *idx, int32_t *score, cudaStream_t s)
 {
-    return hd_search_mma_dot_run(lib, form, reinterpret_cast<const int8_t *>(q), qm, qz, n, win, 1, idx, score, s);
+    return hd_search_dot_dispatch(lib, form, reinterpret_cast<const int8_t *>(q), qm, qz, n, win, 1, idx, score, s);
 }
 
 // The cascade over query rows of row_bytes bytes; SSM scores of type T
@@ -355,13 +355,8 @@ hd_status hd_cascade_search_dot(const hd_library *lib, const int8_t *d_q_comp, c
     const std::string name = "hd_cascade_search_dot";
     if (!lib) return hd_fail(HD_ERR_INVALID_ARG, name + ": null library");
     if (hd_lib_binary(lib)) return hd_fail(HD_ERR_INVALID_ARG, name + ": binary library (use hd_cascade_search)");
-    if (form != HD_FORM_AUTO && !hd_is_tc_form(form))
-        return hd_fail(HD_ERR_INVALID_ARG, name + ": form must be AUTO or a tensor-core form");
-    form = hd_dot_form(lib, form);
-    if (!hd_tc_copy(lib, form) && lib->n > 0)
-        return hd_fail(HD_ERR_INVALID_ARG, name + ": call hd_library_prepare for this form first");
-    if (form == HD_FORM_TC_MXF4 && lib->dim % 256 != 0)
-        return hd_fail(HD_ERR_INVALID_ARG, name + ": the kind::mxf4 form needs D to be a multiple of 256");
+    hd_status st0 = hd_dot_check(lib, &form, name);
+    if (st0 != HD_OK) return st0;
     if (n_q == 0) return HD_OK;
     if (!d_q_comp || !d_q_mz || !d_q_charge || !d_out_idx || !d_out_score || !d_out_q || !d_out_level)
         return hd_fail(HD_ERR_INVALID_ARG, name + ": null buffer");

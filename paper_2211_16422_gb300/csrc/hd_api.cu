@@ -124,6 +124,8 @@ void lib_release(hd_library *lib)
     cudaFree(lib->x_fp4);
     cudaFree(lib->decoy);
     cudaFree(lib->comp);
+    cudaFree(lib->x_planes);
+    cudaFree(lib->usum);
     status_free(lib->status);
     delete lib;
 }
@@ -162,6 +164,18 @@ hd_status hd_make_qwin(const uint8_t *cls, const hd_window *windows, uint32_t n_
         w.w[i] = hd_single_window(windows[i].tol, windows[i].unit).w[0];
     }
     *out = w;
+    return HD_OK;
+}
+
+hd_status hd_dot_check(const hd_library *lib, hd_search_form *form, const std::string &name)
+{
+    if (*form != HD_FORM_AUTO && *form != HD_FORM_POPC && !hd_is_tc_form(*form))
+        return hd_fail(HD_ERR_INVALID_ARG, name + ": form must be AUTO, POPC or a tensor-core form");
+    *form = hd_dot_form(lib, *form);
+    if (!hd_dot_copy(lib, *form) && lib->n > 0)
+        return hd_fail(HD_ERR_INVALID_ARG, name + ": call hd_library_prepare for this form first");
+    if (*form == HD_FORM_TC_MXF4 && lib->dim % 256 != 0)
+        return hd_fail(HD_ERR_INVALID_ARG, name + ": the kind::mxf4 form needs D to be a multiple of 256");
     return HD_OK;
 }
 
@@ -478,18 +492,15 @@ hd_status hd_search_dot(const hd_library *lib, const int8_t *d_q_comp, const dou
     HD_CHECK(k >= 1 && k <= 16, "hd_search_dot: k must be in [1, 16]");
     HD_CHECK(tol_ok(tol), "hd_search_dot: tol must be finite and >= 0");
     HD_CHECK(unit_ok(unit), "hd_search_dot: bad unit");
-    HD_CHECK(form == HD_FORM_AUTO || hd_is_tc_form(form), "hd_search_dot: form must be AUTO or a tensor-core form");
-    form = hd_dot_form(lib, form);
-    HD_CHECK(hd_tc_copy(lib, form) || lib->n == 0, "hd_search_dot: call hd_library_prepare for this form first");
-    HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
-             "hd_search_dot: the kind::mxf4 form needs D to be a multiple of 256");
+    hd_status st = hd_dot_check(lib, &form, "hd_search_dot");
+    if (st != HD_OK) return st;
     if (n_q == 0) return HD_OK;
     HD_CHECK(d_q_comp && d_q_mz && d_q_charge && d_out_idx && d_out_score, "hd_search_dot: null buffer");
     HD_CHECK(aligned16(d_q_comp), "hd_search_dot: d_q_comp must be 16-byte aligned");
-    hd_status st = check_device(lib->device);
+    st = check_device(lib->device);
     if (st != HD_OK) return st;
-    return hd_search_mma_dot_run(lib, form, d_q_comp, d_q_mz, d_q_charge, n_q, hd_single_window(tol, unit), k,
-                                 d_out_idx, d_out_score, (cudaStream_t)stream);
+    return hd_search_dot_dispatch(lib, form, d_q_comp, d_q_mz, d_q_charge, n_q, hd_single_window(tol, unit), k,
+                                  d_out_idx, d_out_score, (cudaStream_t)stream);
 }
 
 hd_status hd_search_dot_multi(const hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
@@ -500,22 +511,18 @@ hd_status hd_search_dot_multi(const hd_library *lib, const int8_t *d_q_comp, con
     HD_CHECK(lib, "hd_search_dot_multi: null library");
     HD_CHECK(lib->bits > 1, "hd_search_dot_multi: binary library (use hd_search_open_multi)");
     HD_CHECK(k >= 1 && k <= 16, "hd_search_dot_multi: k must be in [1, 16]");
-    HD_CHECK(form == HD_FORM_AUTO || hd_is_tc_form(form),
-             "hd_search_dot_multi: form must be AUTO or a tensor-core form");
     hd_qwin win;
     hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
     if (st != HD_OK) return st;
-    form = hd_dot_form(lib, form);
-    HD_CHECK(hd_tc_copy(lib, form) || lib->n == 0, "hd_search_dot_multi: call hd_library_prepare for this form first");
-    HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
-             "hd_search_dot_multi: the kind::mxf4 form needs D to be a multiple of 256");
+    st = hd_dot_check(lib, &form, "hd_search_dot_multi");
+    if (st != HD_OK) return st;
     if (n_q == 0) return HD_OK;
     HD_CHECK(d_q_comp && d_q_mz && d_q_charge && d_out_idx && d_out_score, "hd_search_dot_multi: null buffer");
     HD_CHECK(aligned16(d_q_comp), "hd_search_dot_multi: d_q_comp must be 16-byte aligned");
     st = check_device(lib->device);
     if (st != HD_OK) return st;
-    return hd_search_mma_dot_run(lib, form, d_q_comp, d_q_mz, d_q_charge, n_q, win, k, d_out_idx, d_out_score,
-                                 (cudaStream_t)stream);
+    return hd_search_dot_dispatch(lib, form, d_q_comp, d_q_mz, d_q_charge, n_q, win, k, d_out_idx, d_out_score,
+                                  (cudaStream_t)stream);
 }
 
 void hd_library_free(hd_library *lib) { lib_release(lib); }
@@ -741,13 +748,12 @@ hd_status hd_library_prepare(hd_library *lib, hd_search_form form)
     HD_CHECK(form == HD_FORM_POPC || hd_is_tc_form(form), "hd_library_prepare: unknown form");
     HD_CHECK(form != HD_FORM_TC_MXF4 || lib->dim % 256 == 0,
              "hd_library_prepare: the kind::mxf4 form needs D to be a multiple of 256");
-    HD_CHECK(form != HD_FORM_POPC || hd_lib_binary(lib), "hd_library_prepare: popc scores binary HVs only");
     hd_status st = check_device(lib->device);
-    if (st != HD_OK || form == HD_FORM_POPC) return st;
+    if (st != HD_OK || (form == HD_FORM_POPC && hd_lib_binary(lib))) return st;   // binary rows need no copy
     scoped_stream ss;
     if (cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) != cudaSuccess)
         return hd_fail(HD_ERR_CUDA, "hd_library_prepare: stream creation failed");
-    st = hd_library_expand(lib, form, ss.s);
+    st = form == HD_FORM_POPC ? hd_library_planes(lib, ss.s) : hd_library_expand(lib, form, ss.s);
     if (st != HD_OK) return st;
     HD_CUDA_TRY(cudaStreamSynchronize(ss.s));
     return HD_OK;

@@ -78,6 +78,8 @@ struct hd_library {
     uint8_t *decoy = nullptr;      // [n] decoy flags, input order, optional
     uint32_t bits = 1;             // component bits: 1 = binary rows in hv; 2..5 = int8 rows in comp
     int8_t *comp = nullptr;        // [n][D] multi-bit components, sorted rows (bits > 1)
+    uint32_t *x_planes = nullptr;  // popc form of a multi-bit library: bit planes of h + m, [n][bits * D/32]
+    uint32_t *usum = nullptr;      // [n] sum over d of (h_d + m) of each sorted row
     hd_mma_tuning mma_tuning;
     hd_search_form auto_form = HD_FORM_AUTO;   // set by the autotuner
     uint64_t wait_ns = 0;                      // device wait limit (0: HD_WAIT_NS)
@@ -197,6 +199,22 @@ void hd_encode_mb_launch(const hd_ctx *ctx, const uint32_t *off, const uint32_t 
 hd_status hd_search_mma_dot_run(const hd_library *lib, hd_search_form form, const int8_t *q_comp,
                                 const double *q_mz, const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win,
                                 uint32_t k, uint32_t *out_idx, int32_t *out_score, cudaStream_t s);
+// The popcount form of the dot product (bit planes of the offset components
+// h + m, S = sum over plane pairs of 2^(i+j) popc(Q_i & R_j) - m (U_q + U_r)
+// + D m^2), and the library's planes it reads (hd_library_prepare).
+hd_status hd_library_planes(hd_library *lib, cudaStream_t s);
+hd_status hd_search_popc_dot_run(const hd_library *lib, const int8_t *q_comp, const double *q_mz,
+                                 const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
+                                 uint32_t *out_idx, int32_t *out_score, cudaStream_t s);
+inline hd_status hd_search_dot_dispatch(const hd_library *lib, hd_search_form form, const int8_t *q_comp,
+                                        const double *q_mz, const uint8_t *q_charge, uint32_t n_q,
+                                        const hd_qwin &win, uint32_t k, uint32_t *out_idx, int32_t *out_score,
+                                        cudaStream_t s)
+{
+    return form == HD_FORM_POPC
+               ? hd_search_popc_dot_run(lib, q_comp, q_mz, q_charge, n_q, win, k, out_idx, out_score, s)
+               : hd_search_mma_dot_run(lib, form, q_comp, q_mz, q_charge, n_q, win, k, out_idx, out_score, s);
+}
 inline uint32_t hd_comp_max(uint32_t bits) { return (1u << (bits - 1)) - 1u; }
 // The tensor-core copy a form scores (kind::mxf4 shares the e2m1 rows), and
 // the fastest tensor-core form the library is prepared for (HD_FORM_AUTO when
@@ -218,17 +236,27 @@ inline hd_search_form hd_fastest_tc_form(const hd_library *lib)
     if (lib->x_bf16) return HD_FORM_TC_BF16;
     return HD_FORM_AUTO;
 }
+// The copy a dot-product form reads: the bit planes for popc, else the
+// tensor-core copy.
+inline const void *hd_dot_copy(const hd_library *lib, hd_search_form f)
+{
+    return f == HD_FORM_POPC ? static_cast<const void *>(lib->x_planes) : static_cast<const void *>(hd_tc_copy(lib, f));
+}
 // Form of a dot-product search (multi-bit library): AUTO takes the
 // autotuner's choice when the library holds its copy, else the fastest
-// prepared tensor-core form, else bf16 (which the caller then finds
-// unprepared).
+// prepared tensor-core form, else popc on prepared bit planes, else bf16
+// (which the caller then finds unprepared).
 inline hd_search_form hd_dot_form(const hd_library *lib, hd_search_form f)
 {
     if (f != HD_FORM_AUTO) return f;
-    if (hd_is_tc_form(lib->auto_form) && hd_tc_copy(lib, lib->auto_form)) return lib->auto_form;
+    if (lib->auto_form != HD_FORM_AUTO && hd_dot_copy(lib, lib->auto_form)) return lib->auto_form;
     const hd_search_form g = hd_fastest_tc_form(lib);
-    return g == HD_FORM_AUTO ? HD_FORM_TC_BF16 : g;
+    if (g != HD_FORM_AUTO) return g;
+    return lib->x_planes ? HD_FORM_POPC : HD_FORM_TC_BF16;
 }
+// Checks of a dot-product form (resolving AUTO): a known form the library
+// holds the copy of (an empty library needs none); kind::mxf4 needs D % 256.
+hd_status hd_dot_check(const hd_library *lib, hd_search_form *form, const std::string &name);
 // Entry points that score binary HVs refuse a multi-bit library.
 inline bool hd_lib_binary(const hd_library *lib) { return lib->bits == 1; }
 

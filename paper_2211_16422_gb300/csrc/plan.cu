@@ -220,13 +220,8 @@ hd_status hd_plan_create_dot(hd_ctx *ctx, const hd_library *lib, const uint32_t 
         return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: null buffer");
     if (reinterpret_cast<uintptr_t>(d_q_comp_work) & 15u)
         return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: d_q_comp_work must be 16-byte aligned");
-    if (form != HD_FORM_AUTO && !hd_is_tc_form(form))
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: form must be AUTO or a tensor-core form");
-    form = hd_dot_form(lib, form);
-    if (!hd_tc_copy(lib, form) && lib->n > 0)
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: call hd_library_prepare for this form first");
-    if (form == HD_FORM_TC_MXF4 && lib->dim % 256 != 0)
-        return hd_fail(HD_ERR_INVALID_ARG, "hd_plan_create_dot: the kind::mxf4 form needs D to be a multiple of 256");
+    hd_status st0 = hd_dot_check(lib, &form, "hd_plan_create_dot");
+    if (st0 != HD_OK) return st0;
     hd_qwin win;
     hd_status st = hd_make_qwin(d_q_class, windows, n_windows, &win);
     if (st != HD_OK) return st;
@@ -237,8 +232,8 @@ hd_status hd_plan_create_dot(hd_ctx *ctx, const hd_library *lib, const uint32_t 
     return plan_capture(dev, [&](cudaStream_t s) -> hd_status {
         hd_encode_mb_launch(ctx, d_offsets, d_bins, d_levels, n_q, bits, d_q_comp_work, s);
         HD_CUDA_TRY(cudaGetLastError());
-        return hd_search_mma_dot_run(lib, form, d_q_comp_work, d_q_mz, d_q_charge, n_q, win, k, d_out_idx,
-                                     d_out_score, s);
+        return hd_search_dot_dispatch(lib, form, d_q_comp_work, d_q_mz, d_q_charge, n_q, win, k, d_out_idx,
+                                      d_out_score, s);
     }, out);
 }
 
@@ -292,12 +287,12 @@ hd_status hd_library_autotune_dot(hd_library *lib, const int8_t *d_q_comp, const
     hd_status st = tune_checks(lib, d_q_comp, d_q_mz, d_q_charge, d_q_class, n_q, windows, n_windows, k, &win,
                                "hd_library_autotune_dot");
     if (st != HD_OK) return st;
-    std::vector<hd_tune_result> cand = tc_candidates(lib, false);
-    if (cand.empty()) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune_dot: no tensor-core copy prepared");
+    std::vector<hd_tune_result> cand = tc_candidates(lib, lib->x_planes != nullptr);   // popc on prepared bit planes
+    if (cand.empty()) return hd_fail(HD_ERR_INVALID_ARG, "hd_library_autotune_dot: no tensor-core copy or bit planes prepared");
     return tune(lib, cand, n_q, k, best, all, cap, n_all,
                 [&](hd_search_form f, uint32_t *oi, void *osc, cudaStream_t s) {
-                    return hd_search_mma_dot_run(lib, f, d_q_comp, d_q_mz, d_q_charge, n_q, win, k, oi,
-                                                 static_cast<int32_t *>(osc), s);
+                    return hd_search_dot_dispatch(lib, f, d_q_comp, d_q_mz, d_q_charge, n_q, win, k, oi,
+                                                  static_cast<int32_t *>(osc), s);
                 });
 }
 

@@ -352,6 +352,375 @@ hd_status hd_search_popc_run_scratch(const hd_library *lib, const uint64_t *q_hv
 #undef HD_RUN_K
 }
 
+// ------------------------------------- popcount form of multi-bit components
+// Components h in [-m, m] (Section 4.3) as offset values u = h + m in b bit
+// planes; with P = sum over d of u_q,d u_r,d = sum over plane pairs (i, j) of
+// 2^(i+j) popc(Q_i & R_j), the dot product is S = P - m (U_q + U_r) + D m^2
+// (U the row sums of u).  Keys carry D m^2 - S = m (U_q + U_r) - P, the
+// multi-bit key distance of the tensor-core form, so the same top-k lists and
+// ties serve both.  Plane layout of a row: chunks of 1024 components, each
+// chunk the b planes' 32-bit words one plane after the other (the last chunk
+// holds the row's remaining words), so a row's chunk is one bulk copy.
+namespace {
+
+constexpr uint32_t MB_CW = 32;   // 32-bit words of one plane in a chunk
+
+__host__ __device__ inline uint32_t mb_pitch(uint32_t bits) { return bits * MB_CW + 4; }   // words, conflict-free LDS.128
+__host__ __device__ inline uint32_t mb_stage_bytes(uint32_t bits) { return (BQ + BR) * mb_pitch(bits) * 4; }
+
+// int8 components [n][D] -> planes [n][bits * D/32] and row sums; one warp
+// per row, one ballot per plane and 32-component word.  A component outside
+// [-m, m] flags the status word and counts as 0.
+__global__ void k_comp_planes(const int8_t *__restrict__ comp, uint32_t n, uint32_t D, uint32_t bits, int32_t m,
+                              uint32_t *__restrict__ planes, uint32_t *__restrict__ usum, uint32_t *status)
+{
+    const uint32_t row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const uint32_t lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const uint32_t W32 = D / 32;
+    const int8_t *c = comp + (size_t)row * D;
+    uint32_t *dst = planes + (size_t)row * bits * W32;
+    uint32_t sum = 0;
+    bool bad = false;
+    for (uint32_t w = 0; w < W32; ++w) {
+        int32_t h = c[32 * w + lane];
+        if (h < -m || h > m) {
+            bad = true;
+            h = 0;
+        }
+        const uint32_t u = (uint32_t)(h + m);
+        sum += u;
+        const uint32_t ch = w / MB_CW, cw = min(MB_CW, W32 - ch * MB_CW);
+        for (uint32_t i = 0; i < bits; ++i) {
+            const uint32_t word = __ballot_sync(0xFFFFFFFFu, (u >> i) & 1u);
+            if (lane == i) dst[bits * MB_CW * ch + i * cw + (w - ch * MB_CW)] = word;
+        }
+    }
+    sum = __reduce_add_sync(0xFFFFFFFFu, sum);
+    if (lane == 0) usum[row] = sum;
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) hd_flag(status, HD_DEV_BAD_INPUT);
+}
+
+struct mb_args {
+    const uint32_t *lib_planes, *lib_usum, *lib_orig;
+    const uint32_t *q_planes, *q_usum;   // queries in input order
+    const uint32_t *perm;
+    const uint32_t *lo, *hi;
+    const uint32_t *blk_lo, *blk_hi, *blk_nt, *item_start;
+    uint32_t *meta;
+    uint64_t *partial;
+    uint32_t *status;
+    uint32_t n_q, n_blocks, W32, bits, m, nst;
+    uint64_t wait_ns;
+    uint32_t stall;
+};
+
+// The popcount search of k_search_popc on bit planes: the same persistent
+// work list, stage ring (nst buffers, one CTA barrier per step) and 4 x 4
+// pairs per thread; per pair and 32-bit word, b^2 AND + popcount terms
+// weighted 2^(i+j).
+template <int K>
+__global__ void __launch_bounds__(THREADS, 1) k_search_popc_mb(mb_args a)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t bits = a.bits, pitch = mb_pitch(bits), stage_b = mb_stage_bytes(bits), nst = a.nst;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + nst * stage_b);
+    __shared__ uint32_t s_item;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int qg = 2 * warp + (lane >> 4);
+    const int rg = lane & 15;
+    const uint32_t nchunks = (a.W32 + MB_CW - 1) / MB_CW;
+    const uint32_t row_words = bits * a.W32;
+
+    if (tid == 0) {
+        for (uint32_t i = 0; i < nst; ++i) mbar_init(&bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const uint32_t total_items = a.item_start[a.n_blocks];
+    const uint32_t tpi = a.meta[0];
+    uint32_t parity = 0;
+    bool first_item = true;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&a.meta[1], 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();
+        if (item >= total_items) break;
+
+        uint32_t lo_b = 0, hi_b = a.n_blocks;
+        while (hi_b - lo_b > 1) {
+            const uint32_t mid = (lo_b + hi_b) >> 1;
+            if (a.item_start[mid] <= item) lo_b = mid; else hi_b = mid;
+        }
+        const uint32_t b = lo_b;
+        const uint32_t nt = a.blk_nt[b];
+        const uint32_t row_base = a.blk_lo[b];
+        const uint32_t t0 = (item - a.item_start[b]) * tpi;
+        const uint32_t t1 = min(nt, t0 + tpi);
+        const uint32_t steps = (t1 - t0) * nchunks;
+        const uint32_t q0 = b * BQ;
+        const uint32_t nq = min((uint32_t)BQ, a.n_q - q0);
+        const uint32_t row_end = a.blk_hi[b];
+
+        uint32_t qlo[4], qhi[4], uq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t s = q0 + qg + 16 * i;
+            qlo[i] = s < a.n_q ? a.lo[s] : 0u;
+            qhi[i] = s < a.n_q ? a.hi[s] : 0u;
+            uq[i] = s < a.n_q ? a.q_usum[a.perm[s]] : 0u;
+        }
+        uint64_t best[4][K];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int t = 0; t < K; ++t) best[i][t] = KEY_NONE;
+        uint32_t acc[4][4];   // P of pair (i, j) so far
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+
+        auto issue = [&](uint32_t st_step) {
+            const uint32_t tile = t0 + st_step / nchunks, ch = st_step % nchunks;
+            const uint32_t cw = min(MB_CW, a.W32 - ch * MB_CW);
+            const uint32_t rb = bits * cw * 4;
+            const uint32_t r0 = row_base + tile * BR;
+            const uint32_t nr = min((uint32_t)BR, row_end - r0);
+            const uint32_t sb = st_step % nst;
+            uint8_t *stage = smem + sb * stage_b;
+            if (lane == 0) mbar_expect_tx(&bar[sb], (nq + nr) * rb);
+            __syncwarp();
+            if (a.stall && first_item && st_step == 0) return;   // nothing completes this stage
+            for (uint32_t x = lane; x < nq; x += 32)
+                bulk_load(stage + x * pitch * 4, a.q_planes + (size_t)a.perm[q0 + x] * row_words + bits * MB_CW * ch,
+                          rb, &bar[sb]);
+            for (uint32_t x = lane; x < nr; x += 32)
+                bulk_load(stage + (BQ + x) * pitch * 4, a.lib_planes + (size_t)(r0 + x) * row_words + bits * MB_CW * ch,
+                          rb, &bar[sb]);
+        };
+
+        if (warp == 0)
+            for (uint32_t p = 0; p + 1 < nst && p < steps; ++p) issue(p);
+        uint32_t waited = 0;
+        bool aborted = false;
+        for (uint32_t s = 0; s < steps; ++s) {
+            const uint32_t st = s % nst;
+            const bool ok = mbar_wait(&bar[st], (parity >> st) & 1u, a.wait_ns);
+            parity ^= 1u << st;
+            ++waited;
+            if (__syncthreads_or(!ok)) {
+                aborted = true;
+                break;
+            }
+            if (warp == 0 && s + nst - 1 < steps) issue(s + nst - 1);
+            const uint32_t tile = t0 + s / nchunks, ch = s % nchunks;
+            const uint32_t cw = min(MB_CW, a.W32 - ch * MB_CW);
+            const uint32_t *qs = reinterpret_cast<const uint32_t *>(smem + st * stage_b);
+            const uint32_t *rs = qs + BQ * pitch;
+            for (uint32_t w = 0; w < cw; w += 4) {
+#pragma unroll 1
+                for (uint32_t pi = 0; pi < bits; ++pi) {
+                    uint4 qv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        qv[i] = *reinterpret_cast<const uint4 *>(qs + (qg + 16 * i) * pitch + pi * cw + w);
+#pragma unroll 1
+                    for (uint32_t pj = 0; pj < bits; ++pj) {
+                        uint4 rv[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            rv[j] = *reinterpret_cast<const uint4 *>(rs + (rg + 16 * j) * pitch + pj * cw + w);
+                        const uint32_t sh = pi + pj;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                acc[i][j] += (uint32_t)(__popc(qv[i].x & rv[j].x) + __popc(qv[i].y & rv[j].y) +
+                                                        __popc(qv[i].z & rv[j].z) + __popc(qv[i].w & rv[j].w))
+                                             << sh;
+                    }
+                }
+            }
+            if (ch == nchunks - 1) {
+                const uint32_t r0 = row_base + tile * BR;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t row = r0 + rg + 16 * j;
+                    const bool in = row < row_end;
+                    const uint32_t o = in ? __ldg(a.lib_orig + row) : 0u;
+                    const uint32_t ur = in ? __ldg(a.lib_usum + row) : 0u;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t kd = a.m * (uq[i] + ur) - acc[i][j];   // D m^2 - S >= 0
+                        acc[i][j] = 0;
+                        if (row >= qlo[i] && row < qhi[i]) {
+                            const uint64_t key = ((uint64_t)kd << 32) | o;
+                            if (key < best[i][K - 1]) topk_insert<K>(best[i], key);
+                        }
+                    }
+                }
+            }
+        }
+        if (aborted) {
+            if (tid == 0) hd_flag(a.status, HD_DEV_TIMEOUT);
+            const uint32_t in_flight = min(steps, waited + nst - 2);
+            for (uint32_t s = waited; s < in_flight; ++s) {
+                mbar_wait(&bar[s % nst], (parity >> (s % nst)) & 1u, a.wait_ns);
+                parity ^= 1u << (s % nst);
+            }
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int off = 1; off < 16; off <<= 1) {
+                uint64_t other[K];
+#pragma unroll
+                for (int t = 0; t < K; ++t) other[t] = __shfl_xor_sync(0xffffffffu, best[i][t], off);
+                topk_merge<K>(best[i], other);
+            }
+            if (rg == 0) {
+                uint64_t *dst = a.partial + ((size_t)item * BQ + qg + 16 * i) * K;
+#pragma unroll
+                for (int t = 0; t < K; ++t) dst[t] = best[i][t];
+            }
+        }
+        first_item = false;
+    }
+}
+
+// Final merge of the items' lists into the caller's order, as k_merge, with
+// the dot-product score S = bias - key distance (INT32_MIN for a missing slot).
+template <int K>
+__global__ void k_merge_score(const uint64_t *__restrict__ partial, const uint32_t *__restrict__ item_start,
+                              uint32_t bq, const uint32_t *__restrict__ perm, uint32_t n_q, uint32_t k, uint32_t bias,
+                              uint32_t *__restrict__ out_idx, int32_t *__restrict__ out_score)
+{
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_q) return;
+    const uint32_t b = s / bq, ql = s % bq;
+    uint64_t best[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) best[t] = KEY_NONE;
+    for (uint32_t it = item_start[b]; it < item_start[b + 1]; ++it) {
+        const uint64_t *p = partial + ((size_t)it * bq + ql) * K;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const uint64_t key = p[t];
+            if (key >= best[K - 1]) break;
+            topk_insert<K>(best, key);
+        }
+    }
+    const uint32_t q = perm[s];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        if ((uint32_t)t < k) {
+            const bool none = best[t] == KEY_NONE;
+            out_idx[(size_t)q * k + t] = none ? 0xFFFFFFFFu : (uint32_t)best[t];
+            out_score[(size_t)q * k + t] = none ? INT32_MIN : (int32_t)(bias - (uint32_t)(best[t] >> 32));
+        }
+    }
+}
+
+template <int K>
+hd_status run_mb(const hd_library *lib, const int8_t *q_comp, const double *q_mz, const uint8_t *q_z, uint32_t n_q,
+                 const hd_qwin &win, uint32_t k, uint32_t *out_idx, int32_t *out_score, cudaStream_t s)
+{
+    const uint32_t bits = lib->bits, W32 = lib->dim / 32, m = hd_comp_max(bits);
+    const uint32_t stage_b = mb_stage_bytes(bits);
+    const uint32_t nst = 3 * stage_b + 64 <= 227u * 1024u ? 3u : 2u;
+    const uint32_t smem_b = nst * stage_b + 64;
+    const uint32_t n_blocks = (n_q + BQ - 1) / BQ;
+    int occ = 0;
+    HD_CUDA_TRY(cudaFuncSetAttribute(k_search_popc_mb<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
+    HD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search_popc_mb<K>, THREADS, smem_b));
+    if (occ < 1) return hd_fail(HD_ERR_UNSUPPORTED, "multi-bit popcount kernel does not fit on this GPU");
+    const uint32_t grid = (uint32_t)(lib->num_sms * occ);
+    const uint32_t target_items = 8 * grid;
+
+    auto carve = [&](hd_arena &ar, uint32_t **perm, uint32_t **lo, uint32_t **hi, uint32_t **blo, uint32_t **bhi,
+                     uint32_t **bnt, uint32_t **ist, uint32_t **meta, uint64_t **part, uint32_t **qp,
+                     uint32_t **qu) {
+        *perm = ar.take<uint32_t>(n_q);
+        *lo = ar.take<uint32_t>(n_q);
+        *hi = ar.take<uint32_t>(n_q);
+        *blo = ar.take<uint32_t>(n_blocks);
+        *bhi = ar.take<uint32_t>(n_blocks);
+        *bnt = ar.take<uint32_t>(n_blocks);
+        *ist = ar.take<uint32_t>(n_blocks + 1);
+        *meta = ar.take<uint32_t>(4);
+        *part = ar.take<uint64_t>((size_t)(target_items + n_blocks) * BQ * K);
+        *qp = ar.take<uint32_t>((size_t)n_q * bits * W32);
+        *qu = ar.take<uint32_t>(n_q);
+    };
+    uint32_t *perm, *lo, *hi, *blo, *bhi, *bnt, *ist, *meta, *qp, *qu;
+    uint64_t *part;
+    hd_arena plan;
+    carve(plan, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part, &qp, &qu);
+    hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, nullptr, plan, s);
+    hd_arena ar;
+    if (cudaMallocAsync((void **)&ar.base, plan.used, s) != cudaSuccess) {
+        cudaGetLastError();
+        return hd_fail(HD_ERR_OOM, "multi-bit popcount search: scratch allocation failed");
+    }
+    carve(ar, &perm, &lo, &hi, &blo, &bhi, &bnt, &ist, &meta, &part, &qp, &qu);
+    hd_count_launches(1), k_comp_planes<<<hd_ceil_div(n_q, 8), 256, 0, s>>>(q_comp, n_q, lib->dim, bits, (int32_t)m, qp,
+                                                                             qu, lib->status.dev);
+    hd_sort_charge_mz(q_mz, q_z, win.cls, n_q, perm, ar, s);
+    hd_count_launches(1), k_windows<<<hd_ceil_div(n_q, 256), 256, 0, s>>>(lib->mz, lib->charge_start, q_mz, q_z, perm,
+                                                                        n_q, win, lo, hi);
+    hd_count_launches(1), k_worklist<<<1, 1024, 0, s>>>(lo, hi, n_q, BQ, BR, n_blocks, target_items, blo, bhi, bnt,
+                                                        ist, meta);
+    mb_args ma{lib->x_planes, lib->usum, lib->orig, qp, qu, perm, lo, hi, blo, bhi, bnt, ist, meta, part,
+               lib->status.dev, n_q, n_blocks, W32, bits, m, nst, hd_wait_limit(lib),
+               hd_take_injected_stall(lib) ? 1u : 0u};
+    {
+        hd_prof_scope timed(HD_KERNEL_SEARCH, s);
+        hd_count_launches(1), k_search_popc_mb<K><<<grid, THREADS, smem_b, s>>>(ma);
+    }
+    hd_count_launches(1), k_merge_score<K><<<hd_ceil_div(n_q, 128), 128, 0, s>>>(part, ist, BQ, perm, n_q, k,
+                                                                             lib->dim * m * m, out_idx, out_score);
+    HD_CUDA_TRY(cudaGetLastError());
+    HD_CUDA_TRY(cudaFreeAsync(ar.base, s));
+    return HD_OK;
+}
+
+}  // namespace
+
+hd_status hd_library_planes(hd_library *lib, cudaStream_t s)
+{
+    if (lib->x_planes || lib->n == 0) return HD_OK;
+    const uint32_t W32 = lib->dim / 32;
+    if (cudaMalloc(&lib->x_planes, (size_t)lib->n * lib->bits * W32 * 4) != cudaSuccess ||
+        cudaMalloc(&lib->usum, (size_t)lib->n * 4) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(lib->x_planes);
+        cudaFree(lib->usum);
+        lib->x_planes = nullptr;
+        lib->usum = nullptr;
+        return hd_fail(HD_ERR_OOM, "hd_library_prepare: bit-plane allocation failed");
+    }
+    hd_count_launches(1), k_comp_planes<<<hd_ceil_div(lib->n, 8), 256, 0, s>>>(
+        lib->comp, lib->n, lib->dim, lib->bits, (int32_t)hd_comp_max(lib->bits), lib->x_planes, lib->usum,
+        lib->status.dev);
+    HD_CUDA_TRY(cudaGetLastError());
+    return HD_OK;
+}
+
+hd_status hd_search_popc_dot_run(const hd_library *lib, const int8_t *q_comp, const double *q_mz,
+                                 const uint8_t *q_charge, uint32_t n_q, const hd_qwin &win, uint32_t k,
+                                 uint32_t *out_idx, int32_t *out_score, cudaStream_t s)
+{
+    if (k <= 1) return run_mb<1>(lib, q_comp, q_mz, q_charge, n_q, win, k, out_idx, out_score, s);
+    if (k <= 8) return run_mb<8>(lib, q_comp, q_mz, q_charge, n_q, win, k, out_idx, out_score, s);
+    return run_mb<16>(lib, q_comp, q_mz, q_charge, n_q, win, k, out_idx, out_score, s);
+}
+
 // ----------------------------------------------- integer-pipe microbenchmarks
 // Sixteen independent chains per thread, 32 warps per SM.  k_peak_popc: one
 // population count of a 32-bit word per step (plus the XOR that makes the

@@ -198,8 +198,8 @@ struct hd_server {
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
-            st = multibit ? hd_search_mma_dot_run(lib, form, reinterpret_cast<const int8_t *>(d_hv), d_mz, d_z, nq, win,
-                                                  p.k, d_oi, d_os, s.stream)
+            st = multibit ? hd_search_dot_dispatch(lib, form, reinterpret_cast<const int8_t *>(d_hv), d_mz, d_z, nq, win,
+                                                   p.k, d_oi, d_os, s.stream)
                           : hd_search_dispatch(lib, d_hv, d_mz, d_z, nq, win, p.k, p.form, d_oi, d_od, s.stream);
             if (st != HD_OK) e = cudaErrorUnknown;
         }
@@ -383,11 +383,9 @@ hd_status hd_server_create(hd_ctx *ctx, const hd_library *lib, const hd_server_p
     srv->p = *params;
     srv->multibit = !hd_lib_binary(lib);
     srv->form = params->form;
-    if (srv->multibit) {   // the dot-product search runs on a tensor-core copy the library holds
-        srv->form = hd_dot_form(lib, srv->form);
-        if (!hd_is_tc_form(srv->form) || (!hd_tc_copy(lib, srv->form) && lib->n) ||
-            (srv->form == HD_FORM_TC_MXF4 && lib->dim % 256 != 0))
-            return hd_fail(HD_ERR_INVALID_ARG, "hd_server_create: multi-bit library needs a prepared tensor-core form");
+    if (srv->multibit) {   // the dot-product search runs on a copy the library holds
+        hd_status st0 = hd_dot_check(lib, &srv->form, "hd_server_create (multi-bit library)");
+        if (st0 != HD_OK) return st0;
     }
     const size_t row_tc = (size_t)lib->dim * 2;
     srv->per_query_bytes = (srv->multibit ? (size_t)lib->dim : (size_t)lib->dim / 8) + row_tc + 1024 +

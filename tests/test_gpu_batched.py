@@ -265,7 +265,7 @@ def _setup_mb(hd, refs, qs, D, Q, bits, seed=0):
     return ctx, lib, q_csr, o_r, o_q, pp
 
 
-@pytest.mark.parametrize("bits,forms", [(3, ("tc_mxf4", "tc_fp4", "tc_bf16")), (4, ("tc_fp8",))])
+@pytest.mark.parametrize("bits,forms", [(3, ("tc_mxf4", "tc_fp4", "tc_bf16", "popc")), (4, ("tc_fp8", "popc"))])
 def test_multi_window_dot_exact(hd, bits, forms):
     D, Q = 2048, 32
     refs, qs, cls, _ = _batched_workload(11 + bits, 5000, 24, 10, 300)
@@ -273,7 +273,7 @@ def test_multi_window_dot_exact(hd, bits, forms):
     q_comp = hd.hd_encode_multibit(ctx, *q_csr, bits)
     want = _oracle_dot_by_class(o_r, refs, o_q, qs, cls, 5)
     for form in forms:
-        if form == "tc_bf16":
+        if form in ("tc_bf16", "popc"):
             hd.hd_library_prepare(lib, form)
         i, s = hd.hd_search_dot_multi(lib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, k=5,
                                       form=form)
@@ -302,6 +302,13 @@ def test_plan_dot_matches_oracle_and_refills(hd):
         lib.status()
         assert np.array_equal(hd.as_u32(i), want[0]) and np.array_equal(s.cpu().numpy(), want[1])
     assert np.array_equal(plan.q_comp.cpu().numpy(), o_q)     # the plan's own multi-bit encode
+    hd.hd_library_prepare(lib, "popc")                           # the popcount form in a plan of its own
+    pplan = hd.Plan(ctx, lib, off, b, lv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS, k=5, form="popc")
+    i, s = pplan.launch()
+    torch.cuda.synchronize()
+    lib.status()
+    assert np.array_equal(hd.as_u32(i), want[0]) and np.array_equal(s.cpu().numpy(), want[1])
+    pplan.close()
     rng = np.random.Generator(np.random.PCG64(98))
     qs2 = synth.make_queries(refs, qs.n, rng)
     off2, bins2, lv2 = oracle.preprocess(qs2.offsets, qs2.mz, qs2.intensity, **pp)

@@ -232,7 +232,7 @@ def _check_dot(hd, got, want):
 
 
 @pytest.mark.parametrize("bits,form", [(2, "tc_mxf4"), (3, "tc_mxf4"), (3, "tc_fp4"), (4, "tc_fp8"),
-                                       (5, "tc_bf16"), (3, "auto")])
+                                       (5, "tc_bf16"), (3, "auto"), (4, "popc")])
 @pytest.mark.parametrize("levels,fdr", [(LEVELS2, 0.01), (LEVELS3, 0.05)])
 def test_cascade_dot_matches_oracle(hd, bits, form, levels, fdr):
     D, m = 2048, (1 << (bits - 1)) - 1
@@ -240,7 +240,7 @@ def test_cascade_dot_matches_oracle(hd, bits, form, levels, fdr):
     ctx = hd.Ctx(D, 4, 10, D // 2, 0)
     lib = hd.hd_build_library_multibit(ctx, dev(comp), dev(mz), dev(z), bits)
     hd.hd_library_set_decoys(lib, dev(dec))
-    if form == "tc_bf16":   # bits <= 3 come with the e2m1 copy, bits 4..5 with e4m3
+    if form in ("tc_bf16", "popc"):   # bits <= 3 come with the e2m1 copy, bits 4..5 with e4m3
         hd.hd_library_prepare(lib, form)
     got = hd.hd_cascade_search_dot(lib, dev(q), dev(q_mz), dev(q_z), levels, fdr, form=form)
     torch.cuda.synchronize()

@@ -53,8 +53,10 @@ def test_stalled_wait_times_out_then_recovers(hd, form, cluster, cta_group):
     assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
 
 
-def test_stalled_dot_search_times_out_then_recovers(hd):
-    """The same bounded-wait path for the multi-bit dot-product search."""
+@pytest.mark.parametrize("form", ["tc_fp4", "popc"])
+def test_stalled_dot_search_times_out_then_recovers(hd, form):
+    """The same bounded-wait path for the multi-bit dot-product search (the
+    tensor-core form and the popcount form on bit planes)."""
     rng = np.random.default_rng(13)
     D, n, bits = 1024, 3000, 3
     R = rng.integers(-3, 4, (n, D)).astype(np.int8)
@@ -62,16 +64,17 @@ def test_stalled_dot_search_times_out_then_recovers(hd):
     z = np.full(n, 2, np.uint8)
     ctx = hd.Ctx(D, 4, 10, D // 2, 0)
     lib = hd.hd_build_library_multibit(ctx, dev(R), dev(mz), dev(z), bits)
+    hd.hd_library_prepare(lib, form)
     q, qm, qz = dev(R[:300]), dev(mz[:300]), dev(z[:300])
     hd.hd_library_set_wait_limit(lib, 0.05)
     hd.hd_library_inject_stall(lib, 1)
-    hd.hd_search_dot(lib, q, qm, qz, 50.0, "da", 3, "tc_fp4")
+    hd.hd_search_dot(lib, q, qm, qz, 50.0, "da", 3, form)
     torch.cuda.synchronize()
     with pytest.raises(hd.HDError) as e:
         lib.status()
     assert e.value.status == hd.HD_ERR_TIMEOUT
     lib.status()
-    i, sc = hd.hd_search_dot(lib, q, qm, qz, 50.0, "da", 3, "tc_fp4")
+    i, sc = hd.hd_search_dot(lib, q, qm, qz, 50.0, "da", 3, form)
     torch.cuda.synchronize()
     lib.status()
     oi, osc = oracle.search_dot(R, mz, z, R[:300], mz[:300], z[:300], 50.0, "da", 3)

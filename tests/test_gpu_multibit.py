@@ -101,7 +101,7 @@ def test_search_dot_encoded_spectra(hd, bits):
     ref_mz, ref_z, q_mz, q_z = windowed(rng, n_ref, n_q)
     lib = hd.hd_build_library_multibit(ctx, r_gpu, dev(ref_mz), dev(ref_z), bits)
     assert hd.hd_library_component_bits(lib) == bits
-    forms = ["tc_fp8", "tc_bf16"] + (["tc_fp4", "tc_mxf4"] if bits <= 3 else [])
+    forms = ["tc_fp8", "tc_bf16", "popc"] + (["tc_fp4", "tc_mxf4"] if bits <= 3 else [])
     for form in forms:
         hd.hd_library_prepare(lib, form)
     for form in forms:
@@ -113,7 +113,7 @@ def test_search_dot_encoded_spectra(hd, bits):
 
 
 @pytest.mark.parametrize("cluster,cta_group", [(2, 2), (1, 1)])
-@pytest.mark.parametrize("form,bits", [("tc_fp4", 3), ("tc_fp8", 4), ("tc_mxf4", 3)])
+@pytest.mark.parametrize("form,bits", [("tc_fp4", 3), ("tc_fp8", 4), ("tc_mxf4", 3), ("popc", 5)])
 def test_search_dot_random_components_schedules(hd, form, bits, cluster, cta_group):
     """Random components in [-m, m], duplicate rows (ties go to the lower input
     index) and rows of all +m / all -m (scores D m^2 and -D m^2, the ends of
@@ -182,8 +182,10 @@ def test_multibit_argument_checks(hd):
     with pytest.raises(hd.HDError):                    # binary entry points refuse it
         hd.hd_search_open(lib, torch.zeros((4, D // 64), dtype=torch.int64, device="cuda"),
                           dev(mz[:4]), dev(z[:4]), 1.0, "da", 1)
-    with pytest.raises(hd.HDError):
-        hd.hd_library_prepare(lib, "popc")
+    with pytest.raises(hd.HDError):                    # the popcount form needs its bit planes first
+        hd.hd_search_dot(lib, dev(R[:4]), dev(mz[:4]), dev(z[:4]), 1.0, "da", 1, "popc")
+    hd.hd_library_prepare(lib, "popc")
+    check_dot(hd, lib, R, mz, z, R[:4], mz[:4], z[:4], 1.0, "da", 3, "popc")
     binary = hd.hd_build_library(ctx, torch.zeros((300, D // 64), dtype=torch.int64, device="cuda"),
                                  dev(mz), dev(z))
     with pytest.raises(hd.HDError):                    # hd_search_dot refuses a binary library
@@ -249,3 +251,38 @@ def test_search_dot_full_size_sampled(hd):
                                 spec["unit"], k)
     oi_g = np.where(oi == 0xFFFFFFFF, 0xFFFFFFFF, z4[np.minimum(oi, z4.size - 1)]).astype(np.uint32)
     assert np.array_equal(gi[which], oi_g) and np.array_equal(gs[which], osc)
+
+
+@pytest.mark.parametrize("bits,D", [(2, 128), (3, 1024), (3, 1152), (4, 2176), (5, 4096)])
+def test_search_dot_popc_chunks(hd, bits, D):
+    """The popcount form on bit planes: one chunk of 1024 components, a ragged
+    last chunk (1152 = 1024 + 128, 2176 = 2 x 1024 + 128), D below one chunk;
+    random components with duplicate rows and all +m / all -m rows; k 1 / 5 /
+    16 and the three window units against the oracle; equal to a tensor-core
+    form on every query."""
+    m = 2 ** (bits - 1) - 1
+    rng = np.random.default_rng(bits * 100 + D)
+    n_ref, n_q = 1500, 300
+    R = rng.integers(-m, m + 1, (n_ref, D)).astype(np.int8)
+    Qv = rng.integers(-m, m + 1, (n_q, D)).astype(np.int8)
+    ref_mz, ref_z, q_mz, q_z = windowed(rng, n_ref, n_q, 400.0, 420.0)
+    R[7], ref_mz[7], ref_z[7] = R[3], ref_mz[3], ref_z[3]
+    R[10], R[11] = m, -m
+    ref_z[11], ref_mz[11] = ref_z[10], ref_mz[10]
+    Qv[0], q_mz[0], q_z[0] = m, ref_mz[10], ref_z[10]
+    Qv[1], q_mz[1], q_z[1] = R[3], ref_mz[3], ref_z[3]
+    ctx = hd.Ctx(D, 8, 100, D // 2, 1)
+    lib = hd.hd_build_library_multibit(ctx, dev(R), dev(ref_mz), dev(ref_z), bits)
+    hd.hd_library_prepare(lib, "popc")
+    for unit, tol, k in (("da", 3.0, 5), ("ppm", 5000.0, 1), ("mass", 9.0, 16)):
+        oi = check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, tol, unit, k, "popc")
+    gi, gs = hd.hd_search_dot(lib, dev(Qv[:2]), dev(q_mz[:2]), dev(q_z[:2]), 0.0, "da", 16, "popc")
+    s0, i0 = gs.cpu().numpy(), u32(gi)
+    assert s0[0, 0] == D * m * m and s0[0][i0[0] == 11][0] == -D * m * m
+    assert i0[1, 0] == 3 and i0[1, 1] == 7 and s0[1, 0] == s0[1, 1]
+    tc = "tc_fp4" if bits <= 3 else "tc_fp8"
+    hd.hd_library_prepare(lib, tc)
+    a = hd.hd_search_dot(lib, dev(Qv), dev(q_mz), dev(q_z), 10.0, "da", 5, "popc")
+    b = hd.hd_search_dot(lib, dev(Qv), dev(q_mz), dev(q_z), 10.0, "da", 5, tc)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
