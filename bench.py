@@ -315,8 +315,8 @@ def popc_roofline(comparisons, D, avg_search_ms, n_sm, sm_mhz, peaks):
     spends 2.5 integer-pipe operations per word: the XOR, and per two words a
     majority, a three-input XOR and a shift-add of one carry count (bound: the
     measured LOP3 rate / 2.5).  Counting two carries per three-input add (2.25
-    operations per word) left the kernel's time unchanged (942 ms), so the
-    integer issue rate is a bound it does not reach, not what limits it."""
+    operations per word) left the kernel's time unchanged (942 ms with the
+    two-stage ring), so the integer issue rate is a bound it does not reach."""
     words = comparisons * (D // 32)
     achieved = words / (avg_search_ms / 1e3) / 1e12
     pp, pl = (peaks or {}).get("popc"), (peaks or {}).get("lop3")
@@ -333,6 +333,24 @@ def popc_roofline(comparisons, D, avg_search_ms, n_sm, sm_mhz, peaks):
             "peak_basis": "integer-issue bound of the carry-save kernel: " + basis,
             "popcount_unit_bound": {"peak": popc_bound, "frac": achieved / popc_bound,
                                     "basis": "one popc32 per word (the paper's form): " + basis}}
+
+
+def popc_mb_roofline(comparisons, D, bits, avg_search_ms, peaks):
+    """Roofline of the popcount form of the multi-bit dot product: per pair of
+    32-bit words, bits^2 terms popc(Q_i & R_j) (bound: the popcount unit's
+    measured rate / bits^2), each with about two integer-pipe operations, the
+    AND and the add of its count (bound: the measured LOP3 rate / (2 bits^2))."""
+    words = comparisons * (D // 32)
+    achieved = words / (avg_search_ms / 1e3) / 1e12
+    pp, pl = (peaks or {}).get("popc"), (peaks or {}).get("lop3")
+    popc_bound = pp["best_per_s"] / bits ** 2 / 1e12
+    issue_bound = pl["best_per_s"] / (2 * bits ** 2) / 1e12
+    basis = "measured (own microbenchmarks hd_measure_peak 'popc' and 'lop3')"
+    return {"kernel": "k_search_popc_mb", "bound": "alu", "unit": "Tword32/s (pairs of 32-bit words)",
+            "achieved": achieved, "peak": popc_bound, "frac": achieved / popc_bound,
+            "peak_basis": f"popcount unit / {bits ** 2} terms per word pair: " + basis,
+            "integer_issue_bound": {"peak": issue_bound, "frac": achieved / issue_bound,
+                                    "basis": f"LOP3 rate / (2 x {bits ** 2}) operations per word pair: " + basis}}
 
 
 def pctl(xs, q):
@@ -964,8 +982,12 @@ def run_multibit(args):
     lib.status()
     ms = ev0.elapsed_time(ev1) / args.steps
     avg_search_ms = search_ms / max(1, search_n)
-    pk, pclk = measure_peaks(hd, (form,))
-    roofline = tensor_roofline(form, comparisons, D, avg_search_ms, pk, pclk, sched)
+    if form == "popc":
+        pk, pclk = measure_peaks(hd, ("popc", "lop3"))
+        roofline = popc_mb_roofline(comparisons, D, bits, avg_search_ms, pk)
+    else:
+        pk, pclk = measure_peaks(hd, (form,))
+        roofline = tensor_roofline(form, comparisons, D, avg_search_ms, pk, pclk, sched)
     roofline.update({"traffic": None, "avg_launch_ms": avg_search_ms, "launches": search_n,
                      "step_share": search_ms / (ms * args.steps)})
     cpu = None
