@@ -18,6 +18,10 @@
  *    caller owns every buffer it passes; the library owns hd_ctx and
  *    hd_library objects and the scratch it allocates (stream-ordered, freed
  *    on the same stream).
+ *  - Scratch is allocated stream-ordered (cudaMallocAsync) from the device's
+ *    default memory pool; hd_ctx_create raises that pool's release threshold
+ *    to 4 GiB (never lowers it) so scratch stays mapped across the calls
+ *    that synchronise.
  *  - Calls taking a stream are asynchronous on it unless stated otherwise;
  *    results are valid once the stream has been synchronised.  A NULL stream
  *    is the legacy default stream.

@@ -304,6 +304,25 @@ const char *hd_last_error_message(void) { return g_msg.c_str(); }
 
 uint32_t hd_version(void) { return 100u; }
 
+// Scratch comes from the device's default stream-ordered pool, which by
+// default returns its memory at every synchronisation, so each call ending in
+// one (hd_search_host, a cascade level) would map its scratch again: 0.5 ms of
+// a 36.5 ms end-to-end call at 1M x 50k, D = 8192.  The pool keeps up to
+// HD_SCRATCH_RETAIN bytes mapped instead; a higher threshold the caller set
+// stays.
+constexpr uint64_t HD_SCRATCH_RETAIN = 4ull << 30;
+static void keep_scratch_mapped(int device)
+{
+    cudaMemPool_t pool;
+    uint64_t cur = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < HD_SCRATCH_RETAIN) {
+        uint64_t want = HD_SCRATCH_RETAIN;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &want);
+    }
+    cudaGetLastError();   // a pool that cannot be tuned only costs the re-mapping
+}
+
 hd_status hd_ctx_create(const hd_params *p, hd_ctx **out)
 {
     HD_CHECK(p && out, "hd_ctx_create: null argument");
@@ -329,6 +348,7 @@ hd_status hd_ctx_create(const hd_params *p, hd_ctx **out)
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return fail(hd_fail(HD_ERR_CUDA, "hd_ctx_create: no usable CUDA device"));
+    keep_scratch_mapped(c->device);
     const size_t nF = (size_t)p->n_bins * c->W, nL = (size_t)p->n_levels * c->W;
     if (cudaMalloc(&c->F, nF * 8) != cudaSuccess || cudaMalloc(&c->L, nL * 8) != cudaSuccess ||
         cudaMalloc(&c->rank_F, (size_t)p->dim * 4) != cudaSuccess ||

@@ -111,7 +111,7 @@ def test_noalloc_binding_checks_caller_outputs(hd):
 class _DefaultPool:
     """The device's default stream-ordered memory pool (where cudaMallocAsync
     takes memory), read through the CUDA driver API."""
-    USED_MEM_CURRENT, USED_MEM_HIGH = 7, 8
+    RELEASE_THRESHOLD, USED_MEM_CURRENT, USED_MEM_HIGH = 4, 7, 8
 
     def __init__(self):
         self.cu = ctypes.CDLL("libcuda.so.1")
@@ -176,3 +176,16 @@ def test_noalloc_call_allocates_nothing(hd):
     n0 = hd.hd_launch_count()
     hd.hd_search_open_noalloc(lib, q[:0], qm[:0], qz[:0], 500.0, "da", k)
     assert hd.hd_launch_count() == n0
+
+
+def test_ctx_keeps_scratch_mapped(hd):
+    """A context raises the default pool's release threshold to 4 GiB (stream-
+    ordered scratch stays mapped across synchronising calls) and never lowers
+    a higher one."""
+    pool = _DefaultPool()
+    hd.Ctx(128, 4, 10, 64, 0)
+    assert pool.get(pool.RELEASE_THRESHOLD) >= 4 << 30
+    big = ctypes.c_uint64(8 << 30)
+    assert pool.cu.cuMemPoolSetAttribute(pool.pool, pool.RELEASE_THRESHOLD, ctypes.byref(big)) == 0
+    hd.Ctx(128, 4, 10, 64, 0)
+    assert pool.get(pool.RELEASE_THRESHOLD) == 8 << 30
