@@ -337,20 +337,22 @@ def popc_roofline(comparisons, D, avg_search_ms, n_sm, sm_mhz, peaks):
 
 def popc_mb_roofline(comparisons, D, bits, avg_search_ms, peaks):
     """Roofline of the popcount form of the multi-bit dot product: per pair of
-    32-bit words, bits^2 terms popc(Q_i & R_j) (bound: the popcount unit's
-    measured rate / bits^2), each with about two integer-pipe operations, the
-    AND and the add of its count (bound: the measured LOP3 rate / (2 bits^2))."""
+    32-bit words, bits^2 plane-pair terms, each counted by the carry-save adder
+    of the binary kernel: 2.5 integer-pipe operations per word and term (the
+    AND, and per two words a majority, a three-input XOR and a shift-add;
+    bound: the measured LOP3 rate / (2.5 bits^2)) and half a popcount (bound:
+    the popcount unit's measured rate / (0.5 bits^2))."""
     words = comparisons * (D // 32)
     achieved = words / (avg_search_ms / 1e3) / 1e12
     pp, pl = (peaks or {}).get("popc"), (peaks or {}).get("lop3")
-    popc_bound = pp["best_per_s"] / bits ** 2 / 1e12
-    issue_bound = pl["best_per_s"] / (2 * bits ** 2) / 1e12
-    basis = "measured (own microbenchmarks hd_measure_peak 'popc' and 'lop3')"
+    issue_bound = pl["best_per_s"] / (OPS_PER_WORD * bits ** 2) / 1e12
+    popc_bound = pp["best_per_s"] / (0.5 * bits ** 2) / 1e12
+    basis = "measured (own microbenchmarks hd_measure_peak 'lop3' and 'popc')"
     return {"kernel": "k_search_popc_mb", "bound": "alu", "unit": "Tword32/s (pairs of 32-bit words)",
-            "achieved": achieved, "peak": popc_bound, "frac": achieved / popc_bound,
-            "peak_basis": f"popcount unit / {bits ** 2} terms per word pair: " + basis,
-            "integer_issue_bound": {"peak": issue_bound, "frac": achieved / issue_bound,
-                                    "basis": f"LOP3 rate / (2 x {bits ** 2}) operations per word pair: " + basis}}
+            "achieved": achieved, "peak": issue_bound, "frac": achieved / issue_bound,
+            "peak_basis": f"integer-issue bound: LOP3 rate / ({OPS_PER_WORD} x {bits ** 2}) per word pair: " + basis,
+            "popcount_unit_bound": {"peak": popc_bound, "frac": achieved / popc_bound,
+                                    "basis": f"popcount unit / (0.5 x {bits ** 2}) per word pair: " + basis}}
 
 
 def pctl(xs, q):

@@ -417,8 +417,8 @@ struct mb_args {
 
 // The popcount search of k_search_popc on bit planes: the same persistent
 // work list, stage ring (nst buffers, one CTA barrier per step) and 4 x 4
-// pairs per thread; per pair and 32-bit word, b^2 AND + popcount terms
-// weighted 2^(i+j).
+// pairs per thread; per pair, b^2 plane pairs whose AND words are counted by
+// the carry-save adder (one popcount per two words), weighted 2^(i+j).
 template <int K>
 __global__ void __launch_bounds__(THREADS, 1) k_search_popc_mb(mb_args a)
 {
@@ -522,28 +522,39 @@ __global__ void __launch_bounds__(THREADS, 1) k_search_popc_mb(mb_args a)
             const uint32_t cw = min(MB_CW, a.W32 - ch * MB_CW);
             const uint32_t *qs = reinterpret_cast<const uint32_t *>(smem + st * stage_b);
             const uint32_t *rs = qs + BQ * pitch;
-            for (uint32_t w = 0; w < cw; w += 4) {
+            // per plane pair, the chunk's AND words go through the carry-save
+            // adder of k_search_popc (one popcount per two words), and the
+            // pair's count enters P with weight 2^(pi + pj)
 #pragma unroll 1
-                for (uint32_t pi = 0; pi < bits; ++pi) {
-                    uint4 qv[4];
+            for (uint32_t pi = 0; pi < bits; ++pi) {
+#pragma unroll 1
+                for (uint32_t pj = 0; pj < bits; ++pj) {
+                    uint32_t ones[4][4], cnt[4][4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        qv[i] = *reinterpret_cast<const uint4 *>(qs + (qg + 16 * i) * pitch + pi * cw + w);
-#pragma unroll 1
-                    for (uint32_t pj = 0; pj < bits; ++pj) {
-                        uint4 rv[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) ones[i][j] = cnt[i][j] = 0;
+                    for (uint32_t w = 0; w < cw; w += 4) {
+                        uint4 qv[4], rv[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            qv[i] = *reinterpret_cast<const uint4 *>(qs + (qg + 16 * i) * pitch + pi * cw + w);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
                             rv[j] = *reinterpret_cast<const uint4 *>(rs + (rg + 16 * j) * pitch + pj * cw + w);
-                        const uint32_t sh = pi + pj;
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                acc[i][j] += (uint32_t)(__popc(qv[i].x & rv[j].x) + __popc(qv[i].y & rv[j].y) +
-                                                        __popc(qv[i].z & rv[j].z) + __popc(qv[i].w & rv[j].w))
-                                             << sh;
+                            for (int j = 0; j < 4; ++j) {
+                                csa2(ones[i][j], cnt[i][j], qv[i].x & rv[j].x, qv[i].y & rv[j].y);
+                                csa2(ones[i][j], cnt[i][j], qv[i].z & rv[j].z, qv[i].w & rv[j].w);
+                            }
                     }
+                    const uint32_t sh = pi + pj;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] += (cnt[i][j] + (uint32_t)__popc(ones[i][j])) << sh;
                 }
             }
             if (ch == nchunks - 1) {
