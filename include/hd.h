@@ -339,7 +339,7 @@ HD_API hd_status hd_cascade_search(const hd_library *lib, const uint64_t *d_q_hv
 /* hd_cascade_search for a multi-bit library (Section 4.3 components scored
  * by the dot product): each level searches the unidentified queries' rows
  * d_q_comp [n_q][D] int8 (16-byte aligned) with k = 1 as hd_search_dot with
- * `form` (AUTO or a tensor-core form the library holds), and the SSMs are
+ * `form` (AUTO, HD_FORM_POPC or a tensor-core form the library holds), and the SSMs are
  * ranked by their score S.  Thresholds, q-values and identification as
  * hd_cascade_search.  d_out_score [n_q] receives S (INT32_MIN without a
  * candidate).  HD_ERR_INVALID_ARG on a binary library (and
@@ -366,8 +366,8 @@ HD_API hd_status hd_plan_create(hd_ctx *ctx, const hd_library *lib, const uint32
                                 hd_plan **out);
 /* The plan for a multi-bit library (Section 4.3): multi-bit encoding
  * (hd_encode_multibit with the library's bits) into d_q_comp_work [n_q][D]
- * int8 (16-byte aligned) plus hd_search_dot_multi with `form` (AUTO or a
- * tensor-core form the library holds); d_out_score [n_q][k] receives the
+ * int8 (16-byte aligned) plus hd_search_dot_multi with `form` (AUTO,
+ * HD_FORM_POPC or a tensor-core form the library holds); d_out_score [n_q][k] receives the
  * scores.  hd_plan_create refuses a multi-bit library and this call a
  * binary one (HD_ERR_INVALID_ARG). */
 HD_API hd_status hd_plan_create_dot(hd_ctx *ctx, const hd_library *lib, const uint32_t *d_offsets,
@@ -403,10 +403,11 @@ HD_API hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, co
                                      uint32_t *n_all);
 /* The autotuner for a multi-bit library (Section 4.3): times the
  * dot-product search (hd_search_dot_multi) over the same tensor-core forms
- * and schedules on the queries' components d_q_comp [n_q][D] int8 (16-byte
- * aligned; no popc candidate) and keeps the fastest as the library's
- * HD_FORM_AUTO, which every dot-product call then takes.  HD_ERR_INVALID_ARG
- * on a binary library or one without a tensor-core copy (and
+ * and schedules, and the popcount form when hd_library_prepare built the bit
+ * planes, on the queries' components d_q_comp [n_q][D] int8 (16-byte
+ * aligned) and keeps the fastest as the library's HD_FORM_AUTO, which every
+ * dot-product call then takes.  HD_ERR_INVALID_ARG on a binary library or
+ * one with neither a tensor-core copy nor bit planes (and
  * hd_library_autotune refuses a multi-bit library). */
 HD_API hd_status hd_library_autotune_dot(hd_library *lib, const int8_t *d_q_comp, const double *d_q_mz,
                                          const uint8_t *d_q_charge, const uint8_t *d_q_class, uint32_t n_q,
