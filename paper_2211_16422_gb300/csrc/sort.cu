@@ -88,8 +88,9 @@ void hd_exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint32_t n, hd_are
 
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort of (charge, m/z): eight 8-bit passes over an
-// order-preserving image of the IEEE double, then one pass over the charge.
-// Stability keeps equal keys in input order, so ties fall to the input index.
+// order-preserving image of the IEEE double, then one pass over the charge
+// (and one over the group when given).  Stability keeps equal keys in input
+// order, so ties fall to the input index.  Small inputs take k_sort_small.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -181,6 +182,47 @@ k_scatter(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ idx
     }
 }
 
+// Up to SMALL_SORT_MAX items: one CTA sorts them in shared memory by a
+// bitonic network over the composite key (group, charge, m/z image, input
+// index) in two 64-bit words -- the same total order the stable radix passes
+// give, in one launch instead of about thirty (small query batches, served
+// requests).  np is n rounded up to a power of two; the padding keys sort last.
+constexpr uint32_t SMALL_SORT_MAX = 4096;
+constexpr int SMALL_SORT_THREADS = 1024;
+
+__global__ void __launch_bounds__(SMALL_SORT_THREADS)
+k_sort_small(const double *__restrict__ mz, const uint8_t *__restrict__ charge, const uint8_t *__restrict__ group,
+             uint32_t n, uint32_t np, uint32_t *__restrict__ perm)
+{
+    extern __shared__ ulonglong2 sk[];
+    for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
+        ulonglong2 v = make_ulonglong2(~0ull, ~0ull);
+        if (i < n) {
+            const uint64_t m = order_key(mz[i]);
+            v.x = ((uint64_t)(group ? group[i] : 0u) << 56) | ((uint64_t)charge[i] << 48) | (m >> 16);
+            v.y = ((m & 0xFFFFull) << 32) | i;
+        }
+        sk[i] = v;
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= np; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < np; i += blockDim.x) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const ulonglong2 a = sk[i], b = sk[l];
+                    const bool a_gt = a.x > b.x || (a.x == b.x && a.y > b.y);
+                    if (a_gt == ((i & k) == 0)) {   // ascending runs where bit k of i is 0
+                        sk[i] = b;
+                        sk[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) perm[i] = (uint32_t)sk[i].y;
+}
+
 }  // namespace
 
 void hd_sort_charge_mz(const double *mz, const uint8_t *charge, const uint8_t *group, uint32_t n,
@@ -201,6 +243,15 @@ void hd_sort_charge_mz(const double *mz, const uint8_t *charge, const uint8_t *g
         return;
     }
     if (n == 0) return;
+    if (n <= SMALL_SORT_MAX) {
+        uint32_t np = 1;
+        while (np < n) np <<= 1;
+        const size_t smem = (size_t)np * sizeof(ulonglong2);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SMALL_SORT_MAX * 16));
+        hd_count_launches(1), k_sort_small<<<1, SMALL_SORT_THREADS, smem, s>>>(mz, charge, group, n, np, perm);
+        return;
+    }
     hd_count_launches(1), k_make_keys<<<hd_ceil_div(n, 256), 256, 0, s>>>(mz, n, ka, ia);
     for (int pass = 0; pass < 8; ++pass) {
         hd_count_launches(1), k_hist<false><<<tiles, RS_THREADS, 0, s>>>(ka, ia, charge, n, 8 * pass, hist);

@@ -180,15 +180,17 @@ def test_encode_skips_bad_peaks(hd, D, f, Q):
 # --------------------------------------------------------------- library
 def _refs_with_ties(rng, n):
     mz = np.round(rng.uniform(400, 420, n), 1)
-    mz[:3] = [0.0, -0.0, 0.0]
+    mz[:3] = [0.0, -0.0, 0.0][:min(3, n)]
     z = rng.integers(0, 6, n).astype(np.uint8)
     hv = rng.integers(-2**63, 2**63, (n, 4), dtype=np.int64).view(np.uint64)
     return hv, mz, z
 
 
-def test_library_order_and_rows(hd):
-    rng = np.random.default_rng(3)
-    n = 20000
+@pytest.mark.parametrize("n", [1, 2, 3, 1000, 4095, 4096, 4097, 20000])
+def test_library_order_and_rows(hd, n):
+    """Sorted rows against the oracle's order, through the one-CTA sort (up to
+    4096 rows) and the radix passes (above), with equal m/z values and +-0.0."""
+    rng = np.random.default_rng(3 + n)
     hv, mz, z = _refs_with_ties(rng, n)
     ctx = hd.Ctx(256, 4, 10, 128, 0)
     lib = hd.hd_build_library(ctx, dev(hv), dev(mz), dev(z))
