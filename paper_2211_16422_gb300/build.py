@@ -42,7 +42,17 @@ def _stale(target, deps):
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Compiles what is stale (or everything with force) and links libhd.so.
+    Processes building at once (one per rank) take turns on a lock file, so
+    none reads an object another is writing."""
     os.makedirs(BUILD, exist_ok=True)
+    import fcntl
+    with open(os.path.join(BUILD, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        return _build_locked(force, verbose, extra)
+
+
+def _build_locked(force, verbose, extra) -> str:
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "hd.h"))
     exe = nvcc()
