@@ -91,8 +91,6 @@ constexpr uint32_t TMEM_COLS = 2 * TN;
 constexpr int EPI2_WARPS = HD_MMA2_EPI_WARPS;
 constexpr int EPI2_SPLIT = EPI2_WARPS / 4;
 static_assert(EPI2_WARPS % 4 == 0 && (TN / 32) % EPI2_SPLIT == 0, "epilogue split");
-constexpr int THREADS2 = 64 + 32 * EPI2_WARPS;
-constexpr uint32_t EPI2_THREADS = 32 * EPI2_WARPS;
 static_assert(TN % 32 == 0 && TN <= 256 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "tile shape");
 static_assert(STAGES * STAGE_BYTES + 1280 <= 232448, "shared memory");
 
@@ -309,7 +307,7 @@ __device__ __forceinline__ void score_group(const uint32_t (&v)[G], uint32_t c0,
         if (key < min(best[K - 1], seed)) topk_insert<K>(best, key);
     }
 }
-__device__ __forceinline__ void epi_bar2() { asm volatile("bar.sync 1, %0;" ::"r"(EPI2_THREADS) : "memory"); }
+__device__ __forceinline__ void epi_bar_n(uint32_t n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
 
 // One CTA per SM: each CTA stages its own query block and whole reference
 // tiles, and its MMAs commit to its own barriers.
@@ -717,39 +715,82 @@ __device__ __forceinline__ void mxf4_unit_scales(uint32_t tmem, uint32_t quarter
     tmem_st_wait();
 }
 
+// Query stages shared by two reference tiles (kind::mxf4).  Each stage holds
+// one K-chunk of the query block (A) and the same K-chunk of two consecutive
+// reference tiles (B0, B1); the MMA thread scores A x B0 into accumulator 0
+// and A x B1 into accumulator 1, so every query byte staged serves 480
+// reference rows instead of 240: 28% fewer bytes cross from L2 to the SM
+// and are written into shared memory per product.  The two accumulators then
+// fill and drain together, so eight epilogue warps (four per accumulator)
+// shorten the drain the tensor pipe waits for (four stages of 46 KB).  At
+// 1M x 50k, D = 8192: 34.9 -> 34.2 ms.  0 gives the one-tile stages with
+// double-buffered accumulators.
+#ifndef HD_MXF4_APAIR
+#define HD_MXF4_APAIR 1
+#endif
+#ifndef HD_MXF4_AP_STAGES
+#define HD_MXF4_AP_STAGES 4
+#endif
+
 // Per-format shape of the pair kernel: reference rows per tile (the MMA's N),
-// bytes of one stage, shared memory, and the tensor-memory column of each
-// accumulator.
+// tiles per stage, stages, bytes of one stage, shared memory, epilogue warps
+// and threads, and the tensor-memory column of each accumulator.
 template <int FMT> __host__ __device__ constexpr uint32_t pair_tn() { return FMT == FMT_MXF4 ? (uint32_t)TN_MX : (uint32_t)TN; }
-template <int FMT> __host__ __device__ constexpr uint32_t pair_stage_bytes() { return A_BYTES + (pair_tn<FMT>() / 2) * KB; }
+template <int FMT> __host__ __device__ constexpr bool pair_ap() { return FMT == FMT_MXF4 && HD_MXF4_APAIR != 0; }
+template <int FMT> __host__ __device__ constexpr uint32_t pair_nt() { return pair_ap<FMT>() ? 2u : 1u; }
+template <int FMT> __host__ __device__ constexpr uint32_t pair_stages()
+{
+    return pair_ap<FMT>() ? (uint32_t)HD_MXF4_AP_STAGES : (uint32_t)STAGES2;
+}
+template <int FMT> __host__ __device__ constexpr uint32_t pair_b_bytes() { return (pair_tn<FMT>() / 2) * KB; }
+template <int FMT> __host__ __device__ constexpr uint32_t pair_stage_bytes()
+{
+    return A_BYTES + pair_nt<FMT>() * pair_b_bytes<FMT>();
+}
 template <int FMT> __host__ __device__ constexpr uint32_t pair_smem_bytes()
 {
-    return STAGES2 * pair_stage_bytes<FMT>() + PAD2_BYTES + 1024 + 256;
+    return pair_stages<FMT>() * pair_stage_bytes<FMT>() + PAD2_BYTES + 1024 + 256;
 }
+template <int FMT> __host__ __device__ constexpr uint32_t pair_epi_warps() { return pair_ap<FMT>() ? 8u : (uint32_t)EPI2_WARPS; }
+template <int FMT> __host__ __device__ constexpr uint32_t pair_threads() { return 64u + 32u * pair_epi_warps<FMT>(); }
 template <int FMT> __device__ __forceinline__ uint32_t pair_acc_col(uint32_t buf)
 {
     return FMT == FMT_MXF4 ? (buf ? MX_BUF1_COL : 0u) : buf * TN;
 }
 static_assert(pair_smem_bytes<FMT_MXF4>() <= 232448 && (EPI2_SPLIT == 1 || TN_MX % (32 * EPI2_SPLIT) == 0),
               "mxf4 pair shape");
+static_assert(pair_b_bytes<FMT_MXF4>() % 1024 == 0 && pair_stage_bytes<FMT_MXF4>() % 1024 == 0,
+              "128B-swizzled operands start on 1024-byte boundaries");
+static_assert(2 * pair_stages<FMT_MXF4>() + 5 <= 32, "barriers fit in their 256 bytes");
 
 // A cluster of two CTAs on an SM pair (cluster ranks 0 and 1; rank 0 issues
 // the pair's MMAs).  Each CTA holds its own block of 128 queries (A) and its
-// half of the pair's reference tile (B); all loads complete on rank 0's stage
-// barrier.
+// half of the pair's reference tile (B; of two tiles when a query stage serves
+// two); all loads complete on rank 0's stage barrier.
 template <int K, int FMT>
-__global__ void __launch_bounds__(THREADS2, 1)
+__global__ void __launch_bounds__(pair_threads<FMT>(), 1)
 k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
     constexpr uint32_t CS = 2;
+    constexpr bool AP = pair_ap<FMT>();                     // two reference tiles per query stage
+    constexpr uint32_t NT = pair_nt<FMT>();
+    constexpr uint32_t NST = pair_stages<FMT>();
     constexpr uint32_t TNF = pair_tn<FMT>();                // reference rows per tile
-    constexpr uint32_t STAGE2F = pair_stage_bytes<FMT>();   // A block slice + this CTA's half of the tile
-    constexpr uint32_t EPI2_COLS_F = TNF / EPI2_SPLIT;      // accumulator columns per epilogue warp
+    constexpr uint32_t BHF = pair_b_bytes<FMT>();           // this CTA's half of one tile, one K-chunk
+    constexpr uint32_t STAGE2F = pair_stage_bytes<FMT>();   // A block slice + this CTA's half of NT tiles
+    constexpr uint32_t EPT = 32u * pair_epi_warps<FMT>();   // epilogue threads per CTA
+    // the epilogue warps form SPLITF groups of four (one warp per lane quarter):
+    // with shared query stages group g drains accumulator g, otherwise group g
+    // scores columns [g, g + 1) * TNF / SPLITF of the accumulator of the tile
+    constexpr uint32_t SPLITF = AP ? 2u : (uint32_t)EPI2_SPLIT;
+    constexpr uint32_t EPI2_COLS_F = AP ? TNF : TNF / SPLITF;   // accumulator columns per epilogue warp
+    // arrivals that free one accumulator: its epilogue threads in both CTAs
+    constexpr uint32_t ACC_RELEASE = 2u * (AP ? EPT / 2u : EPT);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES2 * STAGE2F + PAD2_BYTES);
-    uint64_t *empty = full + STAGES2;
-    uint64_t *acc_full = empty + STAGES2;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NST * STAGE2F + PAD2_BYTES);
+    uint64_t *empty = full + NST;
+    uint64_t *acc_full = empty + NST;
     uint64_t *acc_empty = acc_full + 2;
     uint64_t *drain = acc_empty + 2;
     __shared__ uint32_t s_tmem;
@@ -758,13 +799,13 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t crank = cluster_rank();   // 0: issues the pair's MMAs
     if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES2; ++i) {
+        for (uint32_t i = 0; i < NST; ++i) {
             mbar_init(&full[i], 1);    // rank 0's producer arms it for both CTAs' bytes
             mbar_init(&empty[i], 1);   // one commit arrive (sent to both CTAs) per use
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 2 * EPI2_THREADS);   // every epilogue thread of both CTAs
+            mbar_init(&acc_empty[i], ACC_RELEASE);
         }
         mbar_init(drain, 1);
         s_abort = 0;
@@ -790,7 +831,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
         hd_flag(a.status, HD_DEV_TMEM);
     }
     if (FMT == FMT_MXF4) {   // unit scale factors in both CTAs before the first MMA
-        if (warp >= 2) mxf4_unit_scales(tmem, (uint32_t)warp & 3u);
+        if (warp >= 2 && warp < 6) mxf4_unit_scales(tmem, (uint32_t)warp & 3u);
         tc_fence_before();
         __syncthreads();
         cluster_sync();
@@ -811,20 +852,23 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 uint32_t b, t0, t1;
                 item_range(a, item, b, t0, t1);
                 const int32_t ya = (int32_t)((b * CS + crank) * TM);
-                for (uint32_t t = t0; t < t1 && !*abort_flag; ++t) {
-                    const int32_t rb = (int32_t)(t * TNF + crank * (TNF / 2));
+                for (uint32_t t = t0; t < t1 && !*abort_flag; t += NT) {
+                    const uint32_t nt = min(NT, t1 - t);   // tiles this stage run carries
                     for (uint32_t c = 0; c < nchunks; ++c, ++it) {
-                        const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
+                        const uint32_t s = it % NST, ph = (it / NST) & 1u;
                         if (!mbar_wait(&empty[s], ph ^ 1u, a.wait_ns)) { give_up(); break; }
-                        if (crank == 0) mbar_expect_tx(&full[s], tx_bytes(FMT, 2 * STAGE2F));
+                        if (crank == 0) mbar_expect_tx(&full[s], tx_bytes(FMT, 2 * (A_BYTES + nt * BHF)));
                         if (a.stall && it == 0) continue;   // nothing ever completes this stage
                         uint8_t *sa = smem + s * STAGE2F, *sb = sa + A_BYTES;
                         const uint32_t bar = full0 + s * 8u;
                         const int32_t x = (int32_t)(c * KB);
                         if (HD_MMA2_HINT_A) tma_load_2d_pair_hint(sa, &qmap, x, ya, bar, pol_a);
                         else tma_load_2d_pair(sa, &qmap, x, ya, bar);
-                        if (HD_MMA2_HINT_B) tma_load_2d_pair_hint(sb, &lmap, x, rb, bar, pol_b);
-                        else tma_load_2d_pair(sb, &lmap, x, rb, bar);
+                        for (uint32_t u = 0; u < nt; ++u) {
+                            const int32_t rb = (int32_t)((t + u) * TNF + crank * (TNF / 2));
+                            if (HD_MMA2_HINT_B) tma_load_2d_pair_hint(sb + u * BHF, &lmap, x, rb, bar, pol_b);
+                            else tma_load_2d_pair(sb + u * BHF, &lmap, x, rb, bar);
+                        }
                     }
                 }
             }
@@ -838,15 +882,20 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 for (uint32_t item = cid; item < total && !*abort_flag; item += ncl) {
                     uint32_t b, t0, t1;
                     item_range(a, item, b, t0, t1);
-                    for (uint32_t t = t0; t < t1 && !*abort_flag; ++t, ++acc_it) {
-                        const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
-                        const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
+                    for (uint32_t t = t0; t < t1 && !*abort_flag; t += NT, ++acc_it) {
+                        const uint32_t nt = min(NT, t1 - t);
+                        // one tile per stage: the tiles alternate between the two
+                        // accumulators; two tiles per stage: both are in use, once
+                        // per stage run
+                        const uint32_t buf = (!AP && BUFS2 == 2) ? (acc_it & 1u) : 0u;
+                        const uint32_t aph = ((!AP && BUFS2 == 2) ? (acc_it >> 1) : acc_it) & 1u;
                         if (!mbar_wait(&acc_empty[buf], aph ^ 1u, a.wait_ns)) { give_up(); break; }
+                        if (AP && !mbar_wait(&acc_empty[1], aph ^ 1u, a.wait_ns)) { give_up(); break; }
                         tc_fence_after();
                         const uint32_t d_tmem = tmem + pair_acc_col<FMT>(buf);
                         bool ok = true;
                         for (uint32_t c = 0; c < nchunks; ++c, ++it) {
-                            const uint32_t s = it % STAGES2, ph = (it / STAGES2) & 1u;
+                            const uint32_t s = it % NST, ph = (it / NST) & 1u;
                             if (!mbar_wait(&full[s], ph, a.wait_ns)) { give_up(); ok = false; break; }
                             tc_fence_after();
                             const uint32_t sa = smem_addr(smem + s * STAGE2F), sb = sa + A_BYTES;
@@ -859,10 +908,18 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                                 else
                                     mma_issue2<FMT>(d_tmem, da + 2 * j, db + 2 * j, idesc, (c | j) != 0);
                             }
+                            if (AP && nt > 1) {   // the second tile of the stage into accumulator 1
+                                const uint64_t db1 = sw128_desc(sb + BHF);
+#pragma unroll
+                                for (uint32_t j = 0; j < KB / 32; ++j)
+                                    mma_issue2_mxf4(tmem + pair_acc_col<FMT>(1), da + 2 * j, db1 + 2 * j, idesc,
+                                                    tmem + MX_SF_COL, tmem + MX_SF_COL, (c | j) != 0);
+                            }
                             mma_commit2_mc(&empty[s], 0x3);
                         }
                         if (!ok) break;
                         mma_commit2_mc(&acc_full[buf], 0x3);
+                        if (AP) mma_commit2_mc(&acc_full[1], 0x3);
                     }
                 }
                 // every issued MMA has finished before either CTA releases its memory
@@ -874,7 +931,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
     } else {
         // ------------------------------------------------------- epilogue
         const uint32_t quarter = warp & 3;              // TMEM lanes this warp may read
-        const uint32_t slice = (uint32_t)(warp - 2) >> 2;  // which EPI2_COLS of the TN columns
+        const uint32_t slice = (uint32_t)(warp - 2) >> 2;  // its group of four warps
         const uint32_t row = quarter * 32 + lane;       // query row within the block
         const uint32_t lane_addr = (quarter * 32) << 16;
         const bool leader = threadIdx.x == 64;
@@ -895,32 +952,37 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
 #pragma unroll
             for (int i = 0; i < K; ++i) best[i] = KEY_NONE;
             bool ok = true;
-            for (uint32_t t = t0; t < t1; ++t, ++acc_it) {
-                const uint32_t buf = BUFS2 == 2 ? (acc_it & 1u) : 0u;
-                const uint32_t aph = (BUFS2 == 2 ? (acc_it >> 1) : acc_it) & 1u;
-                const uint32_t r0 = t * TNF;
+            for (uint32_t t = t0; t < t1; t += NT, ++acc_it) {
+                // this warp's accumulator and its tile
+                const uint32_t buf = AP ? slice : ((BUFS2 == 2) ? (acc_it & 1u) : 0u);
+                const uint32_t aph = ((!AP && BUFS2 == 2) ? (acc_it >> 1) : acc_it) & 1u;
+                const uint32_t tt = AP ? t + slice : t;
+                const uint32_t r0 = tt * TNF;
                 if (!mbar_wait(&acc_full[buf], aph, a.wait_ns)) { give_up(); ok = false; break; }
                 tc_fence_after();
+                if (tt < t1) {
+                    const uint32_t cg0 = AP ? 0u : slice * (EPI2_COLS_F / 32);
 #pragma unroll 1
-                for (uint32_t cg = slice * (EPI2_COLS_F / 32); cg < (slice + 1) * (EPI2_COLS_F / 32); ++cg) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + lane_addr + pair_acc_col<FMT>(buf) + cg * 32, v);
-                    tmem_ld_wait();
-                    score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
-                }
-                if (TNF % 32 != 0) {   // the last 16 columns of a 240-column tile (one epilogue warp per quarter)
-                    constexpr uint32_t c16 = TNF / 32 * 32;
-                    uint32_t v[16];
-                    tmem_ld16(tmem + lane_addr + pair_acc_col<FMT>(buf) + c16, v);
-                    tmem_ld_wait();
-                    score_group<K, 16>(v, r0 + c16, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
+                    for (uint32_t cg = cg0; cg < cg0 + EPI2_COLS_F / 32; ++cg) {
+                        uint32_t v[32];
+                        tmem_ld32(tmem + lane_addr + pair_acc_col<FMT>(buf) + cg * 32, v);
+                        tmem_ld_wait();
+                        score_group<K>(v, r0 + cg * 32, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
+                    }
+                    if (TNF % 32 != 0) {   // the last 16 columns of a 240-column tile
+                        constexpr uint32_t c16 = TNF / 32 * 32;
+                        uint32_t v[16];
+                        tmem_ld16(tmem + lane_addr + pair_acc_col<FMT>(buf) + c16, v);
+                        tmem_ld_wait();
+                        score_group<K, 16>(v, r0 + c16, lo, span, a.bias, a.shift, a.lib_orig, seed, best);
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive_remote(acc_empty0 + buf * 8u);
             }
             // merge into the block's running top-k under its lock (bounded spin),
-            // the EPI2_SPLIT partial lists of each row one after the other
-            epi_bar2();
+            // the SPLITF partial lists of each row one after the other
+            epi_bar_n(EPT);
             if (leader) {
                 int got = 0;
                 if (ok && !*abort_flag) {
@@ -933,9 +995,9 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                 }
                 s_lock_ok = got;
             }
-            epi_bar2();
+            epi_bar_n(EPT);
             const bool locked = s_lock_ok != 0;
-            for (uint32_t ph = 0; ph < (uint32_t)EPI2_SPLIT; ++ph) {
+            for (uint32_t ph = 0; ph < SPLITF; ++ph) {
                 if (locked && slice == ph) {
                     if (sq < a.n_q) {
                         unsigned long long *g = reinterpret_cast<unsigned long long *>(a.top + (size_t)sq * K);
@@ -948,7 +1010,7 @@ k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ 
                     }
                     __threadfence();
                 }
-                epi_bar2();
+                epi_bar_n(EPT);
             }
             if (leader && locked) atomicExch(&a.locks[sb_], 0u);
             if (!locked) break;
@@ -1428,7 +1490,7 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
     }();
     const uint32_t tn = pair ? pair_tn<FMT>() : (uint32_t)TN;   // reference rows per tile
     const uint32_t smem_bytes = pair ? pair_smem_bytes<FMT>() : SMEM_BYTES;
-    const uint32_t threads = pair ? (uint32_t)THREADS2 : (uint32_t)THREADS;
+    const uint32_t threads = pair ? pair_threads<FMT>() : (uint32_t)THREADS;
     HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
     if (cs > 1) HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     uint32_t grid = (uint32_t)lib->num_sms / cs * cs;
