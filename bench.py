@@ -46,17 +46,59 @@ L2_BYTES = 129 * 2**20
 KERNEL_SOURCES = ("paper_2211_16422_gb300/csrc/search_mma.cu", "paper_2211_16422_gb300/csrc/search_common.cuh")
 POPC_SOURCES = ("paper_2211_16422_gb300/csrc/search_popc.cu", "paper_2211_16422_gb300/csrc/search_common.cuh")
 TRAFFIC = {
+    # key: (kernel, form, tile_group, super_group, cluster, cta_group, tiles_per_stage)
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
-    #     --popc-steps 0 --no-peaks --form <form> --schedule <tile_group,super_group,cluster,cta_group>
-    ("k_search_mma2", "tc_mxf4", 16, 2, 2, 2): {"bytes": 175.169e9 + 0.13250e9, "sha256": "fd03760f22912b03"},
-    ("k_search_mma2", "tc_mxf4", 32, 2, 2, 2): {"bytes": 183.691e9 + 0.08475e9, "sha256": "fd03760f22912b03"},
-    ("k_search_mma2", "tc_mxf4", 16, 16, 2, 2): {"bytes": 219.509e9 + 0.02162e9, "sha256": "fd03760f22912b03"},
+    #     --popc-steps 0 --no-peaks --form <form> --schedule <tile_group,super_group,cluster,cta_group,tiles>
+    ("k_search_mma2", "tc_mxf4", 16, 2, 2, 2, 2): {"bytes": 186.900e9 + 0.09986e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 16, 2, 2, 2, 1): {"bytes": 176.523e9 + 0.11182e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 32, 2, 2, 2, 2): {"bytes": 183.868e9 + 0.06897e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 32, 2, 2, 2, 1): {"bytes": 181.403e9 + 0.07096e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 16, 16, 2, 2, 2): {"bytes": 218.315e9 + 0.02146e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 16, 16, 2, 2, 1): {"bytes": 221.438e9 + 0.02168e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 2, 2, 2, 2): {"bytes": 162.048e9 + 0.18906e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 2, 2, 2, 1): {"bytes": 142.911e9 + 0.27436e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 16, 2, 2, 2): {"bytes": 195.379e9 + 0.06076e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 16, 2, 2, 1): {"bytes": 193.309e9 + 0.06281e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 32, 16, 2, 2, 2): {"bytes": 224.915e9 + 0.01352e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 32, 16, 2, 2, 1): {"bytes": 227.719e9 + 0.01352e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
 }
 
 # The arithmetic type the search computes in: the tensor-core operand format
 # (products accumulated in fp32, exact), or 32-bit words for XOR + popcount.
 DTYPE_OF_FORM = {"tc_mxf4": "e2m1", "tc_fp4": "e2m1", "tc_fp8": "e4m3", "tc_bf16": "bf16", "popc": "u32"}
+
+
+# Schedule of the tensor-core forms: work-item shape, SM pairing, and the
+# kind::mxf4 form's reference tiles per query stage; the library's default.
+SCHEDULE_KEYS = ("tile_group", "super_group", "cluster", "cta_group", "tiles_per_stage")
+DEFAULT_SCHEDULE = {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2, "tiles_per_stage": 1}
+
+
+def parse_schedule(text):
+    """'tile_group,super_group,cluster,cta_group[,tiles_per_stage]' -> dict (tiles_per_stage 1 if absent)."""
+    v = [int(x) for x in text.split(",")]
+    if len(v) not in (4, 5):
+        raise SystemExit("--schedule takes 4 or 5 comma-separated integers")
+    return dict(zip(SCHEDULE_KEYS, v + [1] * (5 - len(v))))
+
+
+def apply_schedule(hd, lib, sched):
+    hd.hd_library_set_schedule(lib, sched["tile_group"], sched["super_group"], sched["cluster"], sched["cta_group"])
+    hd.hd_library_set_stage_tiles(lib, sched.get("tiles_per_stage", 1))
+    return sched
 
 
 def kernel_source_hash(sources=KERNEL_SOURCES):
@@ -82,8 +124,8 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--form", default="auto")
     ap.add_argument("--schedule", default=None,
-                    help="tile_group,super_group,cluster,cta_group of the tensor-core form (with --form; "
-                         "default: the library's 16,16,2,2)")
+                    help="tile_group,super_group,cluster,cta_group[,tiles_per_stage] of the tensor-core "
+                         "form (with --form; default: the library's 16,16,2,2,1)")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (testing only)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -280,7 +322,7 @@ def tensor_roofline(form, comparisons, D, avg_search_ms, peaks, peak_clocks, sch
     pair = sched.get("cta_group") == 2
     kname = "k_search_mma2" if pair else "k_search_mma"
     r = {"kernel": kname, "bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
-         "schedule": {k_: sched.get(k_) for k_ in ("tile_group", "super_group", "cluster", "cta_group")},
+         "schedule": {k_: sched.get(k_) for k_ in SCHEDULE_KEYS},
          "derived_peak": {"peak": derived, "frac": achieved / derived,
                           "basis": "MEASURED_PEAKS burst cuBLAS bf16" + (
                               " x 2 (nominal fp8/bf16 ratio 4.5/2.25)" if eight_bit_kind else
@@ -400,9 +442,7 @@ def run_ours(args, rank, world, local_rank):
         hd.hd_library_prepare(lib, f)
         setup["prepare_" + f + "_s"] = time.perf_counter() - t
     if args.schedule:
-        tg_, sg_, cs_, cg_ = (int(x) for x in args.schedule.split(","))
-        hd.hd_library_set_schedule(lib, tg_, sg_, cs_, cg_)
-        setup["schedule"] = {"tile_group": tg_, "super_group": sg_, "cluster": cs_, "cta_group": cg_}
+        setup["schedule"] = apply_schedule(hd, lib, parse_schedule(args.schedule))
     q_mz, q_z = dev(queries.precursor_mz), dev(queries.charge)
     if args.form == "auto":
         # the library's autotuner picks form and schedule on a second, separately seeded batch
@@ -540,8 +580,7 @@ def run_ours(args, rank, world, local_rank):
     sm_mhz = (cs or {}).get("sm_mhz") or 1455.0
     avg_search_ms = search_ms / max(1, search_n)
     if form.startswith("tc_"):
-        sched = (setup.get("autotune_choice") or setup.get("schedule")
-                 or {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2})
+        sched = setup.get("autotune_choice") or setup.get("schedule") or dict(DEFAULT_SCHEDULE)
         roofline = tensor_roofline(form, comparisons, D, avg_search_ms, peaks, peak_clocks, sched)
     else:
         roofline = popc_roofline(comparisons, D, avg_search_ms, n_sm, sm_mhz, peaks)
@@ -554,8 +593,7 @@ def run_ours(args, rank, world, local_rank):
     traffic = None
     if form.startswith("tc_") and args.scale == 1.0:
         s_ = roofline["schedule"]
-        t_ = TRAFFIC.get((roofline["kernel"], form, s_["tile_group"], s_["super_group"], s_["cluster"],
-                          s_["cta_group"]))
+        t_ = TRAFFIC.get((roofline["kernel"], form) + tuple(s_.get(k_) or 1 for k_ in SCHEDULE_KEYS))
         if t_ and t_["sha256"] == kernel_source_hash():
             traffic = t_["bytes"]
     roofline.update({"traffic": traffic, "traffic_unit": "bytes per launch", "avg_launch_ms": avg_search_ms,
@@ -940,16 +978,12 @@ def run_multibit(args):
         tuned, _ = hd.hd_library_autotune(lib, tq_comp, dev(tq.precursor_mz), dev(tq.charge), None, [(tol, unit)], k)
         del tq_comp
         form = tuned["form"]
-        sched = {key: tuned[key] for key in ("tile_group", "super_group", "cluster", "cta_group")}
+        sched = {key: tuned[key] for key in SCHEDULE_KEYS}
     else:
         form = args.form if args.form != "auto" else ("tc_mxf4" if bits <= 3 else "tc_fp8")
         hd.hd_library_prepare(lib, form)
-        sched = {"tile_group": 16, "super_group": 16, "cluster": 2, "cta_group": 2}
-        if args.schedule:
-            tg_, sg_, cs_, cg_ = (int(x) for x in args.schedule.split(","))
-            sched = {"tile_group": tg_, "super_group": sg_, "cluster": cs_, "cta_group": cg_}
-    hd.hd_library_set_schedule(lib, sched["tile_group"], sched["super_group"], sched["cluster"],
-                               sched["cta_group"])
+        sched = parse_schedule(args.schedule) if args.schedule else dict(DEFAULT_SCHEDULE)
+    apply_schedule(hd, lib, sched)
     q_mz, q_z = dev(queries.precursor_mz), dev(queries.charge)
     lo, hi = hd.hd_query_windows(lib, q_mz, q_z, tol, unit)
     comparisons = int((hd.as_u32(hi).astype(np.int64) - hd.as_u32(lo).astype(np.int64)).sum())

@@ -259,6 +259,17 @@ HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
  * flight. */
 HD_API hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t super_group,
                                          uint32_t cluster, uint32_t cta_group);
+/* Schedule of the kind::mxf4 form (no counterpart in the paper): reference
+ * tiles per query stage.  2: each query chunk staged in shared memory is
+ * scored against two consecutive reference tiles at once, into both
+ * tensor-memory accumulators, so a quarter fewer operand bytes leave L2 per
+ * product, but the accumulators drain together and the reference tiles'
+ * L2 hit rate falls (faster for large query sets, slower for small ones);
+ * 0 or 1: one tile per stage with double-buffered accumulators (the
+ * default).  The other forms always stage one tile.  hd_library_autotune
+ * tries both.  HD_ERR_INVALID_ARG above 2.  Results do not depend on it.
+ * Not to be changed while a search on this library is in flight. */
+HD_API hd_status hd_library_set_stage_tiles(hd_library *lib, uint32_t tiles_per_stage);
 
 /* Candidate windows (Section 3.4, Table 1): for each query, rows [lo, hi) of
  * the sorted library whose charge equals the query's and whose precursor
@@ -385,7 +396,8 @@ HD_API void hd_plan_destroy(hd_plan *plan);
  * is prepared for (HD_FORM_TC_MXF4 too when the e2m1 copy exists and D is a
  * multiple of 256) and, for the tensor-core forms, work-item shapes
  * tile_group x super_group x (cluster, cta_group) in {4, 16, 32} x {2, 16} x
- * {(1, 1), (2, 2)} ((2, 2) only for kind::mxf4), on the
+ * {(1, 1), (2, 2)} ((2, 2) only for kind::mxf4, with one and with two
+ * reference tiles per query stage, hd_library_set_stage_tiles), on the
  * given queries (the real query set, or one of the same density per window:
  * a subset's sorted blocks span wider m/z ranges and can favour another
  * schedule), and keeps the fastest as the library's
@@ -394,6 +406,7 @@ HD_API void hd_plan_destroy(hd_plan *plan);
 typedef struct {
     hd_search_form form;
     uint32_t tile_group, super_group, cluster, cta_group;
+    uint32_t tiles_per_stage;   /* see hd_library_set_stage_tiles; 1 for the other forms, 0 for popc */
     double ms;
 } hd_tune_result;
 HD_API hd_status hd_library_autotune(hd_library *lib, const uint64_t *d_q_hv, const double *d_q_mz,

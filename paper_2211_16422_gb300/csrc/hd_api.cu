@@ -811,6 +811,14 @@ hd_status hd_library_set_schedule(hd_library *lib, uint32_t tile_group, uint32_t
     return HD_OK;
 }
 
+hd_status hd_library_set_stage_tiles(hd_library *lib, uint32_t tiles_per_stage)
+{
+    HD_CHECK(lib, "hd_library_set_stage_tiles: null library");
+    HD_CHECK(tiles_per_stage <= 2, "hd_library_set_stage_tiles: tiles_per_stage must be 0, 1 or 2");
+    lib->mma_tuning.tiles_per_stage = tiles_per_stage;
+    return HD_OK;
+}
+
 hd_status hd_query_windows(const hd_library *lib, const double *d_q_mz, const uint8_t *d_q_charge,
                            uint32_t n_q, double tol, hd_tol_unit unit, uint32_t *d_lo, uint32_t *d_hi,
                            hd_stream stream)

@@ -61,6 +61,7 @@ struct hd_mma_tuning {
     uint32_t super_group = 0;
     uint32_t cluster = 0;    // CTAs per cluster: 2 for the SM pair, 1 for one SM
     uint32_t cta_group = 0;  // 2: SM pairs issue M = 256 MMAs (cluster of 2); 0/1: one SM per MMA
+    uint32_t tiles_per_stage = 0;   // kind::mxf4 on SM pairs: reference tiles per query stage (0/1 or 2)
 };
 
 struct hd_library {

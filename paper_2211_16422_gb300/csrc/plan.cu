@@ -91,19 +91,23 @@ hd_status tune_checks(const hd_library *lib, const void *d_q, const double *d_q_
 
 // Candidates: popc (binary rows only), then for every prepared tensor-core
 // form (tile_group, super_group) in {4, 16, 32} x {2, 16} on one SM and on SM
-// pairs (kind::mxf4 on pairs only, and only when D is a multiple of 256).
+// pairs (kind::mxf4 on pairs only, and only when D is a multiple of 256, with
+// one or two reference tiles per query stage).
 std::vector<hd_tune_result> tc_candidates(const hd_library *lib, bool with_popc)
 {
     std::vector<hd_tune_result> cand;
-    if (with_popc) cand.push_back({HD_FORM_POPC, 0, 0, 0, 0, 0.0});
+    if (with_popc) cand.push_back({HD_FORM_POPC, 0, 0, 0, 0, 0, 0.0});
     const uint32_t tgs[3] = {4, 16, 32}, sgs[2] = {2, 16};
     const uint32_t shapes[2][2] = {{1, 1}, {2, 2}};   // (cluster, cta_group): one SM, or the SM pair
     for (hd_search_form f : {HD_FORM_TC_MXF4, HD_FORM_TC_FP4, HD_FORM_TC_FP8, HD_FORM_TC_BF16}) {
         if (!hd_tc_copy(lib, f) || (f == HD_FORM_TC_MXF4 && lib->dim % 256 != 0)) continue;
         for (uint32_t tg : tgs)
             for (uint32_t sg : sgs)
-                for (const auto &sh : shapes)
-                    if (f != HD_FORM_TC_MXF4 || sh[1] == 2) cand.push_back({f, tg, sg, sh[0], sh[1], 0.0});
+                for (const auto &sh : shapes) {
+                    if (f != HD_FORM_TC_MXF4) cand.push_back({f, tg, sg, sh[0], sh[1], 1, 0.0});
+                    else if (sh[1] == 2)
+                        for (uint32_t tps : {1u, 2u}) cand.push_back({f, tg, sg, sh[0], sh[1], tps, 0.0});
+                }
     }
     return cand;
 }
@@ -134,6 +138,7 @@ hd_status tune(hd_library *lib, std::vector<hd_tune_result> cand, uint32_t n_q, 
         lib->mma_tuning.super_group = c.super_group;
         lib->mma_tuning.cluster = c.cluster;
         lib->mma_tuning.cta_group = c.cta_group;
+        lib->mma_tuning.tiles_per_stage = c.tiles_per_stage;
         double bestms = 1e30;
         for (int rep = 0; rep < 3 && st == HD_OK; ++rep) {   // first run warms up
             cudaEventRecord(e0, ss.s);
@@ -161,6 +166,7 @@ hd_status tune(hd_library *lib, std::vector<hd_tune_result> cand, uint32_t n_q, 
     lib->mma_tuning.super_group = it->super_group;
     lib->mma_tuning.cluster = it->cluster;
     lib->mma_tuning.cta_group = it->cta_group;
+    lib->mma_tuning.tiles_per_stage = it->tiles_per_stage;
     lib->auto_form = it->form;
     if (best) *best = *it;
     if (n_all) *n_all = (uint32_t)cand.size();

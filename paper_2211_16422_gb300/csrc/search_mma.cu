@@ -715,70 +715,70 @@ __device__ __forceinline__ void mxf4_unit_scales(uint32_t tmem, uint32_t quarter
     tmem_st_wait();
 }
 
-// Query stages shared by two reference tiles (kind::mxf4).  Each stage holds
-// one K-chunk of the query block (A) and the same K-chunk of two consecutive
-// reference tiles (B0, B1); the MMA thread scores A x B0 into accumulator 0
-// and A x B1 into accumulator 1, so every query byte staged serves 480
-// reference rows instead of 240: 28% fewer bytes cross from L2 to the SM
-// and are written into shared memory per product.  The two accumulators then
-// fill and drain together, so eight epilogue warps (four per accumulator)
-// shorten the drain the tensor pipe waits for (four stages of 46 KB).  At
-// 1M x 50k, D = 8192: 34.9 -> 34.2 ms.  0 gives the one-tile stages with
-// double-buffered accumulators.
-#ifndef HD_MXF4_APAIR
-#define HD_MXF4_APAIR 1
-#endif
+// Query stages shared by two reference tiles (kind::mxf4, a schedule
+// choice: hd_mma_tuning::tiles_per_stage = 2).  Each stage holds one K-chunk
+// of the query block (A) and the same K-chunk of two consecutive reference
+// tiles (B0, B1); the MMA thread scores A x B0 into accumulator 0 and A x B1
+// into accumulator 1, so every query byte staged serves 480 reference rows
+// instead of 240: 28% fewer bytes cross from L2 to the SM and are written
+// into shared memory per product.  The two accumulators then fill and drain
+// together, so eight epilogue warps (four per accumulator) shorten the drain
+// the tensor pipe waits for (four stages of 46 KB).  At 1M x 50k, D = 8192:
+// 34.9 -> 34.2 ms; with 10k queries (40 query blocks) 12% slower, as the
+// reference tiles' L2 hit rate falls: the autotuner decides.
 #ifndef HD_MXF4_AP_STAGES
 #define HD_MXF4_AP_STAGES 4
 #endif
 
-// Per-format shape of the pair kernel: reference rows per tile (the MMA's N),
-// tiles per stage, stages, bytes of one stage, shared memory, epilogue warps
-// and threads, and the tensor-memory column of each accumulator.
+// Per-format shape of the pair kernel (AP: two reference tiles per query
+// stage): reference rows per tile (the MMA's N), tiles per stage, stages,
+// bytes of one stage, shared memory, epilogue warps and threads, and the
+// tensor-memory column of each accumulator.
 template <int FMT> __host__ __device__ constexpr uint32_t pair_tn() { return FMT == FMT_MXF4 ? (uint32_t)TN_MX : (uint32_t)TN; }
-template <int FMT> __host__ __device__ constexpr bool pair_ap() { return FMT == FMT_MXF4 && HD_MXF4_APAIR != 0; }
-template <int FMT> __host__ __device__ constexpr uint32_t pair_nt() { return pair_ap<FMT>() ? 2u : 1u; }
-template <int FMT> __host__ __device__ constexpr uint32_t pair_stages()
+template <bool AP> __host__ __device__ constexpr uint32_t pair_nt() { return AP ? 2u : 1u; }
+template <bool AP> __host__ __device__ constexpr uint32_t pair_stages()
 {
-    return pair_ap<FMT>() ? (uint32_t)HD_MXF4_AP_STAGES : (uint32_t)STAGES2;
+    return AP ? (uint32_t)HD_MXF4_AP_STAGES : (uint32_t)STAGES2;
 }
 template <int FMT> __host__ __device__ constexpr uint32_t pair_b_bytes() { return (pair_tn<FMT>() / 2) * KB; }
-template <int FMT> __host__ __device__ constexpr uint32_t pair_stage_bytes()
+template <int FMT, bool AP> __host__ __device__ constexpr uint32_t pair_stage_bytes()
 {
-    return A_BYTES + pair_nt<FMT>() * pair_b_bytes<FMT>();
+    return A_BYTES + pair_nt<AP>() * pair_b_bytes<FMT>();
 }
-template <int FMT> __host__ __device__ constexpr uint32_t pair_smem_bytes()
+template <int FMT, bool AP> __host__ __device__ constexpr uint32_t pair_smem_bytes()
 {
-    return pair_stages<FMT>() * pair_stage_bytes<FMT>() + PAD2_BYTES + 1024 + 256;
+    return pair_stages<AP>() * pair_stage_bytes<FMT, AP>() + PAD2_BYTES + 1024 + 256;
 }
-template <int FMT> __host__ __device__ constexpr uint32_t pair_epi_warps() { return pair_ap<FMT>() ? 8u : (uint32_t)EPI2_WARPS; }
-template <int FMT> __host__ __device__ constexpr uint32_t pair_threads() { return 64u + 32u * pair_epi_warps<FMT>(); }
+template <bool AP> __host__ __device__ constexpr uint32_t pair_epi_warps() { return AP ? 8u : (uint32_t)EPI2_WARPS; }
+template <bool AP> __host__ __device__ constexpr uint32_t pair_threads() { return 64u + 32u * pair_epi_warps<AP>(); }
 template <int FMT> __device__ __forceinline__ uint32_t pair_acc_col(uint32_t buf)
 {
     return FMT == FMT_MXF4 ? (buf ? MX_BUF1_COL : 0u) : buf * TN;
 }
-static_assert(pair_smem_bytes<FMT_MXF4>() <= 232448 && (EPI2_SPLIT == 1 || TN_MX % (32 * EPI2_SPLIT) == 0),
+static_assert(pair_smem_bytes<FMT_MXF4, false>() <= 232448 && pair_smem_bytes<FMT_MXF4, true>() <= 232448 &&
+                  (EPI2_SPLIT == 1 || TN_MX % (32 * EPI2_SPLIT) == 0),
               "mxf4 pair shape");
-static_assert(pair_b_bytes<FMT_MXF4>() % 1024 == 0 && pair_stage_bytes<FMT_MXF4>() % 1024 == 0,
+static_assert(pair_b_bytes<FMT_MXF4>() % 1024 == 0 && pair_stage_bytes<FMT_MXF4, true>() % 1024 == 0,
               "128B-swizzled operands start on 1024-byte boundaries");
-static_assert(2 * pair_stages<FMT_MXF4>() + 5 <= 32, "barriers fit in their 256 bytes");
+static_assert(2 * pair_stages<true>() + 5 <= 32 && 2 * pair_stages<false>() + 5 <= 32,
+              "barriers fit in their 256 bytes");
 
 // A cluster of two CTAs on an SM pair (cluster ranks 0 and 1; rank 0 issues
 // the pair's MMAs).  Each CTA holds its own block of 128 queries (A) and its
 // half of the pair's reference tile (B; of two tiles when a query stage serves
 // two); all loads complete on rank 0's stage barrier.
-template <int K, int FMT>
-__global__ void __launch_bounds__(pair_threads<FMT>(), 1)
+template <int K, int FMT, bool AP>
+__global__ void __launch_bounds__(pair_threads<AP>(), 1)
 k_search_mma2(const __grid_constant__ CUtensorMap qmap, const __grid_constant__ CUtensorMap lmap, mma_args a)
 {
+    static_assert(!AP || FMT == FMT_MXF4, "two tiles per query stage: kind::mxf4 only");
     constexpr uint32_t CS = 2;
-    constexpr bool AP = pair_ap<FMT>();                     // two reference tiles per query stage
-    constexpr uint32_t NT = pair_nt<FMT>();
-    constexpr uint32_t NST = pair_stages<FMT>();
+    constexpr uint32_t NT = pair_nt<AP>();                  // reference tiles per query stage
+    constexpr uint32_t NST = pair_stages<AP>();
     constexpr uint32_t TNF = pair_tn<FMT>();                // reference rows per tile
     constexpr uint32_t BHF = pair_b_bytes<FMT>();           // this CTA's half of one tile, one K-chunk
-    constexpr uint32_t STAGE2F = pair_stage_bytes<FMT>();   // A block slice + this CTA's half of NT tiles
-    constexpr uint32_t EPT = 32u * pair_epi_warps<FMT>();   // epilogue threads per CTA
+    constexpr uint32_t STAGE2F = pair_stage_bytes<FMT, AP>();   // A block slice + this CTA's half of NT tiles
+    constexpr uint32_t EPT = 32u * pair_epi_warps<AP>();    // epilogue threads per CTA
     // the epilogue warps form SPLITF groups of four (one warp per lane quarter):
     // with shared query stages group g drains accumulator g, otherwise group g
     // scores columns [g, g + 1) * TNF / SPLITF of the accumulator of the tile
@@ -1484,13 +1484,15 @@ hd_status run_mma(const hd_library *lib, const uint64_t *q_hv, const double *q_m
         return hd_fail(HD_ERR_UNSUPPORTED, "kind::mxf4 form needs D to be a multiple of 256");
     const uint8_t *lib_x = XF == FMT_BF16 ? lib->x_bf16 : (XF == FMT_E4M3 ? lib->x_fp8 : lib->x_fp4);
     if (!lib_x) return hd_fail(HD_ERR_INVALID_ARG, "library not prepared for this tensor-core form");
+    // kind::mxf4 on SM pairs may share each query stage between two reference tiles
+    const bool ap = FMT == FMT_MXF4 && tune.tiles_per_stage == 2;
     auto kern = [&]() {
-        if constexpr (FMT == FMT_MXF4) return k_search_mma2<K, FMT>;
-        else return pair ? k_search_mma2<K, FMT> : k_search_mma<K, FMT>;
+        if constexpr (FMT == FMT_MXF4) return ap ? k_search_mma2<K, FMT, true> : k_search_mma2<K, FMT, false>;
+        else return pair ? k_search_mma2<K, FMT, false> : k_search_mma<K, FMT>;
     }();
     const uint32_t tn = pair ? pair_tn<FMT>() : (uint32_t)TN;   // reference rows per tile
-    const uint32_t smem_bytes = pair ? pair_smem_bytes<FMT>() : SMEM_BYTES;
-    const uint32_t threads = pair ? pair_threads<FMT>() : (uint32_t)THREADS;
+    const uint32_t smem_bytes = !pair ? SMEM_BYTES : (ap ? pair_smem_bytes<FMT, true>() : pair_smem_bytes<FMT, false>());
+    const uint32_t threads = !pair ? (uint32_t)THREADS : (ap ? pair_threads<true>() : pair_threads<false>());
     HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
     if (cs > 1) HD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     uint32_t grid = (uint32_t)lib->num_sms / cs * cs;

@@ -49,7 +49,8 @@ class _Window(C.Structure):
 
 class _TuneResult(C.Structure):
     _fields_ = [("form", C.c_int), ("tile_group", C.c_uint32), ("super_group", C.c_uint32),
-                ("cluster", C.c_uint32), ("cta_group", C.c_uint32), ("ms", C.c_double)]
+                ("cluster", C.c_uint32), ("cta_group", C.c_uint32), ("tiles_per_stage", C.c_uint32),
+                ("ms", C.c_double)]
 
 
 def _windows(windows):
@@ -82,6 +83,7 @@ _SIGS = {
     "hd_library_status": ([P], i32),
     "hd_library_prepare": ([P, i32], i32),
     "hd_library_set_schedule": ([P, u32, u32, u32, u32], i32),
+    "hd_library_set_stage_tiles": ([P, u32], i32),
     "hd_library_set_wait_limit": ([P, u64], i32),
     "hd_library_inject_stall": ([P, u32], i32),
     "hd_query_windows": ([P, P, P, u32, dbl, i32, P, P, P], i32),
@@ -410,6 +412,12 @@ def hd_library_set_schedule(lib: Library, tile_group: int = 0, super_group: int 
                                           int(cta_group)))
 
 
+def hd_library_set_stage_tiles(lib: Library, tiles_per_stage: int = 0):
+    """Reference tiles per query stage of the kind::mxf4 form: 2 shares each staged
+    query chunk between two tiles; 0 or 1 stages one tile (the default)."""
+    _check(load().hd_library_set_stage_tiles(lib.handle, int(tiles_per_stage)))
+
+
 def hd_library_set_wait_limit(lib: Library, seconds: float = 0.0):
     """Bound of every device wait of searches on `lib` (0: the 2 s default)."""
     _check(load().hd_library_set_wait_limit(lib.handle, int(seconds * 1e9)))
@@ -640,7 +648,8 @@ def hd_library_autotune(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=
               int(k), C.byref(best), allr, 64, C.byref(n_all)))
     names = {v: k_ for k_, v in FORMS.items()}
     conv = lambda r: {"form": names[r.form], "tile_group": r.tile_group, "super_group": r.super_group,
-                      "cluster": r.cluster, "cta_group": r.cta_group, "ms": r.ms}
+                      "cluster": r.cluster, "cta_group": r.cta_group, "tiles_per_stage": r.tiles_per_stage,
+                      "ms": r.ms}
     return conv(best), [conv(allr[i]) for i in range(min(64, n_all.value))]
 
 

@@ -348,9 +348,10 @@ def test_multibit_batched_argument_errors(hd):
 
 
 def test_autotune_dot_keeps_results(hd):
-    """The multi-bit autotuner: mxf4 pairs (6 schedules) and e2m1 (12) for a
-    3-bit library; the chosen form and schedule serve AUTO in the dot search
-    and in a multi-bit plan, with the oracle's results."""
+    """The multi-bit autotuner: mxf4 pairs (6 schedules, each with one and
+    with two reference tiles per query stage) and e2m1 (12) for a 3-bit
+    library; the chosen form and schedule serve AUTO in the dot search and in
+    a multi-bit plan, with the oracle's results."""
     D, Q, bits = 2048, 32, 3
     refs, qs, cls, _ = _batched_workload(29, 8000, 9, 50, 400)
     ctx, lib, q_csr, o_r, o_q, _ = _setup_mb(hd, refs, qs, D, Q, bits)
@@ -358,8 +359,10 @@ def test_autotune_dot_keeps_results(hd):
     args = (lib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
     best, allr = hd.hd_library_autotune(*args, 5)
     forms = [r["form"] for r in allr]
-    assert forms.count("tc_mxf4") == 6 and forms.count("tc_fp4") == 12 and len(allr) == 18
+    assert forms.count("tc_mxf4") == 12 and forms.count("tc_fp4") == 12 and len(allr) == 24
     assert all((r["cluster"], r["cta_group"]) == (2, 2) for r in allr if r["form"] == "tc_mxf4")
+    assert sorted(r["tiles_per_stage"] for r in allr if r["form"] == "tc_mxf4") == [1] * 6 + [2] * 6
+    assert all(r["tiles_per_stage"] == 1 for r in allr if r["form"] == "tc_fp4")
     assert best["ms"] == min(r["ms"] for r in allr) and best["form"] in ("tc_mxf4", "tc_fp4")
     want = _oracle_dot_by_class(o_r, refs, o_q, qs, cls, 5)
     i, s = hd.hd_search_dot_multi(*args, 5, form="auto")

@@ -24,9 +24,10 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("form,cluster,cta_group", [("popc", 0, 0), ("tc_fp8", 1, 1), ("tc_fp8", 2, 2),
-                                                    ("tc_fp4", 1, 1), ("tc_fp4", 2, 2), ("tc_mxf4", 2, 2)])
-def test_stalled_wait_times_out_then_recovers(hd, form, cluster, cta_group):
+@pytest.mark.parametrize("form,cluster,cta_group,tiles", [("popc", 0, 0, 1), ("tc_fp8", 1, 1, 1), ("tc_fp8", 2, 2, 1),
+                                                          ("tc_fp4", 1, 1, 1), ("tc_fp4", 2, 2, 1),
+                                                          ("tc_mxf4", 2, 2, 1), ("tc_mxf4", 2, 2, 2)])
+def test_stalled_wait_times_out_then_recovers(hd, form, cluster, cta_group, tiles):
     rng = np.random.default_rng(12)
     D, W, n = 2048, 32, 3000
     refs = rng.integers(-2**63, 2**63, (n, W), dtype=np.int64)
@@ -36,6 +37,7 @@ def test_stalled_wait_times_out_then_recovers(hd, form, cluster, cta_group):
     lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
     hd.hd_library_prepare(lib, form if form in ("tc_fp4", "tc_mxf4") else "tc_fp8")
     hd.hd_library_set_schedule(lib, 0, 0, cluster, cta_group)
+    hd.hd_library_set_stage_tiles(lib, tiles)
     q, qm, qz = dev(refs[:300]), dev(mz[:300]), dev(z[:300])
     hd.hd_library_set_wait_limit(lib, 0.05)
     hd.hd_library_inject_stall(lib, 1)

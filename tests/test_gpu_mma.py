@@ -267,3 +267,51 @@ def test_e2m1_schedules_exact(hd, form, tg, sg, cs, cg):
     lib.status()
     oi, od = oracle.search(D, refs, mz, z, q, mz[:m], z[:m], 100.0, "da", 4)
     assert np.array_equal(hd.as_u32(i), oi) and np.array_equal(hd.as_u16(d), od)
+
+
+@pytest.mark.parametrize("D,tg,sg,k,n_q,tol,unit", [(256, 1, 1, 4, 333, 100.0, "da"), (2048, 3, 5, 4, 333, 100.0, "da"),
+                                                    (2048, 16, 2, 1, 257, 500.0, "da"),
+                                                    (2048, 5, 16, 16, 700, 20.0, "ppm"),
+                                                    (8192, 16, 2, 5, 1, 500.0, "da"),
+                                                    (8192, 7, 3, 8, 513, 150.0, "da")])
+def test_mxf4_two_tiles_per_stage_exact(hd, D, tg, sg, k, n_q, tol, unit):
+    """kind::mxf4 with each staged query chunk scored against two reference
+    tiles (both accumulators filled and drained together): odd tile groups
+    leave one-tile stage runs at the end of items, blocks are ragged (257,
+    513, 1 queries) and windows narrow or wide; the top-k is the oracle's and
+    that of one tile per stage."""
+    rng = np.random.default_rng(300 + D + tg)
+    n = 7000 if D <= 2048 else 3000
+    refs = _rand_hv(rng, n, D // 64)
+    mz = rng.uniform(400, 700, n)
+    z = rng.integers(2, 4, n).astype(np.uint8)
+    src = rng.integers(0, n, n_q)
+    q = refs[src] ^ (_rand_hv(rng, n_q, D // 64) & np.uint64(0x0000FFFF0000FFFF))
+    qm, qz = mz[src] + rng.uniform(-1, 1, n_q), z[src]
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library(ctx, dev(refs), dev(mz), dev(z))
+    hd.hd_library_prepare(lib, "tc_mxf4")
+    hd.hd_library_set_schedule(lib, tg, sg, 2, 2)
+    got = []
+    for tps in (2, 1):
+        hd.hd_library_set_stage_tiles(lib, tps)
+        i, d = hd.hd_search_open(lib, dev(q), dev(qm), dev(qz), tol, unit, k, form="tc_mxf4")
+        torch.cuda.synchronize()
+        lib.status()
+        got.append((hd.as_u32(i), hd.as_u16(d)))
+    oi, od = oracle.search(D, refs, mz, z, q, qm, qz, tol, unit, k)
+    assert np.array_equal(got[0][0], oi) and np.array_equal(got[0][1], od)
+    assert np.array_equal(got[1][0], oi) and np.array_equal(got[1][1], od)
+
+
+def test_stage_tiles_argument_checked(hd):
+    rng = np.random.default_rng(4)
+    D, W, n = 2048, 32, 100
+    ctx = hd.Ctx(D, 4, 10, D // 2, 0)
+    lib = hd.hd_build_library(ctx, dev(rng.integers(-2**63, 2**63, (n, W), dtype=np.int64)),
+                              dev(rng.uniform(400, 600, n)), dev(np.full(n, 2, np.uint8)))
+    with pytest.raises(hd.HDError) as e:
+        hd.hd_library_set_stage_tiles(lib, 3)
+    assert e.value.status == hd.HD_ERR_INVALID_ARG
+    for tps in (0, 1, 2):
+        hd.hd_library_set_stage_tiles(lib, tps)

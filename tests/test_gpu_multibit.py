@@ -286,3 +286,21 @@ def test_search_dot_popc_chunks(hd, bits, D):
     b = hd.hd_search_dot(lib, dev(Qv), dev(q_mz), dev(q_z), 10.0, "da", 5, tc)
     torch.cuda.synchronize()
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("bits,tg", [(2, 3), (3, 16)])
+def test_search_dot_mxf4_two_tiles_per_stage(hd, bits, tg):
+    """Multi-bit components through kind::mxf4 with each staged query chunk
+    scored against two reference tiles: the oracle's scores and indices."""
+    D, m = 1024, 2 ** (bits - 1) - 1
+    rng = np.random.default_rng(500 + bits)
+    n_ref, n_q = 5200, 300
+    R = rng.integers(-m, m + 1, (n_ref, D)).astype(np.int8)
+    Qv = rng.integers(-m, m + 1, (n_q, D)).astype(np.int8)
+    ref_mz, ref_z, q_mz, q_z = windowed(rng, n_ref, n_q, 400.0, 410.0)
+    ctx = hd.Ctx(D, 8, 100, D // 2, 1)
+    lib = hd.hd_build_library_multibit(ctx, dev(R), dev(ref_mz), dev(ref_z), bits)
+    hd.hd_library_prepare(lib, "tc_mxf4")
+    hd.hd_library_set_schedule(lib, tg, 2, 2, 2)
+    hd.hd_library_set_stage_tiles(lib, 2)
+    check_dot(hd, lib, R, ref_mz, ref_z, Qv, q_mz, q_z, 3.0, "da", 8, "tc_mxf4")

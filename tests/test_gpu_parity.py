@@ -401,15 +401,18 @@ def test_full_size_sampled(hd):
     qq = np.nonzero(ok)[0]
     assert np.all(refs.charge[rows] == qs.charge[qq])
     assert np.all(np.abs(refs.precursor_mz[rows] - qs.precursor_mz[qq]) <= spec["tol"])
-    # the benchmark's form and schedules: e2m1 SM pairs at the autotuner's usual picks, e4m3, and
-    # the 1-SM form; each equal to the oracle on the sample and to the popcount form on every query
+    # the benchmark's form and schedules: e2m1 SM pairs at the autotuner's usual picks (kind::mxf4
+    # with one and with two reference tiles per query stage), e4m3, and the 1-SM form; each equal
+    # to the oracle on the sample and to the popcount form on every query
     hd.hd_library_prepare(lib, "tc_fp4")
     hd.hd_library_prepare(lib, "tc_fp8")
     for form, sched in (("tc_fp4", (16, 16, 2, 2)), ("tc_fp4", (32, 16, 2, 2)), ("tc_fp4", (32, 2, 2, 2)),
                         ("tc_fp4", (16, 2, 2, 2)), ("tc_fp8", (16, 16, 2, 2)), ("tc_fp4", (16, 16, 1, 1)),
                         ("tc_mxf4", (16, 2, 2, 2)), ("tc_mxf4", (32, 2, 2, 2)), ("tc_mxf4", (16, 16, 2, 2)),
-                        ("tc_mxf4", (4, 2, 2, 2))):
-        hd.hd_library_set_schedule(lib, *sched)
+                        ("tc_mxf4", (4, 2, 2, 2)), ("tc_mxf4", (16, 2, 2, 2, 2)), ("tc_mxf4", (32, 2, 2, 2, 2)),
+                        ("tc_mxf4", (16, 16, 2, 2, 2))):
+        hd.hd_library_set_schedule(lib, *sched[:4])
+        hd.hd_library_set_stage_tiles(lib, sched[4] if len(sched) > 4 else 1)
         ti, td = hd.hd_search_open(lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), spec["tol"], spec["unit"], k,
                                    form=form)
         torch.cuda.synchronize()
