@@ -649,7 +649,8 @@ def run_batched(args):
     round-robin over 20 ppm / 150 Da / 500 Da, against a 2,000,000-reference
     library, at D=4096 and D=8192: autotune on the whole query set, capture
     encode + search of every batch as one CUDA graph, time its replays, then
-    each batch alone for its latency.  One JSON line per D."""
+    each batch alone for its latency, with the graph's schedule and with one
+    tuned on a median-size batch of the widest window.  One JSON line per D."""
     import torch
     from paper_2211_16422_gb300 import build, hd
     build.build()
@@ -724,17 +725,29 @@ def run_batched(args):
             batches.append((dev((off_np[a_:e_ + 1] - p0).astype(np.uint32)), bins[p0:p1].contiguous(),
                             lv[p0:p1].contiguous(), q_mz[a_:e_].contiguous(), q_z[a_:e_].contiguous(),
                             windows[b_ % len(windows)]))
-        lat = []
-        for off_b, bins_b, lv_b, mz_b, z_b, (tol_b, unit_b) in batches:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            hv_b = hd.hd_encode(ctx, off_b, bins_b, lv_b)
-            hd.hd_search_open(lib, hv_b, mz_b, z_b, tol_b, unit_b, spec["k"], form=best["form"])
-            e1.record(stream)
-            torch.cuda.synchronize()
-            lat.append(e0.elapsed_time(e1))
-        lib.status()
-        lat = np.asarray(lat)
+        def alone(form_):
+            lat_ = []
+            for off_b, bins_b, lv_b, mz_b, z_b, (tol_b, unit_b) in batches:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hv_b = hd.hd_encode(ctx, off_b, bins_b, lv_b)
+                hd.hd_search_open(lib, hv_b, mz_b, z_b, tol_b, unit_b, spec["k"], form=form_)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                lat_.append(e0.elapsed_time(e1))
+            lib.status()
+            return np.asarray(lat_)
+
+        lat_tp = alone(best["form"])   # with the schedule tuned for the whole set's throughput
+        # a batch searched alone is a latency question: tune on one batch of the median size
+        # with the widest window (setup, not timed) and time every batch alone again
+        widest = max((w for w in windows if w[1] == "da"), key=lambda w: w[0], default=windows[-1])
+        wide = [b_ for b_ in range(len(sizes)) if batches[b_][5] == widest]
+        pick = min(wide, key=lambda b_: (abs(int(sizes[b_]) - float(np.median(sizes))), b_))
+        off_b, bins_b, lv_b, mz_b, z_b, win_b = batches[pick]
+        best_lat, _ = hd.hd_library_autotune(lib, hd.hd_encode(ctx, off_b, bins_b, lv_b), mz_b, z_b, None,
+                                             [win_b], spec["k"])
+        lat = alone(best_lat["form"])
         # the roofline comes from one eager launch timed alone, against the measured rate of its instruction
         if best["form"].startswith("tc_"):
             pk, pclk = measure_peaks(hd, (best["form"],))
@@ -756,7 +769,12 @@ def run_batched(args):
                 "queries_per_s": qs.n / (ms / 1e3), "comparisons_per_step": comparisons,
                 "batch_latency_ms": {"all_batches_one_graph": ms, "one_batch_alone_p50": float(np.percentile(lat, 50)),
                                      "one_batch_alone_p99": float(np.percentile(lat, 99)),
-                                     "one_batch_alone_max": float(lat.max())},
+                                     "one_batch_alone_max": float(lat.max()),
+                                     "one_batch_alone_schedule": best_lat,
+                                     "one_batch_alone_tuned_on": f"batch {pick} ({int(sizes[pick])} queries, "
+                                                                 f"{win_b[0]} {win_b[1]})",
+                                     "one_batch_alone_with_graph_schedule_p50": float(np.percentile(lat_tp, 50)),
+                                     "one_batch_alone_with_graph_schedule_p99": float(np.percentile(lat_tp, 99))},
                 "graph_kernel_nodes": plan.kernel_nodes, "gpu_launches": plan.kernel_nodes * args.steps,
                 "autotune": {"best": best, "candidates": len(table)},
                 "roofline": roof,
