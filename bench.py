@@ -50,25 +50,49 @@ TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
     #     -k regex:k_search_mma -s 0 -c 1 python bench.py --steps 2 --warmup 3 --no-e2e --no-cpu-baseline
     #     --popc-steps 0 --no-peaks --form <form> --schedule <tile_group,super_group,cluster,cta_group,tiles>
+    ("k_search_mma2", "tc_mxf4", 4, 2, 2, 2, 2): {"bytes": 162.048e9 + 0.18906e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 2, 2, 2, 1): {"bytes": 142.911e9 + 0.27436e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 4, 2, 2, 2): {"bytes": 176.168e9 + 0.15872e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 4, 2, 2, 1): {"bytes": 154.274e9 + 0.20655e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 16, 2, 2, 2): {"bytes": 195.379e9 + 0.06076e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 4, 16, 2, 2, 1): {"bytes": 193.309e9 + 0.06281e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 8, 2, 2, 2, 2): {"bytes": 177.418e9 + 0.16138e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 8, 2, 2, 2, 1): {"bytes": 159.751e9 + 0.18949e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 8, 4, 2, 2, 2): {"bytes": 184.797e9 + 0.12673e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 8, 4, 2, 2, 1): {"bytes": 176.310e9 + 0.16065e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 8, 16, 2, 2, 2): {"bytes": 210.660e9 + 0.03568e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
+    ("k_search_mma2", "tc_mxf4", 8, 16, 2, 2, 1): {"bytes": 210.051e9 + 0.03628e9,
+                                                  "sha256": "6fc3e0e0bf68e41f"},
     ("k_search_mma2", "tc_mxf4", 16, 2, 2, 2, 2): {"bytes": 186.900e9 + 0.09986e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
     ("k_search_mma2", "tc_mxf4", 16, 2, 2, 2, 1): {"bytes": 176.523e9 + 0.11182e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
-    ("k_search_mma2", "tc_mxf4", 32, 2, 2, 2, 2): {"bytes": 183.868e9 + 0.06897e9,
+    ("k_search_mma2", "tc_mxf4", 16, 4, 2, 2, 2): {"bytes": 194.750e9 + 0.08237e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
-    ("k_search_mma2", "tc_mxf4", 32, 2, 2, 2, 1): {"bytes": 181.403e9 + 0.07096e9,
+    ("k_search_mma2", "tc_mxf4", 16, 4, 2, 2, 1): {"bytes": 187.700e9 + 0.08059e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
     ("k_search_mma2", "tc_mxf4", 16, 16, 2, 2, 2): {"bytes": 218.315e9 + 0.02146e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
     ("k_search_mma2", "tc_mxf4", 16, 16, 2, 2, 1): {"bytes": 221.438e9 + 0.02168e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
-    ("k_search_mma2", "tc_mxf4", 4, 2, 2, 2, 2): {"bytes": 162.048e9 + 0.18906e9,
+    ("k_search_mma2", "tc_mxf4", 32, 2, 2, 2, 2): {"bytes": 183.868e9 + 0.06897e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
-    ("k_search_mma2", "tc_mxf4", 4, 2, 2, 2, 1): {"bytes": 142.911e9 + 0.27436e9,
+    ("k_search_mma2", "tc_mxf4", 32, 2, 2, 2, 1): {"bytes": 181.403e9 + 0.07096e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
-    ("k_search_mma2", "tc_mxf4", 4, 16, 2, 2, 2): {"bytes": 195.379e9 + 0.06076e9,
+    ("k_search_mma2", "tc_mxf4", 32, 4, 2, 2, 2): {"bytes": 197.430e9 + 0.05047e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
-    ("k_search_mma2", "tc_mxf4", 4, 16, 2, 2, 1): {"bytes": 193.309e9 + 0.06281e9,
+    ("k_search_mma2", "tc_mxf4", 32, 4, 2, 2, 1): {"bytes": 198.752e9 + 0.04694e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},
     ("k_search_mma2", "tc_mxf4", 32, 16, 2, 2, 2): {"bytes": 224.915e9 + 0.01352e9,
                                                   "sha256": "6fc3e0e0bf68e41f"},

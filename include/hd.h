@@ -395,7 +395,7 @@ HD_API void hd_plan_destroy(hd_plan *plan);
 /* Autotuner (no counterpart in the paper): times each search form the library
  * is prepared for (HD_FORM_TC_MXF4 too when the e2m1 copy exists and D is a
  * multiple of 256) and, for the tensor-core forms, work-item shapes
- * tile_group x super_group x (cluster, cta_group) in {4, 16, 32} x {2, 16} x
+ * tile_group x super_group x (cluster, cta_group) in {4, 8, 16, 32} x {2, 4, 16} x
  * {(1, 1), (2, 2)} ((2, 2) only for kind::mxf4, with one and with two
  * reference tiles per query stage, hd_library_set_stage_tiles), on the
  * given queries (the real query set, or one of the same density per window:

@@ -90,14 +90,14 @@ hd_status tune_checks(const hd_library *lib, const void *d_q, const double *d_q_
 }
 
 // Candidates: popc (binary rows only), then for every prepared tensor-core
-// form (tile_group, super_group) in {4, 16, 32} x {2, 16} on one SM and on SM
+// form (tile_group, super_group) in {4, 8, 16, 32} x {2, 4, 16} on one SM and on SM
 // pairs (kind::mxf4 on pairs only, and only when D is a multiple of 256, with
 // one or two reference tiles per query stage).
 std::vector<hd_tune_result> tc_candidates(const hd_library *lib, bool with_popc)
 {
     std::vector<hd_tune_result> cand;
     if (with_popc) cand.push_back({HD_FORM_POPC, 0, 0, 0, 0, 0, 0.0});
-    const uint32_t tgs[3] = {4, 16, 32}, sgs[2] = {2, 16};
+    const uint32_t tgs[4] = {4, 8, 16, 32}, sgs[3] = {2, 4, 16};
     const uint32_t shapes[2][2] = {{1, 1}, {2, 2}};   // (cluster, cta_group): one SM, or the SM pair
     for (hd_search_form f : {HD_FORM_TC_MXF4, HD_FORM_TC_FP4, HD_FORM_TC_FP8, HD_FORM_TC_BF16}) {
         if (!hd_tc_copy(lib, f) || (f == HD_FORM_TC_MXF4 && lib->dim % 256 != 0)) continue;

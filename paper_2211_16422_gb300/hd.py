@@ -640,17 +640,17 @@ def hd_library_autotune(lib: Library, q_hv, q_mz, q_charge, q_class, windows, k=
         q_class = _need(_dev(q_class, torch.uint8, "q_class"), n, "q_class")
     torch.cuda.current_stream().synchronize()
     best = _TuneResult()
-    allr = (_TuneResult * 64)()
+    allr = (_TuneResult * 128)()
     n_all = C.c_uint32()
     w = _windows(windows)
     fn = load().hd_library_autotune_dot if multibit else load().hd_library_autotune
     _check(fn(lib.handle, _ptr(q), _ptr(q_mz), _ptr(q_charge), _ptr(q_class), q_mz.numel(), w, len(windows),
-              int(k), C.byref(best), allr, 64, C.byref(n_all)))
+              int(k), C.byref(best), allr, 128, C.byref(n_all)))
     names = {v: k_ for k_, v in FORMS.items()}
     conv = lambda r: {"form": names[r.form], "tile_group": r.tile_group, "super_group": r.super_group,
                       "cluster": r.cluster, "cta_group": r.cta_group, "tiles_per_stage": r.tiles_per_stage,
                       "ms": r.ms}
-    return conv(best), [conv(allr[i]) for i in range(min(64, n_all.value))]
+    return conv(best), [conv(allr[i]) for i in range(min(128, n_all.value))]
 
 
 class _PeakResult(C.Structure):

@@ -140,8 +140,8 @@ def test_autotune_keeps_results(hd):
     args = (lib, q_hv, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
     i0, d0 = hd.hd_search_open_multi(*args, 5, form="popc")
     best, allr = hd.hd_library_autotune(*args, 5)
-    # popc, then 3 tile groups x 2 super groups x {(1, 1), (2, 2)} for the prepared e4m3 copy
-    assert best["ms"] > 0 and len(allr) == 1 + 12
+    # popc, then 4 tile groups x 3 super groups x {(1, 1), (2, 2)} for the prepared e4m3 copy
+    assert best["ms"] > 0 and len(allr) == 1 + 24
     assert {(r["cluster"], r["cta_group"]) for r in allr[1:]} == {(1, 1), (2, 2)}
     assert best["ms"] == min(r["ms"] for r in allr)
     i1, d1 = hd.hd_search_open_multi(*args, 5, form="auto")
@@ -348,8 +348,8 @@ def test_multibit_batched_argument_errors(hd):
 
 
 def test_autotune_dot_keeps_results(hd):
-    """The multi-bit autotuner: mxf4 pairs (6 schedules, each with one and
-    with two reference tiles per query stage) and e2m1 (12) for a 3-bit
+    """The multi-bit autotuner: mxf4 pairs (12 schedules, each with one and
+    with two reference tiles per query stage) and e2m1 (24) for a 3-bit
     library; the chosen form and schedule serve AUTO in the dot search and in
     a multi-bit plan, with the oracle's results."""
     D, Q, bits = 2048, 32, 3
@@ -359,9 +359,9 @@ def test_autotune_dot_keeps_results(hd):
     args = (lib, q_comp, dev(qs.precursor_mz), dev(qs.charge), dev(cls), WINDOWS)
     best, allr = hd.hd_library_autotune(*args, 5)
     forms = [r["form"] for r in allr]
-    assert forms.count("tc_mxf4") == 12 and forms.count("tc_fp4") == 12 and len(allr) == 24
+    assert forms.count("tc_mxf4") == 24 and forms.count("tc_fp4") == 24 and len(allr) == 48
     assert all((r["cluster"], r["cta_group"]) == (2, 2) for r in allr if r["form"] == "tc_mxf4")
-    assert sorted(r["tiles_per_stage"] for r in allr if r["form"] == "tc_mxf4") == [1] * 6 + [2] * 6
+    assert sorted(r["tiles_per_stage"] for r in allr if r["form"] == "tc_mxf4") == [1] * 12 + [2] * 12
     assert all(r["tiles_per_stage"] == 1 for r in allr if r["form"] == "tc_fp4")
     assert best["ms"] == min(r["ms"] for r in allr) and best["form"] in ("tc_mxf4", "tc_fp4")
     want = _oracle_dot_by_class(o_r, refs, o_q, qs, cls, 5)
