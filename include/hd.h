@@ -245,10 +245,11 @@ HD_API hd_status hd_library_status(hd_library *lib);
  * idempotent. */
 HD_API hd_status hd_library_prepare(hd_library *lib, hd_search_form form);
 /* Schedule of the tensor-core forms (no counterpart in the paper).  Reference
- * rows form tiles of 256 on a grid fixed to row 0; one work item scores one
- * block of 128 sorted queries against `tile_group` consecutive tiles, and
- * items are ordered so that the CTAs running at once share `super_group`
- * consecutive groups of tiles through L2.  (cluster, cta_group) = (2, 2)
+ * rows form tiles of 256 (240 for HD_FORM_TC_MXF4) on a grid fixed to row 0;
+ * one work item scores one block of 128 sorted queries (256 on SM pairs)
+ * against `tile_group` consecutive tiles, and items are ordered so that the
+ * CTAs running at once share `super_group` consecutive groups of tiles
+ * through L2.  (cluster, cta_group) = (2, 2)
  * pairs two CTAs on neighbouring SMs into one M = 256 tensor-core operation
  * (each SM stages its own query block and half of every reference tile);
  * (1, 1) runs one CTA per SM at M = 128.  A 0 in either place takes the
