@@ -42,3 +42,28 @@ def test_every_name_in_bench_is_defined():
     missing = sorted({n.id for n in ast.walk(tree)
                       if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load) and n.id not in known})
     assert not missing, f"names used in bench.py but defined nowhere: {missing}"
+
+
+def test_schedule_parsing_and_traffic_keys():
+    """--schedule takes four or five values (the fifth, reference tiles per
+    query stage, defaults to one), and every captured DRAM figure is keyed by
+    kernel, form and all five schedule values, which is how the bench looks
+    it up."""
+    import sys
+    import pytest
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.parse_schedule("16,2,2,2") == {"tile_group": 16, "super_group": 2, "cluster": 2,
+                                                "cta_group": 2, "tiles_per_stage": 1}
+    assert bench.parse_schedule("8,2,2,2,2")["tiles_per_stage"] == 2
+    with pytest.raises(SystemExit):
+        bench.parse_schedule("16,2,2")
+    assert bench.TRAFFIC
+    for key, v in bench.TRAFFIC.items():
+        assert len(key) == 2 + len(bench.SCHEDULE_KEYS) and key[0].startswith("k_search")
+        assert v["bytes"] > 0 and len(v["sha256"]) == 16
+    # the default schedule and every kind::mxf4 candidate of the autotuner's grid resolve to a figure
+    for tg in (4, 8, 16, 32):
+        for sg in (2, 4, 16):
+            for tps in (1, 2):
+                assert ("k_search_mma2", "tc_mxf4", tg, sg, 2, 2, tps) in bench.TRAFFIC
